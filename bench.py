@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark: finest-grid MDOF/s of the level-dependent Helmholtz multigrid
+solved to a 1e-6 relative residual, plus the dominant kernel's bandwidth
+against the measured HBM peak.
+
+Workload (default): 1023 x 1023 interior points (h = 1/1024), constant
+k = 640 (kh = 0.625), ECS absorbing layers of 32 cells, unit point source at
+(0.5, 0.5); complex64 V(1,1)-cycles inside FP64 iterative refinement.  One
+step = one complete solve from u = 0 to ||f - A u|| / ||f|| <= 1e-6 (setup
+excluded).  Inputs are resident in HBM; L2 is flushed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own replica of the workload (replicas
+only: the single-grid solve has no data-parallel split); value = the units
+of all ranks / the slowest rank's time.  --impl reference times the FP64 CPU
+oracle on this host (a bounded sample of the same workload).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+# Algorithmic bytes per finest-grid point of each level-0 kernel in the
+# complex64 cycle (c64 = 8 B, k^2 field float32 = 4 B, coarse arrays 1/4):
+#   pre-smoothing sweep     read u, f, k2; write u          = 28 B
+#   residual + restriction  read u, f, k2; write f_c (1/4)  = 22 B
+#   correction + sweep      read u, e (1/4), f, k2; write u = 30 B
+#   FP64 refinement         read u64, e32, f64, k2_64; write u64, rhs32 = 72 B
+KERNEL_BYTES = {0: ("pre_smooth", 28.0), 1: ("residual_restrict", 22.0),
+                2: ("correct_post_smooth", 30.0), 3: ("refine_fp64", 72.0)}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def launches_per_solve(levels, info, nu1=1, nu2=1, mixed=True):
+    """Kernels of this library launched by one solve: every iteration of the
+    graph's WHILE body runs the whole cycle sequence ((levels-1) levels of
+    nu1 sweeps + residual/restriction + nu2 sweeps, the stop test, the coarse
+    LU); one iteration more per loop than cycles (the stop test that ends
+    it); plus norm, state init, finish, and per refinement the FP64 residual
+    and the outer stop test."""
+    per_iter = (levels - 1) * (nu1 + 1 + nu2) + 2
+    if mixed:
+        loops = info["refinements"]
+        return (info["cycles"] + loops) * per_iter + 2 * (loops + 1) + 3
+    return (info["cycles"] + 1) * per_iter + 3
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1211_4752_gb300 import HelmholtzMG, workloads as W
+    from paper_1211_4752_gb300 import _binding as B
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = getattr(W, args.workload)()
+    n, dim = w["n"], w["dim"]
+    pts = (n - 1) ** dim
+    k2 = w["k2"]
+    k2_t = torch.from_numpy(k2).cuda() if isinstance(k2, np.ndarray) else float(k2)
+    mixed = args.precision == "mixed"
+    t0 = time.perf_counter()
+    mg = HelmholtzMG(n, dim=dim, k2=k2_t, layers=w["layers"], precision=args.precision,
+                     max_batch=1)
+    setup_s = time.perf_counter() - t0
+    f = torch.from_numpy(w["rhs"]).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    infos = []
+    for _ in range(args.warmup):
+        _, info = mg.solve(f, tol=args.tol)
+        infos.append(info[0])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                       # evict L2 between steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, info = mg.solve(f, tol=args.tol)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        infos.append(info[0])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total = sum(times)
+    if dist:
+        t = torch.tensor([total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+        dist.barrier()
+    last = infos[-1]
+    ok = all(i["status"] == "OK" for i in infos)
+    value = pts * args.steps * world / total / 1e6
+
+    # end to end through the host-buffer C-ABI call (pinned host memory)
+    fh = torch.from_numpy(w["rhs"]).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    mg.solve_host(fh, uh, tol=args.tol)
+    e_times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mg.solve_host(fh, uh, tol=args.tol)
+        e1.record(stream)
+        e1.synchronize()
+        e_times.append(e0.elapsed_time(e1) / 1e3)
+    e2e_total = sum(e_times)
+    if dist:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    # dominant kernel, timed live on this stream (level 0, back to back)
+    import ctypes as ct
+    peak, peak_kind = measured_peaks()
+    kt = {}
+    for kid in (0, 1, 2) + ((3,) if mixed else ()):
+        ms = ct.c_double()
+        B.check(B.lib().hh_time_kernel(mg._h, kid, 0, 1, 50, ct.byref(ms),
+                                       ct.c_void_p(stream.cuda_stream)))
+        kt[kid] = ms.value
+    dom = max((0, 1, 2), key=lambda k: kt[k])
+    name, bpp = KERNEL_BYTES[dom]
+    if not mixed:
+        bpp *= 2.0                     # complex128 / FP64 k^2: twice the bytes
+    achieved = bpp * pts / (kt[dom] * 1e-3) / 1e9
+    traffic = None
+    tf = ROOT / "profiles" / "traffic.json"
+    if tf.exists():
+        d = json.loads(tf.read_text())
+        key = f"{w['name']}:{args.precision}:{name}"
+        traffic = d.get(key)
+
+    fp64 = None
+    if mixed and args.compare_fp64:
+        mg64 = HelmholtzMG(n, dim=dim, k2=k2_t, layers=w["layers"], precision="fp64", max_batch=1)
+        mg64.solve(f, tol=args.tol)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, i64 = mg64.solve(f, tol=args.tol)
+        e1.record(stream)
+        e1.synchronize()
+        s64 = e0.elapsed_time(e1) / 1e3
+        fp64 = {"value": pts / s64 / 1e6, "unit": "MDOF/s", "cycles": i64[0]["cycles"],
+                "status": i64[0]["status"], "ms_per_solve": s64 * 1e3}
+        mg64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args, last["cycles"])
+    if rank == 0:
+        line = {
+            "metric": "finest-grid MDOF/s solved to 1e-6 rel. residual",
+            "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+f64" if mixed else "c128",
+            "data": "synthetic (seeded point source; constant k)",
+            "config": {"workload": w["name"], "n": n, "interior": n - 1, "dim": dim,
+                       "k2": float(k2) if not isinstance(k2, np.ndarray) else "field",
+                       "ecs_layer": w["layers"], "precision": args.precision,
+                       "tol": args.tol, "parallelism": f"replicas{world}",
+                       "l2": "flushed between steps (256 MB write)",
+                       "setup_s": setup_s},
+            "solve": {"cycles": last["cycles"], "refinements": last["refinements"],
+                      "rel_residual": last["rel_residual"], "all_ok": ok},
+            "e2e": {"value": pts * args.steps * world / e2e_total / 1e6, "unit": "MDOF/s",
+                    "h2d_bytes_per_step": pts * 16, "d2h_bytes_per_step": pts * 16},
+            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "bytes_per_point": bpp,
+                         "launch_ms": {KERNEL_BYTES[k][0]: v for k, v in kt.items()}},
+            "cpu_baseline": cpu,
+            "fp64_gpu": fp64,
+            "gpu_launches": args.steps * launches_per_solve(mg.levels, last, mixed=mixed),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    mg.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, args, cycles_hint):
+    """The FP64 oracle on this host: time a bounded number of V-cycles of the
+    same workload and scale to one complete solve with the oracle's own cycle
+    count (from its committed golden fixture when present)."""
+    import numpy as np
+
+    import oracle as O
+    n, dim = w["n"], w["dim"]
+    pts = (n - 1) ** dim
+    t0 = time.perf_counter()
+    H = O.build_hierarchy(n, dim, w["k2"], layers=w["layers"])
+    f = w["rhs"][0]
+    u = np.zeros_like(f)
+    t1 = time.perf_counter()
+    ncyc = 0
+    while True:
+        u = O.vcycle(H, 0, u, f)
+        O.residual_norm(H, u, f)
+        ncyc += 1
+        el = time.perf_counter() - t1
+        if el > args.cpu_seconds or ncyc >= 200:
+            break
+    s_per_cycle = el / ncyc
+    gold = ROOT / "tests" / "golden" / f"{w['name']}.json"
+    if gold.exists():
+        cycles = json.loads(gold.read_text())["cycles"]
+        src = "oracle cycle count from its golden fixture"
+    else:
+        cycles = cycles_hint
+        src = "cycle count of this run's solve"
+    return {"value": pts / (s_per_cycle * cycles) / 1e6, "unit": "MDOF/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{ncyc} V-cycles of {w['name']} ({s_per_cycle:.3f} s/cycle, numpy FP64, "
+                      f"1 thread) scaled to {cycles} cycles ({src}); setup {t1 - t0:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    from paper_1211_4752_gb300 import workloads as W
+    w = getattr(W, args.workload)()
+    import numpy as np
+
+    import oracle as O
+    n, dim = w["n"], w["dim"]
+    pts = (n - 1) ** dim
+    H = O.build_hierarchy(n, dim, w["k2"], layers=w["layers"])
+    f = w["rhs"][0]
+    gold = ROOT / "tests" / "golden" / f"{w['name']}.json"
+    cycles = json.loads(gold.read_text())["cycles"] if gold.exists() else None
+    per = max(1, int(args.cpu_cycles))
+    u = np.zeros_like(f)
+    for _ in range(args.warmup):
+        u = O.vcycle(H, 0, u, f)
+    t = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per):
+            u = O.vcycle(H, 0, u, f)
+            O.residual_norm(H, u, f)
+        t += time.perf_counter() - t0
+    s_per_cycle = t / (args.steps * per)
+    ncyc = cycles if cycles else per
+    value = pts / (s_per_cycle * ncyc) / 1e6
+    line = {"impl": "reference", "metric": "finest-grid MDOF/s solved to 1e-6 rel. residual",
+            "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": s_per_cycle * ncyc * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128", "data": "synthetic (seeded point source; constant k)",
+            "config": {"workload": w["name"], "n": n, "interior": n - 1, "dim": dim,
+                       "precision": "fp64 oracle", "tol": args.tol},
+            "cpu_baseline": {"value": value, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per} V-cycles per step, scaled to {ncyc} cycles"},
+            "e2e": {"value": value, "unit": "MDOF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="ecs_const")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-cycles", type=int, default=4)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

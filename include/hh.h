@@ -1,0 +1,230 @@
+/*
+ * hh.h -- C ABI of the GB300 level-dependent Helmholtz multigrid library.
+ *
+ * The library solves the discrete indefinite Helmholtz problem
+ *     (-Delta^h - k^2(x)) u = f                         (paper Eq. (HH), Sec. 2)
+ * on the unit square (2-D, 5-point stencil) or unit cube (3-D, 7-point
+ * stencil) with n = 2^P intervals per axis, by repeated level-dependent
+ * V(nu1,nu2)-cycles (Cools, Reps, Vanroose, arXiv 1211.4752, Sec. 3.1 and
+ * Sec. 4.1):
+ *   - level l (l = 0 finest) rediscretises the operator with n/2^l intervals
+ *     and the complex shift beta_l = e^{i theta_l} on k^2 (CSL form,
+ *     Eq. (cslvariant)) or the rotation e^{-i theta_l} of the Laplacian (CSG
+ *     form, Eq. (csgvariant)); theta_l = l * dtheta, dtheta = theta_max / p;
+ *     theta_0 = 0 keeps the original operator on the finest level;
+ *   - smoothing is weighted Jacobi (Eq. (wjacobi)); transfers are full
+ *     weighting and (bi/tri-)linear interpolation (text after
+ *     Eq. (standardtg)); the restricted residual is scaled by c_l
+ *     (Eq. (erreq1)); the coarsest level is solved by dense LU;
+ *   - absorbing boundaries are exterior complex scaling layers (Sec. 2.4,
+ *     Sec. 4.1): inside a layer of the given width the grid distance is
+ *     rotated by e^{i gamma}; outside the unit square u = 0.
+ *
+ * Array layout everywhere: interior points only, row-major with x fastest
+ * ([batch][y][x] in 2-D, [batch][z][y][x] in 3-D), N = n - 1 points per axis.
+ * Complex arrays are interleaved (re, im) double pairs (C99 double complex /
+ * torch.complex128).  Every "device" pointer is CUDA global memory on the
+ * device that was current at hh_setup; every "host" pointer is ordinary host
+ * memory (pinned memory makes the copies of hh_solve_host asynchronous).
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  All device work is enqueued on it.  Functions that return
+ * per-right-hand-side information to host memory synchronise that stream
+ * before returning; the others are asynchronous.
+ *
+ * Errors: every function returns an hh_status; no exception or longjmp
+ * crosses the ABI.  hh_last_error() returns a thread-local message for the
+ * last failing call on the calling thread.  Arguments are validated before
+ * any device work is enqueued; HH_ERR_ARG leaves all outputs untouched.
+ *
+ * Ownership: the caller owns every array it passes; the library never keeps
+ * a caller pointer after a call returns.  The handle owns its device
+ * workspace (allocated in hh_setup, freed in hh_destroy).
+ */
+#ifndef HH_H
+#define HH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HH_API_VERSION 1
+
+typedef struct hh_handle hh_handle;
+
+typedef enum {
+  HH_OK = 0,
+  HH_ERR_ARG = 1,           /* invalid argument (nothing was enqueued) */
+  HH_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  HH_ERR_OOM = 3,           /* device allocation failed */
+  HH_ERR_NOT_CONVERGED = 4, /* max_cycles reached; best iterate left in u */
+  HH_ERR_DIVERGED = 5,      /* rho_k > div_limit or not finite */
+  HH_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+  HH_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+} hh_status;
+
+/* Shift form of Sec. 3.1. */
+enum { HH_FORM_CSL = 0,   /* A_l = -Delta_l - e^{i theta_l} k^2          */
+       HH_FORM_CSG = 1 }; /* A_l = -Delta_l e^{-i theta_l} - k^2         */
+
+/* Arithmetic of the cycle. */
+enum { HH_FP64 = 0,       /* complex128 everywhere                        */
+       HH_MIXED = 1 };    /* complex64 cycles inside FP64 refinement      */
+
+/* hh_solve flags. */
+enum { HH_USE_GUESS = 1 };  /* u holds the initial guess (else u_0 = 0)  */
+
+typedef struct {
+  int dim;          /* 2 or 3 */
+  int n;            /* intervals per axis on the finest level: a power of
+                       two with 8 <= n <= 16384 (2-D) or 8 <= n <= 512 (3-D) */
+  int layer_lo;     /* ECS layer width in fine cells at the low end of every
+                       axis; 0 = plain homogeneous Dirichlet at that end */
+  int layer_hi;     /* same at the high end; layer_lo + layer_hi < n */
+  double ecs_angle; /* ECS rotation angle gamma in radians, 0 <= gamma < pi/2 */
+} hh_grid;
+
+typedef struct {
+  int form;            /* HH_FORM_CSL or HH_FORM_CSG */
+  double theta_max;    /* dtheta = theta_max / p (paper default pi/6) */
+  int p;               /* 0: p = log2(n), as in the paper's tables */
+  const double *theta; /* optional host array, one angle per level, overrides
+                          l*dtheta (copied during hh_setup) */
+  const double *c;     /* optional host array of 2*(levels-1) doubles: the
+                          complex scale c_l of the residual restricted from
+                          level l to l+1 (Eq. (erreq1)); NULL = 1 */
+} hh_shift;
+
+typedef struct {
+  double omega_re, omega_im; /* Jacobi weight (default 0.8 + 0i) */
+  int nu1, nu2;              /* pre-/post-smoothing sweeps, 1..4 (default 1, 1) */
+  int precision;             /* HH_FP64 (default) or HH_MIXED */
+  int coarsest;              /* intervals per axis on the coarsest level:
+                                2 or 4 (default 4: 3^dim unknowns) */
+  int max_cycles;            /* V-cycles per solve before HH_ERR_NOT_CONVERGED
+                                (default 20000; counts inner cycles in MIXED) */
+  double div_limit;          /* rho_k above this is divergence (default 1e3) */
+  double inner_tol;          /* MIXED: relative residual reduction of the
+                                complex64 cycles per refinement (default 1e-3) */
+  int max_inner;             /* MIXED: inner cycles per refinement (default 4000) */
+} hh_options;
+
+typedef struct {
+  int cycles;          /* V-cycles run for this right-hand side */
+  int refinements;     /* MIXED: FP64 refinement steps; FP64: 0 */
+  double rel_residual; /* ||f - A_0 u||_2 / ||f||_2 of the returned u (FP64) */
+  int status;          /* hh_status of this right-hand side */
+} hh_solve_info;
+
+/* Fill defaults (paper values: theta_max = pi/6, p = log2 n, CSL, c = 1;
+ * Jacobi 0.8, V(1,1), coarsest 3^dim unknowns). */
+void hh_default_shift(hh_shift *shift);
+void hh_default_options(hh_options *opt);
+
+/* Build the level hierarchy (Sec. 3.1): per-level complex coefficient tables
+ * of the three-point formula on the ECS grid, shifts beta_l and scales c_l,
+ * k^2 injected to every level, the LU factors of the coarsest operator, and
+ * workspace for `max_batch` right-hand sides.
+ *   k2_dev   device, double[N^dim]: the real fine-grid k^2 field; may be NULL,
+ *            then k^2 = k2_const everywhere.  Read during the call only.
+ * Returns HH_ERR_ARG for an invalid grid/shift/options, HH_ERR_OOM when the
+ * workspace does not fit.  *out is set only on HH_OK. */
+hh_status hh_setup(const hh_grid *grid, const double *k2_dev, double k2_const,
+                   const hh_shift *shift, const hh_options *opt,
+                   int max_batch, void *stream, hh_handle **out);
+
+/* Solve A_0 u_b = f_b for b < batch by repeated V-cycles until
+ * ||f_b - A_0 u_b||_2 / ||f_b||_2 <= tol (Sec. 4.1), each right-hand side
+ * stopping on its own.
+ *   rhs_dev  device, complex128[batch][N^dim], read only.
+ *   u_dev    device, complex128[batch][N^dim]: initial guess if
+ *            flags & HH_USE_GUESS (else ignored), solution on return.
+ *   info     host, batch entries, or NULL.
+ * Returns HH_OK when every right-hand side converged, else the worst per-RHS
+ * status (NOT_CONVERGED / DIVERGED); u always holds the last iterate.
+ * Synchronises `stream`. */
+hh_status hh_solve(hh_handle *h, const void *rhs_dev, void *u_dev, int batch,
+                   double tol, int flags, hh_solve_info *info, void *stream);
+
+/* hh_solve on HOST arrays: copies rhs in, solves, copies u out (the copies
+ * are part of the call).  Same layout and semantics as hh_solve. */
+hh_status hh_solve_host(hh_handle *h, const void *rhs_host, void *u_host,
+                        int batch, double tol, int flags, hh_solve_info *info,
+                        void *stream);
+
+/* Adjoint solve A_0^H lambda_b = g_b with the same V-cycle run on the
+ * conjugate-transposed hierarchy (each level's tridiagonal factors
+ * transposed and conjugated, conj(beta_l), conj(c_l), conj(omega)).
+ * Layout, flags, info and return value as hh_solve (lambda_dev in/out). */
+hh_status hh_adjoint(hh_handle *h, const void *g_dev, void *lambda_dev,
+                     int batch, double tol, int flags, hh_solve_info *info,
+                     void *stream);
+
+/* grad_k2[x] = sum_b Re(conj(lambda_b[x]) * u_b[x]): the derivative of a real
+ * loss with respect to the fine k^2 field, given u_b = A_0^{-1} f_b and
+ * lambda_b = A_0^{-H} (dloss/du_b) (A_0 = L - diag(k^2)).
+ *   u_dev, lambda_dev  device, complex128[batch][N^dim]
+ *   grad_dev           device, double[N^dim], overwritten.  Asynchronous. */
+hh_status hh_grad_k2(hh_handle *h, const void *u_dev, const void *lambda_dev,
+                     int batch, double *grad_dev, void *stream);
+
+/* y_b = A_l x_b (adjoint != 0: A_l^H x_b) on level l (Eq. (HH) with the
+ * level's shift), complex128[batch][N_l^dim] device arrays.  Asynchronous. */
+hh_status hh_apply(hh_handle *h, int level, int adjoint, const void *x_dev,
+                   void *y_dev, int batch, void *stream);
+
+/* Exactly `ncycles` V-cycles (no stop test) on A_0 u = f from the given u,
+ * in the handle's precision (MIXED: complex64 cycles, arrays still
+ * complex128).  u_dev in/out.  Asynchronous.  For step-by-step checks. */
+hh_status hh_cycles(hh_handle *h, const void *rhs_dev, void *u_dev, int batch,
+                    int ncycles, void *stream);
+
+/* One weighted-Jacobi sweep on level l, Eq. (wjacobi), complex128:
+ * u_out = u_in + omega D_l^{-1} (f - A_l u_in).  Asynchronous. */
+hh_status hh_smooth(hh_handle *h, int level, const void *u_in_dev,
+                    const void *f_dev, void *u_out_dev, int batch, void *stream);
+
+/* fc = c_l * FW(f - A_l u) on level l -> l+1 (full weighting of the residual,
+ * Eq. (erreq1)), complex128.  Asynchronous. */
+hh_status hh_residual_restrict(hh_handle *h, int level, const void *u_dev,
+                               const void *f_dev, void *fc_dev, int batch,
+                               void *stream);
+
+/* u_out = Jacobi sweep of (u_in + P e) on level l, where e lives on level l+1
+ * and P is (bi/tri-)linear interpolation (correction + post-smoothing),
+ * complex128.  Asynchronous. */
+hh_status hh_correct_smooth(hh_handle *h, int level, const void *u_in_dev,
+                            const void *e_dev, const void *f_dev,
+                            void *u_out_dev, int batch, void *stream);
+
+/* e = A_{L-1}^{-1} f on the coarsest level by the LU factors of hh_setup
+ * (partial pivoting, FP64), complex128[batch][N_{L-1}^dim].  Asynchronous. */
+hh_status hh_coarse_solve(hh_handle *h, const void *f_dev, void *e_dev,
+                          int batch, void *stream);
+
+/* Measurement hook: launch one kernel of the cycle `reps` times back to back
+ * on `stream` over the handle's own workspace and return the mean duration
+ * per launch in *ms (CUDA events recorded on `stream`; synchronises it).
+ *   kernel 0: pre-smoothing sweep (with the level-0 residual norm) on `level`
+ *   kernel 1: residual + full-weighting restriction on `level`
+ *   kernel 2: correction + post-smoothing sweep on `level`
+ *   kernel 3: FP64 refinement residual on level 0 (MIXED handles only)
+ * Kernels 0-2 run in the handle's precision.  Workspace contents are
+ * overwritten (the handle stays valid).  For benchmarks and profiles. */
+hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
+                         int reps, double *ms, void *stream);
+
+/* Hierarchy queries. */
+int hh_num_levels(const hh_handle *h);
+int hh_level_points(const hh_handle *h, int level); /* N_l per axis */
+
+/* Release the handle and its workspace (NULL is allowed). */
+hh_status hh_destroy(hh_handle *h);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *hh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HH_H */

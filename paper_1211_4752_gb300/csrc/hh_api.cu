@@ -1,0 +1,901 @@
+// Host side of the C ABI (include/hh.h): hierarchy setup, workspace, the
+// cycle sequence, and the solve drivers (plain complex128 cycles, complex64
+// cycles inside FP64 iterative refinement, adjoint).
+//
+// The cycle loop runs on the device: one V-cycle is captured into the body
+// of a CUDA-graph WHILE node whose condition is set by the stop-test kernel,
+// so a whole solve (FP64) or a whole refinement step (MIXED) is one graph
+// launch with no host round trip per cycle.
+#include "../../include/hh.h"
+#include "hh_internal.h"
+
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+using cd = std::complex<double>;
+using namespace hh;
+
+namespace {
+
+thread_local std::string g_err;
+
+hh_status fail(hh_status s, const std::string &m) {
+  g_err = m;
+  return s;
+}
+
+#define HH_CK(call)                                                           \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? HH_ERR_OOM : HH_ERR_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    }                                                                         \
+  } while (0)
+
+#define HH_TRY(expr)                 \
+  do {                               \
+    hh_status s_ = (expr);           \
+    if (s_ != HH_OK) return s_;      \
+  } while (0)
+
+constexpr int MAXL = 20;
+
+template <typename R> struct Work {
+  using C = typename Cx<R>::T;
+  C *u_pre[MAXL] = {};
+  C *u_post[MAXL] = {};
+  C *f[MAXL] = {};
+  C *tmp[MAXL] = {};
+};
+
+struct LevelHost {
+  int n = 0, N = 0;
+  size_t pts = 0;
+  double2 *coef64[2] = {nullptr, nullptr};  // [fwd/adj] dim*3*N
+  float2 *coef32[2] = {nullptr, nullptr};
+  double2 beta64[2];
+  float2 beta32[2];
+  double2 c64[2];  // scale of the residual restricted to the next level
+  float2 c32[2];
+  double *k2_64 = nullptr;
+  float *k2_32 = nullptr;
+};
+
+struct GraphEntry {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct hh_handle {
+  hh_grid grid;
+  hh_options opt;
+  int dim = 2, n = 0, L = 0, max_batch = 0, device = 0;
+  int m = 0;  // unknowns on the coarsest level
+  std::vector<LevelHost> lv;
+  double2 *lu[2] = {nullptr, nullptr};
+  int *piv[2] = {nullptr, nullptr};
+  Work<double> w64;
+  Work<float> w32;
+  double2 *u64[2] = {nullptr, nullptr};
+  double *partials = nullptr;
+  int nparts = 0;
+  SolveState *st = nullptr;
+  SolveParams *params = nullptr;
+  int *flag = nullptr;
+  int *flag_h = nullptr;           // pinned
+  SolveParams *params_h = nullptr;  // pinned
+  SolveState *st_h = nullptr;       // pinned
+  cudaStream_t cap = nullptr;       // private stream for graph capture
+  std::vector<void *> allocs;
+  std::map<std::tuple<int, int, int>, GraphEntry> graphs;
+
+  double2 omega64() const { return make_double2(opt.omega_re, opt.omega_im); }
+};
+
+namespace {
+
+hh_status dev_alloc(hh_handle *h, void **p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HH_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                " bytes): " + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(*p);
+  return HH_OK;
+}
+
+template <typename T> hh_status dev_alloc_n(hh_handle *h, T **p, size_t n) {
+  return dev_alloc(h, reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+// Complex node coordinates of the exterior-complex-scaled unit interval
+// (Sec. 2.4 and Sec. 4.1): z(x) = x on [a, b], rotated by e^{i gamma} about
+// the nearer end point outside it.
+cd ecs_z(double x, double a, double b, double gamma) {
+  const cd rot = std::polar(1.0, gamma);
+  if (x < a) return a + (x - a) * rot;
+  if (x > b) return b + (x - b) * rot;
+  return cd(x, 0.0);
+}
+
+// -D2 on a level with n_l intervals: lo/dg/up at the n_l - 1 interior nodes of
+// the three-point formula on the non-uniform complex grid.
+void lap1d(int n_l, double a, double b, double gamma, std::vector<cd> &lo,
+           std::vector<cd> &dg, std::vector<cd> &up) {
+  std::vector<cd> h(n_l);
+  cd zp = ecs_z(0.0, a, b, gamma);
+  for (int i = 0; i < n_l; ++i) {
+    const cd zn = ecs_z(double(i + 1) / double(n_l), a, b, gamma);
+    h[i] = zn - zp;
+    zp = zn;
+  }
+  const int N = n_l - 1;
+  lo.resize(N);
+  dg.resize(N);
+  up.resize(N);
+  for (int i = 0; i < N; ++i) {
+    const cd hm = h[i], hp = h[i + 1];
+    lo[i] = 2.0 / ((hm + hp) * hm);
+    up[i] = 2.0 / ((hm + hp) * hp);
+    dg[i] = lo[i] + up[i];
+  }
+}
+
+template <typename R> LevelK<R> levelk(const hh_handle *h, int l, int dir);
+template <> LevelK<double> levelk<double>(const hh_handle *h, int l, int dir) {
+  const LevelHost &v = h->lv[l];
+  return LevelK<double>{v.N, v.coef64[dir], v.beta64[dir], v.k2_64};
+}
+template <> LevelK<float> levelk<float>(const hh_handle *h, int l, int dir) {
+  const LevelHost &v = h->lv[l];
+  return LevelK<float>{v.N, v.coef32[dir], v.beta32[dir], v.k2_32};
+}
+template <typename R> Work<R> &work(hh_handle *h);
+template <> Work<double> &work<double>(hh_handle *h) { return h->w64; }
+template <> Work<float> &work<float>(hh_handle *h) { return h->w32; }
+template <typename R> typename Cx<R>::T cscal(const hh_handle *h, int l, int dir);
+template <> double2 cscal<double>(const hh_handle *h, int l, int dir) { return h->lv[l].c64[dir]; }
+template <> float2 cscal<float>(const hh_handle *h, int l, int dir) { return h->lv[l].c32[dir]; }
+template <typename R> typename Cx<R>::T omega(const hh_handle *h, int dir) {
+  const double im = dir ? -h->opt.omega_im : h->opt.omega_im;  // conj(omega) for A^H
+  typename Cx<R>::T w;
+  w.x = (R)h->opt.omega_re;
+  w.y = (R)im;
+  return w;
+}
+
+enum { CHECK_NONE = 0, CHECK_CYCLE = 1, CHECK_INNER = 2 };
+
+// One level-dependent V(nu1,nu2)-cycle (Sec. 3.1): per level pre-smoothing,
+// scaled full-weighting restriction of the residual, LU on the coarsest level,
+// interpolated correction + post-smoothing.  The level-0 iterate is read from
+// and written to W.u_post[0]; W.f[0] holds the right-hand side.
+template <typename R, int DIM>
+void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
+                   unsigned long long cond, cudaStream_t s) {
+  Work<R> &W = work<R>(h);
+  const SolveState *st = check != CHECK_NONE ? h->st : nullptr;
+  const auto om = omega<R>(h, dir);
+  const int L = h->L;
+  for (int l = 0; l + 1 < L; ++l) {
+    const LevelK<R> K = levelk<R>(h, l, dir);
+    const typename Cx<R>::T *in = l == 0 ? W.u_post[0] : nullptr;
+    for (int j = 0; j < h->opt.nu1; ++j) {
+      typename Cx<R>::T *out = ((h->opt.nu1 - 1 - j) % 2 == 0) ? W.u_pre[l] : W.tmp[l];
+      const int zm = j == 0 ? (l == 0 ? zero0 : ZERO_ALL) : ZERO_NONE;
+      const bool norm = (l == 0 && j == 0 && check != CHECK_NONE);
+      launch_smooth<R, DIM>(K, in, zm, W.f[l], out, om, batch, st,
+                            norm ? h->partials : nullptr, h->nparts, s);
+      if (norm) {
+        if (check == CHECK_CYCLE)
+          launch_check_cycle(h->st, h->partials, h->params, h->flag, cond, s);
+        else
+          launch_check_inner(h->st, h->partials, h->params, h->flag, cond, s);
+      }
+      in = out;
+    }
+    launch_resid_restrict<R, DIM>(K, W.u_pre[l], W.f[l], W.f[l + 1],
+                                  cscal<R>(h, l, dir), batch, st, s);
+  }
+  launch_coarse_solve<R>(h->lu[dir], h->piv[dir], h->m, W.f[L - 1],
+                         W.u_post[L - 1], batch, st, s);
+  for (int l = L - 2; l >= 0; --l) {
+    const LevelK<R> K = levelk<R>(h, l, dir);
+    const typename Cx<R>::T *in = nullptr;
+    for (int j = 0; j < h->opt.nu2; ++j) {
+      typename Cx<R>::T *out = ((h->opt.nu2 - 1 - j) % 2 == 0) ? W.u_post[l] : W.tmp[l];
+      if (j == 0)
+        launch_correct_smooth<R, DIM>(K, W.u_pre[l], W.u_post[l + 1], W.f[l],
+                                      out, om, batch, st, s);
+      else
+        launch_smooth<R, DIM>(K, in, ZERO_NONE, W.f[l], out, om, batch, st,
+                              nullptr, h->nparts, s);
+      in = out;
+    }
+  }
+}
+
+template <typename R>
+void cycle_dispatch(hh_handle *h, int dir, int batch, int zero0, int check,
+                    unsigned long long cond, cudaStream_t s) {
+  if (h->dim == 2)
+    enqueue_cycle<R, 2>(h, dir, batch, zero0, check, cond, s);
+  else
+    enqueue_cycle<R, 3>(h, dir, batch, zero0, check, cond, s);
+}
+
+void refine_dispatch(hh_handle *h, int dir, const double2 *u_in, int u_zero,
+                     const float2 *e, double2 *u_out, int batch,
+                     cudaStream_t s) {
+  const LevelK<double> K = levelk<double>(h, 0, dir);
+  if (h->dim == 2)
+    launch_refine<2>(K, u_in, u_zero, e, u_out, h->w64.f[0], h->w32.f[0],
+                     batch, h->st, h->partials, h->nparts, s);
+  else
+    launch_refine<3>(K, u_in, u_zero, e, u_out, h->w64.f[0], h->w32.f[0],
+                     batch, h->st, h->partials, h->nparts, s);
+}
+
+// The graph for (precision, direction, batch): a WHILE node whose body is
+// one V-cycle with the stop test after the level-0 pre-smoothing sweep.
+hh_status get_graph(hh_handle *h, int prec, int dir, int batch,
+                    cudaGraphExec_t *out) {
+  auto key = std::make_tuple(prec, dir, batch);
+  auto it = h->graphs.find(key);
+  if (it != h->graphs.end()) {
+    *out = it->second.exec;
+    return HH_OK;
+  }
+  GraphEntry g;
+  HH_CK(cudaGraphCreate(&g.graph, 0));
+  cudaGraphConditionalHandle cond;
+  HH_CK(cudaGraphConditionalHandleCreate(&cond, g.graph, 1,
+                                         cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  HH_CK(cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  HH_CK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal));
+  const unsigned long long c = (unsigned long long)cond;
+  if (prec == HH_FP64)
+    cycle_dispatch<double>(h, dir, batch, ZERO_NONE, CHECK_CYCLE, c, h->cap);
+  else
+    cycle_dispatch<float>(h, dir, batch, ZERO_FLAG, CHECK_INNER, c, h->cap);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ec = cudaStreamEndCapture(h->cap, &captured);
+  if (ec != cudaSuccess) {
+    cudaGraphDestroy(g.graph);
+    return fail(HH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+  }
+  HH_CK(cudaGraphInstantiate(&g.exec, g.graph, 0));
+  h->graphs[key] = g;
+  *out = g.exec;
+  return HH_OK;
+}
+
+hh_status read_info(hh_handle *h, int batch, hh_solve_info *info,
+                    cudaStream_t s) {
+  HH_CK(cudaMemcpyAsync(h->st_h, h->st, sizeof(SolveState) * batch,
+                        cudaMemcpyDeviceToHost, s));
+  HH_CK(cudaStreamSynchronize(s));
+  hh_status worst = HH_OK;
+  for (int b = 0; b < batch; ++b) {
+    const SolveState &q = h->st_h[b];
+    if (info) {
+      info[b].cycles = q.cycles;
+      info[b].refinements = q.refinements;
+      info[b].rel_residual = q.fnorm2 > 0 ? std::sqrt(q.rnorm2 / q.fnorm2) : 0.0;
+      info[b].status = q.status;
+    }
+    if (q.status == HH_ERR_DIVERGED) worst = HH_ERR_DIVERGED;
+    else if (q.status != HH_OK && worst == HH_OK) worst = (hh_status)q.status;
+  }
+  if (worst != HH_OK)
+    g_err = worst == HH_ERR_DIVERGED ? "solve diverged" : "solve did not converge";
+  return worst;
+}
+
+hh_status set_params(hh_handle *h, int batch, double tol, cudaStream_t s) {
+  SolveParams &P = *h->params_h;
+  P.tol = tol;
+  P.div_limit = h->opt.div_limit;
+  P.inner_tol = h->opt.inner_tol;
+  P.max_cycles = h->opt.max_cycles;
+  P.max_inner = h->opt.max_inner;
+  P.batch = batch;
+  P.nparts = h->nparts;
+  HH_CK(cudaMemcpyAsync(h->params, h->params_h, sizeof(SolveParams),
+                        cudaMemcpyHostToDevice, s));
+  return HH_OK;
+}
+
+// Core solve.  rhs: device complex128 (copied to w64.f[0] unless it is that
+// buffer); guess: device or NULL; out: device.  dir 1 = adjoint.
+hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
+                     const double2 *guess, double2 *out, int batch, double tol,
+                     hh_solve_info *info, cudaStream_t s) {
+  const size_t pts = h->lv[0].pts;
+  const size_t bytes = pts * batch * sizeof(double2);
+  if (rhs != h->w64.f[0])
+    HH_CK(cudaMemcpyAsync(h->w64.f[0], rhs, bytes, cudaMemcpyDeviceToDevice, s));
+  HH_TRY(set_params(h, batch, tol, s));
+  launch_norm2(h->w64.f[0], pts, batch, h->partials, h->nparts, s);
+  launch_state_init(h->st, h->partials, h->params, h->flag, s);
+
+  if (h->opt.precision == HH_FP64) {
+    if (guess && guess != h->w64.u_post[0])
+      HH_CK(cudaMemcpyAsync(h->w64.u_post[0], guess, bytes, cudaMemcpyDeviceToDevice, s));
+    else if (!guess)
+      HH_CK(cudaMemsetAsync(h->w64.u_post[0], 0, bytes, s));
+    cudaGraphExec_t ex;
+    HH_TRY(get_graph(h, HH_FP64, dir, batch, &ex));
+    HH_CK(cudaGraphLaunch(ex, s));
+    launch_finish(h->st, h->w64.u_post[0], out, pts, batch, s);
+    HH_CK(cudaGetLastError());
+    return read_info(h, batch, info, s);
+  }
+
+  // MIXED: FP64 refinement around complex64 cycles.
+  int cur = 0;
+  if (guess && guess != h->u64[0])
+    HH_CK(cudaMemcpyAsync(h->u64[0], guess, bytes, cudaMemcpyDeviceToDevice, s));
+  refine_dispatch(h, dir, h->u64[0], guess ? 0 : 1, nullptr, h->u64[1], batch, s);
+  cur = 1;
+  launch_check_outer(h->st, h->partials, h->params, h->flag, s);
+  cudaGraphExec_t ex;
+  HH_TRY(get_graph(h, HH_MIXED, dir, batch, &ex));
+  for (int it = 0; it < h->opt.max_cycles + 2; ++it) {
+    HH_CK(cudaMemcpyAsync(h->flag_h, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HH_CK(cudaStreamSynchronize(s));
+    if (*h->flag_h == 0) break;
+    HH_CK(cudaGraphLaunch(ex, s));
+    refine_dispatch(h, dir, h->u64[cur], 0, h->w32.u_post[0], h->u64[1 - cur], batch, s);
+    cur = 1 - cur;
+    launch_check_outer(h->st, h->partials, h->params, h->flag, s);
+  }
+  launch_finish(h->st, h->u64[cur], out, pts, batch, s);
+  HH_CK(cudaGetLastError());
+  return read_info(h, batch, info, s);
+}
+
+// One launch of a cycle kernel on the workspace (for hh_time_kernel).
+template <typename R>
+void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
+  Work<R> &W = work<R>(h);
+  const LevelK<R> K = levelk<R>(h, level, 0);
+  const auto om = omega<R>(h, 0);
+  const bool two = h->dim == 2;
+  if (kernel == 0) {
+    double *parts = level == 0 ? h->partials : nullptr;
+    if (two) launch_smooth<R, 2>(K, W.u_post[level], ZERO_NONE, W.f[level], W.u_pre[level], om, batch, nullptr, parts, h->nparts, s);
+    else launch_smooth<R, 3>(K, W.u_post[level], ZERO_NONE, W.f[level], W.u_pre[level], om, batch, nullptr, parts, h->nparts, s);
+  } else if (kernel == 1) {
+    if (two) launch_resid_restrict<R, 2>(K, W.u_pre[level], W.f[level], W.f[level + 1], cscal<R>(h, level, 0), batch, nullptr, s);
+    else launch_resid_restrict<R, 3>(K, W.u_pre[level], W.f[level], W.f[level + 1], cscal<R>(h, level, 0), batch, nullptr, s);
+  } else {
+    if (two) launch_correct_smooth<R, 2>(K, W.u_pre[level], W.u_post[level + 1], W.f[level], W.u_post[level], om, batch, nullptr, s);
+    else launch_correct_smooth<R, 3>(K, W.u_pre[level], W.u_post[level + 1], W.f[level], W.u_post[level], om, batch, nullptr, s);
+  }
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+hh_status check_handle(const hh_handle *h) {
+  if (!h) return fail(HH_ERR_ARG, "null handle");
+  return HH_OK;
+}
+
+hh_status check_batch(const hh_handle *h, int batch) {
+  if (batch < 1 || batch > h->max_batch)
+    return fail(HH_ERR_ARG, "batch must be in 1..max_batch (" +
+                                std::to_string(h->max_batch) + ")");
+  return HH_OK;
+}
+
+hh_status ensure_device(const hh_handle *h) {
+  int cur = -1;
+  HH_CK(cudaGetDevice(&cur));
+  if (cur != h->device)
+    return fail(HH_ERR_ARG, "the current CUDA device differs from the handle's");
+  return HH_OK;
+}
+
+void destroy_impl(hh_handle *h) {
+  for (auto &kv : h->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  h->graphs.clear();
+  for (void *p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->flag_h) cudaFreeHost(h->flag_h);
+  if (h->params_h) cudaFreeHost(h->params_h);
+  if (h->st_h) cudaFreeHost(h->st_h);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
+                     const hh_shift &sh, cudaStream_t s) {
+  const hh_grid &g = h->grid;
+  const int dim = g.dim, n = g.n;
+  h->dim = dim;
+  h->n = n;
+  int L = 0;
+  for (int nl = n; nl >= h->opt.coarsest; nl /= 2) ++L;
+  h->L = L;
+  if (L > MAXL) return fail(HH_ERR_ARG, "too many levels");
+  h->lv.resize(L);
+  const double a = double(g.layer_lo) / n, b = 1.0 - double(g.layer_hi) / n;
+  int P = 0;
+  while ((1 << P) < n) ++P;
+  const int p = sh.p > 0 ? sh.p : P;
+  const double dtheta = sh.theta_max / p;
+
+  HH_CK(cudaGetDevice(&h->device));
+  HH_CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  HH_CK(cudaMallocHost(&h->flag_h, sizeof(int)));
+  HH_CK(cudaMallocHost(&h->params_h, sizeof(SolveParams)));
+  HH_CK(cudaMallocHost(&h->st_h, sizeof(SolveState) * h->max_batch));
+
+  const int B = h->max_batch;
+  for (int l = 0; l < L; ++l) {
+    LevelHost &v = h->lv[l];
+    v.n = n >> l;
+    v.N = v.n - 1;
+    v.pts = dim == 2 ? (size_t)v.N * v.N : (size_t)v.N * v.N * v.N;
+    const double theta = sh.theta ? sh.theta[l] : l * dtheta;
+    cd alpha(1.0, 0.0), beta(1.0, 0.0);
+    if (sh.form == HH_FORM_CSL) beta = std::polar(1.0, theta);
+    else alpha = std::polar(1.0, -theta);
+    cd c(1.0, 0.0);
+    if (sh.c && l + 1 < L) c = cd(sh.c[2 * l], sh.c[2 * l + 1]);
+    std::vector<cd> lo, dg, up;
+    lap1d(v.n, a, b, g.ecs_angle, lo, dg, up);
+    const int N = v.N;
+    std::vector<double2> t64[2];
+    std::vector<float2> t32[2];
+    for (int dir = 0; dir < 2; ++dir) {
+      t64[dir].resize((size_t)dim * 3 * N);
+      t32[dir].resize((size_t)dim * 3 * N);
+    }
+    for (int ax = 0; ax < dim; ++ax) {
+      for (int i = 0; i < N; ++i) {
+        // forward: alpha * (lo, dg, up)
+        const cd f0 = alpha * lo[i], f1 = alpha * dg[i], f2 = alpha * up[i];
+        // adjoint: (M^H)_{i,i-1} = conj(M_{i-1,i}), (M^H)_{i,i+1} = conj(M_{i+1,i})
+        const cd a0 = i > 0 ? std::conj(alpha * up[i - 1]) : cd(0.0);
+        const cd a1 = std::conj(alpha * dg[i]);
+        const cd a2 = i + 1 < N ? std::conj(alpha * lo[i + 1]) : cd(0.0);
+        const cd fw[3] = {f0, f1, f2}, ad[3] = {a0, a1, a2};
+        for (int j = 0; j < 3; ++j) {
+          const size_t o = (size_t)(3 * ax + j) * N + i;
+          t64[0][o] = make_double2(fw[j].real(), fw[j].imag());
+          t64[1][o] = make_double2(ad[j].real(), ad[j].imag());
+          t32[0][o] = make_float2((float)fw[j].real(), (float)fw[j].imag());
+          t32[1][o] = make_float2((float)ad[j].real(), (float)ad[j].imag());
+        }
+      }
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+      HH_TRY(dev_alloc_n(h, &v.coef64[dir], t64[dir].size()));
+      HH_TRY(dev_alloc_n(h, &v.coef32[dir], t32[dir].size()));
+      HH_CK(cudaMemcpyAsync(v.coef64[dir], t64[dir].data(), t64[dir].size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+      HH_CK(cudaMemcpyAsync(v.coef32[dir], t32[dir].data(), t32[dir].size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+      HH_CK(cudaStreamSynchronize(s));  // host vectors die at scope end
+    }
+    const cd bc = std::conj(beta), cc = std::conj(c);
+    v.beta64[0] = make_double2(beta.real(), beta.imag());
+    v.beta64[1] = make_double2(bc.real(), bc.imag());
+    v.beta32[0] = make_float2((float)beta.real(), (float)beta.imag());
+    v.beta32[1] = make_float2((float)bc.real(), (float)bc.imag());
+    v.c64[0] = make_double2(c.real(), c.imag());
+    v.c64[1] = make_double2(cc.real(), cc.imag());
+    v.c32[0] = make_float2((float)c.real(), (float)c.imag());
+    v.c32[1] = make_float2((float)cc.real(), (float)cc.imag());
+
+    HH_TRY(dev_alloc_n(h, &v.k2_64, v.pts));
+    HH_TRY(dev_alloc_n(h, &v.k2_32, v.pts));
+    if (l == 0) {
+      if (k2_dev) {
+        HH_CK(cudaMemcpyAsync(v.k2_64, k2_dev, v.pts * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      } else {
+        std::vector<double> kc(v.pts, k2_const);
+        HH_CK(cudaMemcpyAsync(v.k2_64, kc.data(), v.pts * sizeof(double), cudaMemcpyHostToDevice, s));
+        HH_CK(cudaStreamSynchronize(s));
+      }
+    } else {
+      if (dim == 2) launch_inject<2>(h->lv[l - 1].k2_64, h->lv[l - 1].N, v.k2_64, v.N, s);
+      else launch_inject<3>(h->lv[l - 1].k2_64, h->lv[l - 1].N, v.k2_64, v.N, s);
+    }
+    launch_to_float(v.k2_64, v.k2_32, v.pts, s);
+
+    const size_t np = v.pts * (size_t)B;
+    HH_TRY(dev_alloc_n(h, &h->w64.u_pre[l], np));
+    HH_TRY(dev_alloc_n(h, &h->w64.u_post[l], np));
+    HH_TRY(dev_alloc_n(h, &h->w64.f[l], np));
+    HH_TRY(dev_alloc_n(h, &h->w32.u_pre[l], np));
+    HH_TRY(dev_alloc_n(h, &h->w32.u_post[l], np));
+    HH_TRY(dev_alloc_n(h, &h->w32.f[l], np));
+    if (h->opt.nu1 > 1 || h->opt.nu2 > 1) {
+      HH_TRY(dev_alloc_n(h, &h->w64.tmp[l], np));
+      HH_TRY(dev_alloc_n(h, &h->w32.tmp[l], np));
+      HH_CK(cudaMemsetAsync(h->w64.tmp[l], 0, np * sizeof(double2), s));
+      HH_CK(cudaMemsetAsync(h->w32.tmp[l], 0, np * sizeof(float2), s));
+    }
+    for (double2 *p : {h->w64.u_pre[l], h->w64.u_post[l], h->w64.f[l]})
+      HH_CK(cudaMemsetAsync(p, 0, np * sizeof(double2), s));
+    for (float2 *p : {h->w32.u_pre[l], h->w32.u_post[l], h->w32.f[l]})
+      HH_CK(cudaMemsetAsync(p, 0, np * sizeof(float2), s));
+  }
+  const size_t np0 = h->lv[0].pts * (size_t)B;
+  HH_TRY(dev_alloc_n(h, &h->u64[0], np0));
+  HH_TRY(dev_alloc_n(h, &h->u64[1], np0));
+  HH_CK(cudaMemsetAsync(h->u64[0], 0, np0 * sizeof(double2), s));
+  HH_CK(cudaMemsetAsync(h->u64[1], 0, np0 * sizeof(double2), s));
+  h->nparts = partial_blocks(h->lv[0].pts);
+  HH_TRY(dev_alloc_n(h, &h->partials, (size_t)h->nparts * B));
+  HH_TRY(dev_alloc_n(h, &h->st, (size_t)B));
+  HH_TRY(dev_alloc_n(h, &h->params, 1));
+  HH_TRY(dev_alloc_n(h, &h->flag, 1));
+
+  // Coarsest level: dense LU of A_{L-1} and of A_{L-1}^H (FP64).
+  const LevelHost &cl = h->lv[L - 1];
+  h->m = (int)cl.pts;
+  if (h->m > 27) return fail(HH_ERR_ARG, "coarsest level too large");
+  int *info_d = nullptr;
+  HH_TRY(dev_alloc_n(h, &info_d, 2));
+  for (int dir = 0; dir < 2; ++dir) {
+    HH_TRY(dev_alloc_n(h, &h->lu[dir], (size_t)h->m * h->m));
+    HH_TRY(dev_alloc_n(h, &h->piv[dir], (size_t)h->m));
+    const LevelK<double> K = levelk<double>(h, L - 1, dir);
+    if (dim == 2) launch_assemble_lu<2>(K, h->lu[dir], h->piv[dir], info_d + dir, s);
+    else launch_assemble_lu<3>(K, h->lu[dir], h->piv[dir], info_d + dir, s);
+  }
+  int info_h[2] = {0, 0};
+  HH_CK(cudaMemcpyAsync(info_h, info_d, sizeof(info_h), cudaMemcpyDeviceToHost, s));
+  HH_CK(cudaStreamSynchronize(s));
+  HH_CK(cudaGetLastError());
+  if (info_h[0] || info_h[1]) return fail(HH_ERR_ARG, "singular coarsest-level operator");
+  return HH_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void hh_default_shift(hh_shift *s) {
+  if (!s) return;
+  std::memset(s, 0, sizeof(*s));
+  s->form = HH_FORM_CSL;
+  s->theta_max = M_PI / 6.0;
+  s->p = 0;
+}
+
+void hh_default_options(hh_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->omega_re = 0.8;
+  o->omega_im = 0.0;
+  o->nu1 = 1;
+  o->nu2 = 1;
+  o->precision = HH_FP64;
+  o->coarsest = 4;
+  o->max_cycles = 20000;
+  o->div_limit = 1e3;
+  o->inner_tol = 1e-3;
+  o->max_inner = 4000;
+}
+
+const char *hh_last_error(void) { return g_err.c_str(); }
+
+hh_status hh_setup(const hh_grid *grid, const double *k2_dev, double k2_const,
+                   const hh_shift *shift, const hh_options *opt, int max_batch,
+                   void *stream, hh_handle **out) {
+  g_err.clear();
+  if (!grid || !out) return fail(HH_ERR_ARG, "grid and out must not be NULL");
+  const hh_grid &g = *grid;
+  if (g.dim != 2 && g.dim != 3) return fail(HH_ERR_ARG, "dim must be 2 or 3");
+  const int nmax = g.dim == 2 ? 16384 : 512;
+  if (!is_pow2(g.n) || g.n < 8 || g.n > nmax)
+    return fail(HH_ERR_ARG, "n must be a power of two in [8, " + std::to_string(nmax) + "]");
+  if (g.layer_lo < 0 || g.layer_hi < 0 || g.layer_lo + g.layer_hi >= g.n)
+    return fail(HH_ERR_ARG, "ECS layers must be >= 0 with layer_lo + layer_hi < n");
+  if (!(g.ecs_angle >= 0.0 && g.ecs_angle < M_PI / 2))
+    return fail(HH_ERR_ARG, "ecs_angle must be in [0, pi/2)");
+  if (max_batch < 1 || max_batch > 4096) return fail(HH_ERR_ARG, "max_batch must be in 1..4096");
+  hh_shift sh;
+  hh_default_shift(&sh);
+  if (shift) sh = *shift;
+  if (sh.form != HH_FORM_CSL && sh.form != HH_FORM_CSG) return fail(HH_ERR_ARG, "bad shift form");
+  if (!std::isfinite(sh.theta_max) || sh.p < 0) return fail(HH_ERR_ARG, "bad theta_max or p");
+  hh_options o;
+  hh_default_options(&o);
+  if (opt) o = *opt;
+  if (o.nu1 < 1 || o.nu1 > 4 || o.nu2 < 1 || o.nu2 > 4) return fail(HH_ERR_ARG, "nu1, nu2 must be in 1..4");
+  if (o.coarsest != 2 && o.coarsest != 4) return fail(HH_ERR_ARG, "coarsest must be 2 or 4");
+  if (o.precision != HH_FP64 && o.precision != HH_MIXED) return fail(HH_ERR_ARG, "bad precision");
+  if (o.max_cycles < 1 || o.max_inner < 1) return fail(HH_ERR_ARG, "max_cycles and max_inner must be >= 1");
+  if (!(o.div_limit > 0) || !(o.inner_tol > 0 && o.inner_tol < 1)) return fail(HH_ERR_ARG, "bad div_limit or inner_tol");
+  if (!std::isfinite(o.omega_re) || !std::isfinite(o.omega_im)) return fail(HH_ERR_ARG, "bad omega");
+  if (!std::isfinite(k2_const)) return fail(HH_ERR_ARG, "k2_const must be finite");
+
+  hh_handle *h = new hh_handle();
+  h->grid = g;
+  h->opt = o;
+  h->max_batch = max_batch;
+  const hh_status st = setup_impl(h, k2_dev, k2_const, sh, (cudaStream_t)stream);
+  if (st != HH_OK) {
+    const std::string keep = g_err;
+    destroy_impl(h);
+    g_err = keep;
+    return st;
+  }
+  *out = h;
+  return HH_OK;
+}
+
+hh_status hh_destroy(hh_handle *h) {
+  if (!h) return HH_OK;
+  destroy_impl(h);
+  return HH_OK;
+}
+
+int hh_num_levels(const hh_handle *h) { return h ? h->L : 0; }
+
+int hh_level_points(const hh_handle *h, int level) {
+  if (!h || level < 0 || level >= h->L) return 0;
+  return h->lv[level].N;
+}
+
+hh_status hh_solve(hh_handle *h, const void *rhs_dev, void *u_dev, int batch,
+                   double tol, int flags, hh_solve_info *info, void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (!rhs_dev || !u_dev) return fail(HH_ERR_ARG, "rhs and u must not be NULL");
+  if (!(tol > 0 && tol < 1)) return fail(HH_ERR_ARG, "tol must be in (0, 1)");
+  HH_TRY(ensure_device(h));
+  const double2 *guess = (flags & HH_USE_GUESS) ? (const double2 *)u_dev : nullptr;
+  return solve_core(h, 0, (const double2 *)rhs_dev, guess, (double2 *)u_dev,
+                    batch, tol, info, (cudaStream_t)stream);
+}
+
+hh_status hh_adjoint(hh_handle *h, const void *g_dev, void *lambda_dev,
+                     int batch, double tol, int flags, hh_solve_info *info,
+                     void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (!g_dev || !lambda_dev) return fail(HH_ERR_ARG, "g and lambda must not be NULL");
+  if (!(tol > 0 && tol < 1)) return fail(HH_ERR_ARG, "tol must be in (0, 1)");
+  HH_TRY(ensure_device(h));
+  const double2 *guess = (flags & HH_USE_GUESS) ? (const double2 *)lambda_dev : nullptr;
+  return solve_core(h, 1, (const double2 *)g_dev, guess, (double2 *)lambda_dev,
+                    batch, tol, info, (cudaStream_t)stream);
+}
+
+hh_status hh_solve_host(hh_handle *h, const void *rhs_host, void *u_host,
+                        int batch, double tol, int flags, hh_solve_info *info,
+                        void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (!rhs_host || !u_host) return fail(HH_ERR_ARG, "rhs and u must not be NULL");
+  if (!(tol > 0 && tol < 1)) return fail(HH_ERR_ARG, "tol must be in (0, 1)");
+  HH_TRY(ensure_device(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = h->lv[0].pts * batch * sizeof(double2);
+  HH_CK(cudaMemcpyAsync(h->w64.f[0], rhs_host, bytes, cudaMemcpyHostToDevice, s));
+  // The guess goes straight into the buffer the solve iterates on; the
+  // result is staged in w64.u_pre[0], which the final copy-out no longer reads.
+  const double2 *guess = nullptr;
+  if (flags & HH_USE_GUESS) {
+    double2 *target = h->opt.precision == HH_FP64 ? h->w64.u_post[0] : h->u64[0];
+    HH_CK(cudaMemcpyAsync(target, u_host, bytes, cudaMemcpyHostToDevice, s));
+    guess = target;
+  }
+  double2 *stage = h->w64.u_pre[0];
+  const hh_status st = solve_core(h, 0, h->w64.f[0], guess, stage, batch, tol, info, s);
+  if (st != HH_OK && st != HH_ERR_NOT_CONVERGED && st != HH_ERR_DIVERGED) return st;
+  HH_CK(cudaMemcpyAsync(u_host, stage, bytes, cudaMemcpyDeviceToHost, s));
+  HH_CK(cudaStreamSynchronize(s));
+  return st;
+}
+
+hh_status hh_grad_k2(hh_handle *h, const void *u_dev, const void *lambda_dev,
+                     int batch, double *grad_dev, void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (!u_dev || !lambda_dev || !grad_dev) return fail(HH_ERR_ARG, "null pointer");
+  HH_TRY(ensure_device(h));
+  launch_grad_k2((const double2 *)u_dev, (const double2 *)lambda_dev,
+                 h->lv[0].pts, batch, grad_dev, (cudaStream_t)stream);
+  HH_CK(cudaGetLastError());
+  return HH_OK;
+}
+
+hh_status hh_apply(hh_handle *h, int level, int adjoint, const void *x_dev,
+                   void *y_dev, int batch, void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (level < 0 || level >= h->L) return fail(HH_ERR_ARG, "bad level");
+  if (!x_dev || !y_dev) return fail(HH_ERR_ARG, "null pointer");
+  HH_TRY(ensure_device(h));
+  const LevelK<double> K = levelk<double>(h, level, adjoint ? 1 : 0);
+  if (h->dim == 2)
+    launch_apply<double, 2>(K, (const double2 *)x_dev, (double2 *)y_dev, batch, (cudaStream_t)stream);
+  else
+    launch_apply<double, 3>(K, (const double2 *)x_dev, (double2 *)y_dev, batch, (cudaStream_t)stream);
+  HH_CK(cudaGetLastError());
+  return HH_OK;
+}
+
+hh_status hh_cycles(hh_handle *h, const void *rhs_dev, void *u_dev, int batch,
+                    int ncycles, void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (!rhs_dev || !u_dev) return fail(HH_ERR_ARG, "null pointer");
+  if (ncycles < 0) return fail(HH_ERR_ARG, "ncycles must be >= 0");
+  HH_TRY(ensure_device(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = h->lv[0].pts * batch;
+  if (h->opt.precision == HH_FP64) {
+    HH_CK(cudaMemcpyAsync(h->w64.f[0], rhs_dev, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    HH_CK(cudaMemcpyAsync(h->w64.u_post[0], u_dev, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < ncycles; ++k)
+      cycle_dispatch<double>(h, 0, batch, ZERO_NONE, CHECK_NONE, 0, s);
+    HH_CK(cudaMemcpyAsync(u_dev, h->w64.u_post[0], n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  } else {
+    launch_c128_to_c64((const double2 *)rhs_dev, h->w32.f[0], n, s);
+    launch_c128_to_c64((const double2 *)u_dev, h->w32.u_post[0], n, s);
+    for (int k = 0; k < ncycles; ++k)
+      cycle_dispatch<float>(h, 0, batch, ZERO_NONE, CHECK_NONE, 0, s);
+    launch_c64_to_c128(h->w32.u_post[0], (double2 *)u_dev, n, s);
+  }
+  HH_CK(cudaGetLastError());
+  return HH_OK;
+}
+
+hh_status hh_smooth(hh_handle *h, int level, const void *u_in_dev,
+                    const void *f_dev, void *u_out_dev, int batch,
+                    void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (level < 0 || level >= h->L) return fail(HH_ERR_ARG, "bad level");
+  if (!u_in_dev || !f_dev || !u_out_dev) return fail(HH_ERR_ARG, "null pointer");
+  if (u_in_dev == u_out_dev) return fail(HH_ERR_ARG, "u_in and u_out must differ");
+  HH_TRY(ensure_device(h));
+  const LevelK<double> K = levelk<double>(h, level, 0);
+  const double2 om = h->omega64();
+  if (h->dim == 2)
+    launch_smooth<double, 2>(K, (const double2 *)u_in_dev, ZERO_NONE, (const double2 *)f_dev,
+                             (double2 *)u_out_dev, om, batch, nullptr, nullptr, 0, (cudaStream_t)stream);
+  else
+    launch_smooth<double, 3>(K, (const double2 *)u_in_dev, ZERO_NONE, (const double2 *)f_dev,
+                             (double2 *)u_out_dev, om, batch, nullptr, nullptr, 0, (cudaStream_t)stream);
+  HH_CK(cudaGetLastError());
+  return HH_OK;
+}
+
+hh_status hh_residual_restrict(hh_handle *h, int level, const void *u_dev,
+                               const void *f_dev, void *fc_dev, int batch,
+                               void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (level < 0 || level + 1 >= h->L) return fail(HH_ERR_ARG, "bad level");
+  if (!u_dev || !f_dev || !fc_dev) return fail(HH_ERR_ARG, "null pointer");
+  HH_TRY(ensure_device(h));
+  const LevelK<double> K = levelk<double>(h, level, 0);
+  const double2 c = h->lv[level].c64[0];
+  if (h->dim == 2)
+    launch_resid_restrict<double, 2>(K, (const double2 *)u_dev, (const double2 *)f_dev,
+                                     (double2 *)fc_dev, c, batch, nullptr, (cudaStream_t)stream);
+  else
+    launch_resid_restrict<double, 3>(K, (const double2 *)u_dev, (const double2 *)f_dev,
+                                     (double2 *)fc_dev, c, batch, nullptr, (cudaStream_t)stream);
+  HH_CK(cudaGetLastError());
+  return HH_OK;
+}
+
+hh_status hh_correct_smooth(hh_handle *h, int level, const void *u_in_dev,
+                            const void *e_dev, const void *f_dev,
+                            void *u_out_dev, int batch, void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (level < 0 || level + 1 >= h->L) return fail(HH_ERR_ARG, "bad level");
+  if (!u_in_dev || !e_dev || !f_dev || !u_out_dev) return fail(HH_ERR_ARG, "null pointer");
+  if (u_in_dev == u_out_dev) return fail(HH_ERR_ARG, "u_in and u_out must differ");
+  HH_TRY(ensure_device(h));
+  const LevelK<double> K = levelk<double>(h, level, 0);
+  const double2 om = h->omega64();
+  if (h->dim == 2)
+    launch_correct_smooth<double, 2>(K, (const double2 *)u_in_dev, (const double2 *)e_dev,
+                                     (const double2 *)f_dev, (double2 *)u_out_dev, om, batch,
+                                     nullptr, (cudaStream_t)stream);
+  else
+    launch_correct_smooth<double, 3>(K, (const double2 *)u_in_dev, (const double2 *)e_dev,
+                                     (const double2 *)f_dev, (double2 *)u_out_dev, om, batch,
+                                     nullptr, (cudaStream_t)stream);
+  HH_CK(cudaGetLastError());
+  return HH_OK;
+}
+
+hh_status hh_coarse_solve(hh_handle *h, const void *f_dev, void *e_dev,
+                          int batch, void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (!f_dev || !e_dev) return fail(HH_ERR_ARG, "null pointer");
+  HH_TRY(ensure_device(h));
+  launch_coarse_solve<double>(h->lu[0], h->piv[0], h->m, (const double2 *)f_dev,
+                              (double2 *)e_dev, batch, nullptr, (cudaStream_t)stream);
+  HH_CK(cudaGetLastError());
+  return HH_OK;
+}
+
+hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
+                         int reps, double *ms, void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (!ms || reps < 1) return fail(HH_ERR_ARG, "ms must not be NULL and reps >= 1");
+  if (kernel < 0 || kernel > 3) return fail(HH_ERR_ARG, "kernel must be 0..3");
+  if (level < 0 || level + 1 >= h->L) return fail(HH_ERR_ARG, "bad level");
+  if (kernel == 3 && (level != 0 || h->opt.precision != HH_MIXED))
+    return fail(HH_ERR_ARG, "kernel 3 is the level-0 refinement of a MIXED handle");
+  HH_TRY(ensure_device(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  HH_CK(cudaEventCreate(&e0));
+  HH_CK(cudaEventCreate(&e1));
+  auto one = [&]() {
+    if (kernel == 3) {
+      refine_dispatch(h, 0, h->u64[0], 0, h->w32.u_post[0], h->u64[1], batch, s);
+      return;
+    }
+    if (h->opt.precision == HH_FP64)
+      time_one<double>(h, kernel, level, batch, s);
+    else
+      time_one<float>(h, kernel, level, batch, s);
+  };
+  one();  // warm-up launch
+  HH_CK(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) one();
+  HH_CK(cudaEventRecord(e1, s));
+  HH_CK(cudaEventSynchronize(e1));
+  float t = 0.f;
+  HH_CK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HH_CK(cudaGetLastError());
+  *ms = double(t) / reps;
+  return HH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,313 @@
+// Dimension-independent kernels: norms, solver state machine, coarsest-level
+// LU substitution, gradient assembly, conversions.
+#include "hh_internal.h"
+#include "hh_complex.cuh"
+#include "../../include/hh.h"
+
+namespace hh {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(const double *p, int n, int lane) {
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += p[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+__global__ void __launch_bounds__(256)
+k_norm2(const double2 *__restrict__ x, size_t pts, double *partials) {
+  const int b = blockIdx.y;
+  x += (size_t)b * pts;
+  double acc = 0.0;
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
+       p += (size_t)gridDim.x * blockDim.x)
+    acc += x[p].x * x[p].x + x[p].y * x[p].y;
+  __shared__ double ws[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) partials[(size_t)b * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_to_float(const double *__restrict__ x, float *__restrict__ y,
+                           size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+__global__ void k_c128_to_c64(const double2 *__restrict__ x,
+                              float2 *__restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = make_float2((float)x[i].x, (float)x[i].y);
+}
+
+__global__ void k_c64_to_c128(const float2 *__restrict__ x,
+                              double2 *__restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = make_double2((double)x[i].x, (double)x[i].y);
+}
+
+// One block; warp w serves right-hand sides w, w+32, ...; the partial sums
+// of each right-hand side are added in a fixed order (deterministic).
+template <typename Body>
+__device__ void for_each_rhs(const SolveParams *P, const double *partials,
+                             SolveState *st, bool only_active, Body body,
+                             int *any_out) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int b = w; b < P->batch; b += nw) {
+    SolveState s = st[b];
+    const bool use = only_active ? (s.active != 0) : (s.done == 0);
+    if (!use) continue;
+    const double r2 = warp_sum(partials + (size_t)b * P->nparts, P->nparts, lane);
+    if (lane == 0) {
+      body(s, r2);
+      st[b] = s;
+      if (s.active) atomicOr(&any, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *any_out = any;
+}
+
+__global__ void k_state_init(SolveState *st, const double *partials,
+                             const SolveParams *P, int *flag) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = w; b < P->batch; b += (blockDim.x >> 5)) {
+    const double f2 = warp_sum(partials + (size_t)b * P->nparts, P->nparts, lane);
+    if (lane == 0) {
+      SolveState s;
+      s.fnorm2 = f2;
+      s.rnorm2 = f2;
+      s.ref2 = 0.0;
+      s.rin2 = 0.0;
+      s.cycles = 0;
+      s.inner = 0;
+      s.refinements = 0;
+      s.status = (f2 >= 0.0) ? HH_OK : HH_ERR_ARG;  // NaN right-hand side
+      s.active = f2 > 0.0 ? 1 : 0;
+      s.zero = 0;
+      s.done = f2 > 0.0 ? 0 : 1;
+      s.zres = f2 > 0.0 ? 0 : 1;
+      st[b] = s;
+      if (s.active) atomicOr(&any, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = any;
+}
+
+// Stop test of the plain cycle loop (Sec. 4.1): r2 = ||f - A_0 u_k||^2 of
+// the iterate u_k that the level-0 pre-smoothing sweep just read.
+__global__ void k_check_cycle(SolveState *st, const double *partials,
+                              const SolveParams *P, int *flag,
+                              unsigned long long cond) {
+  __shared__ int any_s;
+  auto body = [&](SolveState &s, double r2) {
+    const int k = s.cycles;
+    const double rho = sqrt(r2 / s.fnorm2);
+    s.rnorm2 = r2;
+    if (!(rho <= P->div_limit)) {
+      s.status = HH_ERR_DIVERGED; s.active = 0; s.done = 1;
+    } else if (rho <= P->tol) {
+      s.status = HH_OK; s.active = 0; s.done = 1;
+    } else if (k >= P->max_cycles) {
+      s.status = HH_ERR_NOT_CONVERGED; s.active = 0; s.done = 1;
+    } else {
+      s.cycles = k + 1;
+    }
+  };
+  for_each_rhs(P, partials, st, true, body, &any_s);
+  if (threadIdx.x == 0) {
+    *flag = any_s;
+    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, any_s ? 1u : 0u);
+  }
+}
+
+// Stop test of the complex64 inner loop of the refinement: r2 is the inner
+// residual norm of the current correction e_k (k = 0: e = 0, r = rhs).
+__global__ void k_check_inner(SolveState *st, const double *partials,
+                              const SolveParams *P, int *flag,
+                              unsigned long long cond) {
+  __shared__ int any_s;
+  auto body = [&](SolveState &s, double r2) {
+    if (s.zero) {
+      s.ref2 = r2;
+      s.rin2 = r2;
+      s.zero = 0;
+      s.inner = 1;
+      s.cycles += 1;
+      if (!(r2 > 0.0)) s.active = 0;  // zero (or NaN) inner rhs: nothing to do
+      return;
+    }
+    const double rho = sqrt(r2 / s.ref2);
+    s.rin2 = r2;
+    if (!(rho <= P->div_limit)) {
+      s.status = HH_ERR_DIVERGED; s.active = 0; s.done = 1;
+    } else if (rho <= P->inner_tol || s.inner >= P->max_inner ||
+               s.cycles >= P->max_cycles) {
+      s.active = 0;
+    } else {
+      s.inner += 1;
+      s.cycles += 1;
+    }
+  };
+  for_each_rhs(P, partials, st, true, body, &any_s);
+  if (threadIdx.x == 0) {
+    *flag = any_s;
+    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, any_s ? 1u : 0u);
+  }
+}
+
+// Outer stop test of the FP64 refinement: r2 = ||f - A_0 u64||^2.
+__global__ void k_check_outer(SolveState *st, const double *partials,
+                              const SolveParams *P, int *flag) {
+  __shared__ int any_s;
+  auto body = [&](SolveState &s, double r2) {
+    const double rho = sqrt(r2 / s.fnorm2);
+    s.rnorm2 = r2;
+    if (!(rho <= P->div_limit)) {
+      s.status = HH_ERR_DIVERGED; s.active = 0; s.done = 1;
+    } else if (rho <= P->tol) {
+      s.status = HH_OK; s.active = 0; s.done = 1;
+    } else if (s.cycles >= P->max_cycles) {
+      s.status = HH_ERR_NOT_CONVERGED; s.active = 0; s.done = 1;
+    } else {
+      s.refinements += 1; s.active = 1; s.zero = 1; s.inner = 0;
+    }
+  };
+  for_each_rhs(P, partials, st, false, body, &any_s);
+  if (threadIdx.x == 0) *flag = any_s;
+}
+
+__global__ void k_finish(const SolveState *st, const double2 *__restrict__ src,
+                         double2 *__restrict__ dst, size_t pts) {
+  const int b = blockIdx.y;
+  const bool z = st[b].zres != 0;
+  src += (size_t)b * pts;
+  dst += (size_t)b * pts;
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
+       p += (size_t)gridDim.x * blockDim.x)
+    dst[p] = z ? make_double2(0.0, 0.0) : src[p];
+}
+
+__global__ void k_grad_k2(const double2 *__restrict__ u,
+                          const double2 *__restrict__ lam, size_t pts,
+                          int batch, double *__restrict__ grad) {
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
+       p += (size_t)gridDim.x * blockDim.x) {
+    double g = 0.0;
+    for (int b = 0; b < batch; ++b) {
+      const double2 a = lam[(size_t)b * pts + p], v = u[(size_t)b * pts + p];
+      g += a.x * v.x + a.y * v.y;  // Re(conj(lambda) u)
+    }
+    grad[p] = g;
+  }
+}
+
+// Forward/back substitution with the coarsest LU factors (FP64), one block
+// per right-hand side, thread 0 (m <= 27 unknowns).
+template <typename R>
+__global__ void k_coarse_solve(const double2 *__restrict__ lu,
+                               const int *__restrict__ piv, int m,
+                               const typename Cx<R>::T *__restrict__ f,
+                               typename Cx<R>::T *__restrict__ e,
+                               const SolveState *__restrict__ st) {
+  using C = typename Cx<R>::T;
+  const int b = blockIdx.x;
+  if (st && !st[b].active) return;
+  if (threadIdx.x != 0) return;
+  double2 y[27];
+  const C *fb = f + (size_t)b * m;
+  for (int i = 0; i < m; ++i) {
+    const C v = fb[piv[i]];
+    y[i] = make_double2((double)v.x, (double)v.y);
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < i; ++j) y[i] = csub(y[i], cmul(lu[i * m + j], y[j]));
+  for (int i = m - 1; i >= 0; --i) {
+    for (int j = i + 1; j < m; ++j) y[i] = csub(y[i], cmul(lu[i * m + j], y[j]));
+    y[i] = cdiv(y[i], lu[i * m + i]);
+  }
+  C *eb = e + (size_t)b * m;
+  for (int i = 0; i < m; ++i) eb[i] = cmk((R)y[i].x, (R)y[i].y);
+}
+
+int grid_cap(size_t work, int threads = 256, int cap = 8 * 152 * 4) {
+  size_t g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > (size_t)cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace
+
+int partial_blocks(size_t pts) { return grid_cap(pts, 256, 2 * 152); }
+
+void launch_norm2(const double2 *x, size_t pts, int batch, double *partials,
+                  int nparts, cudaStream_t s) {
+  k_norm2<<<dim3(nparts, batch), 256, 0, s>>>(x, pts, partials);
+}
+void launch_to_float(const double *x, float *y, size_t n, cudaStream_t s) {
+  k_to_float<<<grid_cap(n), 256, 0, s>>>(x, y, n);
+}
+void launch_c128_to_c64(const double2 *x, float2 *y, size_t n, cudaStream_t s) {
+  k_c128_to_c64<<<grid_cap(n), 256, 0, s>>>(x, y, n);
+}
+void launch_c64_to_c128(const float2 *x, double2 *y, size_t n, cudaStream_t s) {
+  k_c64_to_c128<<<grid_cap(n), 256, 0, s>>>(x, y, n);
+}
+void launch_state_init(SolveState *st, const double *partials,
+                       const SolveParams *P, int *flag, cudaStream_t s) {
+  k_state_init<<<1, 1024, 0, s>>>(st, partials, P, flag);
+}
+void launch_check_cycle(SolveState *st, const double *partials,
+                        const SolveParams *P, int *flag,
+                        unsigned long long cond, cudaStream_t s) {
+  k_check_cycle<<<1, 1024, 0, s>>>(st, partials, P, flag, cond);
+}
+void launch_check_inner(SolveState *st, const double *partials,
+                        const SolveParams *P, int *flag,
+                        unsigned long long cond, cudaStream_t s) {
+  k_check_inner<<<1, 1024, 0, s>>>(st, partials, P, flag, cond);
+}
+void launch_check_outer(SolveState *st, const double *partials,
+                        const SolveParams *P, int *flag, cudaStream_t s) {
+  k_check_outer<<<1, 1024, 0, s>>>(st, partials, P, flag);
+}
+void launch_finish(const SolveState *st, const double2 *src, double2 *dst,
+                   size_t pts, int batch, cudaStream_t s) {
+  k_finish<<<dim3(grid_cap(pts), batch), 256, 0, s>>>(st, src, dst, pts);
+}
+void launch_grad_k2(const double2 *u, const double2 *lam, size_t pts,
+                    int batch, double *grad, cudaStream_t s) {
+  k_grad_k2<<<grid_cap(pts), 256, 0, s>>>(u, lam, pts, batch, grad);
+}
+template <typename R>
+void launch_coarse_solve(const double2 *lu, const int *piv, int m,
+                         const typename Cx<R>::T *f, typename Cx<R>::T *e,
+                         int batch, const SolveState *st, cudaStream_t s) {
+  k_coarse_solve<R><<<batch, 32, 0, s>>>(lu, piv, m, f, e, st);
+}
+template void launch_coarse_solve<float>(const double2 *, const int *, int,
+                                         const float2 *, float2 *, int,
+                                         const SolveState *, cudaStream_t);
+template void launch_coarse_solve<double>(const double2 *, const int *, int,
+                                          const double2 *, double2 *, int,
+                                          const SolveState *, cudaStream_t);
+
+}  // namespace hh

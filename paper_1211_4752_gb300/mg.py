@@ -1,0 +1,254 @@
+"""Python face of the C ABI: a handle class and a torch.autograd.Function.
+
+Only argument marshalling happens here (tensor checks, pointers, the current
+torch stream); every step of the method runs in the CUDA library.  Arrays are
+torch tensors on the handle's CUDA device: complex128 [batch, N, N] (2-D) or
+[batch, N, N, N] (3-D) with N = n - 1 interior points per axis, x fastest.
+"""
+
+from __future__ import annotations
+
+import ctypes as ct
+import math
+
+import torch
+
+from . import _binding as B
+
+
+def _stream():
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr())
+
+
+class HelmholtzMG:
+    """Level-dependent multigrid hierarchy for (-Delta - k^2) u = f.
+
+    n: intervals per axis (power of two); dim: 2 or 3; k2: fine k^2 field
+    (real tensor of the interior shape, any device) or a float; layers: ECS
+    layer width in fine cells, one int or (lo, hi); form: 'csl' | 'csg';
+    thetas / c: optional per-level angles / per-transfer residual scales;
+    precision: 'fp64' | 'mixed'."""
+
+    def __init__(self, n, dim=2, k2=0.0, layers=0, ecs_angle=math.pi / 6,
+                 form="csl", theta_max=math.pi / 6, p=0, thetas=None, c=None,
+                 omega=0.8, nu1=1, nu2=1, precision="fp64", coarsest=4,
+                 max_cycles=20000, div_limit=1e3, inner_tol=1e-3,
+                 max_inner=4000, max_batch=1, device=None):
+        L = B.lib()
+        self.n, self.dim, self.N = int(n), int(dim), int(n) - 1
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.shape = (self.N,) * self.dim
+        self.max_batch = int(max_batch)
+        self.precision = precision
+        lo, hi = (layers, layers) if isinstance(layers, int) else tuple(layers)
+        g = B.HHGrid(self.dim, self.n, int(lo), int(hi), float(ecs_angle))
+        sh = B.HHShift()
+        L.hh_default_shift(ct.byref(sh))
+        sh.form = B.HH_FORM_CSL if form == "csl" else B.HH_FORM_CSG
+        sh.theta_max = float(theta_max)
+        sh.p = int(p)
+        self._keep = []
+        if thetas is not None:
+            arr = (ct.c_double * len(thetas))(*[float(t) for t in thetas])
+            self._keep.append(arr)
+            sh.theta = ct.cast(arr, ct.POINTER(ct.c_double))
+        if c is not None:
+            flat = []
+            for z in c:
+                z = complex(z)
+                flat += [z.real, z.imag]
+            arr = (ct.c_double * len(flat))(*flat)
+            self._keep.append(arr)
+            sh.c = ct.cast(arr, ct.POINTER(ct.c_double))
+        o = B.HHOptions()
+        L.hh_default_options(ct.byref(o))
+        w = complex(omega)
+        o.omega_re, o.omega_im = w.real, w.imag
+        o.nu1, o.nu2 = int(nu1), int(nu2)
+        o.precision = B.HH_FP64 if precision == "fp64" else B.HH_MIXED
+        o.coarsest = int(coarsest)
+        o.max_cycles = int(max_cycles)
+        o.div_limit = float(div_limit)
+        o.inner_tol = float(inner_tol)
+        o.max_inner = int(max_inner)
+        self.k2_const = 0.0
+        k2_ptr = ct.c_void_p(0)
+        if isinstance(k2, torch.Tensor):
+            k2t = k2.detach().to(device=self.device, dtype=torch.float64).contiguous()
+            if tuple(k2t.shape) != self.shape:
+                raise ValueError(f"k2 must have shape {self.shape}")
+            k2_ptr = _ptr(k2t)
+        else:
+            self.k2_const = float(k2)
+        h = ct.c_void_p()
+        with torch.cuda.device(self.device):
+            B.check(L.hh_setup(ct.byref(g), k2_ptr, self.k2_const, ct.byref(sh),
+                               ct.byref(o), self.max_batch, _stream(), ct.byref(h)))
+        self._h = h
+        self.levels = L.hh_num_levels(h)
+
+    # ---- helpers ---------------------------------------------------------
+    def _vec(self, x, name, level=0):
+        N = self.level_points(level)
+        shape = (N,) * self.dim
+        if not isinstance(x, torch.Tensor) or x.dtype != torch.complex128 or x.device != self.device:
+            raise TypeError(f"{name} must be a complex128 tensor on {self.device}")
+        if tuple(x.shape[-self.dim:]) != shape or x.dim() != self.dim + 1:
+            raise ValueError(f"{name} must have shape [batch, {', '.join(map(str, shape))}]")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return x
+
+    def level_points(self, level):
+        return B.lib().hh_level_points(self._h, int(level))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.lib().hh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _infos(arr, n):
+        return [dict(cycles=arr[i].cycles, refinements=arr[i].refinements,
+                     rel_residual=arr[i].rel_residual,
+                     status=B.STATUS_NAMES.get(arr[i].status, arr[i].status))
+                for i in range(n)]
+
+    # ---- solves ----------------------------------------------------------
+    def _solve(self, fn, f, tol, u0, raise_on_fail):
+        f = self._vec(f, "rhs")
+        nb = f.shape[0]
+        u = torch.empty_like(f) if u0 is None else self._vec(u0, "u0").clone()
+        info = (B.HHSolveInfo * nb)()
+        with torch.cuda.device(self.device):
+            st = fn(self._h, _ptr(f), _ptr(u), nb, float(tol),
+                    B.HH_USE_GUESS if u0 is not None else 0, info, _stream())
+        if st not in (B.HH_OK, B.HH_ERR_NOT_CONVERGED, B.HH_ERR_DIVERGED) or (raise_on_fail and st != B.HH_OK):
+            B.check(st)
+        return u, self._infos(info, nb)
+
+    def solve(self, f, tol=1e-6, u0=None, raise_on_fail=False):
+        """u = A_0^{-1} f by V-cycles to ||f - A_0 u|| / ||f|| <= tol."""
+        return self._solve(B.lib().hh_solve, f, tol, u0, raise_on_fail)
+
+    def adjoint(self, g, tol=1e-6, lam0=None, raise_on_fail=False):
+        """lambda = A_0^{-H} g by V-cycles on the conjugate-transposed hierarchy."""
+        return self._solve(B.lib().hh_adjoint, g, tol, lam0, raise_on_fail)
+
+    def solve_host(self, f_host, u_host, tol=1e-6, use_guess=False):
+        """Solve with HOST (ideally pinned) complex128 tensors; the copies
+        are part of the call.  u_host is overwritten with the solution."""
+        for t, nm in ((f_host, "f_host"), (u_host, "u_host")):
+            if t.device.type != "cpu" or t.dtype != torch.complex128 or not t.is_contiguous():
+                raise TypeError(f"{nm} must be a contiguous complex128 CPU tensor")
+        nb = f_host.shape[0]
+        info = (B.HHSolveInfo * nb)()
+        with torch.cuda.device(self.device):
+            st = B.lib().hh_solve_host(self._h, _ptr(f_host), _ptr(u_host), nb,
+                                       float(tol), B.HH_USE_GUESS if use_guess else 0,
+                                       info, _stream())
+        if st not in (B.HH_OK, B.HH_ERR_NOT_CONVERGED, B.HH_ERR_DIVERGED):
+            B.check(st)
+        return self._infos(info, nb)
+
+    def grad_k2(self, u, lam):
+        u = self._vec(u, "u")
+        lam = self._vec(lam, "lam")
+        g = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().hh_grad_k2(self._h, _ptr(u), _ptr(lam), u.shape[0], _ptr(g), _stream()))
+        return g
+
+    # ---- step API (complex128, FP64 tables) ------------------------------
+    def apply(self, x, level=0, adjoint=False):
+        x = self._vec(x, "x", level)
+        y = torch.empty_like(x)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().hh_apply(self._h, int(level), int(bool(adjoint)), _ptr(x), _ptr(y), x.shape[0], _stream()))
+        return y
+
+    def cycles(self, f, u, ncycles):
+        f = self._vec(f, "f")
+        u = self._vec(u, "u").clone()
+        with torch.cuda.device(self.device):
+            B.check(B.lib().hh_cycles(self._h, _ptr(f), _ptr(u), f.shape[0], int(ncycles), _stream()))
+        return u
+
+    def smooth(self, level, u, f):
+        u = self._vec(u, "u", level)
+        f = self._vec(f, "f", level)
+        out = torch.empty_like(u)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().hh_smooth(self._h, int(level), _ptr(u), _ptr(f), _ptr(out), u.shape[0], _stream()))
+        return out
+
+    def residual_restrict(self, level, u, f):
+        u = self._vec(u, "u", level)
+        f = self._vec(f, "f", level)
+        Nc = self.level_points(level + 1)
+        fc = torch.empty((u.shape[0],) + (Nc,) * self.dim, dtype=torch.complex128, device=self.device)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().hh_residual_restrict(self._h, int(level), _ptr(u), _ptr(f), _ptr(fc), u.shape[0], _stream()))
+        return fc
+
+    def correct_smooth(self, level, u, e, f):
+        u = self._vec(u, "u", level)
+        e = self._vec(e, "e", level + 1)
+        f = self._vec(f, "f", level)
+        out = torch.empty_like(u)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().hh_correct_smooth(self._h, int(level), _ptr(u), _ptr(e), _ptr(f), _ptr(out), u.shape[0], _stream()))
+        return out
+
+    def coarse_solve(self, f):
+        f = self._vec(f, "f", self.levels - 1)
+        e = torch.empty_like(f)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().hh_coarse_solve(self._h, _ptr(f), _ptr(e), f.shape[0], _stream()))
+        return e
+
+
+class HelmholtzSolve(torch.autograd.Function):
+    """u = A_0(k2)^{-1} f with A_0 = -Delta - diag(k2) (finest operator).
+
+    Backward (adjoint method): lambda = A_0^{-H} grad_u by the adjoint
+    V-cycle, grad_f = lambda, grad_k2 = sum_b Re(conj(lambda_b) u_b).
+    `mg_kwargs` are HelmholtzMG keyword arguments (n, dim, layers, ...)."""
+
+    @staticmethod
+    def forward(ctx, k2, f, mg_kwargs, tol=1e-6):
+        kw = dict(mg_kwargs)
+        kw.setdefault("max_batch", f.shape[0])
+        mg = HelmholtzMG(k2=k2.detach(), device=f.device, **kw)
+        u, info = mg.solve(f.detach().contiguous(), tol=tol, raise_on_fail=True)
+        ctx.mg = mg
+        ctx.tol = tol
+        ctx.save_for_backward(u)
+        ctx.info = info
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (u,) = ctx.saved_tensors
+        mg = ctx.mg
+        lam, _ = mg.adjoint(grad_u.contiguous(), tol=ctx.tol, raise_on_fail=True)
+        gk2 = mg.grad_k2(u, lam) if ctx.needs_input_grad[0] else None
+        gf = lam if ctx.needs_input_grad[1] else None
+        ctx.mg = None
+        mg.close()
+        return gk2, gf, None, None
+
+
+def helmholtz_solve(k2, f, tol=1e-6, **mg_kwargs):
+    """Differentiable solve: u = A_0(k2)^{-1} f (see HelmholtzSolve)."""
+    return HelmholtzSolve.apply(k2, f, mg_kwargs, tol)

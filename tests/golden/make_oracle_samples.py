@@ -1,0 +1,53 @@
+"""Write a golden fixture of the FP64 oracle's converged solution of one
+workload: cycle count, final relative residual, residual history (every 50
+cycles), the solution norm and the solution at seeded sample points.
+
+Calls only the oracle (oracle/) and the seeded input generators; nothing from
+the CUDA path.  Usage:
+    python tests/golden/make_oracle_samples.py ecs_const  [out.json]
+    python tests/golden/make_oracle_samples.py layered    [out.json]
+"""
+
+import json
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parents[2]
+sys.path.insert(0, str(ROOT))
+
+import oracle  # noqa: E402
+from paper_1211_4752_gb300 import workloads  # noqa: E402
+
+
+def main():
+    which = sys.argv[1]
+    w = getattr(workloads, which)()
+    out = Path(sys.argv[2]) if len(sys.argv) > 2 else Path(__file__).with_name(w["name"] + ".json")
+    t0 = time.time()
+    H = oracle.build_hierarchy(w["n"], w["dim"], w["k2"], layers=w["layers"])
+    f = w["rhs"][0]
+    res = oracle.solve(H, f, tol=1e-6, max_cycles=20000)
+    u = res.u
+    rng = np.random.default_rng(1234)
+    N = w["n"] - 1
+    idx = [tuple(int(v) for v in rng.integers(0, N, size=w["dim"])) for _ in range(512)]
+    src = tuple(int(v) for v in np.argwhere(f != 0)[0])
+    for d in range(-3, 4):
+        idx.append(tuple(min(max(s + d, 0), N - 1) for s in src))
+    vals = [[float(u[i].real), float(u[i].imag)] for i in idx]
+    data = dict(workload=w["name"], n=w["n"], dim=w["dim"], layers=w["layers"],
+                tol=1e-6, cycles=res.cycles, rel_residual=res.history[-1],
+                history_every50=res.history[::50], u_norm=float(np.linalg.norm(u)),
+                u_maxabs=float(np.abs(u).max()), sample_index=idx,
+                sample_value=vals, seconds=time.time() - t0,
+                note="FP64 oracle, V(1,1) weighted Jacobi 0.8, CSL shifts "
+                     "theta_l = l (pi/6)/log2(n), coarsest 3x3 interior, u0 = 0")
+    out.write_text(json.dumps(data))
+    print(out, res.cycles, res.history[-1], data["seconds"])
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,302 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several thread blocks and ragged tails; ECS and Dirichlet,
+constant and heterogeneous k^2, CSL and CSG forms, batches, 2-D and 3-D."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1211_4752_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relerr(a, b):
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def maxrel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+CASES = [
+    # n, dim, k2 spec, layers, form, c_scale
+    dict(n=16, dim=2, k2=("const", 300.0), layers=0, form="csl"),
+    dict(n=64, dim=2, k2=("field", 10.0, 30.0), layers=(4, 6), form="csl"),
+    dict(n=128, dim=2, k2=("field", 40.0, 70.0), layers=8, form="csg", c=True),
+    dict(n=16, dim=3, k2=("field", 5.0, 9.0), layers=2, form="csl"),
+    dict(n=32, dim=3, k2=("const", 300.0), layers=(2, 3), form="csg"),
+]
+
+
+def k2_of(case, seed=0):
+    spec = case["k2"]
+    if spec[0] == "const":
+        return spec[1]
+    return W.smooth_k2(case["n"], case["dim"], seed, spec[1], spec[2])
+
+
+def make_pair(case, batch=2, **kw):
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n, dim = case["n"], case["dim"]
+    k2 = k2_of(case)
+    P = int(round(math.log2(n)))
+    L = P - 1
+    c = None
+    if case.get("c"):
+        c = [np.exp(-1j * (math.pi / 6) / P)] * (L - 1)
+    H = O.build_hierarchy(n, dim, k2, layers=case["layers"], form=case["form"], c=c,
+                          omega=kw.get("omega", 0.8), nu1=kw.get("nu1", 1), nu2=kw.get("nu2", 1))
+    k2_t = dev(k2) if isinstance(k2, np.ndarray) else float(k2)
+    mg = HelmholtzMG(n, dim=dim, k2=k2_t, layers=case["layers"], form=case["form"], c=c,
+                     max_batch=batch, **kw)
+    return H, mg
+
+
+def rnd(shape, seed):
+    return W.random_field(shape, seed)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c['dim']}d-n{c['n']}-{c['form']}")
+def test_apply_forward_and_adjoint(case):
+    H, mg = make_pair(case, batch=3)
+    Ha = O.adjoint_hierarchy(H)
+    for l in range(len(H.levels)):
+        lv = H.levels[l]
+        x = rnd((3,) + lv.shape, 10 + l)
+        for adj, hier in ((False, H), (True, Ha)):
+            y = host(mg.apply(dev(x), level=l, adjoint=adj))
+            ref = np.stack([O.apply_operator(hier.levels[l], x[b]) for b in range(3)])
+            assert maxrel(y, ref) < 1e-13, (l, adj)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c['dim']}d-n{c['n']}-{c['form']}")
+def test_step_kernels(case):
+    H, mg = make_pair(case, batch=2)
+    for l in range(len(H.levels) - 1):
+        lv, lc = H.levels[l], H.levels[l + 1]
+        u = rnd((2,) + lv.shape, 1 + l)
+        f = rnd((2,) + lv.shape, 2 + l)
+        e = rnd((2,) + lc.shape, 3 + l)
+        # weighted Jacobi, Eq. (wjacobi)
+        got = host(mg.smooth(l, dev(u), dev(f)))
+        ref = np.stack([O.jacobi(lv, u[b], f[b], H.omega) for b in range(2)])
+        assert maxrel(got, ref) < 1e-13
+        # c * FW(f - A u)
+        got = host(mg.residual_restrict(l, dev(u), dev(f)))
+        ref = np.stack([H.c[l] * O.restrict_fw(f[b] - O.apply_operator(lv, u[b])) for b in range(2)])
+        assert maxrel(got, ref) < 1e-12
+        # Jacobi of u + P e
+        got = host(mg.correct_smooth(l, dev(u), dev(e), dev(f)))
+        ref = np.stack([O.jacobi(lv, u[b] + O.prolong(e[b]), f[b], H.omega) for b in range(2)])
+        assert maxrel(got, ref) < 1e-13
+    fL = rnd((2,) + H.levels[-1].shape, 99)
+    got = host(mg.coarse_solve(dev(fL)))
+    ref = np.stack([O.lu_solve(H.lu, fL[b].ravel()).reshape(fL[b].shape) for b in range(2)])
+    assert maxrel(got, ref) < 1e-13
+
+
+@pytest.mark.parametrize("nu", [(1, 1), (2, 3)])
+@pytest.mark.parametrize("case", CASES[1:4], ids=lambda c: f"{c['dim']}d-n{c['n']}-{c['form']}")
+def test_cycles_match_oracle_fp64(case, nu):
+    H, mg = make_pair(case, batch=2, nu1=nu[0], nu2=nu[1], omega=0.8 + 0.05j)
+    f = rnd((2,) + H.levels[0].shape, 5)
+    u0 = rnd((2,) + H.levels[0].shape, 6) * 1e-3
+    got = host(mg.cycles(dev(f), dev(u0), 3))
+    ref = []
+    for b in range(2):
+        u = u0[b].copy()
+        for _ in range(3):
+            u = O.vcycle(H, 0, u, f[b])
+        ref.append(u)
+    assert relerr(got, np.stack(ref)) < 1e-12
+
+
+def test_cycles_complex64_track_oracle():
+    case = CASES[1]
+    H, mg = make_pair(case, batch=1, precision="mixed")
+    f = rnd((1,) + H.levels[0].shape, 5)
+    got = host(mg.cycles(dev(f), dev(np.zeros_like(f)), 2))
+    u = np.zeros_like(f[0])
+    for _ in range(2):
+        u = O.vcycle(H, 0, u, f[0])
+    assert relerr(got[0], u) < 1e-5
+
+
+def point_rhs(n, dim, batch, seed):
+    rng = np.random.default_rng(seed)
+    pos = [tuple(rng.integers(n // 8, n - n // 8 - 1, size=dim)) for _ in range(batch)]
+    return W.point_sources(n, dim, pos)
+
+
+SOLVE_CASES = [
+    dict(n=64, k=40.0, layers=2),     # kh = 0.625, thin layer
+    dict(n=128, k=40.0, layers=16),
+    dict(n=32, k=20.0, layers=4),
+]
+
+
+@pytest.mark.parametrize("sc", SOLVE_CASES, ids=lambda s: f"n{s['n']}-k{s['k']}")
+def test_solve_fp64_matches_oracle(sc):
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n, k, layers = sc["n"], sc["k"], sc["layers"]
+    f = point_rhs(n, 2, 3, n)
+    H = O.build_hierarchy(n, 2, k * k, layers=layers)
+    mg = HelmholtzMG(n, k2=k * k, layers=layers, max_batch=3)
+    u, info = mg.solve(dev(f), tol=1e-6)
+    u = host(u)
+    for b in range(3):
+        res = O.solve(H, f[b], tol=1e-6, max_cycles=20000)
+        assert info[b]["status"] == "OK"
+        assert abs(info[b]["cycles"] - res.cycles) <= 1, (info[b], res.cycles)
+        assert relerr(u[b], res.u) < 1e-10
+        rho = np.linalg.norm(f[b] - O.apply_operator(H.levels[0], u[b])) / np.linalg.norm(f[b])
+        assert rho <= 1e-6 and abs(rho - info[b]["rel_residual"]) < 1e-12
+
+
+@pytest.mark.parametrize("sc", SOLVE_CASES[:2], ids=lambda s: f"n{s['n']}-k{s['k']}")
+def test_solve_mixed_error_vs_oracle(sc):
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n, k, layers = sc["n"], sc["k"], sc["layers"]
+    f = point_rhs(n, 2, 2, n + 1)
+    H = O.build_hierarchy(n, 2, k * k, layers=layers)
+    mg = HelmholtzMG(n, k2=k * k, layers=layers, max_batch=2, precision="mixed")
+    u, info = mg.solve(dev(f), tol=1e-6)
+    u = host(u)
+    for b in range(2):
+        ref = O.solve(H, f[b], tol=1e-10, max_cycles=40000).u
+        assert info[b]["status"] == "OK" and info[b]["refinements"] >= 1
+        rho = np.linalg.norm(f[b] - O.apply_operator(H.levels[0], u[b])) / np.linalg.norm(f[b])
+        assert rho <= 1e-6
+        assert relerr(u[b], ref) <= 1e-5
+
+
+def test_dirichlet_model_problem_stalls_like_oracle():
+    """63^2, k = 40, Dirichlet: neither side reaches 1e-6; iterates agree."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    w = W.dirichlet_const()
+    H = O.build_hierarchy(w["n"], 2, w["k2"], layers=0)
+    mg = HelmholtzMG(w["n"], k2=w["k2"], layers=0, max_cycles=60)
+    u, info = mg.solve(dev(w["rhs"]), tol=1e-6)
+    assert info[0]["status"] == "ERR_NOT_CONVERGED" and info[0]["cycles"] == 60
+    with pytest.raises(O.NotConvergedError):
+        O.solve(H, w["rhs"][0], tol=1e-6, max_cycles=60)
+    ref = np.zeros_like(w["rhs"][0])
+    for _ in range(60):
+        ref = O.vcycle(H, 0, ref, w["rhs"][0])
+    assert relerr(host(u)[0], ref) < 1e-10
+
+
+def test_adjoint_solve_and_gradient_match_oracle():
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n, layers = 64, 4
+    k2 = W.smooth_k2(n, 2, 3, 35.0, 40.0)
+    H = O.build_hierarchy(n, 2, k2, layers=layers)
+    Ha = O.adjoint_hierarchy(H)
+    mg = HelmholtzMG(n, k2=dev(k2), layers=layers, max_batch=2)
+    f = point_rhs(n, 2, 2, 7)
+    g = rnd((2, n - 1, n - 1), 8)
+    u, iu = mg.solve(dev(f), tol=1e-10)
+    lam, il = mg.adjoint(dev(g), tol=1e-10)
+    u_h, lam_h = host(u), host(lam)
+    lam_ref = np.stack([O.solve(Ha, g[b], tol=1e-10).u for b in range(2)])
+    u_ref = np.stack([O.solve(H, f[b], tol=1e-10).u for b in range(2)])
+    assert relerr(lam_h, lam_ref) < 1e-9
+    assert all(i["status"] == "OK" for i in il)
+    grad = host(mg.grad_k2(u, lam))
+    assert maxrel(grad, O.grad_k2(u_ref, lam_ref)) < 1e-8
+    # dot test on the device: <A x, y> = <x, A^H y>
+    x, y = rnd((1, n - 1, n - 1), 1), rnd((1, n - 1, n - 1), 2)
+    lhs = np.vdot(host(mg.apply(dev(x))), y)
+    rhs = np.vdot(x, host(mg.apply(dev(y), adjoint=True)))
+    assert abs(lhs - rhs) <= 1e-13 * 8 * n * n * np.linalg.norm(x) * np.linalg.norm(y)
+
+
+def test_autograd_matches_central_differences():
+    from paper_1211_4752_gb300 import helmholtz_solve
+    n, layers = 32, 4
+    k2 = dev(W.smooth_k2(n, 2, 11, 19.0, 21.0)).requires_grad_(True)
+    f = dev(point_rhs(n, 2, 2, 3)).requires_grad_(True)
+    rows = n - 1 - layers - 1
+    d = dev(rnd((2, n - 1), 4) * 1e-4)
+    kw = dict(n=n, layers=layers)
+
+    def loss_of(k2v, fv):
+        u = helmholtz_solve(k2v, fv, tol=1e-12, **kw)
+        return 0.5 * (u[:, rows, :] - d).abs().pow(2).sum()
+
+    L0 = loss_of(k2, f)
+    L0.backward()
+    gk = k2.grad.detach().cpu().numpy()
+    gf = f.grad.detach().cpu().numpy()
+    k2n = k2.detach().cpu().numpy()
+    rng = np.random.default_rng(0)
+    pts = [tuple(rng.integers(0, n - 1, size=2)) for _ in range(20)]
+    with torch.no_grad():
+        for (i, j) in pts:
+            dk = 1e-4 * k2n[i, j]
+            kp = k2.detach().clone(); kp[i, j] += dk
+            km = k2.detach().clone(); km[i, j] -= dk
+            fd = (loss_of(kp, f.detach()) - loss_of(km, f.detach())).item() / (2 * dk)
+            assert abs(fd - gk[i, j]) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(gk).max())
+        # d loss / d f along a random complex direction: Re <grad_f, v>
+        v = dev(rnd(tuple(f.shape), 5))
+        eps = 1e-3
+        fd = (loss_of(k2.detach(), f.detach() + eps * v) - loss_of(k2.detach(), f.detach() - eps * v)).item() / (2 * eps)
+        pred = np.real(np.vdot(gf, host(v)))
+        assert abs(fd - pred) <= 1e-4 * abs(fd)
+
+
+def test_edge_cases():
+    from paper_1211_4752_gb300 import HelmholtzMG, HHError
+    n = 32
+    mg = HelmholtzMG(n, k2=400.0, layers=4, max_batch=3)
+    f = point_rhs(n, 2, 3, 1)
+    f[1] = 0.0                       # a zero right-hand side in the batch
+    u, info = mg.solve(dev(f), tol=1e-6)
+    u = host(u)
+    assert info[1]["status"] == "OK" and info[1]["cycles"] == 0 and not np.any(u[1])
+    assert info[0]["status"] == "OK" and info[2]["status"] == "OK"
+    # the converged solution as the initial guess: no further cycle needed
+    u2, info2 = mg.solve(dev(f), tol=1e-6, u0=dev(u))
+    assert info2[0]["cycles"] == 0 and info2[2]["cycles"] == 0
+    assert np.array_equal(host(u2)[0], u[0])
+    # host-buffer entry point matches the device one
+    fh = torch.from_numpy(f).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    info3 = mg.solve_host(fh, uh, tol=1e-6)
+    assert np.array_equal(uh.numpy(), u) and info3[0]["cycles"] == info[0]["cycles"]
+    with pytest.raises(HHError):
+        mg.solve(dev(point_rhs(n, 2, 4, 1)))      # batch > max_batch
+    with pytest.raises((HHError, ValueError)):
+        mg.smooth(7, dev(np.zeros((1, 3, 3), complex)), dev(np.zeros((1, 3, 3), complex)))
+
+
+def test_max_cycles_and_divergence_status():
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n = 32
+    # k^2 = 250 diverges with weighted Jacobi (oracle: diverged at cycle 7)
+    f = W.random_field((1, n - 1, n - 1), 2)
+    H = O.build_hierarchy(n, 2, 250.0, layers=4)
+    with pytest.raises(O.DivergedError):
+        O.solve(H, f[0], tol=1e-10)
+    mg = HelmholtzMG(n, k2=250.0, layers=4)
+    u, info = mg.solve(dev(f), tol=1e-10)
+    assert info[0]["status"] == "ERR_DIVERGED"
+    mg2 = HelmholtzMG(n, k2=400.0, layers=4, max_cycles=5)
+    u, info = mg2.solve(dev(point_rhs(n, 2, 1, 3)), tol=1e-10)
+    assert info[0]["status"] == "ERR_NOT_CONVERGED" and info[0]["cycles"] == 5
