@@ -165,7 +165,7 @@ k_resid_restrict(LevelK<R> L, const typename Cx<R>::T *__restrict__ u,
           const size_t p = lin<DIM>(x, y, z, N);
           C Au, D, uc;
           stencil<R, DIM>(L, x, y, z, p, get, Au, D, uc);
-          const R w = R((2 - abs(dx)) * (2 - abs(dy)) * (2 - abs(dz)));
+          const R w = R((2 - abs(dx)) * (2 - abs(dy)) * (DIM == 3 ? 2 - abs(dz) : 1));
           acc = cadd(acc, cscale(csub(f[p], Au), w));
         }
     fc[pc] = cmul(cs, cscale(acc, scale));
