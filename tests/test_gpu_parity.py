@@ -203,8 +203,8 @@ def test_dirichlet_model_problem_stalls_like_oracle():
 
 def test_adjoint_solve_and_gradient_match_oracle():
     from paper_1211_4752_gb300 import HelmholtzMG
-    n, layers = 64, 4
-    k2 = W.smooth_k2(n, 2, 3, 35.0, 40.0)
+    n, layers = 64, 8
+    k2 = W.smooth_k2(n, 2, 3, 38.0, 40.0)   # kh ~ 0.6: the Jacobi cycle converges
     H = O.build_hierarchy(n, 2, k2, layers=layers)
     Ha = O.adjoint_hierarchy(H)
     mg = HelmholtzMG(n, k2=dev(k2), layers=layers, max_batch=2)
