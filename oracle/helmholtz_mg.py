@@ -403,7 +403,7 @@ class SolveResult:
     history: list
 
 
-def solve(hier: Hierarchy, f, tol=1e-6, max_cycles=500, u0=None,
+def solve(hier: Hierarchy, f, tol=1e-6, max_cycles=20000, u0=None,
           div_limit=1e3):
     """Repeat V-cycles from u_0 = 0 (or u0) until
     rho_k = ||f - A_0 u_k||_2 / ||f||_2 <= tol (Sec. 4.1 uses V(1,1)-cycles as
@@ -444,7 +444,7 @@ def symmetrizer_weights(hier: Hierarchy):
     return W
 
 
-def adjoint_solve_symmetrized(hier: Hierarchy, g, tol=1e-6, max_cycles=500):
+def adjoint_solve_symmetrized(hier: Hierarchy, g, tol=1e-6, max_cycles=20000):
     """A_0^H lambda = g through the forward solver:
     lambda = conj(W y) with A_0 y = W^{-1} conj(g)."""
     W = symmetrizer_weights(hier)
