@@ -33,14 +33,25 @@ from pathlib import Path
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-# Algorithmic bytes per finest-grid point of each level-0 kernel in the
-# complex64 cycle (c64 = 8 B, k^2 field float32 = 4 B, coarse arrays 1/4):
-#   pre-smoothing sweep     read u, f, k2; write u          = 28 B
-#   residual + restriction  read u, f, k2; write f_c (1/4)  = 22 B
-#   correction + sweep      read u, e (1/4), f, k2; write u = 30 B
-#   FP64 refinement         read u64, e32, f64, k2_64; write u64, rhs32 = 72 B
-KERNEL_BYTES = {0: ("pre_smooth", 28.0), 1: ("residual_restrict", 22.0),
-                2: ("correct_post_smooth", 30.0), 3: ("refine_fp64", 72.0)}
+# Algorithmic bytes per finest-grid point of the level-0 kernels of the
+# complex64 cycle (c64 = 8 B; the k^2 field, float32 = 4 B, is not read when
+# k is constant; coarse arrays are 1/4 of the fine ones):
+#   down pass (pre-smoothing + residual + restriction):
+#       read u, f (+k2); write v, f_c/4            = 26 B (30 B with a k2 field)
+#   up pass (correction + post-smoothing):
+#       read v, e/4, f (+k2); write u              = 26 B (30 B)
+#   FP64 refinement: read u64, e32, f64, k2_64; write u64, rhs32 = 72 B
+# complex128 cycles: twice the cycle figures.
+KERNELS = {0: "down_pass", 2: "up_pass", 3: "refine_fp64", 4: "tail_levels"}
+
+
+def kernel_bytes(kid, kconst, mixed):
+    if kid == 3:
+        return 72.0
+    if kid == 4:
+        return 0.0
+    b = 26.0 if kconst else 30.0
+    return b if mixed else 2.0 * b
 
 
 def env_rank():
@@ -206,16 +217,16 @@ def run_ours(args):
     # dominant kernel, timed live on this stream (level 0, back to back)
     import ctypes as ct
     peak, peak_kind = measured_peaks()
+    kconst = not isinstance(k2, np.ndarray)
     kt = {}
-    for kid in (0, 1, 2) + ((3,) if mixed else ()):
+    for kid in (0, 2, 4) + ((3,) if mixed else ()):
         ms = ct.c_double()
         B.check(B.lib().hh_time_kernel(mg._h, kid, 0, 1, 50, ct.byref(ms),
                                        ct.c_void_p(stream.cuda_stream)))
         kt[kid] = ms.value
-    dom = max((0, 1, 2), key=lambda k: kt[k])
-    name, bpp = KERNEL_BYTES[dom]
-    if not mixed:
-        bpp *= 2.0                     # complex128 / FP64 k^2: twice the bytes
+    dom = max((0, 2), key=lambda k: kt[k])
+    name = KERNELS[dom]
+    bpp = kernel_bytes(dom, kconst, mixed)
     achieved = bpp * pts / (kt[dom] * 1e-3) / 1e9
     traffic = None
     tf = ROOT / "profiles" / "traffic.json"
@@ -264,7 +275,7 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "bytes_per_point": bpp,
-                         "launch_ms": {KERNEL_BYTES[k][0]: v for k, v in kt.items()}},
+                         "launch_ms": {KERNELS[k]: v for k, v in kt.items()}},
             "cpu_baseline": cpu,
             "fp64_gpu": fp64,
             "gpu_launches": args.steps * launches_per_solve(mg.levels, last, mixed=mixed),

@@ -8,10 +8,13 @@
 // launch with no host round trip per cycle.
 #include "../../include/hh.h"
 #include "hh_internal.h"
+#include "hh_cycle.h"
 
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -95,6 +98,11 @@ struct hh_handle {
   SolveParams *params_h = nullptr;  // pinned
   SolveState *st_h = nullptr;       // pinned
   cudaStream_t cap = nullptr;       // private stream for graph capture
+  int fused = 0;                    // 2-D fused down/up kernels + tail kernel
+  int tail0 = 0;                    // first level run by the tail kernel
+  int kconst = 0;                   // k^2 constant: kernels read k2[0] only
+  int variant[MAXL] = {};           // tile shape per fused level (autotuned)
+  int parts_cap = 0;                // capacity of `partials` per RHS
   std::vector<void *> allocs;
   std::map<std::tuple<int, int, int>, GraphEntry> graphs;
 
@@ -226,10 +234,66 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
   }
 }
 
+template <typename R> TailArgs<R> tail_args(hh_handle *h, int dir) {
+  Work<R> &W = work<R>(h);
+  TailArgs<R> a{};
+  a.nl = h->L - h->tail0;
+  for (int i = 0; i < a.nl; ++i) {
+    const int l = h->tail0 + i;
+    a.lv[i].K = levelk<R>(h, l, dir);
+    a.lv[i].f = W.f[l];
+    a.lv[i].v = W.u_pre[l];
+    a.lv[i].t = W.tmp[l];
+    a.lv[i].u = W.u_post[l];
+    a.lv[i].c = cscal<R>(h, l, dir);
+  }
+  a.lu = h->lu[dir];
+  a.piv = h->piv[dir];
+  a.m = h->m;
+  a.omega = omega<R>(h, dir);
+  a.nu1 = h->opt.nu1;
+  a.nu2 = h->opt.nu2;
+  return a;
+}
+
+// The same V-cycle with the fused 2-D kernels: one down pass per level
+// (pre-smoothing + residual + restriction), one kernel for every level from
+// tail0 to the coarsest, one up pass per level (correction + post-smoothing).
+template <typename R>
+void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
+                         unsigned long long cond, cudaStream_t s) {
+  Work<R> &W = work<R>(h);
+  const SolveState *st = check != CHECK_NONE ? h->st : nullptr;
+  const auto om = omega<R>(h, dir);
+  const int T = h->tail0;
+  for (int l = 0; l < T; ++l) {
+    const LevelK<R> K = levelk<R>(h, l, dir);
+    const bool norm = l == 0 && check != CHECK_NONE;
+    launch_down2d<R>(h->variant[l], K, l == 0 ? W.u_post[0] : nullptr,
+                     l == 0 ? zero0 : ZERO_ALL, W.f[l], W.u_pre[l], W.f[l + 1],
+                     cscal<R>(h, l, dir), om, h->kconst, batch, st,
+                     norm ? h->partials : nullptr, s);
+    if (norm) {
+      if (check == CHECK_CYCLE)
+        launch_check_cycle(h->st, h->partials, h->params, h->flag, cond, s);
+      else
+        launch_check_inner(h->st, h->partials, h->params, h->flag, cond, s);
+    }
+  }
+  launch_tail2d<R>(tail_args<R>(h, dir), batch, st, s);
+  for (int l = T - 1; l >= 0; --l) {
+    const LevelK<R> K = levelk<R>(h, l, dir);
+    launch_up2d<R>(h->variant[l], K, W.u_pre[l], W.u_post[l + 1], W.f[l], W.u_post[l],
+                   om, h->kconst, batch, st, s);
+  }
+}
+
 template <typename R>
 void cycle_dispatch(hh_handle *h, int dir, int batch, int zero0, int check,
                     unsigned long long cond, cudaStream_t s) {
-  if (h->dim == 2)
+  if (h->fused)
+    enqueue_cycle_fused<R>(h, dir, batch, zero0, check, cond, s);
+  else if (h->dim == 2)
     enqueue_cycle<R, 2>(h, dir, batch, zero0, check, cond, s);
   else
     enqueue_cycle<R, 3>(h, dir, batch, zero0, check, cond, s);
@@ -381,6 +445,20 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
   const LevelK<R> K = levelk<R>(h, level, 0);
   const auto om = omega<R>(h, 0);
   const bool two = h->dim == 2;
+  if (h->fused && level < h->tail0 && kernel != 1) {
+    if (kernel == 0)
+      launch_down2d<R>(h->variant[level], K, W.u_post[level], ZERO_NONE, W.f[level],
+                       W.u_pre[level], W.f[level + 1], cscal<R>(h, level, 0), om, h->kconst,
+                       batch, nullptr, level == 0 ? h->partials : nullptr, s);
+    else
+      launch_up2d<R>(h->variant[level], K, W.u_pre[level], W.u_post[level + 1], W.f[level],
+                     W.u_post[level], om, h->kconst, batch, nullptr, s);
+    return;
+  }
+  if (kernel == 4) {
+    launch_tail2d<R>(tail_args<R>(h, 0), batch, nullptr, s);
+    return;
+  }
   if (kernel == 0) {
     double *parts = level == 0 ? h->partials : nullptr;
     if (two) launch_smooth<R, 2>(K, W.u_post[level], ZERO_NONE, W.f[level], W.u_pre[level], om, batch, nullptr, parts, h->nparts, s);
@@ -429,6 +507,64 @@ void destroy_impl(hh_handle *h) {
   if (h->st_h) cudaFreeHost(h->st_h);
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
+}
+
+// Autotuner: per fused level, time the down and up passes of every tile
+// shape on the workspace (handle's precision, one right-hand side) and keep
+// the fastest.  HH_TILE_VARIANT=<k> in the environment forces shape k.
+template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, int *best) {
+  Work<R> &W = work<R>(h);
+  const LevelK<R> K = levelk<R>(h, l, 0);
+  const auto om = omega<R>(h, 0);
+  cudaEvent_t e0, e1;
+  HH_CK(cudaEventCreate(&e0));
+  HH_CK(cudaEventCreate(&e1));
+  float tbest = 1e30f;
+  *best = 0;
+  for (int v = 0; v < kNumTileVariants; ++v) {
+    auto run = [&]() {
+      launch_down2d<R>(v, K, W.u_post[l], ZERO_NONE, W.f[l], W.u_pre[l], W.f[l + 1],
+                       cscal<R>(h, l, 0), om, h->kconst, 1, nullptr, nullptr, s);
+      launch_up2d<R>(v, K, W.u_pre[l], W.u_post[l + 1], W.f[l], W.u_post[l], om,
+                     h->kconst, 1, nullptr, s);
+    };
+    run();
+    HH_CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < 4; ++r) run();
+    HH_CK(cudaEventRecord(e1, s));
+    HH_CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    HH_CK(cudaEventElapsedTime(&t, e0, e1));
+    if (t < tbest) { tbest = t; *best = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HH_CK(cudaGetLastError());
+  return HH_OK;
+}
+
+hh_status autotune(hh_handle *h, cudaStream_t s) {
+  const char *force = std::getenv("HH_TILE_VARIANT");
+  if (force) {
+    const int v = std::atoi(force);
+    if (v < 0 || v >= kNumTileVariants) return fail(HH_ERR_ARG, "HH_TILE_VARIANT out of range");
+    for (int l = 0; l < h->tail0; ++l) h->variant[l] = v;
+    return HH_OK;
+  }
+  for (int l = 0; l < h->tail0; ++l) {
+    if (h->opt.precision == HH_MIXED) HH_TRY(tune_level<float>(h, l, s, &h->variant[l]));
+    else HH_TRY(tune_level<double>(h, l, s, &h->variant[l]));
+  }
+  // the tuning runs overwrote workspace: clear it again
+  for (int l = 0; l < h->L; ++l) {
+    const size_t np = h->lv[l].pts * (size_t)h->max_batch;
+    for (double2 *p : {h->w64.u_pre[l], h->w64.u_post[l], h->w64.f[l]})
+      HH_CK(cudaMemsetAsync(p, 0, np * sizeof(double2), s));
+    for (float2 *p : {h->w32.u_pre[l], h->w32.u_post[l], h->w32.f[l]})
+      HH_CK(cudaMemsetAsync(p, 0, np * sizeof(float2), s));
+  }
+  HH_CK(cudaStreamSynchronize(s));
+  return HH_OK;
 }
 
 hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
@@ -549,8 +685,36 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   HH_TRY(dev_alloc_n(h, &h->u64[1], np0));
   HH_CK(cudaMemsetAsync(h->u64[0], 0, np0 * sizeof(double2), s));
   HH_CK(cudaMemsetAsync(h->u64[1], 0, np0 * sizeof(double2), s));
-  h->nparts = partial_blocks(h->lv[0].pts);
-  HH_TRY(dev_alloc_n(h, &h->partials, (size_t)h->nparts * B));
+  // Fused 2-D path: one-sweep down/up kernels per level above the first
+  // level with at most 63 points per axis; that level and all coarser ones
+  // run inside the single-block tail kernel.
+  h->kconst = k2_dev ? 0 : 1;
+  h->fused = 0;
+  if (dim == 2 && h->opt.nu1 == 1 && h->opt.nu2 == 1) {
+    int t0 = 1;
+    while (t0 < L && h->lv[t0].N > 63) ++t0;
+    if (t0 < L && L - t0 <= kMaxTail) {
+      h->fused = 1;
+      h->tail0 = t0;
+      for (int l = t0; l < L; ++l) {
+        const size_t np = h->lv[l].pts * (size_t)B;
+        if (!h->w64.tmp[l]) {
+          HH_TRY(dev_alloc_n(h, &h->w64.tmp[l], np));
+          HH_CK(cudaMemsetAsync(h->w64.tmp[l], 0, np * sizeof(double2), s));
+        }
+        if (!h->w32.tmp[l]) {
+          HH_TRY(dev_alloc_n(h, &h->w32.tmp[l], np));
+          HH_CK(cudaMemsetAsync(h->w32.tmp[l], 0, np * sizeof(float2), s));
+        }
+      }
+      HH_CK(init_cycle2d<float>());
+      HH_CK(init_cycle2d<double>());
+    }
+  }
+  h->parts_cap = partial_blocks(h->lv[0].pts);
+  for (int v = 0; v < kNumTileVariants; ++v)
+    h->parts_cap = std::max(h->parts_cap, tile_parts(v, h->lv[0].N));
+  HH_TRY(dev_alloc_n(h, &h->partials, (size_t)h->parts_cap * B));
   HH_TRY(dev_alloc_n(h, &h->st, (size_t)B));
   HH_TRY(dev_alloc_n(h, &h->params, 1));
   HH_TRY(dev_alloc_n(h, &h->flag, 1));
@@ -573,6 +737,8 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   HH_CK(cudaStreamSynchronize(s));
   HH_CK(cudaGetLastError());
   if (info_h[0] || info_h[1]) return fail(HH_ERR_ARG, "singular coarsest-level operator");
+  if (h->fused) HH_TRY(autotune(h, s));
+  h->nparts = h->fused ? tile_parts(h->variant[0], h->lv[0].N) : partial_blocks(h->lv[0].pts);
   return HH_OK;
 }
 
@@ -865,8 +1031,11 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
   HH_TRY(check_handle(h));
   HH_TRY(check_batch(h, batch));
   if (!ms || reps < 1) return fail(HH_ERR_ARG, "ms must not be NULL and reps >= 1");
-  if (kernel < 0 || kernel > 3) return fail(HH_ERR_ARG, "kernel must be 0..3");
+  if (kernel < 0 || kernel > 4) return fail(HH_ERR_ARG, "kernel must be 0..4");
   if (level < 0 || level + 1 >= h->L) return fail(HH_ERR_ARG, "bad level");
+  if (kernel == 4 && !h->fused) return fail(HH_ERR_ARG, "kernel 4 needs the fused 2-D path");
+  if (kernel == 1 && h->fused && level < h->tail0)
+    return fail(HH_ERR_ARG, "kernel 1 is part of kernel 0 on fused levels");
   if (kernel == 3 && (level != 0 || h->opt.precision != HH_MIXED))
     return fail(HH_ERR_ARG, "kernel 3 is the level-0 refinement of a MIXED handle");
   HH_TRY(ensure_device(h));

@@ -1,0 +1,48 @@
+// Fused cycle kernels (2-D): declarations shared by hh_cycle2d.cu and the host.
+#pragma once
+#include "hh_internal.h"
+
+namespace hh {
+
+constexpr int kNumTileVariants = 5;  // tile shapes of k_down2d / k_up2d
+constexpr int kMaxTail = 8;          // levels handled by the tail kernel
+
+// One level of the tail: operator, right-hand side, pre-smoothed iterate v,
+// scratch t, result u, and the scale c of the residual restricted from it.
+template <typename R> struct TailLevel {
+  LevelK<R> K;
+  typename Cx<R>::T *f, *v, *t, *u;
+  typename Cx<R>::T c;
+};
+
+template <typename R> struct TailArgs {
+  int nl;                  // levels in the tail (the last one is the coarsest)
+  TailLevel<R> lv[kMaxTail];
+  const double2 *lu;       // coarsest LU factors (FP64), m x m
+  const int *piv;
+  int m;
+  typename Cx<R>::T omega;
+  int nu1, nu2;
+};
+
+int tile_parts(int variant, int N);  // blocks per right-hand side of a level
+
+template <typename R> cudaError_t init_cycle2d();
+
+template <typename R>
+void launch_down2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *u_in,
+                   int zero_mode, const typename Cx<R>::T *f, typename Cx<R>::T *v_out,
+                   typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
+                   int kconst, int batch, const SolveState *st, double *partials,
+                   cudaStream_t s);
+
+template <typename R>
+void launch_up2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *v_in,
+                 const typename Cx<R>::T *e, const typename Cx<R>::T *f,
+                 typename Cx<R>::T *u_out, typename Cx<R>::T omega, int kconst, int batch,
+                 const SolveState *st, cudaStream_t s);
+
+template <typename R>
+void launch_tail2d(const TailArgs<R> &a, int batch, const SolveState *st, cudaStream_t s);
+
+}  // namespace hh
