@@ -46,5 +46,10 @@ template <typename C> __device__ __forceinline__ C cdiv(C a, C b) {
   const auto d = b.x * b.x + b.y * b.y;
   return cmk((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
+// 1 / b (one real division)
+template <typename C> __device__ __forceinline__ C crcp(C b) {
+  const auto s = decltype(b.x)(1) / (b.x * b.x + b.y * b.y);
+  return cmk(b.x * s, -b.y * s);
+}
 
 }  // namespace hh

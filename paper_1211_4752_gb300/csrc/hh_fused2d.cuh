@@ -89,7 +89,7 @@ k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
     const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
     const size_t g = (size_t)gy * N + gx;
     s_f[i] = in ? fb[g] : zc;
-    s_k[i] = in ? (kconst ? L.k2[0] : L.k2[g]) : R(0);
+    if (!kconst) s_k[i] = in ? L.k2[g] : R(0);
   }
   if (!zero) {
     for (int i = tid; i < UW * UH; i += blockDim.x) {
@@ -101,15 +101,17 @@ k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
   }
   __syncthreads();
 
+  const R kc = kconst ? L.k2[0] : R(0);
   // v = u + omega D^{-1}(f - A u) on tile + 1; norm of f - A u on the tile
-  double acc = 0.0;
+  // (accumulated per thread in R, per block in double)
+  R acc = R(0);
   C *vb = v_out + (size_t)b * pts;
   for (int i = tid; i < VW * VH; i += blockDim.x) {
     const int ty = i / VW, tx = i - ty * VW;
     const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
     C v = zc;
     if (gx >= 0 && gx < N && gy >= 0 && gy < N) {
-      const C D = csub(cadd(s_cx[VW + tx], s_cy[VH + ty]), cscale(L.beta, s_k[i]));
+      const C D = csub(cadd(s_cx[VW + tx], s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[i]));
       C r = s_f[i];
       C uc = zc;
       if (!zero) {
@@ -121,10 +123,10 @@ k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
         nb = cfma(s_cy[2 * VH + ty], s_u[j + UW], nb);
         r = cadd(csub(r, cmul(D, uc)), nb);
       }
-      v = cadd(uc, cmul(omega, cdiv(r, D)));
+      v = cadd(uc, cmul(cmul(omega, r), crcp(D)));
       if (tx >= 1 && tx <= BX && ty >= 1 && ty <= BY) {
         vb[(size_t)gy * N + gx] = v;
-        if (partials) acc += (double)r.x * r.x + (double)r.y * r.y;
+        acc += r.x * r.x + r.y * r.y;
       }
     }
     s_v[i] = v;
@@ -139,7 +141,7 @@ k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
     C r = zc;
     if (gx < N && gy < N) {
       const int j = ty * VW + tx;
-      const C D = csub(cadd(s_cx[VW + tx], s_cy[VH + ty]), cscale(L.beta, s_k[j]));
+      const C D = csub(cadd(s_cx[VW + tx], s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[j]));
       C nb = cmul(s_cx[tx], s_v[j - 1]);
       nb = cfma(s_cx[2 * VW + tx], s_v[j + 1], nb);
       nb = cfma(s_cy[ty], s_v[j - VW], nb);
@@ -166,7 +168,7 @@ k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
   }
   if (partials) {
     __shared__ double ws[32];
-    double v = acc;
+    double v = (double)acc;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((tid & 31) == 0) ws[tid >> 5] = v;
     __syncthreads();
@@ -255,6 +257,7 @@ k_up2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ v_in,
   // u' = w + omega D^{-1}(f - A w) on the tile
   const C *fb = f + (size_t)b * pts;
   C *ob = u_out + (size_t)b * pts;
+  const R kc = kconst ? L.k2[0] : R(0);
   for (int i = tid; i < BX * BY; i += blockDim.x) {
     const int ly = i / BX, lx = i - ly * BX;
     const int gx = x0 + lx, gy = y0 + ly;
@@ -262,14 +265,14 @@ k_up2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ v_in,
     const int tx = lx + 1, ty = ly + 1;
     const int j = ty * WW + tx;
     const size_t g = (size_t)gy * N + gx;
-    const R k = kconst ? L.k2[0] : L.k2[g];
+    const R k = kconst ? kc : L.k2[g];
     const C D = csub(cadd(s_cx[WW + tx], s_cy[WH + ty]), cscale(L.beta, k));
     C nb = cmul(s_cx[tx], s_w[j - 1]);
     nb = cfma(s_cx[2 * WW + tx], s_w[j + 1], nb);
     nb = cfma(s_cy[ty], s_w[j - WW], nb);
     nb = cfma(s_cy[2 * WH + ty], s_w[j + WW], nb);
     const C r = cadd(csub(fb[g], cmul(D, s_w[j])), nb);
-    ob[g] = cadd(s_w[j], cmul(omega, cdiv(r, D)));
+    ob[g] = cadd(s_w[j], cmul(cmul(omega, r), crcp(D)));
   }
 }
 
