@@ -69,6 +69,9 @@ struct LevelHost {
   float2 c32[2];
   double *k2_64 = nullptr;
   float *k2_32 = nullptr;
+  int ulo[2] = {1, 1}, uhi[2] = {0, 0};  // uniform-coefficient node range per dir
+  double2 c0_64[2];
+  float2 c0_32[2];
 };
 
 struct GraphEntry {
@@ -103,6 +106,7 @@ struct hh_handle {
   int kconst = 0;                   // k^2 constant: kernels read k2[0] only
   int variant[MAXL] = {};           // tile shape per fused level (autotuned)
   int parts_cap = 0;                // capacity of `partials` per RHS
+  unsigned int *counter = nullptr;  // arrivals of the fused stop test
   std::vector<void *> allocs;
   std::map<std::tuple<int, int, int>, GraphEntry> graphs;
 
@@ -163,11 +167,11 @@ void lap1d(int n_l, double a, double b, double gamma, std::vector<cd> &lo,
 template <typename R> LevelK<R> levelk(const hh_handle *h, int l, int dir);
 template <> LevelK<double> levelk<double>(const hh_handle *h, int l, int dir) {
   const LevelHost &v = h->lv[l];
-  return LevelK<double>{v.N, v.coef64[dir], v.beta64[dir], v.k2_64};
+  return LevelK<double>{v.N, v.coef64[dir], v.beta64[dir], v.k2_64, v.ulo[dir], v.uhi[dir], v.c0_64[dir]};
 }
 template <> LevelK<float> levelk<float>(const hh_handle *h, int l, int dir) {
   const LevelHost &v = h->lv[l];
-  return LevelK<float>{v.N, v.coef32[dir], v.beta32[dir], v.k2_32};
+  return LevelK<float>{v.N, v.coef32[dir], v.beta32[dir], v.k2_32, v.ulo[dir], v.uhi[dir], v.c0_32[dir]};
 }
 template <typename R> Work<R> &work(hh_handle *h);
 template <> Work<double> &work<double>(hh_handle *h) { return h->w64; }
@@ -247,13 +251,30 @@ template <typename R> TailArgs<R> tail_args(hh_handle *h, int dir) {
     a.lv[i].u = W.u_post[l];
     a.lv[i].c = cscal<R>(h, l, dir);
   }
+  int off = 0;
+  for (int i = 0; i < a.nl; ++i) {
+    a.off[i] = off;
+    const int N = h->lv[h->tail0 + i].N;
+    off += 3 * N * N;
+  }
+  a.smem_bytes = off * (int)sizeof(typename Cx<R>::T);
   a.lu = h->lu[dir];
   a.piv = h->piv[dir];
   a.m = h->m;
   a.omega = omega<R>(h, dir);
-  a.nu1 = h->opt.nu1;
-  a.nu2 = h->opt.nu2;
   return a;
+}
+
+template <typename R> CheckCtx check_ctx(hh_handle *h, int check, unsigned long long cond) {
+  CheckCtx c{};
+  c.mode = check == CHECK_CYCLE ? CHECK_MODE_CYCLE : CHECK_MODE_INNER;
+  c.st = h->st;
+  c.P = h->params;
+  c.partials = h->partials;
+  c.counter = h->counter;
+  c.flag = h->flag;
+  c.cond = cond;
+  return c;
 }
 
 // The same V-cycle with the fused 2-D kernels: one down pass per level
@@ -269,16 +290,12 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
   for (int l = 0; l < T; ++l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
     const bool norm = l == 0 && check != CHECK_NONE;
+    // the level-0 pass also runs the stop test in its last block
+    const CheckCtx chk = norm ? check_ctx<R>(h, check, cond) : CheckCtx{};
     launch_down2d<R>(h->variant[l], K, l == 0 ? W.u_post[0] : nullptr,
                      l == 0 ? zero0 : ZERO_ALL, W.f[l], W.u_pre[l], W.f[l + 1],
                      cscal<R>(h, l, dir), om, h->kconst, batch, st,
-                     norm ? h->partials : nullptr, s);
-    if (norm) {
-      if (check == CHECK_CYCLE)
-        launch_check_cycle(h->st, h->partials, h->params, h->flag, cond, s);
-      else
-        launch_check_inner(h->st, h->partials, h->params, h->flag, cond, s);
-    }
+                     norm ? h->partials : nullptr, chk, s);
   }
   launch_tail2d<R>(tail_args<R>(h, dir), batch, st, s);
   for (int l = T - 1; l >= 0; --l) {
@@ -449,7 +466,7 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
     if (kernel == 0)
       launch_down2d<R>(h->variant[level], K, W.u_post[level], ZERO_NONE, W.f[level],
                        W.u_pre[level], W.f[level + 1], cscal<R>(h, level, 0), om, h->kconst,
-                       batch, nullptr, level == 0 ? h->partials : nullptr, s);
+                       batch, nullptr, level == 0 ? h->partials : nullptr, CheckCtx{}, s);
     else
       launch_up2d<R>(h->variant[level], K, W.u_pre[level], W.u_post[level + 1], W.f[level],
                      W.u_post[level], om, h->kconst, batch, nullptr, s);
@@ -524,7 +541,7 @@ template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, 
   for (int v = 0; v < kNumTileVariants; ++v) {
     auto run = [&]() {
       launch_down2d<R>(v, K, W.u_post[l], ZERO_NONE, W.f[l], W.u_pre[l], W.f[l + 1],
-                       cscal<R>(h, l, 0), om, h->kconst, 1, nullptr, nullptr, s);
+                       cscal<R>(h, l, 0), om, h->kconst, 1, nullptr, nullptr, CheckCtx{}, s);
       launch_up2d<R>(v, K, W.u_pre[l], W.u_post[l + 1], W.f[l], W.u_post[l], om,
                      h->kconst, 1, nullptr, s);
     };
@@ -629,6 +646,27 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
         }
       }
     }
+    // uniform-coefficient node range (identical for every axis): the maximal
+    // run around the middle node with lo = up = c0 and dg = 2 c0 exactly
+    for (int dir = 0; dir < 2; ++dir) {
+      const double2 *T = t64[dir].data();
+      auto same = [](double2 a, double2 b) { return a.x == b.x && a.y == b.y; };
+      const int mid = N / 2;
+      const double2 c0 = T[mid];
+      auto uni = [&](int i) {
+        const double2 d = T[N + i];
+        return same(T[i], c0) && same(T[2 * N + i], c0) && d.x == 2.0 * c0.x && d.y == 2.0 * c0.y;
+      };
+      if (uni(mid)) {
+        int lo = mid, hi = mid;
+        while (lo - 1 >= 0 && uni(lo - 1)) --lo;
+        while (hi + 1 < N && uni(hi + 1)) ++hi;
+        v.ulo[dir] = lo;
+        v.uhi[dir] = hi;
+      }
+      v.c0_64[dir] = c0;
+      v.c0_32[dir] = make_float2((float)c0.x, (float)c0.y);
+    }
     for (int dir = 0; dir < 2; ++dir) {
       HH_TRY(dev_alloc_n(h, &v.coef64[dir], t64[dir].size()));
       HH_TRY(dev_alloc_n(h, &v.coef32[dir], t32[dir].size()));
@@ -691,8 +729,15 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   h->kconst = k2_dev ? 0 : 1;
   h->fused = 0;
   if (dim == 2 && h->opt.nu1 == 1 && h->opt.nu2 == 1) {
+    // first level whose tail (it and every coarser level) fits in shared memory
     int t0 = 1;
-    while (t0 < L && h->lv[t0].N > 63) ++t0;
+    auto tail_bytes = [&](int t) {
+      int Ns[MAXL];
+      for (int l = t; l < L; ++l) Ns[l - t] = h->lv[l].N;
+      return h->opt.precision == HH_FP64 ? tail_smem_bytes<double>(Ns, L - t)
+                                         : tail_smem_bytes<float>(Ns, L - t);
+    };
+    while (t0 < L && (h->lv[t0].N > 63 || tail_bytes(t0) > kTailSmemMax)) ++t0;
     if (t0 < L && L - t0 <= kMaxTail) {
       h->fused = 1;
       h->tail0 = t0;
@@ -715,6 +760,8 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   for (int v = 0; v < kNumTileVariants; ++v)
     h->parts_cap = std::max(h->parts_cap, tile_parts(v, h->lv[0].N));
   HH_TRY(dev_alloc_n(h, &h->partials, (size_t)h->parts_cap * B));
+  HH_TRY(dev_alloc_n(h, &h->counter, 1));
+  HH_CK(cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), s));
   HH_TRY(dev_alloc_n(h, &h->st, (size_t)B));
   HH_TRY(dev_alloc_n(h, &h->params, 1));
   HH_TRY(dev_alloc_n(h, &h->flag, 1));

@@ -1,6 +1,7 @@
 // Fused cycle kernels (2-D): declarations shared by hh_cycle2d.cu and the host.
 #pragma once
 #include "hh_internal.h"
+#include "hh_check.cuh"
 
 namespace hh {
 
@@ -18,12 +19,22 @@ template <typename R> struct TailLevel {
 template <typename R> struct TailArgs {
   int nl;                  // levels in the tail (the last one is the coarsest)
   TailLevel<R> lv[kMaxTail];
+  int off[kMaxTail];       // shared-memory offset (elements) of each level's
+                           // f, v, t arrays (3 N^2 elements per level)
+  int smem_bytes;
   const double2 *lu;       // coarsest LU factors (FP64), m x m
   const int *piv;
   int m;
   typename Cx<R>::T omega;
-  int nu1, nu2;
 };
+
+// Shared memory the tail kernel needs for levels of N_0 > N_1 > ... points.
+template <typename R> size_t tail_smem_bytes(const int *N, int nl) {
+  size_t e = 0;
+  for (int i = 0; i < nl; ++i) e += 3 * (size_t)N[i] * N[i];
+  return e * sizeof(typename Cx<R>::T);
+}
+constexpr size_t kTailSmemMax = 200 * 1024;
 
 int tile_parts(int variant, int N);  // blocks per right-hand side of a level
 
@@ -34,7 +45,7 @@ void launch_down2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *u_i
                    int zero_mode, const typename Cx<R>::T *f, typename Cx<R>::T *v_out,
                    typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
                    int kconst, int batch, const SolveState *st, double *partials,
-                   cudaStream_t s);
+                   const CheckCtx &chk, cudaStream_t s);
 
 template <typename R>
 void launch_up2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *v_in,

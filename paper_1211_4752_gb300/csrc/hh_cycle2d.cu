@@ -18,10 +18,10 @@ void down_one(const LevelK<R> &L, const typename Cx<R>::T *u_in, int zero_mode,
               const typename Cx<R>::T *f, typename Cx<R>::T *v_out,
               typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
               int kconst, int batch, const SolveState *st, double *partials,
-              cudaStream_t s) {
+              const CheckCtx &chk, cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
   k_down2d<R, BX, BY><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
-      L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, st, partials);
+      L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, st, partials, chk);
 }
 
 template <typename R, int BX, int BY>
@@ -44,19 +44,41 @@ template <typename R, int BX, int BY> cudaError_t attr_one() {
 }
 
 // ---------------------------------------------------------------------------
-// Tail: all levels of TailArgs in one block per right-hand side, 1024
-// threads, phases separated by __syncthreads (global memory, L1/L2 resident).
+// Tail: every level of TailArgs inside one block of 1024 threads per
+// right-hand side, all arrays in shared memory (one V(1,1) cycle from the
+// first tail level down to the coarsest LU and back), phases separated by
+// __syncthreads.  Only the top level's right-hand side (in) and correction
+// (out) touch global memory.
 // ---------------------------------------------------------------------------
+
+// Row-major walk over an N x N level with runtime N.
+struct WalkN {
+  int x, y, dx, dy, N;
+  __device__ __forceinline__ WalkN(int tid, int nt, int n)
+      : x(tid % n), y(tid / n), dx(nt % n), dy(nt / n), N(n) {}
+  __device__ __forceinline__ void next() {
+    x += dx;
+    y += dy;
+    if (x >= N) { x -= N; ++y; }
+  }
+};
+
+// A w at (x, y) on an N x N shared-memory array (zero outside), general
+// coefficients from the level tables.
 template <typename R>
-__device__ __forceinline__ typename Cx<R>::T jac_at(const LevelK<R> &K, const typename Cx<R>::T *in,
-                                                    const typename Cx<R>::T *f, int x, int y,
-                                                    size_t p, typename Cx<R>::T om) {
+__device__ __forceinline__ typename Cx<R>::T apply_s(const LevelK<R> &K, const typename Cx<R>::T *w,
+                                                     int x, int y, typename Cx<R>::T &D) {
   using C = typename Cx<R>::T;
   const int N = K.N;
-  auto get = [&](int xx, int yy, int) { return in[(size_t)yy * N + xx]; };
-  C Au, D, uc;
-  stencil<R, 2>(K, x, y, 0, p, get, Au, D, uc);
-  return cadd(uc, cmul(om, cdiv(csub(f[p], Au), D)));
+  const C *c = K.coef;
+  const int j = y * N + x;
+  C nb = czero<C>();
+  if (x > 0) nb = cfma(c[x], w[j - 1], nb);
+  if (x < N - 1) nb = cfma(c[2 * N + x], w[j + 1], nb);
+  if (y > 0) nb = cfma(c[3 * N + y], w[j - N], nb);
+  if (y < N - 1) nb = cfma(c[5 * N + y], w[j + N], nb);
+  D = csub(cadd(c[N + x], c[4 * N + y]), cscale(K.beta, K.k2[j]));
+  return csub(cmul(D, w[j]), nb);
 }
 
 template <typename R>
@@ -64,93 +86,101 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
   using C = typename Cx<R>::T;
   const int b = blockIdx.x;
   if (st && !st[b].active) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *sm = reinterpret_cast<C *>(smem_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
   const C om = A.omega;
-  C *vbuf[kMaxTail];
-  for (int l = 0; l + 1 < A.nl; ++l) {
-    const TailLevel<R> &T = A.lv[l];
-    const LevelK<R> &K = T.K;
-    const int N = K.N;
-    const size_t pts = (size_t)N * N;
-    const C *f = T.f + b * pts;
-    C *v = T.v + b * pts, *t = T.t + b * pts;
-    const C *cur = nullptr;
-    for (int j = 0; j < A.nu1; ++j) {
-      C *out = ((A.nu1 - 1 - j) % 2 == 0) ? v : t;
-      for (size_t p = tid; p < pts; p += nt) {
-        const int x = (int)(p % N), y = (int)(p / N);
-        if (j == 0) out[p] = cmul(om, cdiv(f[p], diag_at<R, 2>(K, x, y, 0, p)));
-        else out[p] = jac_at<R>(K, cur, f, x, y, p, om);
-      }
-      __syncthreads();
-      cur = out;
-    }
-    vbuf[l] = v;
-    for (size_t p = tid; p < pts; p += nt) {
-      const int x = (int)(p % N), y = (int)(p / N);
-      auto get = [&](int xx, int yy, int) { return v[(size_t)yy * N + xx]; };
-      C Au, D, uc;
-      stencil<R, 2>(K, x, y, 0, p, get, Au, D, uc);
-      t[p] = csub(f[p], Au);
-    }
-    __syncthreads();
-    const int Nc = (N + 1) / 2 - 1;
-    C *fc = A.lv[l + 1].f + b * (size_t)Nc * Nc;
-    for (int pc = tid; pc < Nc * Nc; pc += nt) {
-      const int cx = pc % Nc, cy = pc / Nc;
-      const int j = (2 * cy + 1) * N + 2 * cx + 1;
-      C a = cscale(t[j], R(4));
-      a = cadd(a, cscale(cadd(cadd(t[j - 1], t[j + 1]), cadd(t[j - N], t[j + N])), R(2)));
-      a = cadd(a, cadd(cadd(t[j - N - 1], t[j - N + 1]), cadd(t[j + N - 1], t[j + N + 1])));
-      fc[pc] = cmul(T.c, cscale(a, R(1.0 / 16.0)));
-    }
-    __syncthreads();
-  }
-  // coarsest level: forward/back substitution with the FP64 LU factors
+  // top level right-hand side into shared memory
   {
-    const TailLevel<R> &T = A.lv[A.nl - 1];
-    const int m = A.m;
-    if (tid == 0) {
-      double2 y[27];
-      const C *fb = T.f + (size_t)b * m;
-      for (int i = 0; i < m; ++i) {
-        const C v = fb[A.piv[i]];
-        y[i] = make_double2((double)v.x, (double)v.y);
+    const int N = A.lv[0].K.N;
+    const C *g = A.lv[0].f + (size_t)b * N * N;
+    C *f = sm + A.off[0];
+    for (int p = tid; p < N * N; p += nt) f[p] = g[p];
+  }
+  __syncthreads();
+  for (int l = 0; l + 1 < A.nl; ++l) {
+    const LevelK<R> &K = A.lv[l].K;
+    const int N = K.N, Nc = (N + 1) / 2 - 1;
+    C *f = sm + A.off[l], *v = f + N * N, *t = v + N * N;
+    // pre-smoothing from the zero initial guess: v = omega D^{-1} f
+    {
+      WalkN w(tid, nt, N);
+      for (int p = tid; p < N * N; p += nt, w.next()) {
+        const C D = csub(cadd(K.coef[N + w.x], K.coef[4 * N + w.y]), cscale(K.beta, K.k2[p]));
+        v[p] = cmul(cmul(om, f[p]), crcp(D));
       }
-      for (int i = 0; i < m; ++i)
-        for (int j = 0; j < i; ++j) y[i] = csub(y[i], cmul(A.lu[i * m + j], y[j]));
-      for (int i = m - 1; i >= 0; --i) {
-        for (int j = i + 1; j < m; ++j) y[i] = csub(y[i], cmul(A.lu[i * m + j], y[j]));
-        y[i] = cdiv(y[i], A.lu[i * m + i]);
+    }
+    __syncthreads();
+    {
+      WalkN w(tid, nt, N);
+      for (int p = tid; p < N * N; p += nt, w.next()) {
+        C D;
+        t[p] = csub(f[p], apply_s<R>(K, v, w.x, w.y, D));
       }
-      C *ub = T.u + (size_t)b * m;
-      for (int i = 0; i < m; ++i) ub[i] = cmk((R)y[i].x, (R)y[i].y);
+    }
+    __syncthreads();
+    {
+      C *fc = sm + A.off[l + 1];
+      const C csc = cscale(A.lv[l].c, R(1.0 / 16.0));
+      WalkN w(tid, nt, Nc);
+      for (int pc = tid; pc < Nc * Nc; pc += nt, w.next()) {
+        const int j = (2 * w.y + 1) * N + 2 * w.x + 1;
+        C a = cscale(t[j], R(4));
+        a = cadd(a, cscale(cadd(cadd(t[j - 1], t[j + 1]), cadd(t[j - N], t[j + N])), R(2)));
+        a = cadd(a, cadd(cadd(t[j - N - 1], t[j - N + 1]), cadd(t[j + N - 1], t[j + N + 1])));
+        fc[pc] = cmul(csc, a);
+      }
     }
     __syncthreads();
   }
+  // coarsest level: LU substitution (FP64) by one warp, lane i owning row i
+  if (tid < 32) {
+    const int m = A.m, i = tid;
+    const C *fl = sm + A.off[A.nl - 1];
+    C *ul = const_cast<C *>(fl) + m;       // the level's v slot holds the solution
+    double2 y = make_double2(0.0, 0.0);
+    if (i < m) {
+      const C q = fl[A.piv[i]];
+      y = make_double2((double)q.x, (double)q.y);
+    }
+    for (int k = 0; k < m; ++k) {            // forward, unit lower triangle
+      const double2 yk = make_double2(__shfl_sync(0xffffffffu, y.x, k), __shfl_sync(0xffffffffu, y.y, k));
+      if (i > k && i < m) y = csub(y, cmul(A.lu[i * m + k], yk));
+    }
+    for (int k = m - 1; k >= 0; --k) {       // backward
+      if (i == k) y = cdiv(y, A.lu[k * m + k]);
+      const double2 yk = make_double2(__shfl_sync(0xffffffffu, y.x, k), __shfl_sync(0xffffffffu, y.y, k));
+      if (i < k) y = csub(y, cmul(A.lu[i * m + k], yk));
+    }
+    if (i < m) ul[i] = cmk((R)y.x, (R)y.y);
+  }
+  __syncthreads();
   for (int l = A.nl - 2; l >= 0; --l) {
-    const TailLevel<R> &T = A.lv[l];
-    const LevelK<R> &K = T.K;
+    const LevelK<R> &K = A.lv[l].K;
     const int N = K.N, Nc = (N + 1) / 2 - 1;
-    const size_t pts = (size_t)N * N;
-    const C *f = T.f + b * pts;
-    C *v = vbuf[l], *t = T.t + b * pts, *u = T.u + b * pts;
-    const C *e = A.lv[l + 1].u + b * (size_t)Nc * Nc;
-    for (size_t p = tid; p < pts; p += nt) {
-      const int x = (int)(p % N), y = (int)(p / N);
-      t[p] = cadd(v[p], prolong_at<R, 2>(e, Nc, x, y, 0));
+    C *f = sm + A.off[l], *v = f + N * N, *t = v + N * N;
+    const C *e = sm + A.off[l + 1] + Nc * Nc;   // coarse v slot: its correction
+    {
+      WalkN w(tid, nt, N);
+      for (int p = tid; p < N * N; p += nt, w.next())
+        t[p] = cadd(v[p], prolong_at<R, 2>(e, Nc, w.x, w.y, 0));
     }
     __syncthreads();
-    const C *cur = t;
-    for (int j = 0; j < A.nu2; ++j) {
-      C *out = ((A.nu2 - 1 - j) % 2 == 0) ? u : v;
-      for (size_t p = tid; p < pts; p += nt) {
-        const int x = (int)(p % N), y = (int)(p / N);
-        out[p] = jac_at<R>(K, cur, f, x, y, p, om);
+    {
+      WalkN w(tid, nt, N);
+      for (int p = tid; p < N * N; p += nt, w.next()) {
+        C D;
+        const C Aw = apply_s<R>(K, t, w.x, w.y, D);
+        v[p] = cadd(t[p], cmul(cmul(om, csub(f[p], Aw)), crcp(D)));
       }
-      __syncthreads();
-      cur = out;
     }
+    __syncthreads();
+  }
+  {
+    const int N = A.lv[0].K.N;
+    C *g = A.lv[0].u + (size_t)b * N * N;
+    const C *v = sm + A.off[0] + N * N;
+    for (int p = tid; p < N * N; p += nt) g[p] = v[p];
   }
 }
 
@@ -168,7 +198,9 @@ cudaError_t init_cycle2d() {
   if ((e = attr_one<R, 32, 16>()) != cudaSuccess) return e;
   if ((e = attr_one<R, 64, 8>()) != cudaSuccess) return e;
   if ((e = attr_one<R, 32, 8>()) != cudaSuccess) return e;
-  return attr_one<R, 128, 8>();
+  if ((e = attr_one<R, 128, 8>()) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_tail2d<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kTailSmemMax);
 }
 
 template <typename R>
@@ -176,13 +208,13 @@ void launch_down2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *u_i
                    int zero_mode, const typename Cx<R>::T *f, typename Cx<R>::T *v_out,
                    typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
                    int kconst, int batch, const SolveState *st, double *partials,
-                   cudaStream_t s) {
+                   const CheckCtx &chk, cudaStream_t s) {
   switch (variant) {
-    case 0: down_one<R, 64, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, s); break;
-    case 1: down_one<R, 32, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, s); break;
-    case 2: down_one<R, 64, 8>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, s); break;
-    case 3: down_one<R, 32, 8>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, s); break;
-    default: down_one<R, 128, 8>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, s); break;
+    case 0: down_one<R, 64, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
+    case 1: down_one<R, 32, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
+    case 2: down_one<R, 64, 8>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
+    case 3: down_one<R, 32, 8>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
+    default: down_one<R, 128, 8>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
   }
 }
 
@@ -202,7 +234,7 @@ void launch_up2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *v_in,
 
 template <typename R>
 void launch_tail2d(const TailArgs<R> &a, int batch, const SolveState *st, cudaStream_t s) {
-  k_tail2d<R><<<batch, 1024, 0, s>>>(a, st);
+  k_tail2d<R><<<batch, 1024, a.smem_bytes, s>>>(a, st);
 }
 
 #define HH_INST_CYCLE2D(R)                                                                  \
@@ -210,7 +242,7 @@ void launch_tail2d(const TailArgs<R> &a, int batch, const SolveState *st, cudaSt
   template void launch_down2d<R>(int, const LevelK<R> &, const Cx<R>::T *, int,             \
                                  const Cx<R>::T *, Cx<R>::T *, Cx<R>::T *, Cx<R>::T,        \
                                  Cx<R>::T, int, int, const SolveState *, double *,          \
-                                 cudaStream_t);                                             \
+                                 const CheckCtx &, cudaStream_t);                           \
   template void launch_up2d<R>(int, const LevelK<R> &, const Cx<R>::T *, const Cx<R>::T *,  \
                                const Cx<R>::T *, Cx<R>::T *, Cx<R>::T, int, int,            \
                                const SolveState *, cudaStream_t);                           \

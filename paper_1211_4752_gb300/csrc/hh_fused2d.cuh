@@ -3,26 +3,34 @@
 // k_down2d: one pass per level on the way down:
 //     v  = u + omega D^{-1} (f - A u)         (pre-smoothing, Eq. (wjacobi))
 //     fc = c * FW(f - A v)                    (residual + full weighting)
-//   plus per-block sums of |f - A u|^2 (the stop test of the cycle loop).
+//   plus per-block sums of |f - A u|^2; on level 0 the last block to finish
+//   adds them in a fixed order and runs the stop test of the cycle loop.
 // k_up2d: one pass per level on the way up:
 //     w  = v + P e ;  u' = w + omega D^{-1} (f - A w)
 //
 // A block owns a BX x BY tile of fine points (x0, y0 even) and the BX/2 x BY/2
 // coarse points whose fine positions (2c+1) fall inside it.  Halos are
 // recomputed instead of exchanged: k_down2d stages u on the tile + 2, computes
-// v on the tile + 1 and the residual on the tile + 1 (high side), so every
+// v on the tile + 1 and the residual on [x0, x0+BX] x [y0, y0+BY], so every
 // value it needs is produced inside the block.  Points outside the domain hold
 // zero (homogeneous Dirichlet) at every stage.
+//
+// Specialisations (block-uniform, chosen at run time):
+//   CHECK: the tile (+ halo) touches the domain boundary -> bounds tests;
+//   FAST : the tile (+ halo) lies where the level's coefficients are uniform
+//          (lo = up = c0, dg = 2 c0 on both axes, i.e. outside ECS layers),
+//          so A u = 4 c0 u - c0 (sum of the 4 neighbours) - beta k2 u.
 #pragma once
 #include "hh_internal.h"
 #include "hh_complex.cuh"
+#include "hh_check.cuh"
 
 namespace hh {
 
 template <typename R, int BX, int BY> struct Down2D {
   using C = typename Cx<R>::T;
   static constexpr int UW = BX + 5, UH = BY + 5;  // u staged on tile + 2
-  static constexpr int VW = BX + 3, VH = BY + 3;  // v (and f, k2) on tile + 1
+  static constexpr int VW = BX + 3, VH = BY + 3;  // v, f, k2 on tile + 1
   static constexpr int RW = BX + 1, RH = BY + 1;  // residual on [x0, x0+BX]
   static constexpr size_t smem =
       sizeof(C) * (size_t)UW * UH +      // s_u, later the residual
@@ -39,145 +47,334 @@ template <typename R, int BX, int BY> struct Up2D {
                                  sizeof(C) * 3 * (size_t)(WW + WH);
 };
 
+// Iterate (x, y) over a W x H region with blockDim.x threads, row-major,
+// without a division per step.
+template <int W> struct Walk {
+  int x, y;
+  __device__ __forceinline__ Walk(int tid) : x(tid % W), y(tid / W) {}
+  __device__ __forceinline__ void next(int stride) {
+    x += stride % W;
+    y += stride / W;
+    if (x >= W) { x -= W; ++y; }
+  }
+};
+
+template <typename R>
+__device__ __forceinline__ bool tile_in(const LevelK<R> &L, int lo, int hi, int N, bool uniform) {
+  // [lo, hi] inside the domain, and (uniform) inside the uniform range
+  return lo >= 0 && hi < N && (!uniform || (lo >= L.ulo && hi <= L.uhi));
+}
+
+template <typename R, int BX, int BY, bool CHECK, bool FAST>
+__device__ __forceinline__ void down_body(
+    const LevelK<R> &L, const typename Cx<R>::T *__restrict__ ub, bool zero,
+    const typename Cx<R>::T *__restrict__ fb, typename Cx<R>::T *__restrict__ vb,
+    typename Cx<R>::T *__restrict__ fcb, typename Cx<R>::T cs, typename Cx<R>::T omega,
+    int kconst, int x0, int y0, unsigned char *smem_raw, R &acc) {
+  using C = typename Cx<R>::T;
+  using S = Down2D<R, BX, BY>;
+  constexpr int UW = S::UW, UH = S::UH, VW = S::VW, VH = S::VH, RW = S::RW, RH = S::RH;
+  constexpr int NT = 256;
+  C *s_u = reinterpret_cast<C *>(smem_raw);
+  C *s_v = s_u + UW * UH;
+  C *s_f = s_v + VW * VH;
+  C *s_cx = s_f + VW * VH;     // [3][VW]: lo, dg, up of columns x0-1 .. x0+BX+1
+  C *s_cy = s_cx + 3 * VW;     // [3][VH]
+  R *s_k = reinterpret_cast<R *>(s_cy + 3 * VH);
+  C *s_r = s_u;                // the residual reuses the staging of u
+  const int N = L.N, Nc = (N + 1) / 2 - 1;
+  const int tid = threadIdx.x;
+  const C zc = czero<C>();
+  const R kc = kconst ? L.k2[0] : R(0);
+
+  if (!FAST) {
+    for (int i = tid; i < VW; i += NT) {
+      const int gx = x0 - 1 + i;
+      const bool in = !CHECK || (gx >= 0 && gx < N);
+      s_cx[i] = in ? L.coef[gx] : zc;
+      s_cx[VW + i] = in ? L.coef[N + gx] : zc;
+      s_cx[2 * VW + i] = in ? L.coef[2 * N + gx] : zc;
+    }
+    for (int i = tid; i < VH; i += NT) {
+      const int gy = y0 - 1 + i;
+      const bool in = !CHECK || (gy >= 0 && gy < N);
+      s_cy[i] = in ? L.coef[3 * N + gy] : zc;
+      s_cy[VH + i] = in ? L.coef[4 * N + gy] : zc;
+      s_cy[2 * VH + i] = in ? L.coef[5 * N + gy] : zc;
+    }
+  }
+  {
+    const C *fo = fb + (y0 - 1) * N + (x0 - 1);
+    const R *ko = L.k2 + (y0 - 1) * N + (x0 - 1);
+    Walk<VW> w(tid);
+    for (int i = tid; i < VW * VH; i += NT, w.next(NT)) {
+      bool in = true;
+      if (CHECK) {
+        const int gx = x0 - 1 + w.x, gy = y0 - 1 + w.y;
+        in = gx >= 0 && gx < N && gy >= 0 && gy < N;
+      }
+      const int o = w.y * N + w.x;
+      s_f[i] = in ? fo[o] : zc;
+      if (!kconst) s_k[i] = in ? ko[o] : R(0);
+    }
+  }
+  if (!zero) {
+    const C *uo = ub + (y0 - 2) * N + (x0 - 2);
+    Walk<UW> w(tid);
+    for (int i = tid; i < UW * UH; i += NT, w.next(NT)) {
+      bool in = true;
+      if (CHECK) {
+        const int gx = x0 - 2 + w.x, gy = y0 - 2 + w.y;
+        in = gx >= 0 && gx < N && gy >= 0 && gy < N;
+      }
+      s_u[i] = in ? uo[w.y * N + w.x] : zc;
+    }
+  }
+  __syncthreads();
+
+  // uniform-coefficient constants (FAST): nb = c0 * (sum of neighbours),
+  // D = 4 c0 - beta k2
+  const C c0 = FAST ? L.c0 : zc;
+  const C d0 = FAST ? cscale(c0, R(4)) : zc;
+  const C Dk = FAST ? csub(d0, cscale(L.beta, kc)) : zc;
+  const C Dkinv = FAST ? crcp(Dk) : zc;
+
+  // v = u + omega D^{-1}(f - A u) on tile + 1; |f - A u|^2 on the tile
+  {
+    C *vo = vb + (y0 - 1) * N + (x0 - 1);
+    Walk<VW> w(tid);
+    for (int i = tid; i < VW * VH; i += NT, w.next(NT)) {
+      const int tx = w.x, ty = w.y;
+      bool in = true;
+      if (CHECK) {
+        const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
+        in = gx >= 0 && gx < N && gy >= 0 && gy < N;
+      }
+      C v = zc;
+      if (in) {
+        C D, Dinv;
+        if (FAST) {
+          if (kconst) { D = Dk; Dinv = Dkinv; }
+          else { D = csub(d0, cscale(L.beta, s_k[i])); Dinv = crcp(D); }
+        } else {
+          D = csub(cadd(s_cx[VW + tx], s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[i]));
+          Dinv = crcp(D);
+        }
+        C r = s_f[i];
+        C uc = zc;
+        if (!zero) {
+          const int j = (ty + 1) * UW + tx + 1;
+          uc = s_u[j];
+          C nb;
+          if (FAST) {
+            nb = cmul(c0, cadd(cadd(s_u[j - 1], s_u[j + 1]), cadd(s_u[j - UW], s_u[j + UW])));
+          } else {
+            nb = cmul(s_cx[tx], s_u[j - 1]);
+            nb = cfma(s_cx[2 * VW + tx], s_u[j + 1], nb);
+            nb = cfma(s_cy[ty], s_u[j - UW], nb);
+            nb = cfma(s_cy[2 * VH + ty], s_u[j + UW], nb);
+          }
+          r = cadd(csub(r, cmul(D, uc)), nb);
+        }
+        v = cadd(uc, cmul(cmul(omega, r), Dinv));
+        if (tx >= 1 && tx <= BX && ty >= 1 && ty <= BY) {
+          vo[ty * N + tx] = v;
+          acc += r.x * r.x + r.y * r.y;
+        }
+      }
+      s_v[i] = v;
+    }
+  }
+  __syncthreads();
+
+  // residual f - A v on [x0, x0+BX] x [y0, y0+BY]
+  {
+    Walk<RW> w(tid);
+    for (int i = tid; i < RW * RH; i += NT, w.next(NT)) {
+      const int tx = w.x + 1, ty = w.y + 1;    // position in the v tile
+      C r = zc;
+      if (!CHECK || (x0 + w.x < N && y0 + w.y < N)) {
+        const int j = ty * VW + tx;
+        C D, nb;
+        if (FAST) {
+          D = kconst ? Dk : csub(d0, cscale(L.beta, s_k[j]));
+          nb = cmul(c0, cadd(cadd(s_v[j - 1], s_v[j + 1]), cadd(s_v[j - VW], s_v[j + VW])));
+        } else {
+          D = csub(cadd(s_cx[VW + tx], s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[j]));
+          nb = cmul(s_cx[tx], s_v[j - 1]);
+          nb = cfma(s_cx[2 * VW + tx], s_v[j + 1], nb);
+          nb = cfma(s_cy[ty], s_v[j - VW], nb);
+          nb = cfma(s_cy[2 * VH + ty], s_v[j + VW], nb);
+        }
+        r = cadd(csub(s_f[j], cmul(D, s_v[j])), nb);
+      }
+      s_r[i] = r;
+    }
+  }
+  __syncthreads();
+
+  // fc = c * FW(r) on the coarse points of this tile
+  constexpr int CW = BX / 2, CH = BY / 2;
+  const C csc = cscale(cs, R(1.0 / 16.0));
+  C *fco = fcb + (y0 / 2) * Nc + x0 / 2;
+  Walk<CW> w(tid);
+  for (int i = tid; i < CW * CH; i += NT, w.next(NT)) {
+    const int cxl = w.x, cyl = w.y;
+    if (!CHECK || (x0 / 2 + cxl < Nc && y0 / 2 + cyl < Nc)) {
+      const int j = (2 * cyl + 1) * RW + 2 * cxl + 1;   // centre (2c+1) in s_r
+      C a = cscale(s_r[j], R(4));
+      a = cadd(a, cscale(cadd(cadd(s_r[j - 1], s_r[j + 1]), cadd(s_r[j - RW], s_r[j + RW])), R(2)));
+      a = cadd(a, cadd(cadd(s_r[j - RW - 1], s_r[j - RW + 1]), cadd(s_r[j + RW - 1], s_r[j + RW + 1])));
+      fco[cyl * Nc + cxl] = cmul(csc, a);
+    }
+  }
+}
+
 template <typename R, int BX, int BY>
 __global__ void __launch_bounds__(256)
 k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
          const typename Cx<R>::T *__restrict__ f, typename Cx<R>::T *__restrict__ v_out,
          typename Cx<R>::T *__restrict__ fc, typename Cx<R>::T cs,
          typename Cx<R>::T omega, int kconst, const SolveState *__restrict__ st,
-         double *__restrict__ partials) {
+         double *__restrict__ partials, CheckCtx chk) {
   using C = typename Cx<R>::T;
-  using S = Down2D<R, BX, BY>;
-  constexpr int UW = S::UW, UH = S::UH, VW = S::VW, VH = S::VH, RW = S::RW, RH = S::RH;
   const int b = blockIdx.z;
-  if (st && !st[b].active) return;
+  // blocks of a finished right-hand side skip the work but still take part
+  // in the arrival count of the stop test
+  const bool act = !(st && !st[b].active);
+  if (!act && !(partials && chk.mode != CHECK_MODE_NONE)) return;
   const bool zero = zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *s_u = reinterpret_cast<C *>(smem_raw);
-  C *s_v = s_u + UW * UH;
-  C *s_f = s_v + VW * VH;
-  C *s_cx = s_f + VW * VH;     // [3][VW]: lo, dg, up of the columns x0-1 ..
-  C *s_cy = s_cx + 3 * VW;     // [3][VH]
-  R *s_k = reinterpret_cast<R *>(s_cy + 3 * VH);
-  C *s_r = s_u;                // the residual reuses the staging of u
   const int N = L.N, Nc = (N + 1) / 2 - 1;
   const size_t pts = (size_t)N * N;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
   const C *ub = u_in + (size_t)b * pts;
   const C *fb = f + (size_t)b * pts;
-  const int tid = threadIdx.x;
-  const C zc = czero<C>();
-
-  // stage: coefficient tables, f and k2 on tile + 1, u on tile + 2
-  for (int i = tid; i < VW; i += blockDim.x) {
-    const int gx = x0 - 1 + i;
-    const bool in = gx >= 0 && gx < N;
-    s_cx[i] = in ? L.coef[gx] : zc;
-    s_cx[VW + i] = in ? L.coef[N + gx] : zc;
-    s_cx[2 * VW + i] = in ? L.coef[2 * N + gx] : zc;
-  }
-  for (int i = tid; i < VH; i += blockDim.x) {
-    const int gy = y0 - 1 + i;
-    const bool in = gy >= 0 && gy < N;
-    s_cy[i] = in ? L.coef[3 * N + gy] : zc;
-    s_cy[VH + i] = in ? L.coef[4 * N + gy] : zc;
-    s_cy[2 * VH + i] = in ? L.coef[5 * N + gy] : zc;
-  }
-  for (int i = tid; i < VW * VH; i += blockDim.x) {
-    const int ty = i / VW, tx = i - ty * VW;
-    const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
-    const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
-    const size_t g = (size_t)gy * N + gx;
-    s_f[i] = in ? fb[g] : zc;
-    if (!kconst) s_k[i] = in ? L.k2[g] : R(0);
-  }
-  if (!zero) {
-    for (int i = tid; i < UW * UH; i += blockDim.x) {
-      const int ty = i / UW, tx = i - ty * UW;
-      const int gx = x0 - 2 + tx, gy = y0 - 2 + ty;
-      const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
-      s_u[i] = in ? ub[(size_t)gy * N + gx] : zc;
-    }
-  }
-  __syncthreads();
-
-  const R kc = kconst ? L.k2[0] : R(0);
-  // v = u + omega D^{-1}(f - A u) on tile + 1; norm of f - A u on the tile
-  // (accumulated per thread in R, per block in double)
-  R acc = R(0);
   C *vb = v_out + (size_t)b * pts;
-  for (int i = tid; i < VW * VH; i += blockDim.x) {
-    const int ty = i / VW, tx = i - ty * VW;
-    const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
-    C v = zc;
-    if (gx >= 0 && gx < N && gy >= 0 && gy < N) {
-      const C D = csub(cadd(s_cx[VW + tx], s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[i]));
-      C r = s_f[i];
-      C uc = zc;
-      if (!zero) {
-        const int j = (ty + 1) * UW + tx + 1;
-        uc = s_u[j];
-        C nb = cmul(s_cx[tx], s_u[j - 1]);
-        nb = cfma(s_cx[2 * VW + tx], s_u[j + 1], nb);
-        nb = cfma(s_cy[ty], s_u[j - UW], nb);
-        nb = cfma(s_cy[2 * VH + ty], s_u[j + UW], nb);
-        r = cadd(csub(r, cmul(D, uc)), nb);
-      }
-      v = cadd(uc, cmul(cmul(omega, r), crcp(D)));
-      if (tx >= 1 && tx <= BX && ty >= 1 && ty <= BY) {
-        vb[(size_t)gy * N + gx] = v;
-        acc += r.x * r.x + r.y * r.y;
-      }
-    }
-    s_v[i] = v;
-  }
-  __syncthreads();
-
-  // residual f - A v on [x0, x0+BX] x [y0, y0+BY]
-  for (int i = tid; i < RW * RH; i += blockDim.x) {
-    const int ry = i / RW, rx = i - ry * RW;
-    const int tx = rx + 1, ty = ry + 1;        // position in the v tile
-    const int gx = x0 + rx, gy = y0 + ry;
-    C r = zc;
-    if (gx < N && gy < N) {
-      const int j = ty * VW + tx;
-      const C D = csub(cadd(s_cx[VW + tx], s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[j]));
-      C nb = cmul(s_cx[tx], s_v[j - 1]);
-      nb = cfma(s_cx[2 * VW + tx], s_v[j + 1], nb);
-      nb = cfma(s_cy[ty], s_v[j - VW], nb);
-      nb = cfma(s_cy[2 * VH + ty], s_v[j + VW], nb);
-      r = cadd(csub(s_f[j], cmul(D, s_v[j])), nb);
-    }
-    s_r[i] = r;
-  }
-  __syncthreads();
-
-  // fc = c * FW(r) on the coarse points of this tile
-  constexpr int CW = BX / 2, CH = BY / 2;
   C *fcb = fc + (size_t)b * Nc * Nc;
-  for (int i = tid; i < CW * CH; i += blockDim.x) {
-    const int cyl = i / CW, cxl = i - cyl * CW;
-    const int cx = x0 / 2 + cxl, cy = y0 / 2 + cyl;
-    if (cx < Nc && cy < Nc) {
-      const int j = (2 * cyl + 1) * RW + 2 * cxl + 1;   // centre (2c+1) in s_r
-      C a = cscale(s_r[j], R(4));
-      a = cadd(a, cscale(cadd(cadd(s_r[j - 1], s_r[j + 1]), cadd(s_r[j - RW], s_r[j + RW])), R(2)));
-      a = cadd(a, cadd(cadd(s_r[j - RW - 1], s_r[j - RW + 1]), cadd(s_r[j + RW - 1], s_r[j + RW + 1])));
-      fcb[(size_t)cy * Nc + cx] = cmul(cs, cscale(a, R(1.0 / 16.0)));
-    }
+  R acc = R(0);
+  const bool inner = tile_in(L, x0 - 2, x0 + BX + 2, N, false) &&
+                     tile_in(L, y0 - 2, y0 + BY + 2, N, false);
+  const bool fast = inner && tile_in(L, x0 - 2, x0 + BX + 2, N, true) &&
+                    tile_in(L, y0 - 2, y0 + BY + 2, N, true);
+  if (act) {
+    if (fast)
+      down_body<R, BX, BY, false, true>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, smem_raw, acc);
+    else if (inner)
+      down_body<R, BX, BY, false, false>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, smem_raw, acc);
+    else
+      down_body<R, BX, BY, true, false>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, smem_raw, acc);
   }
   if (partials) {
-    __shared__ double ws[32];
-    double v = (double)acc;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((tid & 31) == 0) ws[tid >> 5] = v;
-    __syncthreads();
-    if (tid < 32) {
-      double s = tid < (int)(blockDim.x >> 5) ? ws[tid] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (tid == 0)
-        partials[(size_t)b * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = s;
+    const double s = block_sum_d((double)acc);
+    const int nblk = gridDim.x * gridDim.y;
+    if (act && threadIdx.x == 0) partials[(size_t)b * nblk + blockIdx.y * gridDim.x + blockIdx.x] = s;
+    if (chk.mode != CHECK_MODE_NONE) last_block_check(chk, nblk);
+  }
+}
+
+template <typename R, int BX, int BY, bool CHECK, bool FAST>
+__device__ __forceinline__ void up_body(
+    const LevelK<R> &L, const typename Cx<R>::T *__restrict__ vb,
+    const typename Cx<R>::T *__restrict__ eb, const typename Cx<R>::T *__restrict__ fb,
+    typename Cx<R>::T *__restrict__ ob, typename Cx<R>::T omega, int kconst, int x0, int y0,
+    unsigned char *smem_raw) {
+  using C = typename Cx<R>::T;
+  using S = Up2D<R, BX, BY>;
+  constexpr int WW = S::WW, WH = S::WH, EW = S::EW, EH = S::EH;
+  constexpr int NT = 256;
+  C *s_w = reinterpret_cast<C *>(smem_raw);
+  C *s_e = s_w + WW * WH;
+  C *s_cx = s_e + EW * EH;   // [3][WW]
+  C *s_cy = s_cx + 3 * WW;   // [3][WH]
+  const int N = L.N, Nc = (N + 1) / 2 - 1;
+  const int ex0 = x0 / 2 - 1, ey0 = y0 / 2 - 1;
+  const int tid = threadIdx.x;
+  const C zc = czero<C>();
+  const R kc = kconst ? L.k2[0] : R(0);
+
+  if (!FAST) {
+    for (int i = tid; i < WW; i += NT) {
+      const int gx = x0 - 1 + i;
+      const bool in = !CHECK || (gx >= 0 && gx < N);
+      s_cx[i] = in ? L.coef[gx] : zc;
+      s_cx[WW + i] = in ? L.coef[N + gx] : zc;
+      s_cx[2 * WW + i] = in ? L.coef[2 * N + gx] : zc;
     }
+    for (int i = tid; i < WH; i += NT) {
+      const int gy = y0 - 1 + i;
+      const bool in = !CHECK || (gy >= 0 && gy < N);
+      s_cy[i] = in ? L.coef[3 * N + gy] : zc;
+      s_cy[WH + i] = in ? L.coef[4 * N + gy] : zc;
+      s_cy[2 * WH + i] = in ? L.coef[5 * N + gy] : zc;
+    }
+  }
+  {
+    Walk<EW> w(tid);
+    for (int i = tid; i < EW * EH; i += NT, w.next(NT)) {
+      const int cx = ex0 + w.x, cy = ey0 + w.y;
+      // the first coarse row/column of a tile at the low boundary is outside
+      const bool in = cx >= 0 && cx < Nc && cy >= 0 && cy < Nc;
+      s_e[i] = in ? eb[cy * Nc + cx] : zc;
+    }
+  }
+  __syncthreads();
+  // w = v + P e on tile + 1 (zero outside the domain)
+  {
+    const C *vo = vb + (y0 - 1) * N + (x0 - 1);
+    Walk<WW> w(tid);
+    for (int i = tid; i < WW * WH; i += NT, w.next(NT)) {
+      const int tx = w.x, ty = w.y;
+      C val = zc;
+      if (!CHECK || (x0 - 1 + tx >= 0 && x0 - 1 + tx < N && y0 - 1 + ty >= 0 && y0 - 1 + ty < N)) {
+        // fine x odd <-> tx even: coincident coarse column tx/2; else the two
+        // neighbouring coarse columns tx>>1, (tx>>1)+1 (same along y)
+        C p;
+        const int c0 = tx >> 1, r0 = (ty >> 1) * EW;
+        if (!(ty & 1)) {
+          p = (tx & 1) ? cscale(cadd(s_e[r0 + c0], s_e[r0 + c0 + 1]), R(0.5)) : s_e[r0 + c0];
+        } else if (tx & 1) {
+          p = cscale(cadd(cadd(s_e[r0 + c0], s_e[r0 + c0 + 1]),
+                          cadd(s_e[r0 + EW + c0], s_e[r0 + EW + c0 + 1])), R(0.25));
+        } else {
+          p = cscale(cadd(s_e[r0 + c0], s_e[r0 + EW + c0]), R(0.5));
+        }
+        val = cadd(vo[ty * N + tx], p);
+      }
+      s_w[i] = val;
+    }
+  }
+  __syncthreads();
+  // u' = w + omega D^{-1}(f - A w) on the tile
+  const C c0 = FAST ? L.c0 : zc;
+  const C d0 = FAST ? cscale(c0, R(4)) : zc;
+  const C Dk = FAST ? csub(d0, cscale(L.beta, kc)) : zc;
+  const C Dkinv = FAST ? crcp(Dk) : zc;
+  const C *fo = fb + y0 * N + x0;
+  const R *ko = L.k2 + y0 * N + x0;
+  C *oo = ob + y0 * N + x0;
+  Walk<BX> w(tid);
+  for (int i = tid; i < BX * BY; i += NT, w.next(NT)) {
+    const int lx = w.x, ly = w.y;
+    if (CHECK && (x0 + lx >= N || y0 + ly >= N)) continue;
+    const int j = (ly + 1) * WW + lx + 1;
+    const int g = ly * N + lx;
+    C D, Dinv, nb;
+    if (FAST) {
+      if (kconst) { D = Dk; Dinv = Dkinv; }
+      else { D = csub(d0, cscale(L.beta, ko[g])); Dinv = crcp(D); }
+      nb = cmul(c0, cadd(cadd(s_w[j - 1], s_w[j + 1]), cadd(s_w[j - WW], s_w[j + WW])));
+    } else {
+      const int tx = lx + 1, ty = ly + 1;
+      D = csub(cadd(s_cx[WW + tx], s_cy[WH + ty]), cscale(L.beta, kconst ? kc : ko[g]));
+      Dinv = crcp(D);
+      nb = cmul(s_cx[tx], s_w[j - 1]);
+      nb = cfma(s_cx[2 * WW + tx], s_w[j + 1], nb);
+      nb = cfma(s_cy[ty], s_w[j - WW], nb);
+      nb = cfma(s_cy[2 * WH + ty], s_w[j + WW], nb);
+    }
+    const C r = cadd(csub(fo[g], cmul(D, s_w[j])), nb);
+    oo[g] = cadd(s_w[j], cmul(cmul(omega, r), Dinv));
   }
 }
 
@@ -188,92 +385,25 @@ k_up2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ v_in,
        typename Cx<R>::T *__restrict__ u_out, typename Cx<R>::T omega, int kconst,
        const SolveState *__restrict__ st) {
   using C = typename Cx<R>::T;
-  using S = Up2D<R, BX, BY>;
-  constexpr int WW = S::WW, WH = S::WH, EW = S::EW, EH = S::EH;
   const int b = blockIdx.z;
   if (st && !st[b].active) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *s_w = reinterpret_cast<C *>(smem_raw);
-  C *s_e = s_w + WW * WH;
-  C *s_cx = s_e + EW * EH;   // [3][WW]
-  C *s_cy = s_cx + 3 * WW;   // [3][WH]
   const int N = L.N, Nc = (N + 1) / 2 - 1;
   const size_t pts = (size_t)N * N;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-  const int ex0 = x0 / 2 - 1, ey0 = y0 / 2 - 1;
   const C *vb = v_in + (size_t)b * pts;
   const C *eb = e + (size_t)b * Nc * Nc;
-  const int tid = threadIdx.x;
-  const C zc = czero<C>();
-
-  for (int i = tid; i < WW; i += blockDim.x) {
-    const int gx = x0 - 1 + i;
-    const bool in = gx >= 0 && gx < N;
-    s_cx[i] = in ? L.coef[gx] : zc;
-    s_cx[WW + i] = in ? L.coef[N + gx] : zc;
-    s_cx[2 * WW + i] = in ? L.coef[2 * N + gx] : zc;
-  }
-  for (int i = tid; i < WH; i += blockDim.x) {
-    const int gy = y0 - 1 + i;
-    const bool in = gy >= 0 && gy < N;
-    s_cy[i] = in ? L.coef[3 * N + gy] : zc;
-    s_cy[WH + i] = in ? L.coef[4 * N + gy] : zc;
-    s_cy[2 * WH + i] = in ? L.coef[5 * N + gy] : zc;
-  }
-  for (int i = tid; i < EW * EH; i += blockDim.x) {
-    const int ty = i / EW, tx = i - ty * EW;
-    const int cx = ex0 + tx, cy = ey0 + ty;
-    const bool in = cx >= 0 && cx < Nc && cy >= 0 && cy < Nc;
-    s_e[i] = in ? eb[(size_t)cy * Nc + cx] : zc;
-  }
-  __syncthreads();
-  // w = v + P e on tile + 1 (zero outside the domain)
-  for (int i = tid; i < WW * WH; i += blockDim.x) {
-    const int ty = i / WW, tx = i - ty * WW;
-    const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
-    C w = zc;
-    if (gx >= 0 && gx < N && gy >= 0 && gy < N) {
-      // fine gx odd <-> tx even: coincident coarse column tx/2; else the two
-      // neighbouring coarse columns (tx-1)/2, (tx+1)/2 (same along y)
-      C p;
-      if (!(ty & 1)) {
-        const int r = (ty >> 1) * EW;
-        p = (tx & 1) ? cscale(cadd(s_e[r + (tx >> 1)], s_e[r + (tx >> 1) + 1]), R(0.5))
-                     : s_e[r + (tx >> 1)];
-      } else {
-        const int r0 = (ty >> 1) * EW, r1 = r0 + EW;
-        if (tx & 1) {
-          const int c0 = tx >> 1;
-          p = cscale(cadd(cadd(s_e[r0 + c0], s_e[r0 + c0 + 1]), cadd(s_e[r1 + c0], s_e[r1 + c0 + 1])), R(0.25));
-        } else {
-          p = cscale(cadd(s_e[r0 + (tx >> 1)], s_e[r1 + (tx >> 1)]), R(0.5));
-        }
-      }
-      w = cadd(vb[(size_t)gy * N + gx], p);
-    }
-    s_w[i] = w;
-  }
-  __syncthreads();
-  // u' = w + omega D^{-1}(f - A w) on the tile
   const C *fb = f + (size_t)b * pts;
   C *ob = u_out + (size_t)b * pts;
-  const R kc = kconst ? L.k2[0] : R(0);
-  for (int i = tid; i < BX * BY; i += blockDim.x) {
-    const int ly = i / BX, lx = i - ly * BX;
-    const int gx = x0 + lx, gy = y0 + ly;
-    if (gx >= N || gy >= N) continue;
-    const int tx = lx + 1, ty = ly + 1;
-    const int j = ty * WW + tx;
-    const size_t g = (size_t)gy * N + gx;
-    const R k = kconst ? kc : L.k2[g];
-    const C D = csub(cadd(s_cx[WW + tx], s_cy[WH + ty]), cscale(L.beta, k));
-    C nb = cmul(s_cx[tx], s_w[j - 1]);
-    nb = cfma(s_cx[2 * WW + tx], s_w[j + 1], nb);
-    nb = cfma(s_cy[ty], s_w[j - WW], nb);
-    nb = cfma(s_cy[2 * WH + ty], s_w[j + WW], nb);
-    const C r = cadd(csub(fb[g], cmul(D, s_w[j])), nb);
-    ob[g] = cadd(s_w[j], cmul(cmul(omega, r), crcp(D)));
-  }
+  const bool inner = tile_in(L, x0 - 1, x0 + BX, N, false) && tile_in(L, y0 - 1, y0 + BY, N, false);
+  const bool fast = inner && tile_in(L, x0 - 1, x0 + BX, N, true) &&
+                    tile_in(L, y0 - 1, y0 + BY, N, true);
+  if (fast)
+    up_body<R, BX, BY, false, true>(L, vb, eb, fb, ob, omega, kconst, x0, y0, smem_raw);
+  else if (inner)
+    up_body<R, BX, BY, false, false>(L, vb, eb, fb, ob, omega, kconst, x0, y0, smem_raw);
+  else
+    up_body<R, BX, BY, true, false>(L, vb, eb, fb, ob, omega, kconst, x0, y0, smem_raw);
 }
 
 }  // namespace hh

@@ -21,6 +21,8 @@ template <typename R> struct LevelK {
   const C *coef;   // [dim][3][N]: lo, dg, up of axis a at coef + (3a+j)N
   C beta;          // factor of k^2
   const R *k2;     // [N^dim] real k^2 of this level
+  int ulo, uhi;    // nodes ulo..uhi (every axis) have lo = up = c0, dg = 2 c0
+  C c0;            // (the uniform region away from ECS layers); ulo > uhi: none
 };
 
 // Per right-hand-side state of a running solve (device memory).
