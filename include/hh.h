@@ -209,7 +209,9 @@ hh_status hh_coarse_solve(hh_handle *h, const void *f_dev, void *e_dev,
  *   kernel 1: residual + full-weighting restriction on `level`
  *   kernel 2: correction + post-smoothing sweep on `level`
  *   kernel 3: FP64 refinement residual on level 0 (MIXED handles only)
- * Kernels 0-2 run in the handle's precision.  Workspace contents are
+ *   kernel 4: the single-block kernel of the small levels (fused 2-D path)
+ *   kernel 5: one whole V-cycle (no stop test), replayed as a CUDA graph
+ * Kernels 0-2, 4, 5 run in the handle's precision.  Workspace contents are
  * overwritten (the handle stays valid).  For benchmarks and profiles. */
 hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
                          int reps, double *ms, void *stream);

@@ -462,6 +462,10 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
   const LevelK<R> K = levelk<R>(h, level, 0);
   const auto om = omega<R>(h, 0);
   const bool two = h->dim == 2;
+  if (kernel == 4) {
+    launch_tail2d<R>(tail_args<R>(h, 0), batch, nullptr, s);
+    return;
+  }
   if (h->fused && level < h->tail0 && kernel != 1) {
     if (kernel == 0)
       launch_down2d<R>(h->variant[level], K, W.u_post[level], ZERO_NONE, W.f[level],
@@ -470,10 +474,6 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
     else
       launch_up2d<R>(h->variant[level], K, W.u_pre[level], W.u_post[level + 1], W.f[level],
                      W.u_post[level], om, h->kconst, batch, nullptr, s);
-    return;
-  }
-  if (kernel == 4) {
-    launch_tail2d<R>(tail_args<R>(h, 0), batch, nullptr, s);
     return;
   }
   if (kernel == 0) {
@@ -737,7 +737,9 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
       return h->opt.precision == HH_FP64 ? tail_smem_bytes<double>(Ns, L - t)
                                          : tail_smem_bytes<float>(Ns, L - t);
     };
-    while (t0 < L && (h->lv[t0].N > 63 || tail_bytes(t0) > kTailSmemMax)) ++t0;
+    const char *tn = std::getenv("HH_TAIL_N");   // largest level of the tail
+    const int tail_n = tn ? std::atoi(tn) : 63;
+    while (t0 < L && (h->lv[t0].N > tail_n || tail_bytes(t0) > kTailSmemMax)) ++t0;
     if (t0 < L && L - t0 <= kMaxTail) {
       h->fused = 1;
       h->tail0 = t0;
@@ -1078,7 +1080,7 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
   HH_TRY(check_handle(h));
   HH_TRY(check_batch(h, batch));
   if (!ms || reps < 1) return fail(HH_ERR_ARG, "ms must not be NULL and reps >= 1");
-  if (kernel < 0 || kernel > 4) return fail(HH_ERR_ARG, "kernel must be 0..4");
+  if (kernel < 0 || kernel > 5) return fail(HH_ERR_ARG, "kernel must be 0..5");
   if (level < 0 || level + 1 >= h->L) return fail(HH_ERR_ARG, "bad level");
   if (kernel == 4 && !h->fused) return fail(HH_ERR_ARG, "kernel 4 needs the fused 2-D path");
   if (kernel == 1 && h->fused && level < h->tail0)
@@ -1090,7 +1092,22 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
   cudaEvent_t e0, e1;
   HH_CK(cudaEventCreate(&e0));
   HH_CK(cudaEventCreate(&e1));
+  cudaGraphExec_t cyc = nullptr;
+  if (kernel == 5) {  // one V-cycle (no stop test) as a plain captured graph
+    cudaGraph_t g = nullptr;
+    HH_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    if (h->opt.precision == HH_FP64) cycle_dispatch<double>(h, 0, batch, ZERO_NONE, CHECK_NONE, 0, h->cap);
+    else cycle_dispatch<float>(h, 0, batch, ZERO_NONE, CHECK_NONE, 0, h->cap);
+    HH_CK(cudaStreamEndCapture(h->cap, &g));
+    const cudaError_t ei = cudaGraphInstantiate(&cyc, g, 0);
+    cudaGraphDestroy(g);
+    HH_CK(ei);
+  }
   auto one = [&]() {
+    if (kernel == 5) {
+      cudaGraphLaunch(cyc, s);
+      return;
+    }
     if (kernel == 3) {
       refine_dispatch(h, 0, h->u64[0], 0, h->w32.u_post[0], h->u64[1], batch, s);
       return;
@@ -1109,6 +1126,7 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
   HH_CK(cudaEventElapsedTime(&t, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (cyc) cudaGraphExecDestroy(cyc);
   HH_CK(cudaGetLastError());
   *ms = double(t) / reps;
   return HH_OK;
