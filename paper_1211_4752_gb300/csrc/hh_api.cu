@@ -251,13 +251,19 @@ template <typename R> TailArgs<R> tail_args(hh_handle *h, int dir) {
     a.lv[i].u = W.u_post[l];
     a.lv[i].c = cscal<R>(h, l, dir);
   }
-  int off = 0;
+  using C = typename Cx<R>::T;
+  int off = 0, koff = 0, Ns[kMaxTail];
   for (int i = 0; i < a.nl; ++i) {
-    a.off[i] = off;
     const int N = h->lv[h->tail0 + i].N;
-    off += 3 * N * N;
+    Ns[i] = N;
+    a.off[i] = off;
+    off += 3 * N * N + 6 * N;
+    a.koff[i] = koff;
+    koff += N * N;
   }
-  a.smem_bytes = off * (int)sizeof(typename Cx<R>::T);
+  a.kbase = off * (int)sizeof(C);
+  a.lubase = a.kbase + ((koff * (int)sizeof(R) + 15) / 16) * 16;
+  a.smem_bytes = (int)tail_smem_bytes<R>(Ns, a.nl);
   a.lu = h->lu[dir];
   a.piv = h->piv[dir];
   a.m = h->m;

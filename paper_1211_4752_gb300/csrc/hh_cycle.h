@@ -19,8 +19,11 @@ template <typename R> struct TailLevel {
 template <typename R> struct TailArgs {
   int nl;                  // levels in the tail (the last one is the coarsest)
   TailLevel<R> lv[kMaxTail];
-  int off[kMaxTail];       // shared-memory offset (elements) of each level's
-                           // f, v, t arrays (3 N^2 elements per level)
+  int off[kMaxTail];       // shared-memory offset (complex elements) of each
+                           // level's f, v, t arrays (3 N^2) and tables (6 N)
+  int koff[kMaxTail];      // offset (real elements) of each level's k^2
+  int kbase;               // byte offset of the k^2 area
+  int lubase;              // byte offset of the LU factors and pivots
   int smem_bytes;
   const double2 *lu;       // coarsest LU factors (FP64), m x m
   const int *piv;
@@ -28,11 +31,18 @@ template <typename R> struct TailArgs {
   typename Cx<R>::T omega;
 };
 
-// Shared memory the tail kernel needs for levels of N_0 > N_1 > ... points.
+// Shared memory the tail kernel needs for levels of N_0 > N_1 > ... points:
+// per level f, v, t (complex), the coefficient tables (6 N complex) and k^2
+// (real), plus the coarsest LU factors (FP64, at most 27 x 27).
 template <typename R> size_t tail_smem_bytes(const int *N, int nl) {
-  size_t e = 0;
-  for (int i = 0; i < nl; ++i) e += 3 * (size_t)N[i] * N[i];
-  return e * sizeof(typename Cx<R>::T);
+  size_t c = 0, r = 0;
+  for (int i = 0; i < nl; ++i) {
+    c += 3 * (size_t)N[i] * N[i] + 6 * (size_t)N[i];
+    r += (size_t)N[i] * N[i];
+  }
+  const size_t m = (size_t)N[nl - 1] * N[nl - 1];
+  return c * sizeof(typename Cx<R>::T) + ((r * sizeof(R) + 15) / 16) * 16 +
+         m * m * sizeof(double2) + m * sizeof(int);
 }
 constexpr size_t kTailSmemMax = 200 * 1024;
 

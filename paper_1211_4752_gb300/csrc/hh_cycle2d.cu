@@ -64,20 +64,21 @@ struct WalkN {
 };
 
 // A w at (x, y) on an N x N shared-memory array (zero outside), general
-// coefficients from the level tables.
+// coefficients from the level's shared-memory tables cf = [lo|dg|up]_x,
+// [lo|dg|up]_y and k^2 kk.
 template <typename R>
-__device__ __forceinline__ typename Cx<R>::T apply_s(const LevelK<R> &K, const typename Cx<R>::T *w,
-                                                     int x, int y, typename Cx<R>::T &D) {
+__device__ __forceinline__ typename Cx<R>::T apply_s(const typename Cx<R>::T *cf, const R *kk,
+                                                     typename Cx<R>::T beta, int N,
+                                                     const typename Cx<R>::T *w, int x, int y,
+                                                     typename Cx<R>::T &D) {
   using C = typename Cx<R>::T;
-  const int N = K.N;
-  const C *c = K.coef;
   const int j = y * N + x;
   C nb = czero<C>();
-  if (x > 0) nb = cfma(c[x], w[j - 1], nb);
-  if (x < N - 1) nb = cfma(c[2 * N + x], w[j + 1], nb);
-  if (y > 0) nb = cfma(c[3 * N + y], w[j - N], nb);
-  if (y < N - 1) nb = cfma(c[5 * N + y], w[j + N], nb);
-  D = csub(cadd(c[N + x], c[4 * N + y]), cscale(K.beta, K.k2[j]));
+  if (x > 0) nb = cfma(cf[x], w[j - 1], nb);
+  if (x < N - 1) nb = cfma(cf[2 * N + x], w[j + 1], nb);
+  if (y > 0) nb = cfma(cf[3 * N + y], w[j - N], nb);
+  if (y < N - 1) nb = cfma(cf[5 * N + y], w[j + N], nb);
+  D = csub(cadd(cf[N + x], cf[4 * N + y]), cscale(beta, kk[j]));
   return csub(cmul(D, w[j]), nb);
 }
 
@@ -88,25 +89,42 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
   if (st && !st[b].active) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *sm = reinterpret_cast<C *>(smem_raw);
+  R *skk = reinterpret_cast<R *>(smem_raw + A.kbase);
+  double2 *slu = reinterpret_cast<double2 *>(smem_raw + A.lubase);
+  const int m = A.m;
+  int *spiv = reinterpret_cast<int *>(slu + m * m);
   const int tid = threadIdx.x, nt = blockDim.x;
   const C om = A.omega;
-  // top level right-hand side into shared memory
+  // stage everything once: the top right-hand side, every level's tables and
+  // k^2, the coarsest LU factors (all loads independent: one round trip)
   {
     const int N = A.lv[0].K.N;
     const C *g = A.lv[0].f + (size_t)b * N * N;
     C *f = sm + A.off[0];
     for (int p = tid; p < N * N; p += nt) f[p] = g[p];
   }
+  for (int l = 0; l < A.nl; ++l) {
+    const LevelK<R> &K = A.lv[l].K;
+    const int N = K.N;
+    C *cf = sm + A.off[l] + 3 * N * N;
+    for (int i = tid; i < 6 * N; i += nt) cf[i] = K.coef[i];
+    R *kk = skk + A.koff[l];
+    for (int i = tid; i < N * N; i += nt) kk[i] = K.k2[i];
+  }
+  for (int i = tid; i < m * m; i += nt) slu[i] = A.lu[i];
+  for (int i = tid; i < m; i += nt) spiv[i] = A.piv[i];
   __syncthreads();
   for (int l = 0; l + 1 < A.nl; ++l) {
-    const LevelK<R> &K = A.lv[l].K;
-    const int N = K.N, Nc = (N + 1) / 2 - 1;
+    const int N = A.lv[l].K.N, Nc = (N + 1) / 2 - 1;
+    const C beta = A.lv[l].K.beta;
     C *f = sm + A.off[l], *v = f + N * N, *t = v + N * N;
+    const C *cf = t + N * N;
+    const R *kk = skk + A.koff[l];
     // pre-smoothing from the zero initial guess: v = omega D^{-1} f
     {
       WalkN w(tid, nt, N);
       for (int p = tid; p < N * N; p += nt, w.next()) {
-        const C D = csub(cadd(K.coef[N + w.x], K.coef[4 * N + w.y]), cscale(K.beta, K.k2[p]));
+        const C D = csub(cadd(cf[N + w.x], cf[4 * N + w.y]), cscale(beta, kk[p]));
         v[p] = cmul(cmul(om, f[p]), crcp(D));
       }
     }
@@ -115,7 +133,7 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
       WalkN w(tid, nt, N);
       for (int p = tid; p < N * N; p += nt, w.next()) {
         C D;
-        t[p] = csub(f[p], apply_s<R>(K, v, w.x, w.y, D));
+        t[p] = csub(f[p], apply_s<R>(cf, kk, beta, N, v, w.x, w.y, D));
       }
     }
     __syncthreads();
@@ -135,30 +153,32 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
   }
   // coarsest level: LU substitution (FP64) by one warp, lane i owning row i
   if (tid < 32) {
-    const int m = A.m, i = tid;
+    const int i = tid;
     const C *fl = sm + A.off[A.nl - 1];
     C *ul = const_cast<C *>(fl) + m;       // the level's v slot holds the solution
     double2 y = make_double2(0.0, 0.0);
     if (i < m) {
-      const C q = fl[A.piv[i]];
+      const C q = fl[spiv[i]];
       y = make_double2((double)q.x, (double)q.y);
     }
     for (int k = 0; k < m; ++k) {            // forward, unit lower triangle
       const double2 yk = make_double2(__shfl_sync(0xffffffffu, y.x, k), __shfl_sync(0xffffffffu, y.y, k));
-      if (i > k && i < m) y = csub(y, cmul(A.lu[i * m + k], yk));
+      if (i > k && i < m) y = csub(y, cmul(slu[i * m + k], yk));
     }
     for (int k = m - 1; k >= 0; --k) {       // backward
-      if (i == k) y = cdiv(y, A.lu[k * m + k]);
+      if (i == k) y = cdiv(y, slu[k * m + k]);
       const double2 yk = make_double2(__shfl_sync(0xffffffffu, y.x, k), __shfl_sync(0xffffffffu, y.y, k));
-      if (i < k) y = csub(y, cmul(A.lu[i * m + k], yk));
+      if (i < k) y = csub(y, cmul(slu[i * m + k], yk));
     }
     if (i < m) ul[i] = cmk((R)y.x, (R)y.y);
   }
   __syncthreads();
   for (int l = A.nl - 2; l >= 0; --l) {
-    const LevelK<R> &K = A.lv[l].K;
-    const int N = K.N, Nc = (N + 1) / 2 - 1;
+    const int N = A.lv[l].K.N, Nc = (N + 1) / 2 - 1;
+    const C beta = A.lv[l].K.beta;
     C *f = sm + A.off[l], *v = f + N * N, *t = v + N * N;
+    const C *cf = t + N * N;
+    const R *kk = skk + A.koff[l];
     const C *e = sm + A.off[l + 1] + Nc * Nc;   // coarse v slot: its correction
     {
       WalkN w(tid, nt, N);
@@ -170,7 +190,7 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
       WalkN w(tid, nt, N);
       for (int p = tid; p < N * N; p += nt, w.next()) {
         C D;
-        const C Aw = apply_s<R>(K, t, w.x, w.y, D);
+        const C Aw = apply_s<R>(cf, kk, beta, N, t, w.x, w.y, D);
         v[p] = cadd(t[p], cmul(cmul(om, csub(f[p], Aw)), crcp(D)));
       }
     }
