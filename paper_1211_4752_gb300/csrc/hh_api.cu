@@ -261,8 +261,8 @@ template <typename R> TailArgs<R> tail_args(hh_handle *h, int dir) {
     a.koff[i] = koff;
     koff += N * N;
   }
-  a.kbase = off * (int)sizeof(C);
-  a.lubase = a.kbase + ((koff * (int)sizeof(R) + 15) / 16) * 16;
+  a.kbase = (int)tail_k2_base<R>(Ns, a.nl);
+  a.lubase = (int)tail_lu_base<R>(Ns, a.nl);
   a.smem_bytes = (int)tail_smem_bytes<R>(Ns, a.nl);
   a.lu = h->lu[dir];
   a.piv = h->piv[dir];

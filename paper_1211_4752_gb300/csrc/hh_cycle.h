@@ -34,15 +34,22 @@ template <typename R> struct TailArgs {
 // Shared memory the tail kernel needs for levels of N_0 > N_1 > ... points:
 // per level f, v, t (complex), the coefficient tables (6 N complex) and k^2
 // (real), plus the coarsest LU factors (FP64, at most 27 x 27).
+// Byte layout: [complex arrays | k^2 | LU factors | pivots], each area
+// starting on a 16-byte boundary (the LU factors are double2).
+inline size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+template <typename R> size_t tail_k2_base(const int *N, int nl) {
+  size_t c = 0;
+  for (int i = 0; i < nl; ++i) c += 3 * (size_t)N[i] * N[i] + 6 * (size_t)N[i];
+  return align16(c * sizeof(typename Cx<R>::T));
+}
+template <typename R> size_t tail_lu_base(const int *N, int nl) {
+  size_t r = 0;
+  for (int i = 0; i < nl; ++i) r += (size_t)N[i] * N[i];
+  return align16(tail_k2_base<R>(N, nl) + r * sizeof(R));
+}
 template <typename R> size_t tail_smem_bytes(const int *N, int nl) {
-  size_t c = 0, r = 0;
-  for (int i = 0; i < nl; ++i) {
-    c += 3 * (size_t)N[i] * N[i] + 6 * (size_t)N[i];
-    r += (size_t)N[i] * N[i];
-  }
   const size_t m = (size_t)N[nl - 1] * N[nl - 1];
-  return c * sizeof(typename Cx<R>::T) + ((r * sizeof(R) + 15) / 16) * 16 +
-         m * m * sizeof(double2) + m * sizeof(int);
+  return tail_lu_base<R>(N, nl) + m * m * sizeof(double2) + m * sizeof(int);
 }
 constexpr size_t kTailSmemMax = 200 * 1024;
 
