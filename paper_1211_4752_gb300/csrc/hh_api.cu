@@ -334,6 +334,39 @@ void refine_dispatch(hh_handle *h, int dir, const double2 *u_in, int u_zero,
                      batch, h->st, h->partials, h->nparts, s);
 }
 
+// Loop control: a WHILE graph node (default), or HH_LOOP=host in the
+// environment for one plain graph per cycle with the stop flag read by the
+// host after each cycle (same kernels; for profilers that cannot see kernels
+// inside conditional graphs).
+bool host_loop() {
+  const char *e = std::getenv("HH_LOOP");
+  return e && std::strcmp(e, "host") == 0;
+}
+
+// Plain (unconditional) graph of one cycle, for the host-driven loop.
+hh_status get_cycle_graph(hh_handle *h, int prec, int dir, int batch, cudaGraphExec_t *out) {
+  auto key = std::make_tuple(prec + 2, dir, batch);
+  auto it = h->graphs.find(key);
+  if (it != h->graphs.end()) {
+    *out = it->second.exec;
+    return HH_OK;
+  }
+  GraphEntry g;
+  HH_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  if (prec == HH_FP64)
+    cycle_dispatch<double>(h, dir, batch, ZERO_NONE, CHECK_CYCLE, 0, h->cap);
+  else
+    cycle_dispatch<float>(h, dir, batch, ZERO_FLAG, CHECK_INNER, 0, h->cap);
+  HH_CK(cudaStreamEndCapture(h->cap, &g.graph));
+  HH_CK(cudaGraphInstantiate(&g.exec, g.graph, 0));
+  h->graphs[key] = g;
+  *out = g.exec;
+  return HH_OK;
+}
+
+// Run the cycle loop to completion on stream s.
+hh_status run_loop(hh_handle *h, int prec, int dir, int batch, cudaStream_t s);
+
 // The graph for (precision, direction, batch): a WHILE node whose body is
 // one V-cycle with the stop test after the level-0 pre-smoothing sweep.
 hh_status get_graph(hh_handle *h, int prec, int dir, int batch,
@@ -373,6 +406,23 @@ hh_status get_graph(hh_handle *h, int prec, int dir, int batch,
   HH_CK(cudaGraphInstantiate(&g.exec, g.graph, 0));
   h->graphs[key] = g;
   *out = g.exec;
+  return HH_OK;
+}
+
+hh_status run_loop(hh_handle *h, int prec, int dir, int batch, cudaStream_t s) {
+  cudaGraphExec_t ex;
+  if (!host_loop()) {
+    HH_TRY(get_graph(h, prec, dir, batch, &ex));
+    HH_CK(cudaGraphLaunch(ex, s));
+    return HH_OK;
+  }
+  HH_TRY(get_cycle_graph(h, prec, dir, batch, &ex));
+  for (long it = 0; it < (long)h->opt.max_cycles + 2; ++it) {
+    HH_CK(cudaGraphLaunch(ex, s));
+    HH_CK(cudaMemcpyAsync(h->flag_h, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HH_CK(cudaStreamSynchronize(s));
+    if (*h->flag_h == 0) break;
+  }
   return HH_OK;
 }
 
@@ -430,9 +480,7 @@ hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
       HH_CK(cudaMemcpyAsync(h->w64.u_post[0], guess, bytes, cudaMemcpyDeviceToDevice, s));
     else if (!guess)
       HH_CK(cudaMemsetAsync(h->w64.u_post[0], 0, bytes, s));
-    cudaGraphExec_t ex;
-    HH_TRY(get_graph(h, HH_FP64, dir, batch, &ex));
-    HH_CK(cudaGraphLaunch(ex, s));
+    HH_TRY(run_loop(h, HH_FP64, dir, batch, s));
     launch_finish(h->st, h->w64.u_post[0], out, pts, batch, s);
     HH_CK(cudaGetLastError());
     return read_info(h, batch, info, s);
@@ -445,13 +493,11 @@ hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
   refine_dispatch(h, dir, h->u64[0], guess ? 0 : 1, nullptr, h->u64[1], batch, s);
   cur = 1;
   launch_check_outer(h->st, h->partials, h->params, h->flag, s);
-  cudaGraphExec_t ex;
-  HH_TRY(get_graph(h, HH_MIXED, dir, batch, &ex));
   for (int it = 0; it < h->opt.max_cycles + 2; ++it) {
     HH_CK(cudaMemcpyAsync(h->flag_h, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     HH_CK(cudaStreamSynchronize(s));
     if (*h->flag_h == 0) break;
-    HH_CK(cudaGraphLaunch(ex, s));
+    HH_TRY(run_loop(h, HH_MIXED, dir, batch, s));
     refine_dispatch(h, dir, h->u64[cur], 0, h->w32.u_post[0], h->u64[1 - cur], batch, s);
     cur = 1 - cur;
     launch_check_outer(h->st, h->partials, h->params, h->flag, s);

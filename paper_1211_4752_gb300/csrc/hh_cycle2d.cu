@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
       if (i > k && i < m) y = csub(y, cmul(slu[i * m + k], yk));
     }
     for (int k = m - 1; k >= 0; --k) {       // backward
-      if (i == k) y = cdiv(y, slu[k * m + k]);
+      if (i == k) y = cmul(y, slu[k * m + k]);   // the diagonal holds 1 / U_kk
       const double2 yk = make_double2(__shfl_sync(0xffffffffu, y.x, k), __shfl_sync(0xffffffffu, y.y, k));
       if (i < k) y = csub(y, cmul(slu[i * m + k], yk));
     }

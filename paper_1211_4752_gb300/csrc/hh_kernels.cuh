@@ -358,6 +358,9 @@ __global__ void k_assemble_lu(LevelK<double> L, double2 *lu, int *piv,
         lu[i * m + j] = csub(lu[i * m + j], cmul(l, lu[k * m + j]));
     }
   }
+  // store 1 / U_kk on the diagonal: the per-cycle back substitution then
+  // multiplies instead of dividing (an FP64 division costs ~400 cycles here)
+  for (int k = 0; k < m; ++k) lu[k * m + k] = cdiv(make_double2(1.0, 0.0), lu[k * m + k]);
 }
 
 // k2 injection to the next coarser level: kc(c) = kf(2c+1).

@@ -241,7 +241,7 @@ __global__ void k_coarse_solve(const double2 *__restrict__ lu,
     for (int j = 0; j < i; ++j) y[i] = csub(y[i], cmul(lu[i * m + j], y[j]));
   for (int i = m - 1; i >= 0; --i) {
     for (int j = i + 1; j < m; ++j) y[i] = csub(y[i], cmul(lu[i * m + j], y[j]));
-    y[i] = cdiv(y[i], lu[i * m + i]);
+    y[i] = cmul(y[i], lu[i * m + i]);   // the diagonal holds 1 / U_ii
   }
   C *eb = e + (size_t)b * m;
   for (int i = 0; i < m; ++i) eb[i] = cmk((R)y[i].x, (R)y[i].y);
