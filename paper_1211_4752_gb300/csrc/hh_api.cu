@@ -1160,8 +1160,14 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
       cudaGraphLaunch(cyc, s);
       return;
     }
-    if (kernel == 3) {
-      refine_dispatch(h, 0, h->u64[0], 0, h->w32.u_post[0], h->u64[1], batch, s);
+    if (kernel == 3) {  // without solver state: every right-hand side computes
+      const LevelK<double> K = levelk<double>(h, 0, 0);
+      if (h->dim == 2)
+        launch_refine<2>(K, h->u64[0], 0, h->w32.u_post[0], h->u64[1], h->w64.f[0], h->w32.f[0],
+                         batch, nullptr, h->partials, h->nparts, s);
+      else
+        launch_refine<3>(K, h->u64[0], 0, h->w32.u_post[0], h->u64[1], h->w64.f[0], h->w32.f[0],
+                         batch, nullptr, h->partials, h->nparts, s);
       return;
     }
     if (h->opt.precision == HH_FP64)
@@ -1169,9 +1175,27 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
     else
       time_one<float>(h, kernel, level, batch, s);
   };
-  one();  // warm-up launch
+  // the reps launches are replayed from a captured graph, as in a solve
+  cudaGraphExec_t rep = nullptr;
+  if (kernel != 5) {
+    cudaGraph_t g = nullptr;
+    HH_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    const cudaStream_t keep = s;
+    s = h->cap;
+    for (int r = 0; r < reps; ++r) one();
+    s = keep;
+    HH_CK(cudaStreamEndCapture(h->cap, &g));
+    const cudaError_t ei = cudaGraphInstantiate(&rep, g, 0);
+    cudaGraphDestroy(g);
+    HH_CK(ei);
+  }
+  auto all = [&]() {
+    if (kernel == 5) for (int r = 0; r < reps; ++r) one();
+    else cudaGraphLaunch(rep, s);
+  };
+  all();  // warm-up
   HH_CK(cudaEventRecord(e0, s));
-  for (int r = 0; r < reps; ++r) one();
+  all();
   HH_CK(cudaEventRecord(e1, s));
   HH_CK(cudaEventSynchronize(e1));
   float t = 0.f;
@@ -1179,6 +1203,7 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (cyc) cudaGraphExecDestroy(cyc);
+  if (rep) cudaGraphExecDestroy(rep);
   HH_CK(cudaGetLastError());
   *ms = double(t) / reps;
   return HH_OK;

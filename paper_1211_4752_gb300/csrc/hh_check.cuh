@@ -79,6 +79,7 @@ __device__ __forceinline__ double block_sum_d(double v) {
 // Called by every block of the level-0 down pass after it wrote its partial
 // sum: the last block to arrive adds the partials of each right-hand side in
 // a fixed order, updates the solver state, and sets the graph condition.
+template <bool COND>
 __device__ __forceinline__ void last_block_check(const CheckCtx &c, int nblk) {
   __shared__ unsigned int s_last;
   __shared__ int s_any;
@@ -111,7 +112,7 @@ __device__ __forceinline__ void last_block_check(const CheckCtx &c, int nblk) {
   if (threadIdx.x == 0) {
     *c.flag = s_any;
     *c.counter = 0u;
-    if (c.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)c.cond, s_any ? 1u : 0u);
+    if (COND && c.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)c.cond, s_any ? 1u : 0u);
   }
 }
 

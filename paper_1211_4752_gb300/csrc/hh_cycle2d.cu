@@ -20,8 +20,12 @@ void down_one(const LevelK<R> &L, const typename Cx<R>::T *u_in, int zero_mode,
               int kconst, int batch, const SolveState *st, double *partials,
               const CheckCtx &chk, cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
-  k_down2d<R, BX, BY><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
-      L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, st, partials, chk);
+  if (chk.cond)
+    k_down2d<R, BX, BY, true><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
+        L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, st, partials, chk);
+  else
+    k_down2d<R, BX, BY, false><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
+        L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, st, partials, chk);
 }
 
 template <typename R, int BX, int BY>
@@ -34,13 +38,20 @@ void up_one(const LevelK<R> &L, const typename Cx<R>::T *v_in,
                                                              omega, kconst, st);
 }
 
-template <typename R, int BX, int BY> cudaError_t attr_one() {
-  cudaError_t e = cudaFuncSetAttribute(k_down2d<R, BX, BY>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Down2D<R, BX, BY>::smem);
+// Dynamic shared memory limits, and the maximum shared-memory carveout for
+// every cycle kernel so that consecutive kernels never reconfigure L1/shared.
+template <typename K> cudaError_t attrs(K kern, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_up2d<R, BX, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Up2D<R, BX, BY>::smem);
+  return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <typename R, int BX, int BY> cudaError_t attr_one() {
+  cudaError_t e;
+  if ((e = attrs(k_down2d<R, BX, BY, true>, Down2D<R, BX, BY>::smem)) != cudaSuccess) return e;
+  if ((e = attrs(k_down2d<R, BX, BY, false>, Down2D<R, BX, BY>::smem)) != cudaSuccess) return e;
+  return attrs(k_up2d<R, BX, BY>, Up2D<R, BX, BY>::smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -219,8 +230,7 @@ cudaError_t init_cycle2d() {
   if ((e = attr_one<R, 64, 8>()) != cudaSuccess) return e;
   if ((e = attr_one<R, 32, 8>()) != cudaSuccess) return e;
   if ((e = attr_one<R, 128, 8>()) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_tail2d<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kTailSmemMax);
+  return attrs(k_tail2d<R>, kTailSmemMax);
 }
 
 template <typename R>

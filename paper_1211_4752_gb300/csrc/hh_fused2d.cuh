@@ -230,7 +230,9 @@ __device__ __forceinline__ void down_body(
   }
 }
 
-template <typename R, int BX, int BY>
+// COND: the stop test may set the condition of a CUDA-graph WHILE node (the
+// variant without that call serves the host-driven loop and profilers).
+template <typename R, int BX, int BY, bool COND>
 __global__ void __launch_bounds__(256)
 k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
          const typename Cx<R>::T *__restrict__ f, typename Cx<R>::T *__restrict__ v_out,
@@ -269,7 +271,7 @@ k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
     const double s = block_sum_d((double)acc);
     const int nblk = gridDim.x * gridDim.y;
     if (act && threadIdx.x == 0) partials[(size_t)b * nblk + blockIdx.y * gridDim.x + blockIdx.x] = s;
-    if (chk.mode != CHECK_MODE_NONE) last_block_check(chk, nblk);
+    if (chk.mode != CHECK_MODE_NONE) last_block_check<COND>(chk, nblk);
   }
 }
 
