@@ -790,7 +790,7 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
                                          : tail_smem_bytes<float>(Ns, L - t);
     };
     const char *tn = std::getenv("HH_TAIL_N");   // largest level of the tail
-    const int tail_n = tn ? std::atoi(tn) : 63;
+    const int tail_n = tn ? std::atoi(tn) : 31;
     while (t0 < L && (h->lv[t0].N > tail_n || tail_bytes(t0) > kTailSmemMax)) ++t0;
     if (t0 < L && L - t0 <= kMaxTail) {
       h->fused = 1;

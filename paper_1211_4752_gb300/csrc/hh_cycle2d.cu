@@ -11,7 +11,7 @@ namespace hh {
 namespace {
 
 struct Shape { int bx, by; };
-constexpr Shape kShapes[kNumTileVariants] = {{64, 16}, {32, 16}, {64, 8}, {32, 8}, {128, 8}};
+constexpr Shape kShapes[kNumTileVariants] = {{58, 16}, {58, 32}, {26, 32}, {122, 16}, {26, 16}};
 
 template <typename R, int BX, int BY>
 void down_one(const LevelK<R> &L, const typename Cx<R>::T *u_in, int zero_mode,
@@ -225,11 +225,11 @@ int tile_parts(int variant, int N) {
 template <typename R>
 cudaError_t init_cycle2d() {
   cudaError_t e;
-  if ((e = attr_one<R, 64, 16>()) != cudaSuccess) return e;
-  if ((e = attr_one<R, 32, 16>()) != cudaSuccess) return e;
-  if ((e = attr_one<R, 64, 8>()) != cudaSuccess) return e;
-  if ((e = attr_one<R, 32, 8>()) != cudaSuccess) return e;
-  if ((e = attr_one<R, 128, 8>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 58, 16>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 58, 32>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 26, 32>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 122, 16>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 26, 16>()) != cudaSuccess) return e;
   return attrs(k_tail2d<R>, kTailSmemMax);
 }
 
@@ -240,11 +240,11 @@ void launch_down2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *u_i
                    int kconst, int batch, const SolveState *st, double *partials,
                    const CheckCtx &chk, cudaStream_t s) {
   switch (variant) {
-    case 0: down_one<R, 64, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
-    case 1: down_one<R, 32, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
-    case 2: down_one<R, 64, 8>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
-    case 3: down_one<R, 32, 8>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
-    default: down_one<R, 128, 8>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
+    case 0: down_one<R, 58, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
+    case 1: down_one<R, 58, 32>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
+    case 2: down_one<R, 26, 32>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
+    case 3: down_one<R, 122, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
+    default: down_one<R, 26, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
   }
 }
 
@@ -254,11 +254,11 @@ void launch_up2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *v_in,
                  typename Cx<R>::T *u_out, typename Cx<R>::T omega, int kconst, int batch,
                  const SolveState *st, cudaStream_t s) {
   switch (variant) {
-    case 0: up_one<R, 64, 16>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
-    case 1: up_one<R, 32, 16>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
-    case 2: up_one<R, 64, 8>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
-    case 3: up_one<R, 32, 8>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
-    default: up_one<R, 128, 8>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
+    case 0: up_one<R, 58, 16>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
+    case 1: up_one<R, 58, 32>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
+    case 2: up_one<R, 26, 32>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
+    case 3: up_one<R, 122, 16>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
+    default: up_one<R, 26, 16>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
   }
 }
 

@@ -133,82 +133,111 @@ __device__ __forceinline__ void down_body(
   __syncthreads();
 
   // uniform-coefficient constants (FAST): nb = c0 * (sum of neighbours),
-  // D = 4 c0 - beta k2
+  // D = 4 c0 - beta k2, W = omega / D
   const C c0 = FAST ? L.c0 : zc;
   const C d0 = FAST ? cscale(c0, R(4)) : zc;
   const C Dk = FAST ? csub(d0, cscale(L.beta, kc)) : zc;
-  const C Dkinv = FAST ? crcp(Dk) : zc;
+  const C Wk = FAST ? cmul(omega, crcp(Dk)) : zc;
 
+  // Column-segment mapping: thread -> one column of the region and a run of
+  // consecutive rows; the values above, at and below the current point ride
+  // along the column in registers (3 shared loads per point).
   // v = u + omega D^{-1}(f - A u) on tile + 1; |f - A u|^2 on the tile
   {
-    C *vo = vb + (y0 - 1) * N + (x0 - 1);
-    Walk<VW> w(tid);
-    for (int i = tid; i < VW * VH; i += NT, w.next(NT)) {
-      const int tx = w.x, ty = w.y;
-      bool in = true;
-      if (CHECK) {
-        const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
-        in = gx >= 0 && gx < N && gy >= 0 && gy < N;
-      }
-      C v = zc;
-      if (in) {
-        C D, Dinv;
-        if (FAST) {
-          if (kconst) { D = Dk; Dinv = Dkinv; }
-          else { D = csub(d0, cscale(L.beta, s_k[i])); Dinv = crcp(D); }
-        } else {
-          D = csub(cadd(s_cx[VW + tx], s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[i]));
-          Dinv = crcp(D);
-        }
-        C r = s_f[i];
-        C uc = zc;
+    constexpr int NS = NT / VW;                  // row segments per column
+    const int tx = tid % VW, sg = tid / VW;
+    if (sg < NS) {
+      const int r0 = sg * VH / NS, r1 = (sg + 1) * VH / NS;
+      const int gx = x0 - 1 + tx;
+      const bool colin = !CHECK || (gx >= 0 && gx < N);
+      const bool colown = tx >= 1 && tx <= BX;
+      C clo = zc, cdg = zc, cup = zc;
+      if (!FAST) { clo = s_cx[tx]; cdg = s_cx[VW + tx]; cup = s_cx[2 * VW + tx]; }
+      C *vo = vb + (y0 - 1) * N + gx;
+      const C *col = s_u + tx + 1;               // u tile column of this v column
+      C un = zc, uc = zc;
+      if (!zero) { un = col[r0 * UW]; uc = col[(r0 + 1) * UW]; }
+      for (int ty = r0; ty < r1; ++ty) {
+        const int i = ty * VW + tx;
+        C ud = zc, ul = zc, ur = zc;
         if (!zero) {
-          const int j = (ty + 1) * UW + tx + 1;
-          uc = s_u[j];
-          C nb;
-          if (FAST) {
-            nb = cmul(c0, cadd(cadd(s_u[j - 1], s_u[j + 1]), cadd(s_u[j - UW], s_u[j + UW])));
-          } else {
-            nb = cmul(s_cx[tx], s_u[j - 1]);
-            nb = cfma(s_cx[2 * VW + tx], s_u[j + 1], nb);
-            nb = cfma(s_cy[ty], s_u[j - UW], nb);
-            nb = cfma(s_cy[2 * VH + ty], s_u[j + UW], nb);
+          const int j = (ty + 1) * UW;
+          ud = col[j + UW];
+          ul = col[j - 1];
+          ur = col[j + 1];
+        }
+        bool in = colin;
+        if (CHECK) { const int gy = y0 - 1 + ty; in = in && gy >= 0 && gy < N; }
+        C v = zc;
+        if (in) {
+          C D, Wd;
+          if (FAST && kconst) { D = Dk; Wd = Wk; }
+          else {
+            D = FAST ? csub(d0, cscale(L.beta, s_k[i]))
+                     : csub(cadd(cdg, s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[i]));
+            Wd = cmul(omega, crcp(D));
           }
-          r = cadd(csub(r, cmul(D, uc)), nb);
+          C r = s_f[i];
+          if (!zero) {
+            C nb;
+            if (FAST) nb = cmul(c0, cadd(cadd(ul, ur), cadd(un, ud)));
+            else {
+              nb = cmul(clo, ul);
+              nb = cfma(cup, ur, nb);
+              nb = cfma(s_cy[ty], un, nb);
+              nb = cfma(s_cy[2 * VH + ty], ud, nb);
+            }
+            r = cadd(csub(r, cmul(D, uc)), nb);
+          }
+          v = cadd(uc, cmul(Wd, r));
+          if (colown && ty >= 1 && ty <= BY) {
+            vo[ty * N] = v;
+            acc += r.x * r.x + r.y * r.y;
+          }
         }
-        v = cadd(uc, cmul(cmul(omega, r), Dinv));
-        if (tx >= 1 && tx <= BX && ty >= 1 && ty <= BY) {
-          vo[ty * N + tx] = v;
-          acc += r.x * r.x + r.y * r.y;
-        }
+        s_v[i] = v;
+        un = uc;
+        uc = ud;
       }
-      s_v[i] = v;
     }
   }
   __syncthreads();
 
   // residual f - A v on [x0, x0+BX] x [y0, y0+BY]
   {
-    Walk<RW> w(tid);
-    for (int i = tid; i < RW * RH; i += NT, w.next(NT)) {
-      const int tx = w.x + 1, ty = w.y + 1;    // position in the v tile
-      C r = zc;
-      if (!CHECK || (x0 + w.x < N && y0 + w.y < N)) {
-        const int j = ty * VW + tx;
-        C D, nb;
-        if (FAST) {
-          D = kconst ? Dk : csub(d0, cscale(L.beta, s_k[j]));
-          nb = cmul(c0, cadd(cadd(s_v[j - 1], s_v[j + 1]), cadd(s_v[j - VW], s_v[j + VW])));
-        } else {
-          D = csub(cadd(s_cx[VW + tx], s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[j]));
-          nb = cmul(s_cx[tx], s_v[j - 1]);
-          nb = cfma(s_cx[2 * VW + tx], s_v[j + 1], nb);
-          nb = cfma(s_cy[ty], s_v[j - VW], nb);
-          nb = cfma(s_cy[2 * VH + ty], s_v[j + VW], nb);
+    constexpr int NS = NT / RW;
+    const int rx = tid % RW, sg = tid / RW;
+    if (sg < NS) {
+      const int q0 = sg * RH / NS, q1 = (sg + 1) * RH / NS;
+      const int tx = rx + 1;                     // column in the v tile
+      const bool colin = !CHECK || (x0 + rx < N);
+      C clo = zc, cdg = zc, cup = zc;
+      if (!FAST) { clo = s_cx[tx]; cdg = s_cx[VW + tx]; cup = s_cx[2 * VW + tx]; }
+      const C *col = s_v + tx;
+      C vn = col[q0 * VW], vc = col[(q0 + 1) * VW];
+      for (int ry = q0; ry < q1; ++ry) {
+        const int ty = ry + 1;
+        const int j = ty * VW;
+        const C vd = col[j + VW], vl = col[j - 1], vr = col[j + 1];
+        C r = zc;
+        if (colin && (!CHECK || y0 + ry < N)) {
+          C D, nb;
+          if (FAST) {
+            D = kconst ? Dk : csub(d0, cscale(L.beta, s_k[j + tx]));
+            nb = cmul(c0, cadd(cadd(vl, vr), cadd(vn, vd)));
+          } else {
+            D = csub(cadd(cdg, s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[j + tx]));
+            nb = cmul(clo, vl);
+            nb = cfma(cup, vr, nb);
+            nb = cfma(s_cy[ty], vn, nb);
+            nb = cfma(s_cy[2 * VH + ty], vd, nb);
+          }
+          r = cadd(csub(s_f[j + tx], cmul(D, vc)), nb);
         }
-        r = cadd(csub(s_f[j], cmul(D, s_v[j])), nb);
+        s_r[ry * RW + rx] = r;
+        vn = vc;
+        vc = vd;
       }
-      s_r[i] = r;
     }
   }
   __syncthreads();
@@ -347,36 +376,51 @@ __device__ __forceinline__ void up_body(
     }
   }
   __syncthreads();
-  // u' = w + omega D^{-1}(f - A w) on the tile
+  // u' = w + omega D^{-1}(f - A w) on the tile (column-segment mapping)
   const C c0 = FAST ? L.c0 : zc;
   const C d0 = FAST ? cscale(c0, R(4)) : zc;
   const C Dk = FAST ? csub(d0, cscale(L.beta, kc)) : zc;
-  const C Dkinv = FAST ? crcp(Dk) : zc;
-  const C *fo = fb + y0 * N + x0;
-  const R *ko = L.k2 + y0 * N + x0;
-  C *oo = ob + y0 * N + x0;
-  Walk<BX> w(tid);
-  for (int i = tid; i < BX * BY; i += NT, w.next(NT)) {
-    const int lx = w.x, ly = w.y;
-    if (CHECK && (x0 + lx >= N || y0 + ly >= N)) continue;
-    const int j = (ly + 1) * WW + lx + 1;
-    const int g = ly * N + lx;
-    C D, Dinv, nb;
-    if (FAST) {
-      if (kconst) { D = Dk; Dinv = Dkinv; }
-      else { D = csub(d0, cscale(L.beta, ko[g])); Dinv = crcp(D); }
-      nb = cmul(c0, cadd(cadd(s_w[j - 1], s_w[j + 1]), cadd(s_w[j - WW], s_w[j + WW])));
-    } else {
-      const int tx = lx + 1, ty = ly + 1;
-      D = csub(cadd(s_cx[WW + tx], s_cy[WH + ty]), cscale(L.beta, kconst ? kc : ko[g]));
-      Dinv = crcp(D);
-      nb = cmul(s_cx[tx], s_w[j - 1]);
-      nb = cfma(s_cx[2 * WW + tx], s_w[j + 1], nb);
-      nb = cfma(s_cy[ty], s_w[j - WW], nb);
-      nb = cfma(s_cy[2 * WH + ty], s_w[j + WW], nb);
+  const C Wk = FAST ? cmul(omega, crcp(Dk)) : zc;
+  {
+    constexpr int NS = NT / BX;
+    const int lx = tid % BX, sg = tid / BX;
+    if (sg < NS) {
+      const int q0 = sg * BY / NS, q1 = (sg + 1) * BY / NS;
+      const int tx = lx + 1;
+      const bool colin = !CHECK || (x0 + lx < N);
+      C clo = zc, cdg = zc, cup = zc;
+      if (!FAST) { clo = s_cx[tx]; cdg = s_cx[WW + tx]; cup = s_cx[2 * WW + tx]; }
+      const C *col = s_w + tx;
+      const C *fo = fb + y0 * N + x0 + lx;
+      const R *ko = L.k2 + y0 * N + x0 + lx;
+      C *oo = ob + y0 * N + x0 + lx;
+      C wn = col[q0 * WW], wc = col[(q0 + 1) * WW];
+      for (int ly = q0; ly < q1; ++ly) {
+        const int j = (ly + 1) * WW;
+        const C wd = col[j + WW], wl = col[j - 1], wr = col[j + 1];
+        if (colin && (!CHECK || y0 + ly < N)) {
+          const int g = ly * N;
+          C D, Wd, nb;
+          if (FAST) {
+            if (kconst) { D = Dk; Wd = Wk; }
+            else { D = csub(d0, cscale(L.beta, ko[g])); Wd = cmul(omega, crcp(D)); }
+            nb = cmul(c0, cadd(cadd(wl, wr), cadd(wn, wd)));
+          } else {
+            const int ty = ly + 1;
+            D = csub(cadd(cdg, s_cy[WH + ty]), cscale(L.beta, kconst ? kc : ko[g]));
+            Wd = cmul(omega, crcp(D));
+            nb = cmul(clo, wl);
+            nb = cfma(cup, wr, nb);
+            nb = cfma(s_cy[ty], wn, nb);
+            nb = cfma(s_cy[2 * WH + ty], wd, nb);
+          }
+          const C r = cadd(csub(fo[g], cmul(D, wc)), nb);
+          oo[g] = cadd(wc, cmul(Wd, r));
+        }
+        wn = wc;
+        wc = wd;
+      }
     }
-    const C r = cadd(csub(fo[g], cmul(D, s_w[j])), nb);
-    oo[g] = cadd(s_w[j], cmul(cmul(omega, r), Dinv));
   }
 }
 
