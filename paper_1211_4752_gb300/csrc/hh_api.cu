@@ -60,7 +60,9 @@ template <typename R> struct Work {
 
 struct LevelHost {
   int n = 0, N = 0;
-  size_t pts = 0;
+  size_t pts = 0;       // interior points (N^dim)
+  int P = 0;            // row pitch of the level's arrays (n = N + 1)
+  long long S = 0;      // elements per right-hand side (N^(dim-1) rows of P)
   double2 *coef64[2] = {nullptr, nullptr};  // [fwd/adj] dim*3*N
   float2 *coef32[2] = {nullptr, nullptr};
   double2 beta64[2];
@@ -167,11 +169,28 @@ void lap1d(int n_l, double a, double b, double gamma, std::vector<cd> &lo,
 template <typename R> LevelK<R> levelk(const hh_handle *h, int l, int dir);
 template <> LevelK<double> levelk<double>(const hh_handle *h, int l, int dir) {
   const LevelHost &v = h->lv[l];
-  return LevelK<double>{v.N, v.coef64[dir], v.beta64[dir], v.k2_64, v.ulo[dir], v.uhi[dir], v.c0_64[dir]};
+  return LevelK<double>{v.N, v.P, v.S, v.P, v.coef64[dir], v.beta64[dir], v.k2_64,
+                        v.ulo[dir], v.uhi[dir], v.c0_64[dir]};
 }
 template <> LevelK<float> levelk<float>(const hh_handle *h, int l, int dir) {
   const LevelHost &v = h->lv[l];
-  return LevelK<float>{v.N, v.coef32[dir], v.beta32[dir], v.k2_32, v.ulo[dir], v.uhi[dir], v.c0_32[dir]};
+  return LevelK<float>{v.N, v.P, v.S, v.P, v.coef32[dir], v.beta32[dir], v.k2_32,
+                       v.ulo[dir], v.uhi[dir], v.c0_32[dir]};
+}
+// the same level operator on dense caller arrays (row pitch N)
+template <typename R> LevelK<R> levelk_dense(const hh_handle *h, int l, int dir) {
+  LevelK<R> K = levelk<R>(h, l, dir);
+  K.P = K.N;
+  K.S = (long long)h->lv[l].pts;
+  return K;
+}
+Lay lay_of(const hh_handle *h, int l) {
+  const LevelHost &v = h->lv[l];
+  return Lay{v.N, v.P, v.S};
+}
+Lay lay_dense(const hh_handle *h, int l) {
+  const LevelHost &v = h->lv[l];
+  return Lay{v.N, v.N, (long long)v.pts};
 }
 template <typename R> Work<R> &work(hh_handle *h);
 template <> Work<double> &work<double>(hh_handle *h) { return h->w64; }
@@ -217,10 +236,10 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
       }
       in = out;
     }
-    launch_resid_restrict<R, DIM>(K, W.u_pre[l], W.f[l], W.f[l + 1],
+    launch_resid_restrict<R, DIM>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
                                   cscal<R>(h, l, dir), batch, st, s);
   }
-  launch_coarse_solve<R>(h->lu[dir], h->piv[dir], h->m, W.f[L - 1],
+  launch_coarse_solve<R, DIM>(h->lu[dir], h->piv[dir], lay_of(h, L - 1), W.f[L - 1],
                          W.u_post[L - 1], batch, st, s);
   for (int l = L - 2; l >= 0; --l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
@@ -228,7 +247,7 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
     for (int j = 0; j < h->opt.nu2; ++j) {
       typename Cx<R>::T *out = ((h->opt.nu2 - 1 - j) % 2 == 0) ? W.u_post[l] : W.tmp[l];
       if (j == 0)
-        launch_correct_smooth<R, DIM>(K, W.u_pre[l], W.u_post[l + 1], W.f[l],
+        launch_correct_smooth<R, DIM>(K, W.u_pre[l], W.u_post[l + 1], lay_of(h, l + 1), W.f[l],
                                       out, om, batch, st, s);
       else
         launch_smooth<R, DIM>(K, in, ZERO_NONE, W.f[l], out, om, batch, st,
@@ -300,14 +319,14 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
     const CheckCtx chk = norm ? check_ctx<R>(h, check, cond) : CheckCtx{};
     launch_down2d<R>(h->variant[l], K, l == 0 ? W.u_post[0] : nullptr,
                      l == 0 ? zero0 : ZERO_ALL, W.f[l], W.u_pre[l], W.f[l + 1],
-                     cscal<R>(h, l, dir), om, h->kconst, batch, st,
+                     cscal<R>(h, l, dir), om, h->kconst, lay_of(h, l + 1), batch, st,
                      norm ? h->partials : nullptr, chk, s);
   }
   launch_tail2d<R>(tail_args<R>(h, dir), batch, st, s);
   for (int l = T - 1; l >= 0; --l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
     launch_up2d<R>(h->variant[l], K, W.u_pre[l], W.u_post[l + 1], W.f[l], W.u_post[l],
-                   om, h->kconst, batch, st, s);
+                   om, h->kconst, lay_of(h, l + 1), batch, st, s);
   }
 }
 
@@ -462,26 +481,51 @@ hh_status set_params(hh_handle *h, int batch, double tol, cudaStream_t s) {
   return HH_OK;
 }
 
-// Core solve.  rhs: device complex128 (copied to w64.f[0] unless it is that
-// buffer); guess: device or NULL; out: device.  dir 1 = adjoint.
+// Rows of N points per right-hand side on level l (N^(dim-1)).
+size_t rows_of(const hh_handle *h, int l) {
+  const int N = h->lv[l].N;
+  return h->dim == 2 ? (size_t)N : (size_t)N * N;
+}
+
+// Copy a dense caller array (batch right-hand sides of level l) into a
+// pitched library array, or back.  kind: cudaMemcpyKind of the transfer.
+hh_status copy_to_pitched(const hh_handle *h, int l, void *dst, const void *src, int batch,
+                          size_t esize, cudaMemcpyKind kind, cudaStream_t s) {
+  const LevelHost &v = h->lv[l];
+  HH_CK(cudaMemcpy2DAsync(dst, (size_t)v.P * esize, src, (size_t)v.N * esize,
+                          (size_t)v.N * esize, rows_of(h, l) * batch, kind, s));
+  return HH_OK;
+}
+hh_status copy_to_dense(const hh_handle *h, int l, void *dst, const void *src, int batch,
+                        size_t esize, cudaMemcpyKind kind, cudaStream_t s) {
+  const LevelHost &v = h->lv[l];
+  HH_CK(cudaMemcpy2DAsync(dst, (size_t)v.N * esize, src, (size_t)v.P * esize,
+                          (size_t)v.N * esize, rows_of(h, l) * batch, kind, s));
+  return HH_OK;
+}
+
+// Core solve.  rhs: dense device complex128 caller array, or NULL when the
+// right-hand side is already staged in w64.f[0]; guess: dense device array,
+// or the staged iterate buffer itself, or NULL (u_0 = 0); out: dense device
+// array.  dir 1 = adjoint.
 hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
                      const double2 *guess, double2 *out, int batch, double tol,
                      hh_solve_info *info, cudaStream_t s) {
-  const size_t pts = h->lv[0].pts;
-  const size_t bytes = pts * batch * sizeof(double2);
-  if (rhs != h->w64.f[0])
-    HH_CK(cudaMemcpyAsync(h->w64.f[0], rhs, bytes, cudaMemcpyDeviceToDevice, s));
+  const Lay l0 = lay_of(h, 0), d0 = lay_dense(h, 0);
+  const size_t pbytes = (size_t)l0.S * batch * sizeof(double2);
+  if (rhs)
+    HH_TRY(copy_to_pitched(h, 0, h->w64.f[0], rhs, batch, sizeof(double2), cudaMemcpyDeviceToDevice, s));
   HH_TRY(set_params(h, batch, tol, s));
-  launch_norm2(h->w64.f[0], pts, batch, h->partials, h->nparts, s);
+  launch_norm2(h->w64.f[0], (size_t)l0.S, batch, h->partials, h->nparts, s);
   launch_state_init(h->st, h->partials, h->params, h->flag, s);
 
   if (h->opt.precision == HH_FP64) {
     if (guess && guess != h->w64.u_post[0])
-      HH_CK(cudaMemcpyAsync(h->w64.u_post[0], guess, bytes, cudaMemcpyDeviceToDevice, s));
+      HH_TRY(copy_to_pitched(h, 0, h->w64.u_post[0], guess, batch, sizeof(double2), cudaMemcpyDeviceToDevice, s));
     else if (!guess)
-      HH_CK(cudaMemsetAsync(h->w64.u_post[0], 0, bytes, s));
+      HH_CK(cudaMemsetAsync(h->w64.u_post[0], 0, pbytes, s));
     HH_TRY(run_loop(h, HH_FP64, dir, batch, s));
-    launch_finish(h->st, h->w64.u_post[0], out, pts, batch, s);
+    launch_finish(h->st, h->w64.u_post[0], l0, out, d0, h->dim, batch, s);
     HH_CK(cudaGetLastError());
     return read_info(h, batch, info, s);
   }
@@ -489,7 +533,7 @@ hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
   // MIXED: FP64 refinement around complex64 cycles.
   int cur = 0;
   if (guess && guess != h->u64[0])
-    HH_CK(cudaMemcpyAsync(h->u64[0], guess, bytes, cudaMemcpyDeviceToDevice, s));
+    HH_TRY(copy_to_pitched(h, 0, h->u64[0], guess, batch, sizeof(double2), cudaMemcpyDeviceToDevice, s));
   refine_dispatch(h, dir, h->u64[0], guess ? 0 : 1, nullptr, h->u64[1], batch, s);
   cur = 1;
   launch_check_outer(h->st, h->partials, h->params, h->flag, s);
@@ -502,7 +546,7 @@ hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
     cur = 1 - cur;
     launch_check_outer(h->st, h->partials, h->params, h->flag, s);
   }
-  launch_finish(h->st, h->u64[cur], out, pts, batch, s);
+  launch_finish(h->st, h->u64[cur], l0, out, d0, h->dim, batch, s);
   HH_CK(cudaGetLastError());
   return read_info(h, batch, info, s);
 }
@@ -522,10 +566,11 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
     if (kernel == 0)
       launch_down2d<R>(h->variant[level], K, W.u_post[level], ZERO_NONE, W.f[level],
                        W.u_pre[level], W.f[level + 1], cscal<R>(h, level, 0), om, h->kconst,
-                       batch, nullptr, level == 0 ? h->partials : nullptr, CheckCtx{}, s);
+                       lay_of(h, level + 1), batch, nullptr, level == 0 ? h->partials : nullptr,
+                       CheckCtx{}, s);
     else
       launch_up2d<R>(h->variant[level], K, W.u_pre[level], W.u_post[level + 1], W.f[level],
-                     W.u_post[level], om, h->kconst, batch, nullptr, s);
+                     W.u_post[level], om, h->kconst, lay_of(h, level + 1), batch, nullptr, s);
     return;
   }
   if (kernel == 0) {
@@ -533,11 +578,13 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
     if (two) launch_smooth<R, 2>(K, W.u_post[level], ZERO_NONE, W.f[level], W.u_pre[level], om, batch, nullptr, parts, h->nparts, s);
     else launch_smooth<R, 3>(K, W.u_post[level], ZERO_NONE, W.f[level], W.u_pre[level], om, batch, nullptr, parts, h->nparts, s);
   } else if (kernel == 1) {
-    if (two) launch_resid_restrict<R, 2>(K, W.u_pre[level], W.f[level], W.f[level + 1], cscal<R>(h, level, 0), batch, nullptr, s);
-    else launch_resid_restrict<R, 3>(K, W.u_pre[level], W.f[level], W.f[level + 1], cscal<R>(h, level, 0), batch, nullptr, s);
+    const Lay lc = lay_of(h, level + 1);
+    if (two) launch_resid_restrict<R, 2>(K, W.u_pre[level], W.f[level], W.f[level + 1], lc, cscal<R>(h, level, 0), batch, nullptr, s);
+    else launch_resid_restrict<R, 3>(K, W.u_pre[level], W.f[level], W.f[level + 1], lc, cscal<R>(h, level, 0), batch, nullptr, s);
   } else {
-    if (two) launch_correct_smooth<R, 2>(K, W.u_pre[level], W.u_post[level + 1], W.f[level], W.u_post[level], om, batch, nullptr, s);
-    else launch_correct_smooth<R, 3>(K, W.u_pre[level], W.u_post[level + 1], W.f[level], W.u_post[level], om, batch, nullptr, s);
+    const Lay lc = lay_of(h, level + 1);
+    if (two) launch_correct_smooth<R, 2>(K, W.u_pre[level], W.u_post[level + 1], lc, W.f[level], W.u_post[level], om, batch, nullptr, s);
+    else launch_correct_smooth<R, 3>(K, W.u_pre[level], W.u_post[level + 1], lc, W.f[level], W.u_post[level], om, batch, nullptr, s);
   }
 }
 
@@ -593,9 +640,10 @@ template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, 
   for (int v = 0; v < kNumTileVariants; ++v) {
     auto run = [&]() {
       launch_down2d<R>(v, K, W.u_post[l], ZERO_NONE, W.f[l], W.u_pre[l], W.f[l + 1],
-                       cscal<R>(h, l, 0), om, h->kconst, 1, nullptr, nullptr, CheckCtx{}, s);
+                       cscal<R>(h, l, 0), om, h->kconst, lay_of(h, l + 1), 1, nullptr, nullptr,
+                       CheckCtx{}, s);
       launch_up2d<R>(v, K, W.u_pre[l], W.u_post[l + 1], W.f[l], W.u_post[l], om,
-                     h->kconst, 1, nullptr, s);
+                     h->kconst, lay_of(h, l + 1), 1, nullptr, s);
     };
     run();
     HH_CK(cudaEventRecord(e0, s));
@@ -626,7 +674,7 @@ hh_status autotune(hh_handle *h, cudaStream_t s) {
   }
   // the tuning runs overwrote workspace: clear it again
   for (int l = 0; l < h->L; ++l) {
-    const size_t np = h->lv[l].pts * (size_t)h->max_batch;
+    const size_t np = (size_t)h->lv[l].S * h->max_batch;
     for (double2 *p : {h->w64.u_pre[l], h->w64.u_post[l], h->w64.f[l]})
       HH_CK(cudaMemsetAsync(p, 0, np * sizeof(double2), s));
     for (float2 *p : {h->w32.u_pre[l], h->w32.u_post[l], h->w32.f[l]})
@@ -665,6 +713,8 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
     v.n = n >> l;
     v.N = v.n - 1;
     v.pts = dim == 2 ? (size_t)v.N * v.N : (size_t)v.N * v.N * v.N;
+    v.P = v.n;  // power of two: 16-byte aligned rows, zero padding column
+    v.S = (long long)(dim == 2 ? (size_t)v.N : (size_t)v.N * v.N) * v.P;
     const double theta = sh.theta ? sh.theta[l] : l * dtheta;
     cd alpha(1.0, 0.0), beta(1.0, 0.0);
     if (sh.form == HH_FORM_CSL) beta = std::polar(1.0, theta);
@@ -736,23 +786,25 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
     v.c32[0] = make_float2((float)c.real(), (float)c.imag());
     v.c32[1] = make_float2((float)cc.real(), (float)cc.imag());
 
-    HH_TRY(dev_alloc_n(h, &v.k2_64, v.pts));
-    HH_TRY(dev_alloc_n(h, &v.k2_32, v.pts));
+    HH_TRY(dev_alloc_n(h, &v.k2_64, (size_t)v.S));
+    HH_TRY(dev_alloc_n(h, &v.k2_32, (size_t)v.S));
     if (l == 0) {
       if (k2_dev) {
-        HH_CK(cudaMemcpyAsync(v.k2_64, k2_dev, v.pts * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        HH_CK(cudaMemsetAsync(v.k2_64, 0, (size_t)v.S * sizeof(double), s));
+        HH_TRY(copy_to_pitched(h, 0, v.k2_64, k2_dev, 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
       } else {
-        std::vector<double> kc(v.pts, k2_const);
-        HH_CK(cudaMemcpyAsync(v.k2_64, kc.data(), v.pts * sizeof(double), cudaMemcpyHostToDevice, s));
+        std::vector<double> kc((size_t)v.S, k2_const);
+        HH_CK(cudaMemcpyAsync(v.k2_64, kc.data(), (size_t)v.S * sizeof(double), cudaMemcpyHostToDevice, s));
         HH_CK(cudaStreamSynchronize(s));
       }
     } else {
-      if (dim == 2) launch_inject<2>(h->lv[l - 1].k2_64, h->lv[l - 1].N, v.k2_64, v.N, s);
-      else launch_inject<3>(h->lv[l - 1].k2_64, h->lv[l - 1].N, v.k2_64, v.N, s);
+      HH_CK(cudaMemsetAsync(v.k2_64, 0, (size_t)v.S * sizeof(double), s));
+      if (dim == 2) launch_inject<2>(h->lv[l - 1].k2_64, lay_of(h, l - 1), v.k2_64, lay_of(h, l), s);
+      else launch_inject<3>(h->lv[l - 1].k2_64, lay_of(h, l - 1), v.k2_64, lay_of(h, l), s);
     }
-    launch_to_float(v.k2_64, v.k2_32, v.pts, s);
+    launch_to_float(v.k2_64, v.k2_32, (size_t)v.S, s);
 
-    const size_t np = v.pts * (size_t)B;
+    const size_t np = (size_t)v.S * B;
     HH_TRY(dev_alloc_n(h, &h->w64.u_pre[l], np));
     HH_TRY(dev_alloc_n(h, &h->w64.u_post[l], np));
     HH_TRY(dev_alloc_n(h, &h->w64.f[l], np));
@@ -770,7 +822,7 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
     for (float2 *p : {h->w32.u_pre[l], h->w32.u_post[l], h->w32.f[l]})
       HH_CK(cudaMemsetAsync(p, 0, np * sizeof(float2), s));
   }
-  const size_t np0 = h->lv[0].pts * (size_t)B;
+  const size_t np0 = (size_t)h->lv[0].S * B;
   HH_TRY(dev_alloc_n(h, &h->u64[0], np0));
   HH_TRY(dev_alloc_n(h, &h->u64[1], np0));
   HH_CK(cudaMemsetAsync(h->u64[0], 0, np0 * sizeof(double2), s));
@@ -796,7 +848,7 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
       h->fused = 1;
       h->tail0 = t0;
       for (int l = t0; l < L; ++l) {
-        const size_t np = h->lv[l].pts * (size_t)B;
+        const size_t np = (size_t)h->lv[l].S * B;
         if (!h->w64.tmp[l]) {
           HH_TRY(dev_alloc_n(h, &h->w64.tmp[l], np));
           HH_CK(cudaMemsetAsync(h->w64.tmp[l], 0, np * sizeof(double2), s));
@@ -972,17 +1024,18 @@ hh_status hh_solve_host(hh_handle *h, const void *rhs_host, void *u_host,
   HH_TRY(ensure_device(h));
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = h->lv[0].pts * batch * sizeof(double2);
-  HH_CK(cudaMemcpyAsync(h->w64.f[0], rhs_host, bytes, cudaMemcpyHostToDevice, s));
+  HH_TRY(copy_to_pitched(h, 0, h->w64.f[0], rhs_host, batch, sizeof(double2), cudaMemcpyHostToDevice, s));
   // The guess goes straight into the buffer the solve iterates on; the
-  // result is staged in w64.u_pre[0], which the final copy-out no longer reads.
+  // dense result is staged in w64.u_pre[0], which the final copy-out no
+  // longer reads.
   const double2 *guess = nullptr;
   if (flags & HH_USE_GUESS) {
     double2 *target = h->opt.precision == HH_FP64 ? h->w64.u_post[0] : h->u64[0];
-    HH_CK(cudaMemcpyAsync(target, u_host, bytes, cudaMemcpyHostToDevice, s));
+    HH_TRY(copy_to_pitched(h, 0, target, u_host, batch, sizeof(double2), cudaMemcpyHostToDevice, s));
     guess = target;
   }
   double2 *stage = h->w64.u_pre[0];
-  const hh_status st = solve_core(h, 0, h->w64.f[0], guess, stage, batch, tol, info, s);
+  const hh_status st = solve_core(h, 0, nullptr, guess, stage, batch, tol, info, s);
   if (st != HH_OK && st != HH_ERR_NOT_CONVERGED && st != HH_ERR_DIVERGED) return st;
   HH_CK(cudaMemcpyAsync(u_host, stage, bytes, cudaMemcpyDeviceToHost, s));
   HH_CK(cudaStreamSynchronize(s));
@@ -1010,7 +1063,7 @@ hh_status hh_apply(hh_handle *h, int level, int adjoint, const void *x_dev,
   if (level < 0 || level >= h->L) return fail(HH_ERR_ARG, "bad level");
   if (!x_dev || !y_dev) return fail(HH_ERR_ARG, "null pointer");
   HH_TRY(ensure_device(h));
-  const LevelK<double> K = levelk<double>(h, level, adjoint ? 1 : 0);
+  const LevelK<double> K = levelk_dense<double>(h, level, adjoint ? 1 : 0);
   if (h->dim == 2)
     launch_apply<double, 2>(K, (const double2 *)x_dev, (double2 *)y_dev, batch, (cudaStream_t)stream);
   else
@@ -1028,19 +1081,19 @@ hh_status hh_cycles(hh_handle *h, const void *rhs_dev, void *u_dev, int batch,
   if (ncycles < 0) return fail(HH_ERR_ARG, "ncycles must be >= 0");
   HH_TRY(ensure_device(h));
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t n = h->lv[0].pts * batch;
   if (h->opt.precision == HH_FP64) {
-    HH_CK(cudaMemcpyAsync(h->w64.f[0], rhs_dev, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-    HH_CK(cudaMemcpyAsync(h->w64.u_post[0], u_dev, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    HH_TRY(copy_to_pitched(h, 0, h->w64.f[0], rhs_dev, batch, sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    HH_TRY(copy_to_pitched(h, 0, h->w64.u_post[0], u_dev, batch, sizeof(double2), cudaMemcpyDeviceToDevice, s));
     for (int k = 0; k < ncycles; ++k)
       cycle_dispatch<double>(h, 0, batch, ZERO_NONE, CHECK_NONE, 0, s);
-    HH_CK(cudaMemcpyAsync(u_dev, h->w64.u_post[0], n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    HH_TRY(copy_to_dense(h, 0, u_dev, h->w64.u_post[0], batch, sizeof(double2), cudaMemcpyDeviceToDevice, s));
   } else {
-    launch_c128_to_c64((const double2 *)rhs_dev, h->w32.f[0], n, s);
-    launch_c128_to_c64((const double2 *)u_dev, h->w32.u_post[0], n, s);
+    const Lay l0 = lay_of(h, 0), d0 = lay_dense(h, 0);
+    launch_c128_to_c64((const double2 *)rhs_dev, d0, h->w32.f[0], l0, h->dim, batch, s);
+    launch_c128_to_c64((const double2 *)u_dev, d0, h->w32.u_post[0], l0, h->dim, batch, s);
     for (int k = 0; k < ncycles; ++k)
       cycle_dispatch<float>(h, 0, batch, ZERO_NONE, CHECK_NONE, 0, s);
-    launch_c64_to_c128(h->w32.u_post[0], (double2 *)u_dev, n, s);
+    launch_c64_to_c128(h->w32.u_post[0], l0, (double2 *)u_dev, d0, h->dim, batch, s);
   }
   HH_CK(cudaGetLastError());
   return HH_OK;
@@ -1056,7 +1109,7 @@ hh_status hh_smooth(hh_handle *h, int level, const void *u_in_dev,
   if (!u_in_dev || !f_dev || !u_out_dev) return fail(HH_ERR_ARG, "null pointer");
   if (u_in_dev == u_out_dev) return fail(HH_ERR_ARG, "u_in and u_out must differ");
   HH_TRY(ensure_device(h));
-  const LevelK<double> K = levelk<double>(h, level, 0);
+  const LevelK<double> K = levelk_dense<double>(h, level, 0);
   const double2 om = h->omega64();
   if (h->dim == 2)
     launch_smooth<double, 2>(K, (const double2 *)u_in_dev, ZERO_NONE, (const double2 *)f_dev,
@@ -1077,14 +1130,15 @@ hh_status hh_residual_restrict(hh_handle *h, int level, const void *u_dev,
   if (level < 0 || level + 1 >= h->L) return fail(HH_ERR_ARG, "bad level");
   if (!u_dev || !f_dev || !fc_dev) return fail(HH_ERR_ARG, "null pointer");
   HH_TRY(ensure_device(h));
-  const LevelK<double> K = levelk<double>(h, level, 0);
+  const LevelK<double> K = levelk_dense<double>(h, level, 0);
   const double2 c = h->lv[level].c64[0];
+  const Lay lc = lay_dense(h, level + 1);
   if (h->dim == 2)
     launch_resid_restrict<double, 2>(K, (const double2 *)u_dev, (const double2 *)f_dev,
-                                     (double2 *)fc_dev, c, batch, nullptr, (cudaStream_t)stream);
+                                     (double2 *)fc_dev, lc, c, batch, nullptr, (cudaStream_t)stream);
   else
     launch_resid_restrict<double, 3>(K, (const double2 *)u_dev, (const double2 *)f_dev,
-                                     (double2 *)fc_dev, c, batch, nullptr, (cudaStream_t)stream);
+                                     (double2 *)fc_dev, lc, c, batch, nullptr, (cudaStream_t)stream);
   HH_CK(cudaGetLastError());
   return HH_OK;
 }
@@ -1099,14 +1153,15 @@ hh_status hh_correct_smooth(hh_handle *h, int level, const void *u_in_dev,
   if (!u_in_dev || !e_dev || !f_dev || !u_out_dev) return fail(HH_ERR_ARG, "null pointer");
   if (u_in_dev == u_out_dev) return fail(HH_ERR_ARG, "u_in and u_out must differ");
   HH_TRY(ensure_device(h));
-  const LevelK<double> K = levelk<double>(h, level, 0);
+  const LevelK<double> K = levelk_dense<double>(h, level, 0);
   const double2 om = h->omega64();
+  const Lay lc = lay_dense(h, level + 1);
   if (h->dim == 2)
-    launch_correct_smooth<double, 2>(K, (const double2 *)u_in_dev, (const double2 *)e_dev,
+    launch_correct_smooth<double, 2>(K, (const double2 *)u_in_dev, (const double2 *)e_dev, lc,
                                      (const double2 *)f_dev, (double2 *)u_out_dev, om, batch,
                                      nullptr, (cudaStream_t)stream);
   else
-    launch_correct_smooth<double, 3>(K, (const double2 *)u_in_dev, (const double2 *)e_dev,
+    launch_correct_smooth<double, 3>(K, (const double2 *)u_in_dev, (const double2 *)e_dev, lc,
                                      (const double2 *)f_dev, (double2 *)u_out_dev, om, batch,
                                      nullptr, (cudaStream_t)stream);
   HH_CK(cudaGetLastError());
@@ -1120,8 +1175,12 @@ hh_status hh_coarse_solve(hh_handle *h, const void *f_dev, void *e_dev,
   HH_TRY(check_batch(h, batch));
   if (!f_dev || !e_dev) return fail(HH_ERR_ARG, "null pointer");
   HH_TRY(ensure_device(h));
-  launch_coarse_solve<double>(h->lu[0], h->piv[0], h->m, (const double2 *)f_dev,
-                              (double2 *)e_dev, batch, nullptr, (cudaStream_t)stream);
+  if (h->dim == 2)
+    launch_coarse_solve<double, 2>(h->lu[0], h->piv[0], lay_dense(h, h->L - 1), (const double2 *)f_dev,
+                                   (double2 *)e_dev, batch, nullptr, (cudaStream_t)stream);
+  else
+    launch_coarse_solve<double, 3>(h->lu[0], h->piv[0], lay_dense(h, h->L - 1), (const double2 *)f_dev,
+                                   (double2 *)e_dev, batch, nullptr, (cudaStream_t)stream);
   HH_CK(cudaGetLastError());
   return HH_OK;
 }

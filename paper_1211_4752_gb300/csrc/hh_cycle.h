@@ -61,14 +61,14 @@ template <typename R>
 void launch_down2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *u_in,
                    int zero_mode, const typename Cx<R>::T *f, typename Cx<R>::T *v_out,
                    typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
-                   int kconst, int batch, const SolveState *st, double *partials,
-                   const CheckCtx &chk, cudaStream_t s);
+                   int kconst, const Lay &lc, int batch, const SolveState *st,
+                   double *partials, const CheckCtx &chk, cudaStream_t s);
 
 template <typename R>
 void launch_up2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *v_in,
                  const typename Cx<R>::T *e, const typename Cx<R>::T *f,
-                 typename Cx<R>::T *u_out, typename Cx<R>::T omega, int kconst, int batch,
-                 const SolveState *st, cudaStream_t s);
+                 typename Cx<R>::T *u_out, typename Cx<R>::T omega, int kconst, const Lay &lc,
+                 int batch, const SolveState *st, cudaStream_t s);
 
 template <typename R>
 void launch_tail2d(const TailArgs<R> &a, int batch, const SolveState *st, cudaStream_t s);

@@ -17,25 +17,25 @@ template <typename R, int BX, int BY>
 void down_one(const LevelK<R> &L, const typename Cx<R>::T *u_in, int zero_mode,
               const typename Cx<R>::T *f, typename Cx<R>::T *v_out,
               typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
-              int kconst, int batch, const SolveState *st, double *partials,
+              int kconst, const Lay &lc, int batch, const SolveState *st, double *partials,
               const CheckCtx &chk, cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
   if (chk.cond)
     k_down2d<R, BX, BY, true><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
-        L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, st, partials, chk);
+        L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, st, partials, chk);
   else
     k_down2d<R, BX, BY, false><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
-        L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, st, partials, chk);
+        L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, st, partials, chk);
 }
 
 template <typename R, int BX, int BY>
 void up_one(const LevelK<R> &L, const typename Cx<R>::T *v_in,
             const typename Cx<R>::T *e, const typename Cx<R>::T *f,
             typename Cx<R>::T *u_out, typename Cx<R>::T omega, int kconst,
-            int batch, const SolveState *st, cudaStream_t s) {
+            const Lay &lc, int batch, const SolveState *st, cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
   k_up2d<R, BX, BY><<<grid, 256, Up2D<R, BX, BY>::smem, s>>>(L, v_in, e, f, u_out,
-                                                             omega, kconst, st);
+                                                             omega, kconst, lc, st);
 }
 
 // Dynamic shared memory limits, and the maximum shared-memory carveout for
@@ -109,10 +109,12 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
   // stage everything once: the top right-hand side, every level's tables and
   // k^2, the coarsest LU factors (all loads independent: one round trip)
   {
-    const int N = A.lv[0].K.N;
-    const C *g = A.lv[0].f + (size_t)b * N * N;
+    const LevelK<R> &K0 = A.lv[0].K;
+    const int N = K0.N;
+    const C *g = A.lv[0].f + (size_t)b * K0.S;
     C *f = sm + A.off[0];
-    for (int p = tid; p < N * N; p += nt) f[p] = g[p];
+    WalkN w(tid, nt, N);
+    for (int p = tid; p < N * N; p += nt, w.next()) f[p] = g[w.y * K0.P + w.x];
   }
   for (int l = 0; l < A.nl; ++l) {
     const LevelK<R> &K = A.lv[l].K;
@@ -120,7 +122,8 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
     C *cf = sm + A.off[l] + 3 * N * N;
     for (int i = tid; i < 6 * N; i += nt) cf[i] = K.coef[i];
     R *kk = skk + A.koff[l];
-    for (int i = tid; i < N * N; i += nt) kk[i] = K.k2[i];
+    WalkN w(tid, nt, N);
+    for (int i = tid; i < N * N; i += nt, w.next()) kk[i] = K.k2[w.y * K.KP + w.x];
   }
   for (int i = tid; i < m * m; i += nt) slu[i] = A.lu[i];
   for (int i = tid; i < m; i += nt) spiv[i] = A.piv[i];
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
     {
       WalkN w(tid, nt, N);
       for (int p = tid; p < N * N; p += nt, w.next())
-        t[p] = cadd(v[p], prolong_at<R, 2>(e, Nc, w.x, w.y, 0));
+        t[p] = cadd(v[p], prolong_at<R, 2>(e, Lay{Nc, Nc, (long long)Nc * Nc}, w.x, w.y, 0));
     }
     __syncthreads();
     {
@@ -208,10 +211,12 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
     __syncthreads();
   }
   {
-    const int N = A.lv[0].K.N;
-    C *g = A.lv[0].u + (size_t)b * N * N;
+    const LevelK<R> &K0 = A.lv[0].K;
+    const int N = K0.N;
+    C *g = A.lv[0].u + (size_t)b * K0.S;
     const C *v = sm + A.off[0] + N * N;
-    for (int p = tid; p < N * N; p += nt) g[p] = v[p];
+    WalkN w(tid, nt, N);
+    for (int p = tid; p < N * N; p += nt, w.next()) g[w.y * K0.P + w.x] = v[p];
   }
 }
 
@@ -237,28 +242,28 @@ template <typename R>
 void launch_down2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *u_in,
                    int zero_mode, const typename Cx<R>::T *f, typename Cx<R>::T *v_out,
                    typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
-                   int kconst, int batch, const SolveState *st, double *partials,
-                   const CheckCtx &chk, cudaStream_t s) {
+                   int kconst, const Lay &lc, int batch, const SolveState *st,
+                   double *partials, const CheckCtx &chk, cudaStream_t s) {
   switch (variant) {
-    case 0: down_one<R, 58, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
-    case 1: down_one<R, 58, 32>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
-    case 2: down_one<R, 26, 32>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
-    case 3: down_one<R, 122, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
-    default: down_one<R, 26, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, batch, st, partials, chk, s); break;
+    case 0: down_one<R, 58, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, batch, st, partials, chk, s); break;
+    case 1: down_one<R, 58, 32>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, batch, st, partials, chk, s); break;
+    case 2: down_one<R, 26, 32>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, batch, st, partials, chk, s); break;
+    case 3: down_one<R, 122, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, batch, st, partials, chk, s); break;
+    default: down_one<R, 26, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, batch, st, partials, chk, s); break;
   }
 }
 
 template <typename R>
 void launch_up2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *v_in,
                  const typename Cx<R>::T *e, const typename Cx<R>::T *f,
-                 typename Cx<R>::T *u_out, typename Cx<R>::T omega, int kconst, int batch,
-                 const SolveState *st, cudaStream_t s) {
+                 typename Cx<R>::T *u_out, typename Cx<R>::T omega, int kconst, const Lay &lc,
+                 int batch, const SolveState *st, cudaStream_t s) {
   switch (variant) {
-    case 0: up_one<R, 58, 16>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
-    case 1: up_one<R, 58, 32>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
-    case 2: up_one<R, 26, 32>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
-    case 3: up_one<R, 122, 16>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
-    default: up_one<R, 26, 16>(L, v_in, e, f, u_out, omega, kconst, batch, st, s); break;
+    case 0: up_one<R, 58, 16>(L, v_in, e, f, u_out, omega, kconst, lc, batch, st, s); break;
+    case 1: up_one<R, 58, 32>(L, v_in, e, f, u_out, omega, kconst, lc, batch, st, s); break;
+    case 2: up_one<R, 26, 32>(L, v_in, e, f, u_out, omega, kconst, lc, batch, st, s); break;
+    case 3: up_one<R, 122, 16>(L, v_in, e, f, u_out, omega, kconst, lc, batch, st, s); break;
+    default: up_one<R, 26, 16>(L, v_in, e, f, u_out, omega, kconst, lc, batch, st, s); break;
   }
 }
 
@@ -271,11 +276,11 @@ void launch_tail2d(const TailArgs<R> &a, int batch, const SolveState *st, cudaSt
   template cudaError_t init_cycle2d<R>();                                                   \
   template void launch_down2d<R>(int, const LevelK<R> &, const Cx<R>::T *, int,             \
                                  const Cx<R>::T *, Cx<R>::T *, Cx<R>::T *, Cx<R>::T,        \
-                                 Cx<R>::T, int, int, const SolveState *, double *,          \
-                                 const CheckCtx &, cudaStream_t);                           \
+                                 Cx<R>::T, int, const Lay &, int, const SolveState *,       \
+                                 double *, const CheckCtx &, cudaStream_t);                 \
   template void launch_up2d<R>(int, const LevelK<R> &, const Cx<R>::T *, const Cx<R>::T *,  \
-                               const Cx<R>::T *, Cx<R>::T *, Cx<R>::T, int, int,            \
-                               const SolveState *, cudaStream_t);                           \
+                               const Cx<R>::T *, Cx<R>::T *, Cx<R>::T, int, const Lay &,    \
+                               int, const SolveState *, cudaStream_t);                      \
   template void launch_tail2d<R>(const TailArgs<R> &, int, const SolveState *, cudaStream_t);
 
 HH_INST_CYCLE2D(float)

@@ -70,7 +70,7 @@ __device__ __forceinline__ void down_body(
     const LevelK<R> &L, const typename Cx<R>::T *__restrict__ ub, bool zero,
     const typename Cx<R>::T *__restrict__ fb, typename Cx<R>::T *__restrict__ vb,
     typename Cx<R>::T *__restrict__ fcb, typename Cx<R>::T cs, typename Cx<R>::T omega,
-    int kconst, int x0, int y0, unsigned char *smem_raw, R &acc) {
+    int kconst, int x0, int y0, int Pc, unsigned char *smem_raw, R &acc) {
   using C = typename Cx<R>::T;
   using S = Down2D<R, BX, BY>;
   constexpr int UW = S::UW, UH = S::UH, VW = S::VW, VH = S::VH, RW = S::RW, RH = S::RH;
@@ -82,7 +82,7 @@ __device__ __forceinline__ void down_body(
   C *s_cy = s_cx + 3 * VW;     // [3][VH]
   R *s_k = reinterpret_cast<R *>(s_cy + 3 * VH);
   C *s_r = s_u;                // the residual reuses the staging of u
-  const int N = L.N, Nc = (N + 1) / 2 - 1;
+  const int N = L.N, Nc = (N + 1) / 2 - 1, P = L.P, KP = L.KP;
   const int tid = threadIdx.x;
   const C zc = czero<C>();
   const R kc = kconst ? L.k2[0] : R(0);
@@ -104,8 +104,8 @@ __device__ __forceinline__ void down_body(
     }
   }
   {
-    const C *fo = fb + (y0 - 1) * N + (x0 - 1);
-    const R *ko = L.k2 + (y0 - 1) * N + (x0 - 1);
+    const C *fo = fb + (y0 - 1) * P + (x0 - 1);
+    const R *ko = L.k2 + (y0 - 1) * KP + (x0 - 1);
     Walk<VW> w(tid);
     for (int i = tid; i < VW * VH; i += NT, w.next(NT)) {
       bool in = true;
@@ -113,13 +113,12 @@ __device__ __forceinline__ void down_body(
         const int gx = x0 - 1 + w.x, gy = y0 - 1 + w.y;
         in = gx >= 0 && gx < N && gy >= 0 && gy < N;
       }
-      const int o = w.y * N + w.x;
-      s_f[i] = in ? fo[o] : zc;
-      if (!kconst) s_k[i] = in ? ko[o] : R(0);
+      s_f[i] = in ? fo[w.y * P + w.x] : zc;
+      if (!kconst) s_k[i] = in ? ko[w.y * KP + w.x] : R(0);
     }
   }
   if (!zero) {
-    const C *uo = ub + (y0 - 2) * N + (x0 - 2);
+    const C *uo = ub + (y0 - 2) * P + (x0 - 2);
     Walk<UW> w(tid);
     for (int i = tid; i < UW * UH; i += NT, w.next(NT)) {
       bool in = true;
@@ -127,7 +126,7 @@ __device__ __forceinline__ void down_body(
         const int gx = x0 - 2 + w.x, gy = y0 - 2 + w.y;
         in = gx >= 0 && gx < N && gy >= 0 && gy < N;
       }
-      s_u[i] = in ? uo[w.y * N + w.x] : zc;
+      s_u[i] = in ? uo[w.y * P + w.x] : zc;
     }
   }
   __syncthreads();
@@ -153,7 +152,7 @@ __device__ __forceinline__ void down_body(
       const bool colown = tx >= 1 && tx <= BX;
       C clo = zc, cdg = zc, cup = zc;
       if (!FAST) { clo = s_cx[tx]; cdg = s_cx[VW + tx]; cup = s_cx[2 * VW + tx]; }
-      C *vo = vb + (y0 - 1) * N + gx;
+      C *vo = vb + (y0 - 1) * P + gx;
       const C *col = s_u + tx + 1;               // u tile column of this v column
       C un = zc, uc = zc;
       if (!zero) { un = col[r0 * UW]; uc = col[(r0 + 1) * UW]; }
@@ -191,7 +190,7 @@ __device__ __forceinline__ void down_body(
           }
           v = cadd(uc, cmul(Wd, r));
           if (colown && ty >= 1 && ty <= BY) {
-            vo[ty * N] = v;
+            vo[ty * P] = v;
             acc += r.x * r.x + r.y * r.y;
           }
         }
@@ -245,7 +244,7 @@ __device__ __forceinline__ void down_body(
   // fc = c * FW(r) on the coarse points of this tile
   constexpr int CW = BX / 2, CH = BY / 2;
   const C csc = cscale(cs, R(1.0 / 16.0));
-  C *fco = fcb + (y0 / 2) * Nc + x0 / 2;
+  C *fco = fcb + (y0 / 2) * Pc + x0 / 2;
   Walk<CW> w(tid);
   for (int i = tid; i < CW * CH; i += NT, w.next(NT)) {
     const int cxl = w.x, cyl = w.y;
@@ -254,7 +253,7 @@ __device__ __forceinline__ void down_body(
       C a = cscale(s_r[j], R(4));
       a = cadd(a, cscale(cadd(cadd(s_r[j - 1], s_r[j + 1]), cadd(s_r[j - RW], s_r[j + RW])), R(2)));
       a = cadd(a, cadd(cadd(s_r[j - RW - 1], s_r[j - RW + 1]), cadd(s_r[j + RW - 1], s_r[j + RW + 1])));
-      fco[cyl * Nc + cxl] = cmul(csc, a);
+      fco[cyl * Pc + cxl] = cmul(csc, a);
     }
   }
 }
@@ -266,7 +265,7 @@ __global__ void __launch_bounds__(256)
 k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
          const typename Cx<R>::T *__restrict__ f, typename Cx<R>::T *__restrict__ v_out,
          typename Cx<R>::T *__restrict__ fc, typename Cx<R>::T cs,
-         typename Cx<R>::T omega, int kconst, const SolveState *__restrict__ st,
+         typename Cx<R>::T omega, int kconst, Lay lc, const SolveState *__restrict__ st,
          double *__restrict__ partials, CheckCtx chk) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.z;
@@ -277,12 +276,11 @@ k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
   const bool zero = zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = L.N, Nc = (N + 1) / 2 - 1;
-  const size_t pts = (size_t)N * N;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-  const C *ub = u_in + (size_t)b * pts;
-  const C *fb = f + (size_t)b * pts;
-  C *vb = v_out + (size_t)b * pts;
-  C *fcb = fc + (size_t)b * Nc * Nc;
+  const C *ub = u_in + (size_t)b * L.S;
+  const C *fb = f + (size_t)b * L.S;
+  C *vb = v_out + (size_t)b * L.S;
+  C *fcb = fc + (size_t)b * lc.S;
   R acc = R(0);
   const bool inner = tile_in(L, x0 - 2, x0 + BX + 2, N, false) &&
                      tile_in(L, y0 - 2, y0 + BY + 2, N, false);
@@ -290,11 +288,11 @@ k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
                     tile_in(L, y0 - 2, y0 + BY + 2, N, true);
   if (act) {
     if (fast)
-      down_body<R, BX, BY, false, true>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, smem_raw, acc);
+      down_body<R, BX, BY, false, true>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, lc.P, smem_raw, acc);
     else if (inner)
-      down_body<R, BX, BY, false, false>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, smem_raw, acc);
+      down_body<R, BX, BY, false, false>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, lc.P, smem_raw, acc);
     else
-      down_body<R, BX, BY, true, false>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, smem_raw, acc);
+      down_body<R, BX, BY, true, false>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, lc.P, smem_raw, acc);
   }
   if (partials) {
     const double s = block_sum_d((double)acc);
@@ -309,7 +307,7 @@ __device__ __forceinline__ void up_body(
     const LevelK<R> &L, const typename Cx<R>::T *__restrict__ vb,
     const typename Cx<R>::T *__restrict__ eb, const typename Cx<R>::T *__restrict__ fb,
     typename Cx<R>::T *__restrict__ ob, typename Cx<R>::T omega, int kconst, int x0, int y0,
-    unsigned char *smem_raw) {
+    int Pc, unsigned char *smem_raw) {
   using C = typename Cx<R>::T;
   using S = Up2D<R, BX, BY>;
   constexpr int WW = S::WW, WH = S::WH, EW = S::EW, EH = S::EH;
@@ -318,7 +316,7 @@ __device__ __forceinline__ void up_body(
   C *s_e = s_w + WW * WH;
   C *s_cx = s_e + EW * EH;   // [3][WW]
   C *s_cy = s_cx + 3 * WW;   // [3][WH]
-  const int N = L.N, Nc = (N + 1) / 2 - 1;
+  const int N = L.N, Nc = (N + 1) / 2 - 1, P = L.P, KP = L.KP;
   const int ex0 = x0 / 2 - 1, ey0 = y0 / 2 - 1;
   const int tid = threadIdx.x;
   const C zc = czero<C>();
@@ -346,13 +344,13 @@ __device__ __forceinline__ void up_body(
       const int cx = ex0 + w.x, cy = ey0 + w.y;
       // the first coarse row/column of a tile at the low boundary is outside
       const bool in = cx >= 0 && cx < Nc && cy >= 0 && cy < Nc;
-      s_e[i] = in ? eb[cy * Nc + cx] : zc;
+      s_e[i] = in ? eb[cy * Pc + cx] : zc;
     }
   }
   __syncthreads();
   // w = v + P e on tile + 1 (zero outside the domain)
   {
-    const C *vo = vb + (y0 - 1) * N + (x0 - 1);
+    const C *vo = vb + (y0 - 1) * P + (x0 - 1);
     Walk<WW> w(tid);
     for (int i = tid; i < WW * WH; i += NT, w.next(NT)) {
       const int tx = w.x, ty = w.y;
@@ -370,7 +368,7 @@ __device__ __forceinline__ void up_body(
         } else {
           p = cscale(cadd(s_e[r0 + c0], s_e[r0 + EW + c0]), R(0.5));
         }
-        val = cadd(vo[ty * N + tx], p);
+        val = cadd(vo[ty * P + tx], p);
       }
       s_w[i] = val;
     }
@@ -391,23 +389,23 @@ __device__ __forceinline__ void up_body(
       C clo = zc, cdg = zc, cup = zc;
       if (!FAST) { clo = s_cx[tx]; cdg = s_cx[WW + tx]; cup = s_cx[2 * WW + tx]; }
       const C *col = s_w + tx;
-      const C *fo = fb + y0 * N + x0 + lx;
-      const R *ko = L.k2 + y0 * N + x0 + lx;
-      C *oo = ob + y0 * N + x0 + lx;
+      const C *fo = fb + y0 * P + x0 + lx;
+      const R *ko = L.k2 + y0 * KP + x0 + lx;
+      C *oo = ob + y0 * P + x0 + lx;
       C wn = col[q0 * WW], wc = col[(q0 + 1) * WW];
       for (int ly = q0; ly < q1; ++ly) {
         const int j = (ly + 1) * WW;
         const C wd = col[j + WW], wl = col[j - 1], wr = col[j + 1];
         if (colin && (!CHECK || y0 + ly < N)) {
-          const int g = ly * N;
+          const int g = ly * P, gk = ly * KP;
           C D, Wd, nb;
           if (FAST) {
             if (kconst) { D = Dk; Wd = Wk; }
-            else { D = csub(d0, cscale(L.beta, ko[g])); Wd = cmul(omega, crcp(D)); }
+            else { D = csub(d0, cscale(L.beta, ko[gk])); Wd = cmul(omega, crcp(D)); }
             nb = cmul(c0, cadd(cadd(wl, wr), cadd(wn, wd)));
           } else {
             const int ty = ly + 1;
-            D = csub(cadd(cdg, s_cy[WH + ty]), cscale(L.beta, kconst ? kc : ko[g]));
+            D = csub(cadd(cdg, s_cy[WH + ty]), cscale(L.beta, kconst ? kc : ko[gk]));
             Wd = cmul(omega, crcp(D));
             nb = cmul(clo, wl);
             nb = cfma(cup, wr, nb);
@@ -428,28 +426,27 @@ template <typename R, int BX, int BY>
 __global__ void __launch_bounds__(256)
 k_up2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ v_in,
        const typename Cx<R>::T *__restrict__ e, const typename Cx<R>::T *__restrict__ f,
-       typename Cx<R>::T *__restrict__ u_out, typename Cx<R>::T omega, int kconst,
+       typename Cx<R>::T *__restrict__ u_out, typename Cx<R>::T omega, int kconst, Lay lc,
        const SolveState *__restrict__ st) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.z;
   if (st && !st[b].active) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = L.N, Nc = (N + 1) / 2 - 1;
-  const size_t pts = (size_t)N * N;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-  const C *vb = v_in + (size_t)b * pts;
-  const C *eb = e + (size_t)b * Nc * Nc;
-  const C *fb = f + (size_t)b * pts;
-  C *ob = u_out + (size_t)b * pts;
+  const C *vb = v_in + (size_t)b * L.S;
+  const C *eb = e + (size_t)b * lc.S;
+  const C *fb = f + (size_t)b * L.S;
+  C *ob = u_out + (size_t)b * L.S;
   const bool inner = tile_in(L, x0 - 1, x0 + BX, N, false) && tile_in(L, y0 - 1, y0 + BY, N, false);
   const bool fast = inner && tile_in(L, x0 - 1, x0 + BX, N, true) &&
                     tile_in(L, y0 - 1, y0 + BY, N, true);
   if (fast)
-    up_body<R, BX, BY, false, true>(L, vb, eb, fb, ob, omega, kconst, x0, y0, smem_raw);
+    up_body<R, BX, BY, false, true>(L, vb, eb, fb, ob, omega, kconst, x0, y0, lc.P, smem_raw);
   else if (inner)
-    up_body<R, BX, BY, false, false>(L, vb, eb, fb, ob, omega, kconst, x0, y0, smem_raw);
+    up_body<R, BX, BY, false, false>(L, vb, eb, fb, ob, omega, kconst, x0, y0, lc.P, smem_raw);
   else
-    up_body<R, BX, BY, true, false>(L, vb, eb, fb, ob, omega, kconst, x0, y0, smem_raw);
+    up_body<R, BX, BY, true, false>(L, vb, eb, fb, ob, omega, kconst, x0, y0, lc.P, smem_raw);
 }
 
 }  // namespace hh

@@ -15,12 +15,14 @@ __device__ __forceinline__ double warp_sum(const double *p, int n, int lane) {
   return s;
 }
 
+// sum of |x|^2 over the `stride` elements of each right-hand side (the
+// padding of the library's pitched layout is zero)
 __global__ void __launch_bounds__(256)
-k_norm2(const double2 *__restrict__ x, size_t pts, double *partials) {
+k_norm2(const double2 *__restrict__ x, size_t stride, double *partials) {
   const int b = blockIdx.y;
-  x += (size_t)b * pts;
+  x += (size_t)b * stride;
   double acc = 0.0;
-  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < stride;
        p += (size_t)gridDim.x * blockDim.x)
     acc += x[p].x * x[p].x + x[p].y * x[p].y;
   __shared__ double ws[32];
@@ -41,18 +43,35 @@ __global__ void k_to_float(const double *__restrict__ x, float *__restrict__ y,
     y[i] = (float)x[i];
 }
 
-__global__ void k_c128_to_c64(const double2 *__restrict__ x,
-                              float2 *__restrict__ y, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    y[i] = make_float2((float)x[i].x, (float)x[i].y);
+// Layout-converting copies: point (x, y[, z]) of right-hand side b from
+// layout lx to layout ly (dense caller arrays <-> pitched library arrays).
+__device__ __forceinline__ size_t lay_at(const Lay &l, int dim, size_t p, int b) {
+  const int x = (int)(p % l.N);
+  const size_t r = p / l.N;   // row index: y, or z * N + y in 3-D
+  (void)dim;
+  return (size_t)b * l.S + r * l.P + x;
 }
 
-__global__ void k_c64_to_c128(const float2 *__restrict__ x,
-                              double2 *__restrict__ y, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    y[i] = make_double2((double)x[i].x, (double)x[i].y);
+__global__ void k_c128_to_c64(const double2 *__restrict__ x, Lay lx,
+                              float2 *__restrict__ y, Lay ly, int dim) {
+  const int b = blockIdx.y;
+  const size_t pts = dim == 2 ? (size_t)lx.N * lx.N : (size_t)lx.N * lx.N * lx.N;
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
+       p += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = x[lay_at(lx, dim, p, b)];
+    y[lay_at(ly, dim, p, b)] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+__global__ void k_c64_to_c128(const float2 *__restrict__ x, Lay lx,
+                              double2 *__restrict__ y, Lay ly, int dim) {
+  const int b = blockIdx.y;
+  const size_t pts = dim == 2 ? (size_t)lx.N * lx.N : (size_t)lx.N * lx.N * lx.N;
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
+       p += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = x[lay_at(lx, dim, p, b)];
+    y[lay_at(ly, dim, p, b)] = make_double2((double)v.x, (double)v.y);
+  }
 }
 
 // One block; warp w serves right-hand sides w, w+32, ...; the partial sums
@@ -194,15 +213,14 @@ __global__ void k_check_outer(SolveState *st, const double *partials,
   if (threadIdx.x == 0) *flag = any_s;
 }
 
-__global__ void k_finish(const SolveState *st, const double2 *__restrict__ src,
-                         double2 *__restrict__ dst, size_t pts) {
+__global__ void k_finish(const SolveState *st, const double2 *__restrict__ src, Lay ls,
+                         double2 *__restrict__ dst, Lay ld, int dim) {
   const int b = blockIdx.y;
   const bool z = st[b].zres != 0;
-  src += (size_t)b * pts;
-  dst += (size_t)b * pts;
+  const size_t pts = dim == 2 ? (size_t)ls.N * ls.N : (size_t)ls.N * ls.N * ls.N;
   for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
        p += (size_t)gridDim.x * blockDim.x)
-    dst[p] = z ? make_double2(0.0, 0.0) : src[p];
+    dst[lay_at(ld, dim, p, b)] = z ? make_double2(0.0, 0.0) : src[lay_at(ls, dim, p, b)];
 }
 
 __global__ void k_grad_k2(const double2 *__restrict__ u,
@@ -219,34 +237,6 @@ __global__ void k_grad_k2(const double2 *__restrict__ u,
   }
 }
 
-// Forward/back substitution with the coarsest LU factors (FP64), one block
-// per right-hand side, thread 0 (m <= 27 unknowns).
-template <typename R>
-__global__ void k_coarse_solve(const double2 *__restrict__ lu,
-                               const int *__restrict__ piv, int m,
-                               const typename Cx<R>::T *__restrict__ f,
-                               typename Cx<R>::T *__restrict__ e,
-                               const SolveState *__restrict__ st) {
-  using C = typename Cx<R>::T;
-  const int b = blockIdx.x;
-  if (st && !st[b].active) return;
-  if (threadIdx.x != 0) return;
-  double2 y[27];
-  const C *fb = f + (size_t)b * m;
-  for (int i = 0; i < m; ++i) {
-    const C v = fb[piv[i]];
-    y[i] = make_double2((double)v.x, (double)v.y);
-  }
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < i; ++j) y[i] = csub(y[i], cmul(lu[i * m + j], y[j]));
-  for (int i = m - 1; i >= 0; --i) {
-    for (int j = i + 1; j < m; ++j) y[i] = csub(y[i], cmul(lu[i * m + j], y[j]));
-    y[i] = cmul(y[i], lu[i * m + i]);   // the diagonal holds 1 / U_ii
-  }
-  C *eb = e + (size_t)b * m;
-  for (int i = 0; i < m; ++i) eb[i] = cmk((R)y[i].x, (R)y[i].y);
-}
-
 int grid_cap(size_t work, int threads = 256, int cap = 8 * 152 * 4) {
   size_t g = (work + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -258,18 +248,22 @@ int grid_cap(size_t work, int threads = 256, int cap = 8 * 152 * 4) {
 
 int partial_blocks(size_t pts) { return grid_cap(pts, 256, 2 * 152); }
 
-void launch_norm2(const double2 *x, size_t pts, int batch, double *partials,
+void launch_norm2(const double2 *x, size_t stride, int batch, double *partials,
                   int nparts, cudaStream_t s) {
-  k_norm2<<<dim3(nparts, batch), 256, 0, s>>>(x, pts, partials);
+  k_norm2<<<dim3(nparts, batch), 256, 0, s>>>(x, stride, partials);
 }
 void launch_to_float(const double *x, float *y, size_t n, cudaStream_t s) {
   k_to_float<<<grid_cap(n), 256, 0, s>>>(x, y, n);
 }
-void launch_c128_to_c64(const double2 *x, float2 *y, size_t n, cudaStream_t s) {
-  k_c128_to_c64<<<grid_cap(n), 256, 0, s>>>(x, y, n);
+void launch_c128_to_c64(const double2 *x, const Lay &lx, float2 *y, const Lay &ly, int dim,
+                        int batch, cudaStream_t s) {
+  const size_t pts = dim == 2 ? (size_t)lx.N * lx.N : (size_t)lx.N * lx.N * lx.N;
+  k_c128_to_c64<<<dim3(grid_cap(pts), batch), 256, 0, s>>>(x, lx, y, ly, dim);
 }
-void launch_c64_to_c128(const float2 *x, double2 *y, size_t n, cudaStream_t s) {
-  k_c64_to_c128<<<grid_cap(n), 256, 0, s>>>(x, y, n);
+void launch_c64_to_c128(const float2 *x, const Lay &lx, double2 *y, const Lay &ly, int dim,
+                        int batch, cudaStream_t s) {
+  const size_t pts = dim == 2 ? (size_t)lx.N * lx.N : (size_t)lx.N * lx.N * lx.N;
+  k_c64_to_c128<<<dim3(grid_cap(pts), batch), 256, 0, s>>>(x, lx, y, ly, dim);
 }
 void launch_state_init(SolveState *st, const double *partials,
                        const SolveParams *P, int *flag, cudaStream_t s) {
@@ -289,25 +283,13 @@ void launch_check_outer(SolveState *st, const double *partials,
                         const SolveParams *P, int *flag, cudaStream_t s) {
   k_check_outer<<<1, 1024, 0, s>>>(st, partials, P, flag);
 }
-void launch_finish(const SolveState *st, const double2 *src, double2 *dst,
-                   size_t pts, int batch, cudaStream_t s) {
-  k_finish<<<dim3(grid_cap(pts), batch), 256, 0, s>>>(st, src, dst, pts);
+void launch_finish(const SolveState *st, const double2 *src, const Lay &ls, double2 *dst,
+                   const Lay &ld, int dim, int batch, cudaStream_t s) {
+  const size_t pts = dim == 2 ? (size_t)ls.N * ls.N : (size_t)ls.N * ls.N * ls.N;
+  k_finish<<<dim3(grid_cap(pts), batch), 256, 0, s>>>(st, src, ls, dst, ld, dim);
 }
 void launch_grad_k2(const double2 *u, const double2 *lam, size_t pts,
                     int batch, double *grad, cudaStream_t s) {
   k_grad_k2<<<grid_cap(pts), 256, 0, s>>>(u, lam, pts, batch, grad);
 }
-template <typename R>
-void launch_coarse_solve(const double2 *lu, const int *piv, int m,
-                         const typename Cx<R>::T *f, typename Cx<R>::T *e,
-                         int batch, const SolveState *st, cudaStream_t s) {
-  k_coarse_solve<R><<<batch, 32, 0, s>>>(lu, piv, m, f, e, st);
-}
-template void launch_coarse_solve<float>(const double2 *, const int *, int,
-                                         const float2 *, float2 *, int,
-                                         const SolveState *, cudaStream_t);
-template void launch_coarse_solve<double>(const double2 *, const int *, int,
-                                          const double2 *, double2 *, int,
-                                          const SolveState *, cudaStream_t);
-
 }  // namespace hh
