@@ -10,6 +10,8 @@
 #include "hh_internal.h"
 #include "hh_cycle.h"
 
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -109,6 +111,9 @@ struct hh_handle {
   int variant[MAXL] = {};           // tile shape per fused level (autotuned)
   int parts_cap = 0;                // capacity of `partials` per RHS
   unsigned int *counter = nullptr;  // arrivals of the fused stop test
+  int *err = nullptr;               // device status word of bounded waits
+  DownMaps dmap[MAXL];              // tensor maps of the fused kernels, per level
+  UpMaps umap[MAXL];
   std::vector<void *> allocs;
   std::map<std::tuple<int, int, int>, GraphEntry> graphs;
 
@@ -257,6 +262,75 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
   }
 }
 
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on it).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a complex array of level l (scalars of type R, two per
+// point): dims (2N, N, batch), box (2 bw, bh, 1); zero fill outside.
+template <typename R>
+hh_status cmap(const hh_handle *h, int l, const void *base, int bw, int bh, CUtensorMap *m) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(HH_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const LevelHost &v = h->lv[l];
+  const cuuint64_t dims[3] = {2 * (cuuint64_t)v.N, (cuuint64_t)v.N, (cuuint64_t)h->max_batch};
+  const cuuint64_t strides[2] = {(cuuint64_t)v.P * 2 * sizeof(R), (cuuint64_t)v.S * 2 * sizeof(R)};
+  const cuuint32_t box[3] = {2 * (cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                         3, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(HH_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return HH_OK;
+}
+// Tensor map of the real k^2 array of level l: dims (N, N), box (bw, bh).
+template <typename R>
+hh_status kmap(const hh_handle *h, int l, const void *base, int bw, int bh, CUtensorMap *m) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(HH_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const LevelHost &v = h->lv[l];
+  const cuuint64_t dims[2] = {(cuuint64_t)v.N, (cuuint64_t)v.N};
+  const cuuint64_t strides[1] = {(cuuint64_t)v.P * sizeof(R)};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                         2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(HH_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return HH_OK;
+}
+
+template <typename R> const R *k2_ptr(const hh_handle *h, int l);
+template <> const double *k2_ptr<double>(const hh_handle *h, int l) { return h->lv[l].k2_64; }
+template <> const float *k2_ptr<float>(const hh_handle *h, int l) { return h->lv[l].k2_32; }
+
+// Tensor maps of the down and up passes of level l for tile shape `variant`
+// (boxes as laid out in Down2D / Up2D).
+template <typename R>
+hh_status make_maps(hh_handle *h, int l, int variant, DownMaps *dm, UpMaps *um) {
+  Work<R> &W = work<R>(h);
+  const int BX = tile_bx(variant), BY = tile_by(variant);
+  HH_TRY(cmap<R>(h, l, W.u_post[l], BX + 6, BY + 5, &dm->u));
+  HH_TRY(cmap<R>(h, l, W.f[l], BX + 6, BY + 3, &dm->f));
+  HH_TRY(kmap<R>(h, l, k2_ptr<R>(h, l), BX + 8, BY + 3, &dm->k));
+  HH_TRY(cmap<R>(h, l, W.u_pre[l], BX + 4, BY + 2, &um->v));
+  HH_TRY(cmap<R>(h, l + 1, W.u_post[l + 1], BX / 2 + 4, BY / 2 + 2, &um->e));
+  HH_TRY(cmap<R>(h, l, W.f[l], BX, BY, &um->f));
+  HH_TRY(kmap<R>(h, l, k2_ptr<R>(h, l), BX, BY, &um->k));
+  return HH_OK;
+}
+
 template <typename R> TailArgs<R> tail_args(hh_handle *h, int dir) {
   Work<R> &W = work<R>(h);
   TailArgs<R> a{};
@@ -299,6 +373,7 @@ template <typename R> CheckCtx check_ctx(hh_handle *h, int check, unsigned long 
   c.counter = h->counter;
   c.flag = h->flag;
   c.cond = cond;
+  c.err = h->err;
   return c;
 }
 
@@ -317,16 +392,15 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
     const bool norm = l == 0 && check != CHECK_NONE;
     // the level-0 pass also runs the stop test in its last block
     const CheckCtx chk = norm ? check_ctx<R>(h, check, cond) : CheckCtx{};
-    launch_down2d<R>(h->variant[l], K, l == 0 ? W.u_post[0] : nullptr,
-                     l == 0 ? zero0 : ZERO_ALL, W.f[l], W.u_pre[l], W.f[l + 1],
-                     cscal<R>(h, l, dir), om, h->kconst, lay_of(h, l + 1), batch, st,
-                     norm ? h->partials : nullptr, chk, s);
+    launch_down2d<R>(h->variant[l], h->dmap[l], K, l == 0 ? zero0 : ZERO_ALL, W.u_pre[l],
+                     W.f[l + 1], cscal<R>(h, l, dir), om, h->kconst, lay_of(h, l + 1), batch, st,
+                     norm ? h->partials : nullptr, h->err, chk, s);
   }
   launch_tail2d<R>(tail_args<R>(h, dir), batch, st, s);
   for (int l = T - 1; l >= 0; --l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
-    launch_up2d<R>(h->variant[l], K, W.u_pre[l], W.u_post[l + 1], W.f[l], W.u_post[l],
-                   om, h->kconst, lay_of(h, l + 1), batch, st, s);
+    launch_up2d<R>(h->variant[l], h->umap[l], K, W.u_post[l], om, h->kconst, batch, st,
+                   h->err, s);
   }
 }
 
@@ -449,7 +523,9 @@ hh_status read_info(hh_handle *h, int batch, hh_solve_info *info,
                     cudaStream_t s) {
   HH_CK(cudaMemcpyAsync(h->st_h, h->st, sizeof(SolveState) * batch,
                         cudaMemcpyDeviceToHost, s));
+  HH_CK(cudaMemcpyAsync(h->flag_h, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   HH_CK(cudaStreamSynchronize(s));
+  if (*h->flag_h) return fail(HH_ERR_TIMEOUT, "a bounded device wait gave up (TMA copy not completed)");
   hh_status worst = HH_OK;
   for (int b = 0; b < batch; ++b) {
     const SolveState &q = h->st_h[b];
@@ -516,6 +592,7 @@ hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
   if (rhs)
     HH_TRY(copy_to_pitched(h, 0, h->w64.f[0], rhs, batch, sizeof(double2), cudaMemcpyDeviceToDevice, s));
   HH_TRY(set_params(h, batch, tol, s));
+  HH_CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
   launch_norm2(h->w64.f[0], (size_t)l0.S, batch, h->partials, h->nparts, s);
   launch_state_init(h->st, h->partials, h->params, h->flag, s);
 
@@ -564,13 +641,12 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
   }
   if (h->fused && level < h->tail0 && kernel != 1) {
     if (kernel == 0)
-      launch_down2d<R>(h->variant[level], K, W.u_post[level], ZERO_NONE, W.f[level],
-                       W.u_pre[level], W.f[level + 1], cscal<R>(h, level, 0), om, h->kconst,
-                       lay_of(h, level + 1), batch, nullptr, level == 0 ? h->partials : nullptr,
-                       CheckCtx{}, s);
+      launch_down2d<R>(h->variant[level], h->dmap[level], K, ZERO_NONE, W.u_pre[level],
+                       W.f[level + 1], cscal<R>(h, level, 0), om, h->kconst, lay_of(h, level + 1),
+                       batch, nullptr, level == 0 ? h->partials : nullptr, h->err, CheckCtx{}, s);
     else
-      launch_up2d<R>(h->variant[level], K, W.u_pre[level], W.u_post[level + 1], W.f[level],
-                     W.u_post[level], om, h->kconst, lay_of(h, level + 1), batch, nullptr, s);
+      launch_up2d<R>(h->variant[level], h->umap[level], K, W.u_post[level], om, h->kconst,
+                     batch, nullptr, h->err, s);
     return;
   }
   if (kernel == 0) {
@@ -638,12 +714,13 @@ template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, 
   float tbest = 1e30f;
   *best = 0;
   for (int v = 0; v < kNumTileVariants; ++v) {
+    DownMaps dm;
+    UpMaps um;
+    HH_TRY(make_maps<R>(h, l, v, &dm, &um));
     auto run = [&]() {
-      launch_down2d<R>(v, K, W.u_post[l], ZERO_NONE, W.f[l], W.u_pre[l], W.f[l + 1],
-                       cscal<R>(h, l, 0), om, h->kconst, lay_of(h, l + 1), 1, nullptr, nullptr,
-                       CheckCtx{}, s);
-      launch_up2d<R>(v, K, W.u_pre[l], W.u_post[l + 1], W.f[l], W.u_post[l], om,
-                     h->kconst, lay_of(h, l + 1), 1, nullptr, s);
+      launch_down2d<R>(v, dm, K, ZERO_NONE, W.u_pre[l], W.f[l + 1], cscal<R>(h, l, 0), om,
+                       h->kconst, lay_of(h, l + 1), 1, nullptr, nullptr, h->err, CheckCtx{}, s);
+      launch_up2d<R>(v, um, K, W.u_post[l], om, h->kconst, 1, nullptr, h->err, s);
     };
     run();
     HH_CK(cudaEventRecord(e0, s));
@@ -868,6 +945,8 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   HH_TRY(dev_alloc_n(h, &h->partials, (size_t)h->parts_cap * B));
   HH_TRY(dev_alloc_n(h, &h->counter, 1));
   HH_CK(cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), s));
+  HH_TRY(dev_alloc_n(h, &h->err, 1));
+  HH_CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
   HH_TRY(dev_alloc_n(h, &h->st, (size_t)B));
   HH_TRY(dev_alloc_n(h, &h->params, 1));
   HH_TRY(dev_alloc_n(h, &h->flag, 1));
@@ -890,7 +969,13 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   HH_CK(cudaStreamSynchronize(s));
   HH_CK(cudaGetLastError());
   if (info_h[0] || info_h[1]) return fail(HH_ERR_ARG, "singular coarsest-level operator");
-  if (h->fused) HH_TRY(autotune(h, s));
+  if (h->fused) {
+    HH_TRY(autotune(h, s));
+    for (int l = 0; l < h->tail0; ++l) {
+      if (h->opt.precision == HH_FP64) HH_TRY(make_maps<double>(h, l, h->variant[l], &h->dmap[l], &h->umap[l]));
+      else HH_TRY(make_maps<float>(h, l, h->variant[l], &h->dmap[l], &h->umap[l]));
+    }
+  }
   h->nparts = h->fused ? tile_parts(h->variant[0], h->lv[0].N) : partial_blocks(h->lv[0].pts);
   return HH_OK;
 }

@@ -17,6 +17,8 @@ struct CheckCtx {
   unsigned int *counter;     // arrivals; reset to 0 by the last block
   int *flag;                 // any right-hand side still active
   unsigned long long cond;   // cudaGraphConditionalHandle, 0 = none
+  int *err;                  // device status word (HH_ERR_TIMEOUT after a
+                             // bounded wait gave up), or NULL
 };
 
 // Plain cycle loop (Sec. 4.1): r2 = ||f - A_0 u_k||^2 of the iterate that the
@@ -102,8 +104,13 @@ __device__ __forceinline__ void last_block_check(const CheckCtx &c, int nblk) {
     for (int i = lane; i < nblk; i += 32) r2 += __ldcg(p + i);
     for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
     if (lane == 0) {
-      if (c.mode == CHECK_MODE_CYCLE) update_cycle(s, r2, c.P);
-      else update_inner(s, r2, c.P);
+      if (c.err && *(volatile int *)c.err) {   // a bounded wait gave up: stop
+        s.status = HH_ERR_TIMEOUT; s.active = 0; s.done = 1;
+      } else if (c.mode == CHECK_MODE_CYCLE) {
+        update_cycle(s, r2, c.P);
+      } else {
+        update_inner(s, r2, c.P);
+      }
       c.st[b] = s;
       if (s.active) atomicOr(&s_any, 1);
     }

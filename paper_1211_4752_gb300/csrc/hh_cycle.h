@@ -2,6 +2,7 @@
 #pragma once
 #include "hh_internal.h"
 #include "hh_check.cuh"
+#include "hh_tma.cuh"
 
 namespace hh {
 
@@ -54,21 +55,24 @@ template <typename R> size_t tail_smem_bytes(const int *N, int nl) {
 constexpr size_t kTailSmemMax = 200 * 1024;
 
 int tile_parts(int variant, int N);  // blocks per right-hand side of a level
+int tile_bx(int variant);            // tile width (fine points)
+int tile_by(int variant);            // tile height
 
 template <typename R> cudaError_t init_cycle2d();
 
+// Down / up passes of one level.  maps: tensor maps of the staged arrays for
+// this level and tile shape (see hh_tma.cuh); err: device status word.
 template <typename R>
-void launch_down2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *u_in,
-                   int zero_mode, const typename Cx<R>::T *f, typename Cx<R>::T *v_out,
-                   typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
-                   int kconst, const Lay &lc, int batch, const SolveState *st,
-                   double *partials, const CheckCtx &chk, cudaStream_t s);
+void launch_down2d(int variant, const DownMaps &maps, const LevelK<R> &L, int zero_mode,
+                   typename Cx<R>::T *v_out, typename Cx<R>::T *fc, typename Cx<R>::T cs,
+                   typename Cx<R>::T omega, int kconst, const Lay &lc, int batch,
+                   const SolveState *st, double *partials, int *err, const CheckCtx &chk,
+                   cudaStream_t s);
 
 template <typename R>
-void launch_up2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *v_in,
-                 const typename Cx<R>::T *e, const typename Cx<R>::T *f,
-                 typename Cx<R>::T *u_out, typename Cx<R>::T omega, int kconst, const Lay &lc,
-                 int batch, const SolveState *st, cudaStream_t s);
+void launch_up2d(int variant, const UpMaps &maps, const LevelK<R> &L, typename Cx<R>::T *u_out,
+                 typename Cx<R>::T omega, int kconst, int batch, const SolveState *st, int *err,
+                 cudaStream_t s);
 
 template <typename R>
 void launch_tail2d(const TailArgs<R> &a, int batch, const SolveState *st, cudaStream_t s);

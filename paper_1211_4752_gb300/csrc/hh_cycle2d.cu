@@ -11,31 +11,29 @@ namespace hh {
 namespace {
 
 struct Shape { int bx, by; };
-constexpr Shape kShapes[kNumTileVariants] = {{58, 16}, {58, 32}, {26, 32}, {122, 16}, {26, 16}};
+constexpr Shape kShapes[kNumTileVariants] = {{60, 16}, {60, 32}, {28, 32}, {120, 16}, {28, 16}};
 
 template <typename R, int BX, int BY>
-void down_one(const LevelK<R> &L, const typename Cx<R>::T *u_in, int zero_mode,
-              const typename Cx<R>::T *f, typename Cx<R>::T *v_out,
+void down_one(const DownMaps &maps, const LevelK<R> &L, int zero_mode, typename Cx<R>::T *v_out,
               typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
               int kconst, const Lay &lc, int batch, const SolveState *st, double *partials,
-              const CheckCtx &chk, cudaStream_t s) {
+              int *err, const CheckCtx &chk, cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
   if (chk.cond)
     k_down2d<R, BX, BY, true><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
-        L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, st, partials, chk);
+        maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, st, partials, err, chk);
   else
     k_down2d<R, BX, BY, false><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
-        L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, st, partials, chk);
+        maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, st, partials, err, chk);
 }
 
 template <typename R, int BX, int BY>
-void up_one(const LevelK<R> &L, const typename Cx<R>::T *v_in,
-            const typename Cx<R>::T *e, const typename Cx<R>::T *f,
-            typename Cx<R>::T *u_out, typename Cx<R>::T omega, int kconst,
-            const Lay &lc, int batch, const SolveState *st, cudaStream_t s) {
+void up_one(const UpMaps &maps, const LevelK<R> &L, typename Cx<R>::T *u_out,
+            typename Cx<R>::T omega, int kconst, int batch, const SolveState *st, int *err,
+            cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
-  k_up2d<R, BX, BY><<<grid, 256, Up2D<R, BX, BY>::smem, s>>>(L, v_in, e, f, u_out,
-                                                             omega, kconst, lc, st);
+  k_up2d<R, BX, BY><<<grid, 256, Up2D<R, BX, BY>::smem, s>>>(maps, L, u_out, omega, kconst,
+                                                             st, err);
 }
 
 // Dynamic shared memory limits, and the maximum shared-memory carveout for
@@ -226,44 +224,45 @@ int tile_parts(int variant, int N) {
   const Shape sh = kShapes[variant];
   return ((N + sh.bx - 1) / sh.bx) * ((N + sh.by - 1) / sh.by);
 }
+int tile_bx(int variant) { return kShapes[variant].bx; }
+int tile_by(int variant) { return kShapes[variant].by; }
 
 template <typename R>
 cudaError_t init_cycle2d() {
   cudaError_t e;
-  if ((e = attr_one<R, 58, 16>()) != cudaSuccess) return e;
-  if ((e = attr_one<R, 58, 32>()) != cudaSuccess) return e;
-  if ((e = attr_one<R, 26, 32>()) != cudaSuccess) return e;
-  if ((e = attr_one<R, 122, 16>()) != cudaSuccess) return e;
-  if ((e = attr_one<R, 26, 16>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 60, 16>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 60, 32>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 28, 32>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 120, 16>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 28, 16>()) != cudaSuccess) return e;
   return attrs(k_tail2d<R>, kTailSmemMax);
 }
 
 template <typename R>
-void launch_down2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *u_in,
-                   int zero_mode, const typename Cx<R>::T *f, typename Cx<R>::T *v_out,
-                   typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
-                   int kconst, const Lay &lc, int batch, const SolveState *st,
-                   double *partials, const CheckCtx &chk, cudaStream_t s) {
+void launch_down2d(int variant, const DownMaps &maps, const LevelK<R> &L, int zero_mode,
+                   typename Cx<R>::T *v_out, typename Cx<R>::T *fc, typename Cx<R>::T cs,
+                   typename Cx<R>::T omega, int kconst, const Lay &lc, int batch,
+                   const SolveState *st, double *partials, int *err, const CheckCtx &chk,
+                   cudaStream_t s) {
   switch (variant) {
-    case 0: down_one<R, 58, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, batch, st, partials, chk, s); break;
-    case 1: down_one<R, 58, 32>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, batch, st, partials, chk, s); break;
-    case 2: down_one<R, 26, 32>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, batch, st, partials, chk, s); break;
-    case 3: down_one<R, 122, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, batch, st, partials, chk, s); break;
-    default: down_one<R, 26, 16>(L, u_in, zero_mode, f, v_out, fc, cs, omega, kconst, lc, batch, st, partials, chk, s); break;
+    case 0: down_one<R, 60, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, chk, s); break;
+    case 1: down_one<R, 60, 32>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, chk, s); break;
+    case 2: down_one<R, 28, 32>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, chk, s); break;
+    case 3: down_one<R, 120, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, chk, s); break;
+    default: down_one<R, 28, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, chk, s); break;
   }
 }
 
 template <typename R>
-void launch_up2d(int variant, const LevelK<R> &L, const typename Cx<R>::T *v_in,
-                 const typename Cx<R>::T *e, const typename Cx<R>::T *f,
-                 typename Cx<R>::T *u_out, typename Cx<R>::T omega, int kconst, const Lay &lc,
-                 int batch, const SolveState *st, cudaStream_t s) {
+void launch_up2d(int variant, const UpMaps &maps, const LevelK<R> &L, typename Cx<R>::T *u_out,
+                 typename Cx<R>::T omega, int kconst, int batch, const SolveState *st, int *err,
+                 cudaStream_t s) {
   switch (variant) {
-    case 0: up_one<R, 58, 16>(L, v_in, e, f, u_out, omega, kconst, lc, batch, st, s); break;
-    case 1: up_one<R, 58, 32>(L, v_in, e, f, u_out, omega, kconst, lc, batch, st, s); break;
-    case 2: up_one<R, 26, 32>(L, v_in, e, f, u_out, omega, kconst, lc, batch, st, s); break;
-    case 3: up_one<R, 122, 16>(L, v_in, e, f, u_out, omega, kconst, lc, batch, st, s); break;
-    default: up_one<R, 26, 16>(L, v_in, e, f, u_out, omega, kconst, lc, batch, st, s); break;
+    case 0: up_one<R, 60, 16>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
+    case 1: up_one<R, 60, 32>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
+    case 2: up_one<R, 28, 32>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
+    case 3: up_one<R, 120, 16>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
+    default: up_one<R, 28, 16>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
   }
 }
 
@@ -274,13 +273,12 @@ void launch_tail2d(const TailArgs<R> &a, int batch, const SolveState *st, cudaSt
 
 #define HH_INST_CYCLE2D(R)                                                                  \
   template cudaError_t init_cycle2d<R>();                                                   \
-  template void launch_down2d<R>(int, const LevelK<R> &, const Cx<R>::T *, int,             \
-                                 const Cx<R>::T *, Cx<R>::T *, Cx<R>::T *, Cx<R>::T,        \
-                                 Cx<R>::T, int, const Lay &, int, const SolveState *,       \
-                                 double *, const CheckCtx &, cudaStream_t);                 \
-  template void launch_up2d<R>(int, const LevelK<R> &, const Cx<R>::T *, const Cx<R>::T *,  \
-                               const Cx<R>::T *, Cx<R>::T *, Cx<R>::T, int, const Lay &,    \
-                               int, const SolveState *, cudaStream_t);                      \
+  template void launch_down2d<R>(int, const DownMaps &, const LevelK<R> &, int, Cx<R>::T *, \
+                                 Cx<R>::T *, Cx<R>::T, Cx<R>::T, int, const Lay &, int,     \
+                                 const SolveState *, double *, int *, const CheckCtx &,     \
+                                 cudaStream_t);                                             \
+  template void launch_up2d<R>(int, const UpMaps &, const LevelK<R> &, Cx<R>::T *, Cx<R>::T,\
+                               int, int, const SolveState *, int *, cudaStream_t);          \
   template void launch_tail2d<R>(const TailArgs<R> &, int, const SolveState *, cudaStream_t);
 
 HH_INST_CYCLE2D(float)

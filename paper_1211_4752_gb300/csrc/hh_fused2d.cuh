@@ -1,4 +1,4 @@
-// Fused, shared-memory-tiled 2-D cycle kernels (5-point stencil).
+// Fused, TMA-staged 2-D cycle kernels (5-point stencil).
 //
 // k_down2d: one pass per level on the way down:
 //     v  = u + omega D^{-1} (f - A u)         (pre-smoothing, Eq. (wjacobi))
@@ -8,12 +8,17 @@
 // k_up2d: one pass per level on the way up:
 //     w  = v + P e ;  u' = w + omega D^{-1} (f - A w)
 //
-// A block owns a BX x BY tile of fine points (x0, y0 even) and the BX/2 x BY/2
-// coarse points whose fine positions (2c+1) fall inside it.  Halos are
-// recomputed instead of exchanged: k_down2d stages u on the tile + 2, computes
-// v on the tile + 1 and the residual on [x0, x0+BX] x [y0, y0+BY], so every
-// value it needs is produced inside the block.  Points outside the domain hold
-// zero (homogeneous Dirichlet) at every stage.
+// A block owns a BX x BY tile of fine points (x0, y0 multiples of 4) and the
+// BX/2 x BY/2 coarse points whose fine positions (2c+1) fall inside it.
+// Thread 0 fetches the tile and its halo with one tensor-map bulk copy per
+// array (zero-filled outside the domain); halos are recomputed, not
+// exchanged: the down pass computes v on the tile + 1 and the residual on
+// [x0, x0+BX] x [y0, y0+BY], so every value it needs is produced inside the
+// block.  Points outside the domain hold zero at every stage.
+//
+// The compute phases use a column-segment mapping: a thread owns one column
+// of a region and a run of its rows, carrying the values above, at and below
+// the current point in registers (3 shared loads per stencil).
 //
 // Specialisations (block-uniform, chosen at run time):
 //   CHECK: the tile (+ halo) touches the domain boundary -> bounds tests;
@@ -24,28 +29,52 @@
 #include "hh_internal.h"
 #include "hh_complex.cuh"
 #include "hh_check.cuh"
+#include "hh_tma.cuh"
 
 namespace hh {
 
+__host__ __device__ constexpr size_t al128(size_t b) { return (b + 127) / 128 * 128; }
+
 template <typename R, int BX, int BY> struct Down2D {
   using C = typename Cx<R>::T;
-  static constexpr int UW = BX + 5, UH = BY + 5;  // u staged on tile + 2
-  static constexpr int VW = BX + 3, VH = BY + 3;  // v, f, k2 on tile + 1
-  static constexpr int RW = BX + 1, RH = BY + 1;  // residual on [x0, x0+BX]
-  static constexpr size_t smem =
-      sizeof(C) * (size_t)UW * UH +      // s_u, later the residual
-      sizeof(C) * (size_t)VW * VH * 2 +  // s_v, s_f
-      sizeof(R) * (size_t)VW * VH +      // s_k
-      sizeof(C) * 3 * (size_t)(VW + VH); // coefficient tables
+  static_assert(BX % 4 == 0 && BY % 2 == 0, "tile origin must be 16-byte aligned");
+  static constexpr int UW = BX + 6, UH = BY + 5;  // u tile at (x0-2, y0-2)
+  static constexpr int FW = BX + 6, FH = BY + 3;  // f tile at (x0-2, y0-1)
+  static constexpr int KW = BX + 8, KH = BY + 3;  // k2 tile at (x0-4, y0-1)
+  static constexpr int VW = BX + 3, VH = BY + 3;  // v region at (x0-1, y0-1)
+  static constexpr int RW = BX + 1, RH = BY + 1;  // residual region at (x0, y0)
+  static constexpr size_t oU = 0;
+  static constexpr size_t oF = al128(oU + sizeof(C) * UW * UH);
+  static constexpr size_t oK = al128(oF + sizeof(C) * FW * FH);
+  static constexpr size_t oV = al128(oK + sizeof(R) * KW * KH);
+  static constexpr size_t oT = al128(oV + sizeof(C) * VW * VH);
+  static constexpr size_t oB = al128(oT + sizeof(C) * 3 * (VW + VH));
+  static constexpr size_t smem = oB + 16 + 128;   // + base alignment slack
+  static constexpr unsigned bU = sizeof(C) * UW * UH, bF = sizeof(C) * FW * FH,
+                            bK = sizeof(R) * KW * KH;
 };
 
 template <typename R, int BX, int BY> struct Up2D {
   using C = typename Cx<R>::T;
-  static constexpr int WW = BX + 2, WH = BY + 2;            // w on tile + 1
-  static constexpr int EW = BX / 2 + 2, EH = BY / 2 + 2;    // coarse e
-  static constexpr size_t smem = sizeof(C) * ((size_t)WW * WH + (size_t)EW * EH) +
-                                 sizeof(C) * 3 * (size_t)(WW + WH);
+  static constexpr int VW = BX + 4, VH = BY + 2;            // v tile at (x0-2, y0-1)
+  static constexpr int EW = BX / 2 + 4, EH = BY / 2 + 2;    // e tile at (x0/2-2, y0/2-1)
+  static constexpr int WW = BX + 2, WH = BY + 2;            // w region at (x0-1, y0-1)
+  static constexpr size_t oV = 0;
+  static constexpr size_t oE = al128(oV + sizeof(C) * VW * VH);
+  static constexpr size_t oF = al128(oE + sizeof(C) * EW * EH);
+  static constexpr size_t oK = al128(oF + sizeof(C) * BX * BY);
+  static constexpr size_t oW = al128(oK + sizeof(R) * BX * BY);
+  static constexpr size_t oT = al128(oW + sizeof(C) * WW * WH);
+  static constexpr size_t oB = al128(oT + sizeof(C) * 3 * (WW + WH));
+  static constexpr size_t smem = oB + 16 + 128;
+  static constexpr unsigned bV = sizeof(C) * VW * VH, bE = sizeof(C) * EW * EH,
+                            bF = sizeof(C) * BX * BY, bK = sizeof(R) * BX * BY;
 };
+
+__device__ __forceinline__ unsigned char *align_smem128(unsigned char *p) {
+  const uint32_t a = smem_u32(p);
+  return p + ((128u - (a & 127u)) & 127u);
+}
 
 // Iterate (x, y) over a W x H region with blockDim.x threads, row-major,
 // without a division per step.
@@ -65,72 +94,52 @@ __device__ __forceinline__ bool tile_in(const LevelK<R> &L, int lo, int hi, int 
   return lo >= 0 && hi < N && (!uniform || (lo >= L.ulo && hi <= L.uhi));
 }
 
+// Coefficient tables of the columns x0-1+i (i < W) and rows y0-1+j (j < H);
+// zero outside the domain.
+template <typename R, bool CHECK>
+__device__ __forceinline__ void load_tables(const LevelK<R> &L, typename Cx<R>::T *s_cx,
+                                            typename Cx<R>::T *s_cy, int W, int H, int x0,
+                                            int y0) {
+  using C = typename Cx<R>::T;
+  const int N = L.N;
+  const C zc = czero<C>();
+  for (int i = threadIdx.x; i < W; i += blockDim.x) {
+    const int gx = x0 - 1 + i;
+    const bool in = !CHECK || (gx >= 0 && gx < N);
+    s_cx[i] = in ? L.coef[gx] : zc;
+    s_cx[W + i] = in ? L.coef[N + gx] : zc;
+    s_cx[2 * W + i] = in ? L.coef[2 * N + gx] : zc;
+  }
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    const int gy = y0 - 1 + i;
+    const bool in = !CHECK || (gy >= 0 && gy < N);
+    s_cy[i] = in ? L.coef[3 * N + gy] : zc;
+    s_cy[H + i] = in ? L.coef[4 * N + gy] : zc;
+    s_cy[2 * H + i] = in ? L.coef[5 * N + gy] : zc;
+  }
+}
+
 template <typename R, int BX, int BY, bool CHECK, bool FAST>
-__device__ __forceinline__ void down_body(
-    const LevelK<R> &L, const typename Cx<R>::T *__restrict__ ub, bool zero,
-    const typename Cx<R>::T *__restrict__ fb, typename Cx<R>::T *__restrict__ vb,
+__device__ __forceinline__ void down_compute(
+    const LevelK<R> &L, bool zero, typename Cx<R>::T *__restrict__ vb,
     typename Cx<R>::T *__restrict__ fcb, typename Cx<R>::T cs, typename Cx<R>::T omega,
-    int kconst, int x0, int y0, int Pc, unsigned char *smem_raw, R &acc) {
+    int kconst, int x0, int y0, int Pc, unsigned char *base, R &acc) {
   using C = typename Cx<R>::T;
   using S = Down2D<R, BX, BY>;
-  constexpr int UW = S::UW, UH = S::UH, VW = S::VW, VH = S::VH, RW = S::RW, RH = S::RH;
+  constexpr int UW = S::UW, FW = S::FW, KW = S::KW, VW = S::VW, VH = S::VH, RW = S::RW,
+                RH = S::RH;
   constexpr int NT = 256;
-  C *s_u = reinterpret_cast<C *>(smem_raw);
-  C *s_v = s_u + UW * UH;
-  C *s_f = s_v + VW * VH;
-  C *s_cx = s_f + VW * VH;     // [3][VW]: lo, dg, up of columns x0-1 .. x0+BX+1
-  C *s_cy = s_cx + 3 * VW;     // [3][VH]
-  R *s_k = reinterpret_cast<R *>(s_cy + 3 * VH);
-  C *s_r = s_u;                // the residual reuses the staging of u
-  const int N = L.N, Nc = (N + 1) / 2 - 1, P = L.P, KP = L.KP;
+  const C *s_u = reinterpret_cast<const C *>(base + S::oU);
+  const C *s_f = reinterpret_cast<const C *>(base + S::oF);
+  const R *s_k = reinterpret_cast<const R *>(base + S::oK);
+  C *s_v = reinterpret_cast<C *>(base + S::oV);
+  const C *s_cx = reinterpret_cast<const C *>(base + S::oT);
+  const C *s_cy = s_cx + 3 * VW;
+  C *s_r = reinterpret_cast<C *>(base + S::oU);   // the residual reuses the u tile
+  const int N = L.N, Nc = (N + 1) / 2 - 1, P = L.P;
   const int tid = threadIdx.x;
   const C zc = czero<C>();
   const R kc = kconst ? L.k2[0] : R(0);
-
-  if (!FAST) {
-    for (int i = tid; i < VW; i += NT) {
-      const int gx = x0 - 1 + i;
-      const bool in = !CHECK || (gx >= 0 && gx < N);
-      s_cx[i] = in ? L.coef[gx] : zc;
-      s_cx[VW + i] = in ? L.coef[N + gx] : zc;
-      s_cx[2 * VW + i] = in ? L.coef[2 * N + gx] : zc;
-    }
-    for (int i = tid; i < VH; i += NT) {
-      const int gy = y0 - 1 + i;
-      const bool in = !CHECK || (gy >= 0 && gy < N);
-      s_cy[i] = in ? L.coef[3 * N + gy] : zc;
-      s_cy[VH + i] = in ? L.coef[4 * N + gy] : zc;
-      s_cy[2 * VH + i] = in ? L.coef[5 * N + gy] : zc;
-    }
-  }
-  {
-    const C *fo = fb + (y0 - 1) * P + (x0 - 1);
-    const R *ko = L.k2 + (y0 - 1) * KP + (x0 - 1);
-    Walk<VW> w(tid);
-    for (int i = tid; i < VW * VH; i += NT, w.next(NT)) {
-      bool in = true;
-      if (CHECK) {
-        const int gx = x0 - 1 + w.x, gy = y0 - 1 + w.y;
-        in = gx >= 0 && gx < N && gy >= 0 && gy < N;
-      }
-      s_f[i] = in ? fo[w.y * P + w.x] : zc;
-      if (!kconst) s_k[i] = in ? ko[w.y * KP + w.x] : R(0);
-    }
-  }
-  if (!zero) {
-    const C *uo = ub + (y0 - 2) * P + (x0 - 2);
-    Walk<UW> w(tid);
-    for (int i = tid; i < UW * UH; i += NT, w.next(NT)) {
-      bool in = true;
-      if (CHECK) {
-        const int gx = x0 - 2 + w.x, gy = y0 - 2 + w.y;
-        in = gx >= 0 && gx < N && gy >= 0 && gy < N;
-      }
-      s_u[i] = in ? uo[w.y * P + w.x] : zc;
-    }
-  }
-  __syncthreads();
-
   // uniform-coefficient constants (FAST): nb = c0 * (sum of neighbours),
   // D = 4 c0 - beta k2, W = omega / D
   const C c0 = FAST ? L.c0 : zc;
@@ -138,10 +147,8 @@ __device__ __forceinline__ void down_body(
   const C Dk = FAST ? csub(d0, cscale(L.beta, kc)) : zc;
   const C Wk = FAST ? cmul(omega, crcp(Dk)) : zc;
 
-  // Column-segment mapping: thread -> one column of the region and a run of
-  // consecutive rows; the values above, at and below the current point ride
-  // along the column in registers (3 shared loads per point).
-  // v = u + omega D^{-1}(f - A u) on tile + 1; |f - A u|^2 on the tile
+  // v = u + omega D^{-1}(f - A u) on tile + 1; |f - A u|^2 on the tile.
+  // v point (tx, ty) <-> u tile (tx+1, ty+1), f tile (tx+1, ty), k tile (tx+3, ty)
   {
     constexpr int NS = NT / VW;                  // row segments per column
     const int tx = tid % VW, sg = tid / VW;
@@ -153,11 +160,12 @@ __device__ __forceinline__ void down_body(
       C clo = zc, cdg = zc, cup = zc;
       if (!FAST) { clo = s_cx[tx]; cdg = s_cx[VW + tx]; cup = s_cx[2 * VW + tx]; }
       C *vo = vb + (y0 - 1) * P + gx;
-      const C *col = s_u + tx + 1;               // u tile column of this v column
+      const C *col = s_u + tx + 1;
+      const C *fcol = s_f + tx + 1;
+      const R *kcol = s_k + tx + 3;
       C un = zc, uc = zc;
       if (!zero) { un = col[r0 * UW]; uc = col[(r0 + 1) * UW]; }
       for (int ty = r0; ty < r1; ++ty) {
-        const int i = ty * VW + tx;
         C ud = zc, ul = zc, ur = zc;
         if (!zero) {
           const int j = (ty + 1) * UW;
@@ -172,11 +180,12 @@ __device__ __forceinline__ void down_body(
           C D, Wd;
           if (FAST && kconst) { D = Dk; Wd = Wk; }
           else {
-            D = FAST ? csub(d0, cscale(L.beta, s_k[i]))
-                     : csub(cadd(cdg, s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[i]));
+            const R kk = kconst ? kc : kcol[ty * KW];
+            D = FAST ? csub(d0, cscale(L.beta, kk))
+                     : csub(cadd(cdg, s_cy[VH + ty]), cscale(L.beta, kk));
             Wd = cmul(omega, crcp(D));
           }
-          C r = s_f[i];
+          C r = fcol[ty * FW];
           if (!zero) {
             C nb;
             if (FAST) nb = cmul(c0, cadd(cadd(ul, ur), cadd(un, ud)));
@@ -194,7 +203,7 @@ __device__ __forceinline__ void down_body(
             acc += r.x * r.x + r.y * r.y;
           }
         }
-        s_v[i] = v;
+        s_v[ty * VW + tx] = v;
         un = uc;
         uc = ud;
       }
@@ -203,16 +212,19 @@ __device__ __forceinline__ void down_body(
   __syncthreads();
 
   // residual f - A v on [x0, x0+BX] x [y0, y0+BY]
+  // r point (rx, ry) <-> v tile (rx+1, ry+1), f tile (rx+2, ry+1), k tile (rx+4, ry+1)
   {
     constexpr int NS = NT / RW;
     const int rx = tid % RW, sg = tid / RW;
     if (sg < NS) {
       const int q0 = sg * RH / NS, q1 = (sg + 1) * RH / NS;
-      const int tx = rx + 1;                     // column in the v tile
+      const int tx = rx + 1;
       const bool colin = !CHECK || (x0 + rx < N);
       C clo = zc, cdg = zc, cup = zc;
       if (!FAST) { clo = s_cx[tx]; cdg = s_cx[VW + tx]; cup = s_cx[2 * VW + tx]; }
       const C *col = s_v + tx;
+      const C *fcol = s_f + rx + 2;
+      const R *kcol = s_k + rx + 4;
       C vn = col[q0 * VW], vc = col[(q0 + 1) * VW];
       for (int ry = q0; ry < q1; ++ry) {
         const int ty = ry + 1;
@@ -221,17 +233,18 @@ __device__ __forceinline__ void down_body(
         C r = zc;
         if (colin && (!CHECK || y0 + ry < N)) {
           C D, nb;
+          const R kk = kconst ? kc : kcol[ty * KW];
           if (FAST) {
-            D = kconst ? Dk : csub(d0, cscale(L.beta, s_k[j + tx]));
+            D = kconst ? Dk : csub(d0, cscale(L.beta, kk));
             nb = cmul(c0, cadd(cadd(vl, vr), cadd(vn, vd)));
           } else {
-            D = csub(cadd(cdg, s_cy[VH + ty]), cscale(L.beta, kconst ? kc : s_k[j + tx]));
+            D = csub(cadd(cdg, s_cy[VH + ty]), cscale(L.beta, kk));
             nb = cmul(clo, vl);
             nb = cfma(cup, vr, nb);
             nb = cfma(s_cy[ty], vn, nb);
             nb = cfma(s_cy[2 * VH + ty], vd, nb);
           }
-          r = cadd(csub(s_f[j + tx], cmul(D, vc)), nb);
+          r = cadd(csub(fcol[ty * FW], cmul(D, vc)), nb);
         }
         s_r[ry * RW + rx] = r;
         vn = vc;
@@ -262,37 +275,59 @@ __device__ __forceinline__ void down_body(
 // variant without that call serves the host-driven loop and profilers).
 template <typename R, int BX, int BY, bool COND>
 __global__ void __launch_bounds__(256)
-k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
-         const typename Cx<R>::T *__restrict__ f, typename Cx<R>::T *__restrict__ v_out,
-         typename Cx<R>::T *__restrict__ fc, typename Cx<R>::T cs,
-         typename Cx<R>::T omega, int kconst, Lay lc, const SolveState *__restrict__ st,
-         double *__restrict__ partials, CheckCtx chk) {
+k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
+         typename Cx<R>::T *__restrict__ v_out, typename Cx<R>::T *__restrict__ fc,
+         typename Cx<R>::T cs, typename Cx<R>::T omega, int kconst, Lay lc,
+         const SolveState *__restrict__ st, double *__restrict__ partials, int *err,
+         CheckCtx chk) {
   using C = typename Cx<R>::T;
+  using S = Down2D<R, BX, BY>;
   const int b = blockIdx.z;
   // blocks of a finished right-hand side skip the work but still take part
   // in the arrival count of the stop test
-  const bool act = !(st && !st[b].active);
+  bool act = !(st && !st[b].active);
   if (!act && !(partials && chk.mode != CHECK_MODE_NONE)) return;
   const bool zero = zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = L.N, Nc = (N + 1) / 2 - 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *base = align_smem128(smem_raw);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(base + S::oB);
+  const int N = L.N;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-  const C *ub = u_in + (size_t)b * L.S;
-  const C *fb = f + (size_t)b * L.S;
-  C *vb = v_out + (size_t)b * L.S;
-  C *fcb = fc + (size_t)b * lc.S;
   R acc = R(0);
-  const bool inner = tile_in(L, x0 - 2, x0 + BX + 2, N, false) &&
-                     tile_in(L, y0 - 2, y0 + BY + 2, N, false);
-  const bool fast = inner && tile_in(L, x0 - 2, x0 + BX + 2, N, true) &&
-                    tile_in(L, y0 - 2, y0 + BY + 2, N, true);
   if (act) {
-    if (fast)
-      down_body<R, BX, BY, false, true>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, lc.P, smem_raw, acc);
-    else if (inner)
-      down_body<R, BX, BY, false, false>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, lc.P, smem_raw, acc);
-    else
-      down_body<R, BX, BY, true, false>(L, ub, zero, fb, vb, fcb, cs, omega, kconst, x0, y0, lc.P, smem_raw, acc);
+    if (threadIdx.x == 0) {
+      mbar_init(mbar, 1);
+      mbar_fence_init();
+      mbar_expect_tx(mbar, (zero ? 0u : S::bU) + S::bF + (kconst ? 0u : S::bK));
+      if (!zero) tma_load_3d(base + S::oU, &maps.u, 2 * (x0 - 2), y0 - 2, b, mbar);
+      tma_load_3d(base + S::oF, &maps.f, 2 * (x0 - 2), y0 - 1, b, mbar);
+      if (!kconst) tma_load_2d(base + S::oK, &maps.k, x0 - 4, y0 - 1, mbar);
+    }
+    const bool inner = tile_in(L, x0 - 2, x0 + BX + 2, N, false) &&
+                       tile_in(L, y0 - 2, y0 + BY + 2, N, false);
+    const bool fast = inner && tile_in(L, x0 - 2, x0 + BX + 2, N, true) &&
+                      tile_in(L, y0 - 2, y0 + BY + 2, N, true);
+    C *s_cx = reinterpret_cast<C *>(base + S::oT);
+    if (!fast) {
+      if (inner) load_tables<R, false>(L, s_cx, s_cx + 3 * S::VW, S::VW, S::VH, x0, y0);
+      else load_tables<R, true>(L, s_cx, s_cx + 3 * S::VW, S::VW, S::VH, x0, y0);
+    }
+    __syncthreads();   // barrier initialised (and tables written) before any wait
+    const bool ok = mbar_wait_bounded(mbar, 0);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(err, (int)HH_ERR_TIMEOUT);
+      mbar_wait_bounded(mbar, 0);   // let copies still in flight land
+      act = false;
+    } else {
+      C *vb = v_out + (size_t)b * L.S;
+      C *fcb = fc + (size_t)b * lc.S;
+      if (fast)
+        down_compute<R, BX, BY, false, true>(L, zero, vb, fcb, cs, omega, kconst, x0, y0, lc.P, base, acc);
+      else if (inner)
+        down_compute<R, BX, BY, false, false>(L, zero, vb, fcb, cs, omega, kconst, x0, y0, lc.P, base, acc);
+      else
+        down_compute<R, BX, BY, true, false>(L, zero, vb, fcb, cs, omega, kconst, x0, y0, lc.P, base, acc);
+    }
   }
   if (partials) {
     const double s = block_sum_d((double)acc);
@@ -303,63 +338,36 @@ k_down2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in, int zero_mode,
 }
 
 template <typename R, int BX, int BY, bool CHECK, bool FAST>
-__device__ __forceinline__ void up_body(
-    const LevelK<R> &L, const typename Cx<R>::T *__restrict__ vb,
-    const typename Cx<R>::T *__restrict__ eb, const typename Cx<R>::T *__restrict__ fb,
-    typename Cx<R>::T *__restrict__ ob, typename Cx<R>::T omega, int kconst, int x0, int y0,
-    int Pc, unsigned char *smem_raw) {
+__device__ __forceinline__ void up_compute(const LevelK<R> &L, typename Cx<R>::T *__restrict__ ob,
+                                           typename Cx<R>::T omega, int kconst, int x0, int y0,
+                                           unsigned char *base) {
   using C = typename Cx<R>::T;
   using S = Up2D<R, BX, BY>;
-  constexpr int WW = S::WW, WH = S::WH, EW = S::EW, EH = S::EH;
+  constexpr int VW = S::VW, EW = S::EW, WW = S::WW, WH = S::WH;
   constexpr int NT = 256;
-  C *s_w = reinterpret_cast<C *>(smem_raw);
-  C *s_e = s_w + WW * WH;
-  C *s_cx = s_e + EW * EH;   // [3][WW]
-  C *s_cy = s_cx + 3 * WW;   // [3][WH]
-  const int N = L.N, Nc = (N + 1) / 2 - 1, P = L.P, KP = L.KP;
-  const int ex0 = x0 / 2 - 1, ey0 = y0 / 2 - 1;
+  const C *s_v = reinterpret_cast<const C *>(base + S::oV);
+  const C *s_e = reinterpret_cast<const C *>(base + S::oE);
+  const C *s_f = reinterpret_cast<const C *>(base + S::oF);
+  const R *s_k = reinterpret_cast<const R *>(base + S::oK);
+  C *s_w = reinterpret_cast<C *>(base + S::oW);
+  const C *s_cx = reinterpret_cast<const C *>(base + S::oT);
+  const C *s_cy = s_cx + 3 * WW;
+  const int N = L.N, P = L.P;
   const int tid = threadIdx.x;
   const C zc = czero<C>();
   const R kc = kconst ? L.k2[0] : R(0);
-
-  if (!FAST) {
-    for (int i = tid; i < WW; i += NT) {
-      const int gx = x0 - 1 + i;
-      const bool in = !CHECK || (gx >= 0 && gx < N);
-      s_cx[i] = in ? L.coef[gx] : zc;
-      s_cx[WW + i] = in ? L.coef[N + gx] : zc;
-      s_cx[2 * WW + i] = in ? L.coef[2 * N + gx] : zc;
-    }
-    for (int i = tid; i < WH; i += NT) {
-      const int gy = y0 - 1 + i;
-      const bool in = !CHECK || (gy >= 0 && gy < N);
-      s_cy[i] = in ? L.coef[3 * N + gy] : zc;
-      s_cy[WH + i] = in ? L.coef[4 * N + gy] : zc;
-      s_cy[2 * WH + i] = in ? L.coef[5 * N + gy] : zc;
-    }
-  }
+  // w = v + P e on tile + 1 (zero outside the domain).  w point (tx, ty) <->
+  // v tile (tx+1, ty); fine x0-1+tx odd <-> tx even: coincident coarse
+  // column, e tile column tx/2 + 1; else e tile columns (tx>>1)+1, (tx>>1)+2
+  // (same along y with e tile rows ty>>1, (ty>>1)+1)
   {
-    Walk<EW> w(tid);
-    for (int i = tid; i < EW * EH; i += NT, w.next(NT)) {
-      const int cx = ex0 + w.x, cy = ey0 + w.y;
-      // the first coarse row/column of a tile at the low boundary is outside
-      const bool in = cx >= 0 && cx < Nc && cy >= 0 && cy < Nc;
-      s_e[i] = in ? eb[cy * Pc + cx] : zc;
-    }
-  }
-  __syncthreads();
-  // w = v + P e on tile + 1 (zero outside the domain)
-  {
-    const C *vo = vb + (y0 - 1) * P + (x0 - 1);
     Walk<WW> w(tid);
     for (int i = tid; i < WW * WH; i += NT, w.next(NT)) {
       const int tx = w.x, ty = w.y;
       C val = zc;
       if (!CHECK || (x0 - 1 + tx >= 0 && x0 - 1 + tx < N && y0 - 1 + ty >= 0 && y0 - 1 + ty < N)) {
-        // fine x odd <-> tx even: coincident coarse column tx/2; else the two
-        // neighbouring coarse columns tx>>1, (tx>>1)+1 (same along y)
         C p;
-        const int c0 = tx >> 1, r0 = (ty >> 1) * EW;
+        const int c0 = (tx >> 1) + 1, r0 = (ty >> 1) * EW;
         if (!(ty & 1)) {
           p = (tx & 1) ? cscale(cadd(s_e[r0 + c0], s_e[r0 + c0 + 1]), R(0.5)) : s_e[r0 + c0];
         } else if (tx & 1) {
@@ -368,7 +376,7 @@ __device__ __forceinline__ void up_body(
         } else {
           p = cscale(cadd(s_e[r0 + c0], s_e[r0 + EW + c0]), R(0.5));
         }
-        val = cadd(vo[ty * P + tx], p);
+        val = cadd(s_v[ty * VW + tx + 1], p);
       }
       s_w[i] = val;
     }
@@ -389,31 +397,29 @@ __device__ __forceinline__ void up_body(
       C clo = zc, cdg = zc, cup = zc;
       if (!FAST) { clo = s_cx[tx]; cdg = s_cx[WW + tx]; cup = s_cx[2 * WW + tx]; }
       const C *col = s_w + tx;
-      const C *fo = fb + y0 * P + x0 + lx;
-      const R *ko = L.k2 + y0 * KP + x0 + lx;
       C *oo = ob + y0 * P + x0 + lx;
       C wn = col[q0 * WW], wc = col[(q0 + 1) * WW];
       for (int ly = q0; ly < q1; ++ly) {
         const int j = (ly + 1) * WW;
         const C wd = col[j + WW], wl = col[j - 1], wr = col[j + 1];
         if (colin && (!CHECK || y0 + ly < N)) {
-          const int g = ly * P, gk = ly * KP;
           C D, Wd, nb;
+          const R kk = kconst ? kc : s_k[ly * BX + lx];
           if (FAST) {
             if (kconst) { D = Dk; Wd = Wk; }
-            else { D = csub(d0, cscale(L.beta, ko[gk])); Wd = cmul(omega, crcp(D)); }
+            else { D = csub(d0, cscale(L.beta, kk)); Wd = cmul(omega, crcp(D)); }
             nb = cmul(c0, cadd(cadd(wl, wr), cadd(wn, wd)));
           } else {
             const int ty = ly + 1;
-            D = csub(cadd(cdg, s_cy[WH + ty]), cscale(L.beta, kconst ? kc : ko[gk]));
+            D = csub(cadd(cdg, s_cy[WH + ty]), cscale(L.beta, kk));
             Wd = cmul(omega, crcp(D));
             nb = cmul(clo, wl);
             nb = cfma(cup, wr, nb);
             nb = cfma(s_cy[ty], wn, nb);
             nb = cfma(s_cy[2 * WH + ty], wd, nb);
           }
-          const C r = cadd(csub(fo[g], cmul(D, wc)), nb);
-          oo[g] = cadd(wc, cmul(Wd, r));
+          const C r = cadd(csub(s_f[ly * BX + lx], cmul(D, wc)), nb);
+          oo[ly * P] = cadd(wc, cmul(Wd, r));
         }
         wn = wc;
         wc = wd;
@@ -424,29 +430,45 @@ __device__ __forceinline__ void up_body(
 
 template <typename R, int BX, int BY>
 __global__ void __launch_bounds__(256)
-k_up2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ v_in,
-       const typename Cx<R>::T *__restrict__ e, const typename Cx<R>::T *__restrict__ f,
-       typename Cx<R>::T *__restrict__ u_out, typename Cx<R>::T omega, int kconst, Lay lc,
-       const SolveState *__restrict__ st) {
+k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__restrict__ u_out,
+       typename Cx<R>::T omega, int kconst, const SolveState *__restrict__ st, int *err) {
   using C = typename Cx<R>::T;
+  using S = Up2D<R, BX, BY>;
   const int b = blockIdx.z;
   if (st && !st[b].active) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = L.N, Nc = (N + 1) / 2 - 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *base = align_smem128(smem_raw);
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(base + S::oB);
+  const int N = L.N;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-  const C *vb = v_in + (size_t)b * L.S;
-  const C *eb = e + (size_t)b * lc.S;
-  const C *fb = f + (size_t)b * L.S;
-  C *ob = u_out + (size_t)b * L.S;
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    mbar_fence_init();
+    mbar_expect_tx(mbar, S::bV + S::bE + S::bF + (kconst ? 0u : S::bK));
+    tma_load_3d(base + S::oV, &maps.v, 2 * (x0 - 2), y0 - 1, b, mbar);
+    tma_load_3d(base + S::oE, &maps.e, 2 * (x0 / 2 - 2), y0 / 2 - 1, b, mbar);
+    tma_load_3d(base + S::oF, &maps.f, 2 * x0, y0, b, mbar);
+    if (!kconst) tma_load_2d(base + S::oK, &maps.k, x0, y0, mbar);
+  }
   const bool inner = tile_in(L, x0 - 1, x0 + BX, N, false) && tile_in(L, y0 - 1, y0 + BY, N, false);
   const bool fast = inner && tile_in(L, x0 - 1, x0 + BX, N, true) &&
                     tile_in(L, y0 - 1, y0 + BY, N, true);
-  if (fast)
-    up_body<R, BX, BY, false, true>(L, vb, eb, fb, ob, omega, kconst, x0, y0, lc.P, smem_raw);
-  else if (inner)
-    up_body<R, BX, BY, false, false>(L, vb, eb, fb, ob, omega, kconst, x0, y0, lc.P, smem_raw);
-  else
-    up_body<R, BX, BY, true, false>(L, vb, eb, fb, ob, omega, kconst, x0, y0, lc.P, smem_raw);
+  C *s_cx = reinterpret_cast<C *>(base + S::oT);
+  if (!fast) {
+    if (inner) load_tables<R, false>(L, s_cx, s_cx + 3 * S::WW, S::WW, S::WH, x0, y0);
+    else load_tables<R, true>(L, s_cx, s_cx + 3 * S::WW, S::WW, S::WH, x0, y0);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(mbar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(err, (int)HH_ERR_TIMEOUT);
+    mbar_wait_bounded(mbar, 0);
+    return;
+  }
+  C *ob = u_out + (size_t)b * L.S;
+  if (fast) up_compute<R, BX, BY, false, true>(L, ob, omega, kconst, x0, y0, base);
+  else if (inner) up_compute<R, BX, BY, false, false>(L, ob, omega, kconst, x0, y0, base);
+  else up_compute<R, BX, BY, true, false>(L, ob, omega, kconst, x0, y0, base);
 }
 
 }  // namespace hh
