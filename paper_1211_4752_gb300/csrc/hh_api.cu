@@ -16,6 +16,7 @@
 #include <complex>
 #include <cstdio>
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -112,6 +113,7 @@ struct hh_handle {
   int parts_cap = 0;                // capacity of `partials` per RHS
   unsigned int *counter = nullptr;  // arrivals of the fused stop test
   int *err = nullptr;               // device status word of bounded waits
+  float2 *tailop[2] = {nullptr, nullptr};  // tail operator per direction (mixed)
   DownMaps dmap[MAXL];              // tensor maps of the fused kernels, per level
   UpMaps umap[MAXL];
   std::vector<void *> allocs;
@@ -377,6 +379,21 @@ template <typename R> CheckCtx check_ctx(hh_handle *h, int check, unsigned long 
   return c;
 }
 
+// Levels tail0 .. coarsest of a cycle: the dense tail operator where one
+// was built (complex64 cycles), else the single-block tail kernel.
+template <typename R>
+void enqueue_tail(hh_handle *h, int dir, int batch, const SolveState *st, cudaStream_t s) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (h->tailop[dir]) {
+      const LevelHost &v = h->lv[h->tail0];
+      launch_tail_apply(h->tailop[dir], v.N, v.P, (int)v.S, h->w32.f[h->tail0],
+                        h->w32.u_post[h->tail0], batch, st, s);
+      return;
+    }
+  }
+  launch_tail2d<R>(tail_args<R>(h, dir), batch, st, s);
+}
+
 // The same V-cycle with the fused 2-D kernels: one down pass per level
 // (pre-smoothing + residual + restriction), one kernel for every level from
 // tail0 to the coarsest, one up pass per level (correction + post-smoothing).
@@ -396,7 +413,7 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
                      W.f[l + 1], cscal<R>(h, l, dir), om, h->kconst, lay_of(h, l + 1), batch, st,
                      norm ? h->partials : nullptr, h->err, chk, s);
   }
-  launch_tail2d<R>(tail_args<R>(h, dir), batch, st, s);
+  enqueue_tail<R>(h, dir, batch, st, s);
   for (int l = T - 1; l >= 0; --l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
     launch_up2d<R>(h->variant[l], h->umap[l], K, W.u_post[l], om, h->kconst, batch, st,
@@ -636,7 +653,7 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
   const auto om = omega<R>(h, 0);
   const bool two = h->dim == 2;
   if (kernel == 4) {
-    launch_tail2d<R>(tail_args<R>(h, 0), batch, nullptr, s);
+    enqueue_tail<R>(h, 0, batch, nullptr, s);
     return;
   }
   if (h->fused && level < h->tail0 && kernel != 1) {
@@ -734,6 +751,44 @@ template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   HH_CK(cudaGetLastError());
+  return HH_OK;
+}
+
+// Tail operator of direction dir: the FP64 tail kernel run on the N^2 unit
+// right-hand sides of level tail0 (one block each), the responses gathered
+// into rows of T and rounded to complex64.  The two N^2 x S scratch arrays
+// live only during setup.
+hh_status build_tail_op(hh_handle *h, int dir, cudaStream_t s) {
+  const LevelHost &v = h->lv[h->tail0];
+  const int N = v.N, P = v.P, S = (int)v.S, M = N * N;
+  const size_t n = (size_t)M * S;
+  double2 *F = nullptr, *U = nullptr;
+  cudaError_t e = cudaMalloc(&F, n * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&U, n * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, n * sizeof(double2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(U, 0, n * sizeof(double2), s);
+  hh_status r = HH_OK;
+  if (e == cudaSuccess) {
+    r = dev_alloc_n(h, &h->tailop[dir], n);
+    if (r == HH_OK) {
+      launch_unit_rhs(F, N, P, S, s);
+      TailArgs<double> a = tail_args<double>(h, dir);
+      a.lv[0].f = F;
+      a.lv[0].u = U;
+      launch_tail2d<double>(a, M, nullptr, s);
+      launch_tail_gather(U, h->tailop[dir], N, P, S, s);
+      e = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) e = cudaGetLastError();
+    }
+  }
+  if (F) cudaFree(F);
+  if (U) cudaFree(U);
+  if (r != HH_OK) return r;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? HH_ERR_OOM : HH_ERR_CUDA,
+                std::string("tail operator: ") + cudaGetErrorString(e));
+  }
   return HH_OK;
 }
 
@@ -970,6 +1025,12 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   HH_CK(cudaGetLastError());
   if (info_h[0] || info_h[1]) return fail(HH_ERR_ARG, "singular coarsest-level operator");
   if (h->fused) {
+    // complex64 cycles apply the tail as a dense operator (HH_TAIL=kernel in
+    // the environment keeps the tail kernel)
+    const char *te = std::getenv("HH_TAIL");
+    const bool op = !(te && std::strcmp(te, "kernel") == 0);
+    if (op && h->opt.precision == HH_MIXED && h->lv[h->tail0].S <= kTailOpMaxS)
+      for (int dir = 0; dir < 2; ++dir) HH_TRY(build_tail_op(h, dir, s));
     HH_TRY(autotune(h, s));
     for (int l = 0; l < h->tail0; ++l) {
       if (h->opt.precision == HH_FP64) HH_TRY(make_maps<double>(h, l, h->variant[l], &h->dmap[l], &h->umap[l]));

@@ -46,6 +46,9 @@ template <typename C> __device__ __forceinline__ C cdiv(C a, C b) {
   const auto d = b.x * b.x + b.y * b.y;
   return cmk((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
+// fused multiply-add a * b + c in the operands' precision
+__device__ __forceinline__ float fmaf_any(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaf_any(double a, double b, double c) { return fma(a, b, c); }
 // 1 / b (one real division)
 template <typename C> __device__ __forceinline__ C crcp(C b) {
   const auto s = decltype(b.x)(1) / (b.x * b.x + b.y * b.y);

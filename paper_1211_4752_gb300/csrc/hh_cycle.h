@@ -77,4 +77,17 @@ void launch_up2d(int variant, const UpMaps &maps, const LevelK<R> &L, typename C
 template <typename R>
 void launch_tail2d(const TailArgs<R> &a, int batch, const SolveState *st, cudaStream_t s);
 
+// Tail operator.  From a zero initial guess, the part of the V-cycle that the
+// tail kernel runs (levels tail0 .. coarsest) is a fixed linear map
+// u = T f of the right-hand side of level tail0.  T is built once by running
+// the tail kernel on unit right-hand sides; a cycle then applies it as one
+// dense product.  Layout: row i = interior point i of level tail0 (row-major,
+// N x N), column j = pitched position j (0 <= j < S = N * P); the padding
+// columns (j % P >= N) are zero.
+constexpr int kTailOpMaxS = 1024;    // S <= 32 * 32: one register tile per lane
+void launch_unit_rhs(double2 *F, int N, int P, int S, cudaStream_t s);
+void launch_tail_gather(const double2 *U, float2 *T, int N, int P, int S, cudaStream_t s);
+void launch_tail_apply(const float2 *T, int N, int P, int S, const float2 *f, float2 *u,
+                       int batch, const SolveState *st, cudaStream_t s);
+
 }  // namespace hh

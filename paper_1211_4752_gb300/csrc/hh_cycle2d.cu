@@ -218,7 +218,100 @@ __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState
   }
 }
 
+// Column j of the unit right-hand sides: F[j * S + pos(j)] = 1, where pos(j)
+// is the pitched position of interior point j (F zeroed beforehand).
+__global__ void k_unit_rhs(double2 *F, int N, int P, int S) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N * N) return;
+  const int y = j / N, x = j - y * N;
+  F[(size_t)j * S + y * P + x] = make_double2(1.0, 0.0);
+}
+
+// T[i * S + pos(j)] = U[j * S + pos(i)]: response at point i to a unit
+// right-hand side at point j, rounded to complex64; padding columns zero.
+__global__ void k_tail_gather(const double2 *U, float2 *T, int N, int P, int S) {
+  const int M = N * N;
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (size_t)M * S) return;
+  const int i = (int)(q / S), c = (int)(q - (size_t)i * S);
+  const int cy = c / P, cx = c - cy * P;
+  float2 t = make_float2(0.f, 0.f);
+  if (cx < N) {
+    const int j = cy * N + cx;
+    const int iy = i / N, ix = i - iy * N;
+    const double2 v = U[(size_t)j * S + iy * P + ix];
+    t = make_float2((float)v.x, (float)v.y);
+  }
+  T[q] = t;
+}
+
+// u_b = T f_b: one warp per row of T, the row held in registers (lane l
+// owns columns l, l + 32, ...), reused for every right-hand side.  Every
+// load is unconditional (index clamped to column 0 where the column is
+// padding or past S, the value then replaced by zero), so all of a lane's
+// loads are in flight together.  P is a power of two.
+__global__ void __launch_bounds__(256) k_tail_apply(const float2 *__restrict__ T, int N, int P,
+                                                    int S, const float2 *__restrict__ f,
+                                                    float2 *__restrict__ u, int batch,
+                                                    const SolveState *st) {
+  constexpr int Q = kTailOpMaxS / 32;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= N * N) return;
+  float2 t[Q];
+  unsigned live = 0;                      // columns inside the level (not padding)
+  const float2 *row = T + (size_t)i * S;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int c = lane + 32 * q;
+    const bool in = c < S && (c & (P - 1)) < N;
+    const float2 x = __ldg(row + (in ? c : 0));
+    t[q] = in ? x : make_float2(0.f, 0.f);
+    live |= (in ? 1u : 0u) << q;
+  }
+  const int iy = i / N, ix = i - iy * N;
+  for (int b = 0; b < batch; ++b) {
+    if (st && !st[b].active) continue;
+    const float2 *fb = f + (size_t)b * S;
+    float2 v[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const bool in = live >> q & 1u;
+      const float2 x = fb[in ? lane + 32 * q : 0];
+      v[q] = in ? x : make_float2(0.f, 0.f);
+    }
+    float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      ax = fmaf(t[q].x, v[q].x, ax);
+      bx = fmaf(-t[q].y, v[q].y, bx);
+      ay = fmaf(t[q].x, v[q].y, ay);
+      by = fmaf(t[q].y, v[q].x, by);
+    }
+    ax += bx;
+    ay += by;
+    for (int o = 16; o > 0; o >>= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) u[(size_t)b * S + iy * P + ix] = make_float2(ax, ay);
+  }
+}
+
 }  // namespace
+
+void launch_unit_rhs(double2 *F, int N, int P, int S, cudaStream_t s) {
+  const int M = N * N;
+  k_unit_rhs<<<(M + 255) / 256, 256, 0, s>>>(F, N, P, S);
+}
+void launch_tail_gather(const double2 *U, float2 *T, int N, int P, int S, cudaStream_t s) {
+  const size_t tot = (size_t)N * N * S;
+  k_tail_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(U, T, N, P, S);
+}
+void launch_tail_apply(const float2 *T, int N, int P, int S, const float2 *f, float2 *u,
+                       int batch, const SolveState *st, cudaStream_t s) {
+  const int M = N * N;
+  k_tail_apply<<<(M + 7) / 8, 256, 0, s>>>(T, N, P, S, f, u, batch, st);
+}
 
 int tile_parts(int variant, int N) {
   const Shape sh = kShapes[variant];

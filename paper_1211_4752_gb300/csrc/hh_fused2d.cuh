@@ -148,62 +148,76 @@ __device__ __forceinline__ void down_compute(
   const C Wk = FAST ? cmul(omega, crcp(Dk)) : zc;
 
   // v = u + omega D^{-1}(f - A u) on tile + 1; |f - A u|^2 on the tile.
-  // v point (tx, ty) <-> u tile (tx+1, ty+1), f tile (tx+1, ty), k tile (tx+3, ty)
+  // v point (tx, ty) <-> u tile (tx+1, ty+1), f tile (tx+1, ty), k tile (tx+3, ty).
+  // Each thread: one column, RS consecutive rows (compile-time count, the
+  // last segment predicated), so all shared-memory offsets are immediates.
   {
-    constexpr int NS = NT / VW;                  // row segments per column
+    constexpr int NS = NT / VW, RS = (VH + NS - 1) / NS;
     const int tx = tid % VW, sg = tid / VW;
     if (sg < NS) {
-      const int r0 = sg * VH / NS, r1 = (sg + 1) * VH / NS;
+      const int r0 = sg * RS;
       const int gx = x0 - 1 + tx;
       const bool colin = !CHECK || (gx >= 0 && gx < N);
       const bool colown = tx >= 1 && tx <= BX;
       C clo = zc, cdg = zc, cup = zc;
       if (!FAST) { clo = s_cx[tx]; cdg = s_cx[VW + tx]; cup = s_cx[2 * VW + tx]; }
-      C *vo = vb + (y0 - 1) * P + gx;
-      const C *col = s_u + tx + 1;
-      const C *fcol = s_f + tx + 1;
-      const R *kcol = s_k + tx + 3;
+      C *vo = vb + (y0 - 1 + r0) * P + gx;
+      const C *col = s_u + r0 * UW + tx + 1;     // u tile row r0 (above v row r0)
+      const C *fcol = s_f + r0 * FW + tx + 1;
+      const R *kcol = s_k + r0 * KW + tx + 3;
+      C *vcol = s_v + r0 * VW + tx;
       C un = zc, uc = zc;
-      if (!zero) { un = col[r0 * UW]; uc = col[(r0 + 1) * UW]; }
-      for (int ty = r0; ty < r1; ++ty) {
-        C ud = zc, ul = zc, ur = zc;
-        if (!zero) {
-          const int j = (ty + 1) * UW;
-          ud = col[j + UW];
-          ul = col[j - 1];
-          ur = col[j + 1];
-        }
-        bool in = colin;
-        if (CHECK) { const int gy = y0 - 1 + ty; in = in && gy >= 0 && gy < N; }
-        C v = zc;
-        if (in) {
-          C D, Wd;
-          if (FAST && kconst) { D = Dk; Wd = Wk; }
-          else {
-            const R kk = kconst ? kc : kcol[ty * KW];
-            D = FAST ? csub(d0, cscale(L.beta, kk))
-                     : csub(cadd(cdg, s_cy[VH + ty]), cscale(L.beta, kk));
-            Wd = cmul(omega, crcp(D));
-          }
-          C r = fcol[ty * FW];
+      if (!zero) { un = col[0]; uc = col[UW]; }
+#pragma unroll
+      for (int k = 0; k < RS; ++k) {
+        const int ty = r0 + k;
+        C ud = zc;
+        if (ty < VH) {
+          C ul = zc, ur = zc;
           if (!zero) {
-            C nb;
-            if (FAST) nb = cmul(c0, cadd(cadd(ul, ur), cadd(un, ud)));
-            else {
-              nb = cmul(clo, ul);
-              nb = cfma(cup, ur, nb);
-              nb = cfma(s_cy[ty], un, nb);
-              nb = cfma(s_cy[2 * VH + ty], ud, nb);
+            ud = col[(k + 2) * UW];
+            ul = col[(k + 1) * UW - 1];
+            ur = col[(k + 1) * UW + 1];
+          }
+          bool in = colin;
+          if (CHECK) { const int gy = y0 - 1 + ty; in = in && gy >= 0 && gy < N; }
+          C v = zc;
+          if (in) {
+            const C fv = fcol[k * FW];
+            C r;
+            if (FAST && kconst) {
+              // r = f + c0 (uW + uE + uS + uN) - D u ; v = u + W r
+              const C sn = cadd(cadd(ul, ur), cadd(un, ud));
+              r.x = fmaf_any(-Dk.x, uc.x, fmaf_any(Dk.y, uc.y, fmaf_any(c0.x, sn.x, fmaf_any(-c0.y, sn.y, fv.x))));
+              r.y = fmaf_any(-Dk.x, uc.y, fmaf_any(-Dk.y, uc.x, fmaf_any(c0.x, sn.y, fmaf_any(c0.y, sn.x, fv.y))));
+              v.x = fmaf_any(Wk.x, r.x, fmaf_any(-Wk.y, r.y, uc.x));
+              v.y = fmaf_any(Wk.x, r.y, fmaf_any(Wk.y, r.x, uc.y));
+            } else {
+              const R kk = kconst ? kc : kcol[k * KW];
+              const C D = FAST ? csub(d0, cscale(L.beta, kk))
+                               : csub(cadd(cdg, s_cy[VH + ty]), cscale(L.beta, kk));
+              const C Wd = cmul(omega, crcp(D));
+              r = fv;
+              if (!zero) {
+                C nb;
+                if (FAST) nb = cmul(c0, cadd(cadd(ul, ur), cadd(un, ud)));
+                else {
+                  nb = cmul(clo, ul);
+                  nb = cfma(cup, ur, nb);
+                  nb = cfma(s_cy[ty], un, nb);
+                  nb = cfma(s_cy[2 * VH + ty], ud, nb);
+                }
+                r = cadd(csub(r, cmul(D, uc)), nb);
+              }
+              v = cadd(uc, cmul(Wd, r));
             }
-            r = cadd(csub(r, cmul(D, uc)), nb);
+            if (colown && ty >= 1 && ty <= BY) {
+              vo[k * P] = v;
+              acc = fmaf_any(r.x, r.x, fmaf_any(r.y, r.y, acc));
+            }
           }
-          v = cadd(uc, cmul(Wd, r));
-          if (colown && ty >= 1 && ty <= BY) {
-            vo[ty * P] = v;
-            acc += r.x * r.x + r.y * r.y;
-          }
+          vcol[k * VW] = v;
         }
-        s_v[ty * VW + tx] = v;
         un = uc;
         uc = ud;
       }
@@ -214,39 +228,52 @@ __device__ __forceinline__ void down_compute(
   // residual f - A v on [x0, x0+BX] x [y0, y0+BY]
   // r point (rx, ry) <-> v tile (rx+1, ry+1), f tile (rx+2, ry+1), k tile (rx+4, ry+1)
   {
-    constexpr int NS = NT / RW;
+    constexpr int NS = NT / RW, RS = (RH + NS - 1) / NS;
     const int rx = tid % RW, sg = tid / RW;
     if (sg < NS) {
-      const int q0 = sg * RH / NS, q1 = (sg + 1) * RH / NS;
+      const int q0 = sg * RS;
       const int tx = rx + 1;
       const bool colin = !CHECK || (x0 + rx < N);
       C clo = zc, cdg = zc, cup = zc;
       if (!FAST) { clo = s_cx[tx]; cdg = s_cx[VW + tx]; cup = s_cx[2 * VW + tx]; }
-      const C *col = s_v + tx;
-      const C *fcol = s_f + rx + 2;
-      const R *kcol = s_k + rx + 4;
-      C vn = col[q0 * VW], vc = col[(q0 + 1) * VW];
-      for (int ry = q0; ry < q1; ++ry) {
-        const int ty = ry + 1;
-        const int j = ty * VW;
-        const C vd = col[j + VW], vl = col[j - 1], vr = col[j + 1];
-        C r = zc;
-        if (colin && (!CHECK || y0 + ry < N)) {
-          C D, nb;
-          const R kk = kconst ? kc : kcol[ty * KW];
-          if (FAST) {
-            D = kconst ? Dk : csub(d0, cscale(L.beta, kk));
-            nb = cmul(c0, cadd(cadd(vl, vr), cadd(vn, vd)));
-          } else {
-            D = csub(cadd(cdg, s_cy[VH + ty]), cscale(L.beta, kk));
-            nb = cmul(clo, vl);
-            nb = cfma(cup, vr, nb);
-            nb = cfma(s_cy[ty], vn, nb);
-            nb = cfma(s_cy[2 * VH + ty], vd, nb);
+      const C *col = s_v + q0 * VW + tx;         // v tile row q0 (above r row q0)
+      const C *fcol = s_f + (q0 + 1) * FW + rx + 2;
+      const R *kcol = s_k + (q0 + 1) * KW + rx + 4;
+      C *rcol = s_r + q0 * RW + rx;
+      C vn = col[0], vc = col[VW];
+#pragma unroll
+      for (int k = 0; k < RS; ++k) {
+        const int ry = q0 + k;
+        C vd = zc;
+        if (ry < RH) {
+          vd = col[(k + 2) * VW];
+          const C vl = col[(k + 1) * VW - 1], vr = col[(k + 1) * VW + 1];
+          C r = zc;
+          if (colin && (!CHECK || y0 + ry < N)) {
+            const C fv = fcol[k * FW];
+            if (FAST && kconst) {
+              const C sn = cadd(cadd(vl, vr), cadd(vn, vd));
+              r.x = fmaf_any(-Dk.x, vc.x, fmaf_any(Dk.y, vc.y, fmaf_any(c0.x, sn.x, fmaf_any(-c0.y, sn.y, fv.x))));
+              r.y = fmaf_any(-Dk.x, vc.y, fmaf_any(-Dk.y, vc.x, fmaf_any(c0.x, sn.y, fmaf_any(c0.y, sn.x, fv.y))));
+            } else {
+              const int ty = ry + 1;
+              C D, nb;
+              const R kk = kconst ? kc : kcol[k * KW];
+              if (FAST) {
+                D = csub(d0, cscale(L.beta, kk));
+                nb = cmul(c0, cadd(cadd(vl, vr), cadd(vn, vd)));
+              } else {
+                D = csub(cadd(cdg, s_cy[VH + ty]), cscale(L.beta, kk));
+                nb = cmul(clo, vl);
+                nb = cfma(cup, vr, nb);
+                nb = cfma(s_cy[ty], vn, nb);
+                nb = cfma(s_cy[2 * VH + ty], vd, nb);
+              }
+              r = cadd(csub(fv, cmul(D, vc)), nb);
+            }
           }
-          r = cadd(csub(fcol[ty * FW], cmul(D, vc)), nb);
+          rcol[k * RW] = r;
         }
-        s_r[ry * RW + rx] = r;
         vn = vc;
         vc = vd;
       }
@@ -382,44 +409,63 @@ __device__ __forceinline__ void up_compute(const LevelK<R> &L, typename Cx<R>::T
     }
   }
   __syncthreads();
-  // u' = w + omega D^{-1}(f - A w) on the tile (column-segment mapping)
+  // u' = w + omega D^{-1}(f - A w) on the tile (column segments of RS rows)
   const C c0 = FAST ? L.c0 : zc;
   const C d0 = FAST ? cscale(c0, R(4)) : zc;
   const C Dk = FAST ? csub(d0, cscale(L.beta, kc)) : zc;
   const C Wk = FAST ? cmul(omega, crcp(Dk)) : zc;
   {
-    constexpr int NS = NT / BX;
+    constexpr int NS = NT / BX, RS = (BY + NS - 1) / NS;
     const int lx = tid % BX, sg = tid / BX;
     if (sg < NS) {
-      const int q0 = sg * BY / NS, q1 = (sg + 1) * BY / NS;
+      const int q0 = sg * RS;
       const int tx = lx + 1;
       const bool colin = !CHECK || (x0 + lx < N);
       C clo = zc, cdg = zc, cup = zc;
       if (!FAST) { clo = s_cx[tx]; cdg = s_cx[WW + tx]; cup = s_cx[2 * WW + tx]; }
-      const C *col = s_w + tx;
-      C *oo = ob + y0 * P + x0 + lx;
-      C wn = col[q0 * WW], wc = col[(q0 + 1) * WW];
-      for (int ly = q0; ly < q1; ++ly) {
-        const int j = (ly + 1) * WW;
-        const C wd = col[j + WW], wl = col[j - 1], wr = col[j + 1];
-        if (colin && (!CHECK || y0 + ly < N)) {
-          C D, Wd, nb;
-          const R kk = kconst ? kc : s_k[ly * BX + lx];
-          if (FAST) {
-            if (kconst) { D = Dk; Wd = Wk; }
-            else { D = csub(d0, cscale(L.beta, kk)); Wd = cmul(omega, crcp(D)); }
-            nb = cmul(c0, cadd(cadd(wl, wr), cadd(wn, wd)));
-          } else {
-            const int ty = ly + 1;
-            D = csub(cadd(cdg, s_cy[WH + ty]), cscale(L.beta, kk));
-            Wd = cmul(omega, crcp(D));
-            nb = cmul(clo, wl);
-            nb = cfma(cup, wr, nb);
-            nb = cfma(s_cy[ty], wn, nb);
-            nb = cfma(s_cy[2 * WH + ty], wd, nb);
+      const C *col = s_w + q0 * WW + tx;         // w row q0 (above owned row q0)
+      const C *fcol = s_f + q0 * BX + lx;
+      const R *kcol = s_k + q0 * BX + lx;
+      C *oo = ob + (y0 + q0) * P + x0 + lx;
+      C wn = col[0], wc = col[WW];
+#pragma unroll
+      for (int k = 0; k < RS; ++k) {
+        const int ly = q0 + k;
+        C wd = zc;
+        if (ly < BY) {
+          wd = col[(k + 2) * WW];
+          const C wl = col[(k + 1) * WW - 1], wr = col[(k + 1) * WW + 1];
+          if (colin && (!CHECK || y0 + ly < N)) {
+            const C fv = fcol[k * BX];
+            C u;
+            if (FAST && kconst) {
+              const C sn = cadd(cadd(wl, wr), cadd(wn, wd));
+              C r;
+              r.x = fmaf_any(-Dk.x, wc.x, fmaf_any(Dk.y, wc.y, fmaf_any(c0.x, sn.x, fmaf_any(-c0.y, sn.y, fv.x))));
+              r.y = fmaf_any(-Dk.x, wc.y, fmaf_any(-Dk.y, wc.x, fmaf_any(c0.x, sn.y, fmaf_any(c0.y, sn.x, fv.y))));
+              u.x = fmaf_any(Wk.x, r.x, fmaf_any(-Wk.y, r.y, wc.x));
+              u.y = fmaf_any(Wk.x, r.y, fmaf_any(Wk.y, r.x, wc.y));
+            } else {
+              C D, Wd, nb;
+              const R kk = kconst ? kc : kcol[k * BX];
+              if (FAST) {
+                D = csub(d0, cscale(L.beta, kk));
+                Wd = cmul(omega, crcp(D));
+                nb = cmul(c0, cadd(cadd(wl, wr), cadd(wn, wd)));
+              } else {
+                const int ty = ly + 1;
+                D = csub(cadd(cdg, s_cy[WH + ty]), cscale(L.beta, kk));
+                Wd = cmul(omega, crcp(D));
+                nb = cmul(clo, wl);
+                nb = cfma(cup, wr, nb);
+                nb = cfma(s_cy[ty], wn, nb);
+                nb = cfma(s_cy[2 * WH + ty], wd, nb);
+              }
+              const C r = cadd(csub(fv, cmul(D, wc)), nb);
+              u = cadd(wc, cmul(Wd, r));
+            }
+            oo[k * P] = u;
           }
-          const C r = cadd(csub(s_f[ly * BX + lx], cmul(D, wc)), nb);
-          oo[ly * P] = cadd(wc, cmul(Wd, r));
         }
         wn = wc;
         wc = wd;

@@ -137,6 +137,39 @@ def test_cycles_complex64_track_oracle():
     assert relerr(got[0], u) < 1e-5
 
 
+def test_tail_operator_matches_tail_kernel(monkeypatch):
+    """complex64 cycles: the dense tail operator (default) and the recursive
+    tail kernel (HH_TAIL=kernel) run the same V-cycle; both track the oracle."""
+    case = CASES[2]   # 128^2, heterogeneous k^2, CSG with c, ECS layers
+    H, mg = make_pair(case, batch=2, precision="mixed")
+    monkeypatch.setenv("HH_TAIL", "kernel")
+    _, mgk = make_pair(case, batch=2, precision="mixed")
+    f = rnd((2,) + H.levels[0].shape, 11)
+    z = np.zeros_like(f)
+    a = host(mg.cycles(dev(f), dev(z), 3))
+    b = host(mgk.cycles(dev(f), dev(z), 3))
+    u = np.zeros_like(f[1])
+    for _ in range(3):
+        u = O.vcycle(H, 0, u, f[1])
+    assert relerr(a, b) < 2e-6
+    assert relerr(a[1], u) < 1e-5 and relerr(b[1], u) < 1e-5
+
+
+def test_adjoint_mixed_matches_oracle():
+    """Mixed-precision adjoint solve (adjoint tail operator) vs the oracle."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n, layers = 128, 8
+    k2 = W.smooth_k2(n, 2, 4, 76.0, 80.0)
+    H = O.build_hierarchy(n, 2, k2, layers=layers)
+    Ha = O.adjoint_hierarchy(H)
+    mg = HelmholtzMG(n, k2=dev(k2), layers=layers, max_batch=2, precision="mixed")
+    g = rnd((2, n - 1, n - 1), 12)
+    lam, il = mg.adjoint(dev(g), tol=1e-9)
+    lam_ref = np.stack([O.solve(Ha, g[b], tol=1e-11).u for b in range(2)])
+    assert all(i["status"] == "OK" for i in il)
+    assert relerr(host(lam), lam_ref) < 1e-7
+
+
 def point_rhs(n, dim, batch, seed):
     rng = np.random.default_rng(seed)
     pos = [tuple(rng.integers(n // 8, n - n // 8 - 1, size=dim)) for _ in range(batch)]
