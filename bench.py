@@ -121,18 +121,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def launches_per_solve(levels, info, nu1=1, nu2=1, mixed=True):
-    """Kernels of this library launched by one solve: every iteration of the
-    graph's WHILE body runs the whole cycle sequence ((levels-1) levels of
-    nu1 sweeps + residual/restriction + nu2 sweeps, the stop test, the coarse
-    LU); one iteration more per loop than cycles (the stop test that ends
-    it); plus norm, state init, finish, and per refinement the FP64 residual
-    and the outer stop test."""
-    per_iter = (levels - 1) * (nu1 + 1 + nu2) + 2
-    if mixed:
-        loops = info["refinements"]
-        return (info["cycles"] + loops) * per_iter + 2 * (loops + 1) + 3
-    return (info["cycles"] + 1) * per_iter + 3
+def profile_one(args):
+    """Launch one level-0 kernel of the workload twice (warm-up + timed,
+    replayed from a captured graph) and exit: the target of ncu captures."""
+    import numpy as np
+    import torch
+    import ctypes as ct
+    from paper_1211_4752_gb300 import HelmholtzMG, workloads as W
+    from paper_1211_4752_gb300 import _binding as B
+    w = getattr(W, args.workload)()
+    k2 = w["k2"]
+    k2_t = torch.from_numpy(k2).cuda() if isinstance(k2, np.ndarray) else float(k2)
+    mg = HelmholtzMG(w["n"], dim=w["dim"], k2=k2_t, layers=w["layers"],
+                     precision=args.precision, max_batch=1)
+    kid = {v: k for k, v in KERNELS.items()}[args.kernel]
+    ms = ct.c_double()
+    stream = torch.cuda.current_stream()
+    B.check(B.lib().hh_time_kernel(mg._h, kid, 0, 1, 1, ct.byref(ms),
+                                   ct.c_void_p(stream.cuda_stream)))
+    print(json.dumps({"kernel": args.kernel, "level": 0, "ms": ms.value,
+                      "tile": mg.tile_shape(0), "workload": w["name"]}))
+    mg.close()
 
 
 def run_ours(args):
@@ -172,6 +181,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     times = []
+    launches = 0
     for _ in range(args.steps):
         flush.fill_(1.0)                       # evict L2 between steps
         e0 = torch.cuda.Event(enable_timing=True)
@@ -182,6 +192,7 @@ def run_ours(args):
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
         infos.append(info[0])
+        launches += mg.solve_kernels
     torch.cuda.synchronize()
     clocks = sampler.stop()
     total = sum(times)
@@ -275,10 +286,11 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "bytes_per_point": bpp,
+                         "tile_level0": mg.tile_shape(0),
                          "launch_ms": {KERNELS[k]: v for k, v in kt.items()}},
             "cpu_baseline": cpu,
             "fp64_gpu": fp64,
-            "gpu_launches": args.steps * launches_per_solve(mg.levels, last, mixed=mixed),
+            "gpu_launches": launches,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -379,9 +391,13 @@ def main():
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-cycles", type=int, default=4)
+    ap.add_argument("--kernel", choices=sorted(KERNELS.values()),
+                    help="launch one level-0 kernel of the workload and exit (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.kernel:
+        profile_one(args)
     else:
         run_ours(args)
 

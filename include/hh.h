@@ -220,6 +220,23 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
 int hh_num_levels(const hh_handle *h);
 int hh_level_points(const hh_handle *h, int level); /* N_l per axis */
 
+/* Kernels one V-cycle launches: one iteration of the cycle loop of Sec. 4.1,
+ * its stop test included, at the handle's precision (the complex64 cycles
+ * for HH_MIXED).  0 for a NULL handle. */
+int hh_cycle_kernels(const hh_handle *h);
+
+/* Kernels of this library launched by the last completed hh_solve,
+ * hh_adjoint or hh_solve_host on this handle: the cycles the loops launched
+ * (counted on the device, one per stop test) times hh_cycle_kernels, plus
+ * the solve's other kernels (norm, state init, refinements, final copy).
+ * -1 before the first solve or for a NULL handle. */
+long long hh_solve_kernels(const hh_handle *h);
+
+/* Tile shape (fine points, x by y) of the fused 2-D kernels on level l, as
+ * chosen at setup; returns 1, or 0 with *bx = *by = 0 where the level runs
+ * no fused kernel (3-D, nu1 or nu2 > 1, or the tail levels). */
+int hh_tile_shape(const hh_handle *h, int level, int *bx, int *by);
+
 /* Release the handle and its workspace (NULL is allowed). */
 hh_status hh_destroy(hh_handle *h);
 

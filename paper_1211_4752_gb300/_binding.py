@@ -76,6 +76,9 @@ SIGNATURES = {
     "hh_time_kernel": (_I, [_P, _I, _I, _I, _I, ct.POINTER(_D), _P]),
     "hh_num_levels": (_I, [_P]),
     "hh_level_points": (_I, [_P, _I]),
+    "hh_cycle_kernels": (_I, [_P]),
+    "hh_solve_kernels": (ct.c_longlong, [_P]),
+    "hh_tile_shape": (_I, [_P, _I, ct.POINTER(_I), ct.POINTER(_I)]),
     "hh_destroy": (_I, [_P]),
     "hh_last_error": (ct.c_char_p, []),
 }

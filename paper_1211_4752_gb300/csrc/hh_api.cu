@@ -108,11 +108,17 @@ struct hh_handle {
   cudaStream_t cap = nullptr;       // private stream for graph capture
   int fused = 0;                    // 2-D fused down/up kernels + tail kernel
   int tail0 = 0;                    // first level run by the tail kernel
-  int kconst = 0;                   // k^2 constant: kernels read k2[0] only
+  int kconst = 0;                   // k^2 constant: kernels use LevelK::kc
+  double k2c = 0.0;                 // that constant
   int variant[MAXL] = {};           // tile shape per fused level (autotuned)
   int parts_cap = 0;                // capacity of `partials` per RHS
-  unsigned int *counter = nullptr;  // arrivals of the fused stop test
+  cudaStream_t side = nullptr;      // branch of the stop test in the fused cycle
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int *err = nullptr;               // device status word of bounded waits
+  unsigned int *copies = nullptr;   // cycles launched by the current solve
+  unsigned int *copies_h = nullptr; // pinned
+  long long fixed_kernels = 0;      // other kernels of the current solve
+  long long last_kernels = -1;      // kernels of the last completed solve
   float2 *tailop[2] = {nullptr, nullptr};  // tail operator per direction (mixed)
   DownMaps dmap[MAXL];              // tensor maps of the fused kernels, per level
   UpMaps umap[MAXL];
@@ -177,12 +183,12 @@ template <typename R> LevelK<R> levelk(const hh_handle *h, int l, int dir);
 template <> LevelK<double> levelk<double>(const hh_handle *h, int l, int dir) {
   const LevelHost &v = h->lv[l];
   return LevelK<double>{v.N, v.P, v.S, v.P, v.coef64[dir], v.beta64[dir], v.k2_64,
-                        v.ulo[dir], v.uhi[dir], v.c0_64[dir]};
+                        v.ulo[dir], v.uhi[dir], v.c0_64[dir], h->k2c};
 }
 template <> LevelK<float> levelk<float>(const hh_handle *h, int l, int dir) {
   const LevelHost &v = h->lv[l];
   return LevelK<float>{v.N, v.P, v.S, v.P, v.coef32[dir], v.beta32[dir], v.k2_32,
-                       v.ulo[dir], v.uhi[dir], v.c0_32[dir]};
+                       v.ulo[dir], v.uhi[dir], v.c0_32[dir], (float)h->k2c};
 }
 // the same level operator on dense caller arrays (row pitch N)
 template <typename R> LevelK<R> levelk_dense(const hh_handle *h, int l, int dir) {
@@ -237,9 +243,9 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
                             norm ? h->partials : nullptr, h->nparts, s);
       if (norm) {
         if (check == CHECK_CYCLE)
-          launch_check_cycle(h->st, h->partials, h->params, h->flag, cond, s);
+          launch_check_cycle(h->st, h->partials, h->params, h->flag, cond, h->copies, h->err, s);
         else
-          launch_check_inner(h->st, h->partials, h->params, h->flag, cond, s);
+          launch_check_inner(h->st, h->partials, h->params, h->flag, cond, h->copies, h->err, s);
       }
       in = out;
     }
@@ -366,17 +372,21 @@ template <typename R> TailArgs<R> tail_args(hh_handle *h, int dir) {
   return a;
 }
 
-template <typename R> CheckCtx check_ctx(hh_handle *h, int check, unsigned long long cond) {
-  CheckCtx c{};
-  c.mode = check == CHECK_CYCLE ? CHECK_MODE_CYCLE : CHECK_MODE_INNER;
-  c.st = h->st;
-  c.P = h->params;
-  c.partials = h->partials;
-  c.counter = h->counter;
-  c.flag = h->flag;
-  c.cond = cond;
-  c.err = h->err;
-  return c;
+
+// Stop test of a fused cycle on a branch of its own: forked from s once the
+// level-0 down pass has written the partial sums of |f - A u_k|^2, it runs
+// beside the coarser levels and is joined back before the level-0 up pass.
+// The kernels in between may or may not see a right-hand side stop; their
+// outputs feed only that up pass, which skips a finished right-hand side, so
+// the result is the same either way.
+void fork_check(hh_handle *h, int check, unsigned long long cond, cudaStream_t s) {
+  cudaEventRecord(h->ev_fork, s);
+  cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+  if (check == CHECK_CYCLE)
+    launch_check_cycle(h->st, h->partials, h->params, h->flag, cond, h->copies, h->err, h->side);
+  else
+    launch_check_inner(h->st, h->partials, h->params, h->flag, cond, h->copies, h->err, h->side);
+  cudaEventRecord(h->ev_join, h->side);
 }
 
 // Levels tail0 .. coarsest of a cycle: the dense tail operator where one
@@ -407,15 +417,17 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
   for (int l = 0; l < T; ++l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
     const bool norm = l == 0 && check != CHECK_NONE;
-    // the level-0 pass also runs the stop test in its last block
-    const CheckCtx chk = norm ? check_ctx<R>(h, check, cond) : CheckCtx{};
     launch_down2d<R>(h->variant[l], h->dmap[l], K, l == 0 ? zero0 : ZERO_ALL, W.u_pre[l],
                      W.f[l + 1], cscal<R>(h, l, dir), om, h->kconst, lay_of(h, l + 1), batch, st,
-                     norm ? h->partials : nullptr, h->err, chk, s);
+                     norm ? h->partials : nullptr, h->err, s);
+    if (norm) fork_check(h, check, cond, s);
   }
   enqueue_tail<R>(h, dir, batch, st, s);
   for (int l = T - 1; l >= 0; --l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
+    // the level-0 up pass is the one kernel of the cycle that writes the
+    // level-0 iterate: it waits for the stop test
+    if (l == 0 && check != CHECK_NONE) cudaStreamWaitEvent(s, h->ev_join, 0);
     launch_up2d<R>(h->variant[l], h->umap[l], K, W.u_post[l], om, h->kconst, batch, st,
                    h->err, s);
   }
@@ -477,8 +489,20 @@ hh_status get_cycle_graph(hh_handle *h, int prec, int dir, int batch, cudaGraphE
 // Run the cycle loop to completion on stream s.
 hh_status run_loop(hh_handle *h, int prec, int dir, int batch, cudaStream_t s);
 
+// Copies of the V-cycle in one iteration of the WHILE body (HH_UNROLL in the
+// environment, 1..16, default 8).  A copy that runs after the stop test has
+// ended the loop finds every right-hand side inactive and does no work, so
+// the iterates and cycle counts do not depend on it; it only spreads the
+// per-iteration cost of the conditional node over several cycles.
+int loop_unroll() {
+  const char *e = std::getenv("HH_UNROLL");
+  const int u = e ? std::atoi(e) : 8;
+  return u < 1 ? 1 : (u > 16 ? 16 : u);
+}
+
 // The graph for (precision, direction, batch): a WHILE node whose body is
-// one V-cycle with the stop test after the level-0 pre-smoothing sweep.
+// loop_unroll() V-cycles, each with the stop test after its level-0
+// pre-smoothing sweep.
 hh_status get_graph(hh_handle *h, int prec, int dir, int batch,
                     cudaGraphExec_t *out) {
   auto key = std::make_tuple(prec, dir, batch);
@@ -503,10 +527,12 @@ hh_status get_graph(hh_handle *h, int prec, int dir, int batch,
   HH_CK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal));
   const unsigned long long c = (unsigned long long)cond;
-  if (prec == HH_FP64)
-    cycle_dispatch<double>(h, dir, batch, ZERO_NONE, CHECK_CYCLE, c, h->cap);
-  else
-    cycle_dispatch<float>(h, dir, batch, ZERO_FLAG, CHECK_INNER, c, h->cap);
+  for (int k = loop_unroll(); k > 0; --k) {
+    if (prec == HH_FP64)
+      cycle_dispatch<double>(h, dir, batch, ZERO_NONE, CHECK_CYCLE, c, h->cap);
+    else
+      cycle_dispatch<float>(h, dir, batch, ZERO_FLAG, CHECK_INNER, c, h->cap);
+  }
   cudaGraph_t captured = nullptr;
   cudaError_t ec = cudaStreamEndCapture(h->cap, &captured);
   if (ec != cudaSuccess) {
@@ -541,7 +567,9 @@ hh_status read_info(hh_handle *h, int batch, hh_solve_info *info,
   HH_CK(cudaMemcpyAsync(h->st_h, h->st, sizeof(SolveState) * batch,
                         cudaMemcpyDeviceToHost, s));
   HH_CK(cudaMemcpyAsync(h->flag_h, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HH_CK(cudaMemcpyAsync(h->copies_h, h->copies, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
   HH_CK(cudaStreamSynchronize(s));
+  h->last_kernels = (long long)*h->copies_h * hh_cycle_kernels(h) + h->fixed_kernels;
   if (*h->flag_h) return fail(HH_ERR_TIMEOUT, "a bounded device wait gave up (TMA copy not completed)");
   hh_status worst = HH_OK;
   for (int b = 0; b < batch; ++b) {
@@ -610,6 +638,8 @@ hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
     HH_TRY(copy_to_pitched(h, 0, h->w64.f[0], rhs, batch, sizeof(double2), cudaMemcpyDeviceToDevice, s));
   HH_TRY(set_params(h, batch, tol, s));
   HH_CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+  HH_CK(cudaMemsetAsync(h->copies, 0, sizeof(unsigned int), s));
+  h->fixed_kernels = 3;   // norm of f, state init, final copy
   launch_norm2(h->w64.f[0], (size_t)l0.S, batch, h->partials, h->nparts, s);
   launch_state_init(h->st, h->partials, h->params, h->flag, s);
 
@@ -631,6 +661,7 @@ hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
   refine_dispatch(h, dir, h->u64[0], guess ? 0 : 1, nullptr, h->u64[1], batch, s);
   cur = 1;
   launch_check_outer(h->st, h->partials, h->params, h->flag, s);
+  h->fixed_kernels += 2;
   for (int it = 0; it < h->opt.max_cycles + 2; ++it) {
     HH_CK(cudaMemcpyAsync(h->flag_h, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     HH_CK(cudaStreamSynchronize(s));
@@ -639,6 +670,7 @@ hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
     refine_dispatch(h, dir, h->u64[cur], 0, h->w32.u_post[0], h->u64[1 - cur], batch, s);
     cur = 1 - cur;
     launch_check_outer(h->st, h->partials, h->params, h->flag, s);
+    h->fixed_kernels += 2;
   }
   launch_finish(h->st, h->u64[cur], l0, out, d0, h->dim, batch, s);
   HH_CK(cudaGetLastError());
@@ -660,7 +692,7 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
     if (kernel == 0)
       launch_down2d<R>(h->variant[level], h->dmap[level], K, ZERO_NONE, W.u_pre[level],
                        W.f[level + 1], cscal<R>(h, level, 0), om, h->kconst, lay_of(h, level + 1),
-                       batch, nullptr, level == 0 ? h->partials : nullptr, h->err, CheckCtx{}, s);
+                       batch, nullptr, level == 0 ? h->partials : nullptr, h->err, s);
     else
       launch_up2d<R>(h->variant[level], h->umap[level], K, W.u_post[level], om, h->kconst,
                      batch, nullptr, h->err, s);
@@ -712,9 +744,13 @@ void destroy_impl(hh_handle *h) {
   for (void *p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->flag_h) cudaFreeHost(h->flag_h);
+  if (h->copies_h) cudaFreeHost(h->copies_h);
   if (h->params_h) cudaFreeHost(h->params_h);
   if (h->st_h) cudaFreeHost(h->st_h);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 
@@ -736,7 +772,7 @@ template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, 
     HH_TRY(make_maps<R>(h, l, v, &dm, &um));
     auto run = [&]() {
       launch_down2d<R>(v, dm, K, ZERO_NONE, W.u_pre[l], W.f[l + 1], cscal<R>(h, l, 0), om,
-                       h->kconst, lay_of(h, l + 1), 1, nullptr, nullptr, h->err, CheckCtx{}, s);
+                       h->kconst, lay_of(h, l + 1), 1, nullptr, nullptr, h->err, s);
       launch_up2d<R>(v, um, K, W.u_post[l], om, h->kconst, 1, nullptr, h->err, s);
     };
     run();
@@ -835,6 +871,9 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
 
   HH_CK(cudaGetDevice(&h->device));
   HH_CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  HH_CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  HH_CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  HH_CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   HH_CK(cudaMallocHost(&h->flag_h, sizeof(int)));
   HH_CK(cudaMallocHost(&h->params_h, sizeof(SolveParams)));
   HH_CK(cudaMallocHost(&h->st_h, sizeof(SolveState) * h->max_batch));
@@ -963,6 +1002,7 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   // level with at most 63 points per axis; that level and all coarser ones
   // run inside the single-block tail kernel.
   h->kconst = k2_dev ? 0 : 1;
+  h->k2c = k2_dev ? 0.0 : k2_const;
   h->fused = 0;
   if (dim == 2 && h->opt.nu1 == 1 && h->opt.nu2 == 1) {
     // first level whose tail (it and every coarser level) fits in shared memory
@@ -998,10 +1038,10 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   for (int v = 0; v < kNumTileVariants; ++v)
     h->parts_cap = std::max(h->parts_cap, tile_parts(v, h->lv[0].N));
   HH_TRY(dev_alloc_n(h, &h->partials, (size_t)h->parts_cap * B));
-  HH_TRY(dev_alloc_n(h, &h->counter, 1));
-  HH_CK(cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), s));
   HH_TRY(dev_alloc_n(h, &h->err, 1));
   HH_CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+  HH_TRY(dev_alloc_n(h, &h->copies, 1));
+  HH_CK(cudaMallocHost(&h->copies_h, sizeof(unsigned int)));
   HH_TRY(dev_alloc_n(h, &h->st, (size_t)B));
   HH_TRY(dev_alloc_n(h, &h->params, 1));
   HH_TRY(dev_alloc_n(h, &h->flag, 1));
@@ -1130,6 +1170,22 @@ int hh_num_levels(const hh_handle *h) { return h ? h->L : 0; }
 int hh_level_points(const hh_handle *h, int level) {
   if (!h || level < 0 || level >= h->L) return 0;
   return h->lv[level].N;
+}
+
+int hh_cycle_kernels(const hh_handle *h) {
+  if (!h) return 0;
+  if (h->fused) return 2 * h->tail0 + 2;   // down passes, stop test, tail, up passes
+  // per level nu1 sweeps, residual + restriction, nu2 sweeps; stop test; LU
+  return (h->L - 1) * (h->opt.nu1 + 1 + h->opt.nu2) + 2;
+}
+
+long long hh_solve_kernels(const hh_handle *h) { return h ? h->last_kernels : -1; }
+
+int hh_tile_shape(const hh_handle *h, int level, int *bx, int *by) {
+  const bool ok = h && h->fused && level >= 0 && level < h->tail0;
+  if (bx) *bx = ok ? tile_bx(h->variant[level]) : 0;
+  if (by) *by = ok ? tile_by(h->variant[level]) : 0;
+  return ok ? 1 : 0;
 }
 
 hh_status hh_solve(hh_handle *h, const void *rhs_dev, void *u_dev, int batch,

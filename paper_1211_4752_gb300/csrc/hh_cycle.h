@@ -66,8 +66,7 @@ template <typename R>
 void launch_down2d(int variant, const DownMaps &maps, const LevelK<R> &L, int zero_mode,
                    typename Cx<R>::T *v_out, typename Cx<R>::T *fc, typename Cx<R>::T cs,
                    typename Cx<R>::T omega, int kconst, const Lay &lc, int batch,
-                   const SolveState *st, double *partials, int *err, const CheckCtx &chk,
-                   cudaStream_t s);
+                   const SolveState *st, double *partials, int *err, cudaStream_t s);
 
 template <typename R>
 void launch_up2d(int variant, const UpMaps &maps, const LevelK<R> &L, typename Cx<R>::T *u_out,

@@ -17,14 +17,10 @@ template <typename R, int BX, int BY>
 void down_one(const DownMaps &maps, const LevelK<R> &L, int zero_mode, typename Cx<R>::T *v_out,
               typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
               int kconst, const Lay &lc, int batch, const SolveState *st, double *partials,
-              int *err, const CheckCtx &chk, cudaStream_t s) {
+              int *err, cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
-  if (chk.cond)
-    k_down2d<R, BX, BY, true><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
-        maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, st, partials, err, chk);
-  else
-    k_down2d<R, BX, BY, false><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
-        maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, st, partials, err, chk);
+  k_down2d<R, BX, BY><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
+      maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, st, partials, err);
 }
 
 template <typename R, int BX, int BY>
@@ -47,8 +43,7 @@ template <typename K> cudaError_t attrs(K kern, size_t smem) {
 
 template <typename R, int BX, int BY> cudaError_t attr_one() {
   cudaError_t e;
-  if ((e = attrs(k_down2d<R, BX, BY, true>, Down2D<R, BX, BY>::smem)) != cudaSuccess) return e;
-  if ((e = attrs(k_down2d<R, BX, BY, false>, Down2D<R, BX, BY>::smem)) != cudaSuccess) return e;
+  if ((e = attrs(k_down2d<R, BX, BY>, Down2D<R, BX, BY>::smem)) != cudaSuccess) return e;
   return attrs(k_up2d<R, BX, BY>, Up2D<R, BX, BY>::smem);
 }
 
@@ -335,14 +330,13 @@ template <typename R>
 void launch_down2d(int variant, const DownMaps &maps, const LevelK<R> &L, int zero_mode,
                    typename Cx<R>::T *v_out, typename Cx<R>::T *fc, typename Cx<R>::T cs,
                    typename Cx<R>::T omega, int kconst, const Lay &lc, int batch,
-                   const SolveState *st, double *partials, int *err, const CheckCtx &chk,
-                   cudaStream_t s) {
+                   const SolveState *st, double *partials, int *err, cudaStream_t s) {
   switch (variant) {
-    case 0: down_one<R, 60, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, chk, s); break;
-    case 1: down_one<R, 60, 32>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, chk, s); break;
-    case 2: down_one<R, 28, 32>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, chk, s); break;
-    case 3: down_one<R, 120, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, chk, s); break;
-    default: down_one<R, 28, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, chk, s); break;
+    case 0: down_one<R, 60, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
+    case 1: down_one<R, 60, 32>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
+    case 2: down_one<R, 28, 32>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
+    case 3: down_one<R, 120, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
+    default: down_one<R, 28, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
   }
 }
 
@@ -368,8 +362,7 @@ void launch_tail2d(const TailArgs<R> &a, int batch, const SolveState *st, cudaSt
   template cudaError_t init_cycle2d<R>();                                                   \
   template void launch_down2d<R>(int, const DownMaps &, const LevelK<R> &, int, Cx<R>::T *, \
                                  Cx<R>::T *, Cx<R>::T, Cx<R>::T, int, const Lay &, int,     \
-                                 const SolveState *, double *, int *, const CheckCtx &,     \
-                                 cudaStream_t);                                             \
+                                 const SolveState *, double *, int *, cudaStream_t);        \
   template void launch_up2d<R>(int, const UpMaps &, const LevelK<R> &, Cx<R>::T *, Cx<R>::T,\
                                int, int, const SolveState *, int *, cudaStream_t);          \
   template void launch_tail2d<R>(const TailArgs<R> &, int, const SolveState *, cudaStream_t);

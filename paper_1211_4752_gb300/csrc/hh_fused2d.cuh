@@ -139,7 +139,7 @@ __device__ __forceinline__ void down_compute(
   const int N = L.N, Nc = (N + 1) / 2 - 1, P = L.P;
   const int tid = threadIdx.x;
   const C zc = czero<C>();
-  const R kc = kconst ? L.k2[0] : R(0);
+  const R kc = kconst ? L.kc : R(0);
   // uniform-coefficient constants (FAST): nb = c0 * (sum of neighbours),
   // D = 4 c0 - beta k2, W = omega / D
   const C c0 = FAST ? L.c0 : zc;
@@ -298,44 +298,54 @@ __device__ __forceinline__ void down_compute(
   }
 }
 
-// COND: the stop test may set the condition of a CUDA-graph WHILE node (the
-// variant without that call serves the host-driven loop and profilers).
-template <typename R, int BX, int BY, bool COND>
+// partials (level 0 of a solve): per-block sums of |f - A u|^2, read by the
+// stop test that runs beside the coarser levels.
+template <typename R, int BX, int BY>
 __global__ void __launch_bounds__(256)
 k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
          typename Cx<R>::T *__restrict__ v_out, typename Cx<R>::T *__restrict__ fc,
          typename Cx<R>::T cs, typename Cx<R>::T omega, int kconst, Lay lc,
-         const SolveState *__restrict__ st, double *__restrict__ partials, int *err,
-         CheckCtx chk) {
+         const SolveState *__restrict__ st, double *__restrict__ partials, int *err) {
   using C = typename Cx<R>::T;
   using S = Down2D<R, BX, BY>;
   const int b = blockIdx.z;
-  // blocks of a finished right-hand side skip the work but still take part
-  // in the arrival count of the stop test
-  bool act = !(st && !st[b].active);
-  if (!act && !(partials && chk.mode != CHECK_MODE_NONE)) return;
-  const bool zero = zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *base = align_smem128(smem_raw);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(base + S::oB);
   const int N = L.N;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
   R acc = R(0);
-  if (act) {
+  // One right-hand side: thread 0 starts the tile copies before the solver
+  // state is read, so the state's load latency overlaps them (u is fetched
+  // even where the state may say it is zero).  Batches read the state first,
+  // so blocks of finished right-hand sides fetch nothing.
+  const bool spec = gridDim.z == 1;
+  const bool loadu = zero_mode == ZERO_NONE || (spec && zero_mode == ZERO_FLAG);
+  auto issue = [&](bool withu) {
     if (threadIdx.x == 0) {
       mbar_init(mbar, 1);
       mbar_fence_init();
-      mbar_expect_tx(mbar, (zero ? 0u : S::bU) + S::bF + (kconst ? 0u : S::bK));
-      if (!zero) tma_load_3d(base + S::oU, &maps.u, 2 * (x0 - 2), y0 - 2, b, mbar);
+      mbar_expect_tx(mbar, (withu ? S::bU : 0u) + S::bF + (kconst ? 0u : S::bK));
+      if (withu) tma_load_3d(base + S::oU, &maps.u, 2 * (x0 - 2), y0 - 2, b, mbar);
       tma_load_3d(base + S::oF, &maps.f, 2 * (x0 - 2), y0 - 1, b, mbar);
       if (!kconst) tma_load_2d(base + S::oK, &maps.k, x0 - 4, y0 - 1, mbar);
     }
+  };
+  if (spec) issue(loadu);
+  // blocks of a finished right-hand side skip the work
+  bool act = !(st && !st[b].active);
+  const bool zero = zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero);
+  if (!spec) {
+    if (!act) return;
+    issue(!zero);
+  }
+  {
     const bool inner = tile_in(L, x0 - 2, x0 + BX + 2, N, false) &&
                        tile_in(L, y0 - 2, y0 + BY + 2, N, false);
     const bool fast = inner && tile_in(L, x0 - 2, x0 + BX + 2, N, true) &&
                       tile_in(L, y0 - 2, y0 + BY + 2, N, true);
     C *s_cx = reinterpret_cast<C *>(base + S::oT);
-    if (!fast) {
+    if (!fast && act) {
       if (inner) load_tables<R, false>(L, s_cx, s_cx + 3 * S::VW, S::VW, S::VH, x0, y0);
       else load_tables<R, true>(L, s_cx, s_cx + 3 * S::VW, S::VW, S::VH, x0, y0);
     }
@@ -345,7 +355,7 @@ k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
       if (threadIdx.x == 0) atomicExch(err, (int)HH_ERR_TIMEOUT);
       mbar_wait_bounded(mbar, 0);   // let copies still in flight land
       act = false;
-    } else {
+    } else if (act) {
       C *vb = v_out + (size_t)b * L.S;
       C *fcb = fc + (size_t)b * lc.S;
       if (fast)
@@ -360,7 +370,6 @@ k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
     const double s = block_sum_d((double)acc);
     const int nblk = gridDim.x * gridDim.y;
     if (act && threadIdx.x == 0) partials[(size_t)b * nblk + blockIdx.y * gridDim.x + blockIdx.x] = s;
-    if (chk.mode != CHECK_MODE_NONE) last_block_check<COND>(chk, nblk);
   }
 }
 
@@ -382,7 +391,7 @@ __device__ __forceinline__ void up_compute(const LevelK<R> &L, typename Cx<R>::T
   const int N = L.N, P = L.P;
   const int tid = threadIdx.x;
   const C zc = czero<C>();
-  const R kc = kconst ? L.k2[0] : R(0);
+  const R kc = kconst ? L.kc : R(0);
   // w = v + P e on tile + 1 (zero outside the domain).  w point (tx, ty) <->
   // v tile (tx+1, ty); fine x0-1+tx odd <-> tx even: coincident coarse
   // column, e tile column tx/2 + 1; else e tile columns (tx>>1)+1, (tx>>1)+2
@@ -481,12 +490,14 @@ k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__re
   using C = typename Cx<R>::T;
   using S = Up2D<R, BX, BY>;
   const int b = blockIdx.z;
-  if (st && !st[b].active) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *base = align_smem128(smem_raw);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(base + S::oB);
   const int N = L.N;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  // one right-hand side: copies started before the state is read (see k_down2d)
+  const bool spec = gridDim.z == 1;
+  if (!spec && st && !st[b].active) return;
   if (threadIdx.x == 0) {
     mbar_init(mbar, 1);
     mbar_fence_init();
@@ -496,11 +507,12 @@ k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__re
     tma_load_3d(base + S::oF, &maps.f, 2 * x0, y0, b, mbar);
     if (!kconst) tma_load_2d(base + S::oK, &maps.k, x0, y0, mbar);
   }
+  const bool act = !(st && !st[b].active);
   const bool inner = tile_in(L, x0 - 1, x0 + BX, N, false) && tile_in(L, y0 - 1, y0 + BY, N, false);
   const bool fast = inner && tile_in(L, x0 - 1, x0 + BX, N, true) &&
                     tile_in(L, y0 - 1, y0 + BY, N, true);
   C *s_cx = reinterpret_cast<C *>(base + S::oT);
-  if (!fast) {
+  if (!fast && act) {
     if (inner) load_tables<R, false>(L, s_cx, s_cx + 3 * S::WW, S::WW, S::WH, x0, y0);
     else load_tables<R, true>(L, s_cx, s_cx + 3 * S::WW, S::WW, S::WH, x0, y0);
   }
@@ -511,6 +523,7 @@ k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__re
     mbar_wait_bounded(mbar, 0);
     return;
   }
+  if (!act) return;
   C *ob = u_out + (size_t)b * L.S;
   if (fast) up_compute<R, BX, BY, false, true>(L, ob, omega, kconst, x0, y0, base);
   else if (inner) up_compute<R, BX, BY, false, false>(L, ob, omega, kconst, x0, y0, base);

@@ -33,6 +33,7 @@ template <typename R> struct LevelK {
   const R *k2;     // real k^2 of this level (pitch KP)
   int ulo, uhi;    // nodes ulo..uhi (every axis) have lo = up = c0, dg = 2 c0
   C c0;            // (the uniform region away from ECS layers); ulo > uhi: none
+  R kc;            // k^2 where it is constant (k2 then holds kc everywhere)
 };
 
 // Layout of an array of another level (e.g. the coarse one of a transfer).
@@ -124,10 +125,12 @@ void launch_state_init(SolveState *st, const double *partials,
                        const SolveParams *P, int *flag, cudaStream_t s);
 void launch_check_cycle(SolveState *st, const double *partials,
                         const SolveParams *P, int *flag,
-                        unsigned long long cond, cudaStream_t s);
+                        unsigned long long cond, unsigned int *copies, const int *err,
+                        cudaStream_t s);
 void launch_check_inner(SolveState *st, const double *partials,
                         const SolveParams *P, int *flag,
-                        unsigned long long cond, cudaStream_t s);
+                        unsigned long long cond, unsigned int *copies, const int *err,
+                        cudaStream_t s);
 void launch_check_outer(SolveState *st, const double *partials,
                         const SolveParams *P, int *flag, cudaStream_t s);
 void launch_finish(const SolveState *st, const double2 *src, const Lay &ls, double2 *dst,

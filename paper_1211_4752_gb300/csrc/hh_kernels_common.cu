@@ -2,6 +2,7 @@
 // LU substitution, gradient assembly, conversions.
 #include "hh_internal.h"
 #include "hh_complex.cuh"
+#include "hh_check.cuh"
 #include "../../include/hh.h"
 
 namespace hh {
@@ -130,64 +131,29 @@ __global__ void k_state_init(SolveState *st, const double *partials,
   if (threadIdx.x == 0) *flag = any;
 }
 
-// Stop test of the plain cycle loop (Sec. 4.1): r2 = ||f - A_0 u_k||^2 of
-// the iterate u_k that the level-0 pre-smoothing sweep just read.
-__global__ void k_check_cycle(SolveState *st, const double *partials,
-                              const SolveParams *P, int *flag,
-                              unsigned long long cond) {
+// Stop test of a cycle loop (Sec. 4.1).  MODE = CHECK_MODE_CYCLE: plain
+// loop, r2 = ||f - A_0 u_k||^2 of the iterate u_k that the level-0
+// pre-smoothing sweep just read; CHECK_MODE_INNER: the complex64 loop of the
+// refinement (update_inner).  A nonzero device status word (a bounded wait
+// gave up) stops every right-hand side with HH_ERR_TIMEOUT.
+template <int MODE>
+__global__ void k_check(SolveState *st, const double *partials, const SolveParams *P, int *flag,
+                        unsigned long long cond, unsigned int *copies, const int *err) {
   __shared__ int any_s;
+  const bool timeout = err && *(volatile const int *)err;
   auto body = [&](SolveState &s, double r2) {
-    const int k = s.cycles;
-    const double rho = sqrt(r2 / s.fnorm2);
-    s.rnorm2 = r2;
-    if (!(rho <= P->div_limit)) {
-      s.status = HH_ERR_DIVERGED; s.active = 0; s.done = 1;
-    } else if (rho <= P->tol) {
-      s.status = HH_OK; s.active = 0; s.done = 1;
-    } else if (k >= P->max_cycles) {
-      s.status = HH_ERR_NOT_CONVERGED; s.active = 0; s.done = 1;
+    if (timeout) {
+      s.status = HH_ERR_TIMEOUT; s.active = 0; s.done = 1;
+    } else if (MODE == CHECK_MODE_CYCLE) {
+      update_cycle(s, r2, P);
     } else {
-      s.cycles = k + 1;
+      update_inner(s, r2, P);
     }
   };
   for_each_rhs(P, partials, st, true, body, &any_s);
   if (threadIdx.x == 0) {
     *flag = any_s;
-    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, any_s ? 1u : 0u);
-  }
-}
-
-// Stop test of the complex64 inner loop of the refinement: r2 is the inner
-// residual norm of the current correction e_k (k = 0: e = 0, r = rhs).
-__global__ void k_check_inner(SolveState *st, const double *partials,
-                              const SolveParams *P, int *flag,
-                              unsigned long long cond) {
-  __shared__ int any_s;
-  auto body = [&](SolveState &s, double r2) {
-    if (s.zero) {
-      s.ref2 = r2;
-      s.rin2 = r2;
-      s.zero = 0;
-      s.inner = 1;
-      s.cycles += 1;
-      if (!(r2 > 0.0)) s.active = 0;  // zero (or NaN) inner rhs: nothing to do
-      return;
-    }
-    const double rho = sqrt(r2 / s.ref2);
-    s.rin2 = r2;
-    if (!(rho <= P->div_limit)) {
-      s.status = HH_ERR_DIVERGED; s.active = 0; s.done = 1;
-    } else if (rho <= P->inner_tol || s.inner >= P->max_inner ||
-               s.cycles >= P->max_cycles) {
-      s.active = 0;
-    } else {
-      s.inner += 1;
-      s.cycles += 1;
-    }
-  };
-  for_each_rhs(P, partials, st, true, body, &any_s);
-  if (threadIdx.x == 0) {
-    *flag = any_s;
+    if (copies) *copies += 1u;   // cycles launched (stop tests run)
     if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, any_s ? 1u : 0u);
   }
 }
@@ -271,13 +237,15 @@ void launch_state_init(SolveState *st, const double *partials,
 }
 void launch_check_cycle(SolveState *st, const double *partials,
                         const SolveParams *P, int *flag,
-                        unsigned long long cond, cudaStream_t s) {
-  k_check_cycle<<<1, 1024, 0, s>>>(st, partials, P, flag, cond);
+                        unsigned long long cond, unsigned int *copies, const int *err,
+                        cudaStream_t s) {
+  k_check<CHECK_MODE_CYCLE><<<1, 1024, 0, s>>>(st, partials, P, flag, cond, copies, err);
 }
 void launch_check_inner(SolveState *st, const double *partials,
                         const SolveParams *P, int *flag,
-                        unsigned long long cond, cudaStream_t s) {
-  k_check_inner<<<1, 1024, 0, s>>>(st, partials, P, flag, cond);
+                        unsigned long long cond, unsigned int *copies, const int *err,
+                        cudaStream_t s) {
+  k_check<CHECK_MODE_INNER><<<1, 1024, 0, s>>>(st, partials, P, flag, cond, copies, err);
 }
 void launch_check_outer(SolveState *st, const double *partials,
                         const SolveParams *P, int *flag, cudaStream_t s) {

@@ -106,6 +106,22 @@ class HelmholtzMG:
     def level_points(self, level):
         return B.lib().hh_level_points(self._h, int(level))
 
+    @property
+    def cycle_kernels(self):
+        """Kernels one V-cycle launches (stop test included)."""
+        return B.lib().hh_cycle_kernels(self._h)
+
+    @property
+    def solve_kernels(self):
+        """Kernels launched by the last completed solve (-1 before one)."""
+        return B.lib().hh_solve_kernels(self._h)
+
+    def tile_shape(self, level):
+        """(bx, by) of the fused 2-D kernels on `level`, or None."""
+        bx, by = ct.c_int(), ct.c_int()
+        ok = B.lib().hh_tile_shape(self._h, int(level), ct.byref(bx), ct.byref(by))
+        return (bx.value, by.value) if ok else None
+
     def close(self):
         if getattr(self, "_h", None):
             B.lib().hh_destroy(self._h)

@@ -170,6 +170,26 @@ def test_adjoint_mixed_matches_oracle():
     assert relerr(host(lam), lam_ref) < 1e-7
 
 
+def test_loop_unroll_leaves_iterates_unchanged(monkeypatch):
+    """Cycle copies after the stop test do nothing: the iterate, the cycle
+    count and the residual are bit-identical for every unroll factor, and the
+    device-counted kernels follow ceil((cycles + 1) / U) loop iterations."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n, k, layers = 64, 40.0, 2
+    f = point_rhs(n, 2, 1, 3)
+    out = {}
+    for U in (1, 3):
+        monkeypatch.setenv("HH_UNROLL", str(U))
+        mg = HelmholtzMG(n, k2=k * k, layers=layers, max_batch=1)
+        u, info = mg.solve(dev(f), tol=1e-8)
+        c = info[0]["cycles"]
+        assert mg.solve_kernels == U * math.ceil((c + 1) / U) * mg.cycle_kernels + 3
+        out[U] = (host(u), c, info[0]["rel_residual"])
+        mg.close()
+    assert out[1][1] == out[3][1] and out[1][2] == out[3][2]
+    assert np.array_equal(out[1][0], out[3][0])
+
+
 def point_rhs(n, dim, batch, seed):
     rng = np.random.default_rng(seed)
     pos = [tuple(rng.integers(n // 8, n - n // 8 - 1, size=dim)) for _ in range(batch)]

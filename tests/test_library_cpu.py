@@ -91,6 +91,11 @@ def test_calls_with_null_handle_fail_cleanly(hh):
     assert L.hh_adjoint(None, None, None, 1, 1e-6, 0, info, None) == hh.HH_ERR_ARG
     assert L.hh_destroy(None) == hh.HH_OK
     assert L.hh_num_levels(None) == 0
+    assert L.hh_cycle_kernels(None) == 0
+    assert L.hh_solve_kernels(None) == -1
+    bx, by = ct.c_int(7), ct.c_int(7)
+    assert L.hh_tile_shape(None, 0, ct.byref(bx), ct.byref(by)) == 0
+    assert (bx.value, by.value) == (0, 0)
 
 
 def test_python_layer_fails_loudly_without_library(monkeypatch, tmp_path):
