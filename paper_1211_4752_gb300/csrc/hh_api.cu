@@ -756,7 +756,7 @@ void destroy_impl(hh_handle *h) {
 
 // Autotuner: per fused level, time the down and up passes of every tile
 // shape on the workspace (handle's precision, one right-hand side) and keep
-// the fastest.  HH_TILE_VARIANT=<k> in the environment forces shape k.
+// the fastest, preferring the earlier shape within 3 %.  HH_TILE_VARIANT=<k> in the environment forces shape k.
 template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, int *best) {
   Work<R> &W = work<R>(h);
   const LevelK<R> K = levelk<R>(h, l, 0);
@@ -776,13 +776,18 @@ template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, 
       launch_up2d<R>(v, um, K, W.u_post[l], om, h->kconst, 1, nullptr, h->err, s);
     };
     run();
-    HH_CK(cudaEventRecord(e0, s));
-    for (int r = 0; r < 4; ++r) run();
-    HH_CK(cudaEventRecord(e1, s));
-    HH_CK(cudaEventSynchronize(e1));
-    float t = 0.f;
-    HH_CK(cudaEventElapsedTime(&t, e0, e1));
-    if (t < tbest) { tbest = t; *best = v; }
+    float t = 1e30f;   // best of three trials of four down + up passes
+    for (int trial = 0; trial < 3; ++trial) {
+      HH_CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < 4; ++r) run();
+      HH_CK(cudaEventRecord(e1, s));
+      HH_CK(cudaEventSynchronize(e1));
+      float tt = 0.f;
+      HH_CK(cudaEventElapsedTime(&tt, e0, e1));
+      t = std::min(t, tt);
+    }
+    // a later shape must win by more than 3 % (stable choices across runs)
+    if (t < 0.97f * tbest) { tbest = t; *best = v; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

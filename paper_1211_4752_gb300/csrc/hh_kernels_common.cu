@@ -135,8 +135,10 @@ __global__ void k_state_init(SolveState *st, const double *partials,
 // loop, r2 = ||f - A_0 u_k||^2 of the iterate u_k that the level-0
 // pre-smoothing sweep just read; CHECK_MODE_INNER: the complex64 loop of the
 // refinement (update_inner).  A nonzero device status word (a bounded wait
-// gave up) stops every right-hand side with HH_ERR_TIMEOUT.
-template <int MODE>
+// gave up) stops every right-hand side with HH_ERR_TIMEOUT.  COND: the
+// kernel sets the condition of a CUDA-graph WHILE node (the variant without
+// that call serves the host-driven loop, which profilers can observe).
+template <int MODE, bool COND>
 __global__ void k_check(SolveState *st, const double *partials, const SolveParams *P, int *flag,
                         unsigned long long cond, unsigned int *copies, const int *err) {
   __shared__ int any_s;
@@ -154,7 +156,7 @@ __global__ void k_check(SolveState *st, const double *partials, const SolveParam
   if (threadIdx.x == 0) {
     *flag = any_s;
     if (copies) *copies += 1u;   // cycles launched (stop tests run)
-    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, any_s ? 1u : 0u);
+    if (COND && cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, any_s ? 1u : 0u);
   }
 }
 
@@ -239,13 +241,15 @@ void launch_check_cycle(SolveState *st, const double *partials,
                         const SolveParams *P, int *flag,
                         unsigned long long cond, unsigned int *copies, const int *err,
                         cudaStream_t s) {
-  k_check<CHECK_MODE_CYCLE><<<1, 1024, 0, s>>>(st, partials, P, flag, cond, copies, err);
+  if (cond) k_check<CHECK_MODE_CYCLE, true><<<1, 1024, 0, s>>>(st, partials, P, flag, cond, copies, err);
+  else k_check<CHECK_MODE_CYCLE, false><<<1, 1024, 0, s>>>(st, partials, P, flag, cond, copies, err);
 }
 void launch_check_inner(SolveState *st, const double *partials,
                         const SolveParams *P, int *flag,
                         unsigned long long cond, unsigned int *copies, const int *err,
                         cudaStream_t s) {
-  k_check<CHECK_MODE_INNER><<<1, 1024, 0, s>>>(st, partials, P, flag, cond, copies, err);
+  if (cond) k_check<CHECK_MODE_INNER, true><<<1, 1024, 0, s>>>(st, partials, P, flag, cond, copies, err);
+  else k_check<CHECK_MODE_INNER, false><<<1, 1024, 0, s>>>(st, partials, P, flag, cond, copies, err);
 }
 void launch_check_outer(SolveState *st, const double *partials,
                         const SolveParams *P, int *flag, cudaStream_t s) {
