@@ -237,6 +237,25 @@ long long hh_solve_kernels(const hh_handle *h);
  * no fused kernel (3-D, nu1 or nu2 > 1, or the tail levels). */
 int hh_tile_shape(const hh_handle *h, int level, int *bx, int *by);
 
+/* Relative residuals rho_b = ||f_b - A_0 u_b||_2 / ||f_b||_2 (the quantity of
+ * the stop test, Sec. 4.1) of caller arrays, with no allocation of any kind:
+ * the block partial sums live in a fixed 1 MiB device array inside the
+ * library (64 right-hand sides x 1024 blocks x 2 sums of FP64).  The paper
+ * has no counterpart; it serves callers that must not allocate device memory
+ * while they run (cudaFree synchronizes the device; a caller under a fixed
+ * memory budget may get no more).
+ *   u_dev, f_dev: device, complex128, dense [batch][N..][N] as for hh_solve.
+ *   rho_dev: device, batch doubles (out); 0 where f_b and r_b are zero,
+ *   +inf where only f_b is zero.
+ *   batch: 1..64, else HH_ERR_ARG.  Asynchronous on `stream`.
+ * The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * outside any stream capture.  The array is shared by every handle on the
+ * device: calls that overlap in time race, so order them (same stream, or
+ * synchronize).  Nothing in it needs clearing between calls. */
+hh_status hh_rel_residual_static(hh_handle *h, const void *u_dev, const void *f_dev,
+                                 int batch, double *rho_dev, void *stream);
+
 /* Release the handle and its workspace (NULL is allowed). */
 hh_status hh_destroy(hh_handle *h);
 

@@ -78,6 +78,7 @@ SIGNATURES = {
     "hh_level_points": (_I, [_P, _I]),
     "hh_cycle_kernels": (_I, [_P]),
     "hh_solve_kernels": (ct.c_longlong, [_P]),
+    "hh_rel_residual_static": (_I, [_P, _P, _P, _I, _P, _P]),
     "hh_tile_shape": (_I, [_P, _I, ct.POINTER(_I), ct.POINTER(_I)]),
     "hh_destroy": (_I, [_P]),
     "hh_last_error": (ct.c_char_p, []),

@@ -1088,6 +1088,13 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
 
 }  // namespace
 
+namespace hh {
+// hh_noalloc.cu: relative residuals with partial sums in a fixed device array
+hh_status rel_residual_static(const LevelK<double> &L, int dim, int device, const double2 *u,
+                              const double2 *f, int batch, double *rho, cudaStream_t s,
+                              std::string *msg);
+}  // namespace hh
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -1182,6 +1189,20 @@ int hh_cycle_kernels(const hh_handle *h) {
   if (h->fused) return 2 * h->tail0 + 2;   // down passes, stop test, tail, up passes
   // per level nu1 sweeps, residual + restriction, nu2 sweeps; stop test; LU
   return (h->L - 1) * (h->opt.nu1 + 1 + h->opt.nu2) + 2;
+}
+
+hh_status hh_rel_residual_static(hh_handle *h, const void *u_dev, const void *f_dev,
+                                 int batch, double *rho_dev, void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  if (!u_dev || !f_dev || !rho_dev) return fail(HH_ERR_ARG, "u, f and rho must not be NULL");
+  HH_TRY(ensure_device(h));
+  std::string msg;
+  const hh_status st = rel_residual_static(levelk_dense<double>(h, 0, 0), h->dim, h->device,
+                                           (const double2 *)u_dev, (const double2 *)f_dev,
+                                           batch, rho_dev, (cudaStream_t)stream, &msg);
+  if (st != HH_OK) return fail(st, msg);
+  return HH_OK;
 }
 
 long long hh_solve_kernels(const hh_handle *h) { return h ? h->last_kernels : -1; }

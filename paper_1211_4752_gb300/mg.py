@@ -186,6 +186,19 @@ class HelmholtzMG:
         return g
 
     # ---- step API (complex128, FP64 tables) ------------------------------
+    def rel_residual_static(self, u, f):
+        """||f_b - A_0 u_b|| / ||f_b|| per right-hand side (FP64, on the device),
+        computed with the library's fixed scratch array: no allocation by the
+        library (the returned tensor is allocated here, by torch).  At most 64
+        right-hand sides; calls that overlap in time on one device race."""
+        u = self._vec(u, "u")
+        f = self._vec(f, "f")
+        rho = torch.empty(u.shape[0], dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().hh_rel_residual_static(self._h, _ptr(u), _ptr(f), u.shape[0],
+                                                   _ptr(rho), _stream()))
+        return rho
+
     def apply(self, x, level=0, adjoint=False):
         x = self._vec(x, "x", level)
         y = torch.empty_like(x)
