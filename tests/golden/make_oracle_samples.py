@@ -6,6 +6,7 @@ Calls only the oracle (oracle/) and the seeded input generators; nothing from
 the CUDA path.  Usage:
     python tests/golden/make_oracle_samples.py ecs_const  [out.json]
     python tests/golden/make_oracle_samples.py layered    [out.json]
+    python tests/golden/make_oracle_samples.py --divergence layered
 """
 
 import json
@@ -22,8 +23,33 @@ import oracle  # noqa: E402
 from paper_1211_4752_gb300 import workloads  # noqa: E402
 
 
+def divergence(w, out):
+    """Residual history of the oracle's cycle loop on a workload where the
+    weighted-Jacobi cycle diverges (Sec. 3.2): rho_k until rho > 1e3."""
+    H = oracle.build_hierarchy(w["n"], w["dim"], w["k2"], layers=w["layers"])
+    f = w["rhs"][0]
+    u = np.zeros_like(f)
+    nf = np.linalg.norm(f)
+    hist = []
+    while len(hist) < 200:
+        u = oracle.vcycle(H, 0, u, f)
+        rho = float(np.linalg.norm(f - oracle.apply_operator(H.levels[0], u)) / nf)
+        hist.append(rho)
+        if not (rho <= 1e3):
+            break
+    data = dict(workload=w["name"], n=w["n"], dim=w["dim"], layers=w["layers"],
+                diverged_at_cycle=len(hist), history=hist,
+                note="FP64 oracle, V(1,1) weighted Jacobi 0.8, u0 = 0; rho_k after cycle k")
+    out.write_text(json.dumps(data))
+    print(out, len(hist), hist[-1])
+
+
 def main():
     which = sys.argv[1]
+    if which == "--divergence":
+        w = getattr(workloads, sys.argv[2])()
+        divergence(w, Path(__file__).with_name(w["name"] + "_divergence.json"))
+        return
     w = getattr(workloads, which)()
     out = Path(sys.argv[2]) if len(sys.argv) > 2 else Path(__file__).with_name(w["name"] + ".json")
     t0 = time.time()

@@ -1,0 +1,101 @@
+"""CUDA path vs the oracle at the full sizes of the benchmarked workloads.
+
+* 1023^2 constant k, ECS 32 (the benchmark's workload, in the launch
+  configuration the benchmark times): whole iterates after two cycles, and the
+  converged solution at the oracle fixture's seeded sample points.
+* 2047^2 layered medium, 511^2 bump medium, 127^3 cube: the weighted-Jacobi
+  cycle diverges on these (Sec. 3.2); the GPU must diverge at the same cycle
+  with the same residual as the oracle (fixtures written by
+  tests/golden/make_oracle_samples.py --divergence).
+"""
+
+import json
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1211_4752_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLDEN = Path(__file__).resolve().parent / "golden"
+
+
+def relerr(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(np.ravel(b))
+
+
+def _handle(w, precision, batch=1):
+    from paper_1211_4752_gb300 import HelmholtzMG
+    k2 = w["k2"]
+    k2_t = torch.from_numpy(k2).cuda() if isinstance(k2, np.ndarray) else float(k2)
+    return HelmholtzMG(w["n"], dim=w["dim"], k2=k2_t, layers=w["layers"],
+                       precision=precision, max_batch=batch)
+
+
+def test_ecs_1023_two_cycles_match_oracle():
+    w = W.ecs_const()
+    H = O.build_hierarchy(w["n"], 2, w["k2"], layers=w["layers"])
+    f = w["rhs"][:1] + 0.01 * W.random_field(w["rhs"][:1].shape, 3)
+    u = np.zeros_like(f[0])
+    for _ in range(2):
+        u = O.vcycle(H, 0, u, f[0])
+    fd = torch.from_numpy(f).cuda()
+    for precision, tol in (("fp64", 1e-12), ("mixed", 1e-5)):
+        mg = _handle(w, precision)
+        got = mg.cycles(fd, torch.zeros_like(fd), 2).cpu().numpy()
+        assert relerr(got[0], u) < tol, precision
+        mg.close()
+
+
+def test_ecs_1023_solve_matches_oracle_fixture():
+    w = W.ecs_const()
+    g = json.loads((GOLDEN / f"{w['name']}.json").read_text())
+    idx = tuple(np.array(g["sample_index"]).T)
+    ref = np.array(g["sample_value"])
+    ref = ref[:, 0] + 1j * ref[:, 1]
+    f = torch.from_numpy(w["rhs"]).cuda()
+    # plain complex128 cycle: the oracle's iterate, cycle for cycle
+    mg = _handle(w, "fp64")
+    u, info = mg.solve(f, tol=1e-6)
+    assert info[0]["status"] == "OK"
+    assert abs(info[0]["cycles"] - g["cycles"]) <= 1
+    assert abs(info[0]["rel_residual"] - g["rel_residual"]) <= 1e-9 * g["rel_residual"]
+    assert relerr(u.cpu().numpy()[0][idx], ref) < 1e-10
+    mg.close()
+    # complex64 cycles inside FP64 refinement (the benchmarked configuration)
+    mg = _handle(w, "mixed")
+    u, info = mg.solve(f, tol=1e-6)
+    assert info[0]["status"] == "OK" and info[0]["refinements"] >= 1
+    r = (f - mg.apply(u)).cpu().numpy()
+    assert np.linalg.norm(r) / np.linalg.norm(w["rhs"]) <= 1e-6
+    uh = u.cpu().numpy()[0]
+    assert relerr(uh[idx], ref) < 1e-5
+    assert abs(np.linalg.norm(uh) - g["u_norm"]) <= 1e-5 * g["u_norm"]
+    mg.close()
+
+
+@pytest.mark.parametrize("name", ["layered", "bump", "cube"])
+def test_divergence_matches_oracle(name):
+    w = getattr(W, name)()
+    fx = GOLDEN / f"{w['name']}_divergence.json"
+    if not fx.exists():
+        pytest.skip(f"fixture {fx.name} not written")
+    g = json.loads(fx.read_text())
+    hist = g["history"]
+    f = torch.from_numpy(w["rhs"][:1].copy()).cuda()
+    mg = _handle(w, "fp64")
+    # the residual after three cycles
+    u3 = mg.cycles(f, torch.zeros_like(f), 3)
+    rho3 = mg.rel_residual_static(u3, f).cpu().numpy()[0]
+    assert abs(rho3 - hist[2]) <= 1e-9 * hist[2]
+    # the loop stops at the same cycle with the same residual
+    _, info = mg.solve(f, tol=1e-6)
+    assert info[0]["status"] == "ERR_DIVERGED"
+    assert info[0]["cycles"] == g["diverged_at_cycle"]
+    assert abs(info[0]["rel_residual"] - hist[-1]) <= 1e-8 * hist[-1]
+    mg.close()
