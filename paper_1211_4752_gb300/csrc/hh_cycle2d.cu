@@ -13,14 +13,33 @@ namespace {
 struct Shape { int bx, by; };
 constexpr Shape kShapes[kNumTileVariants] = {{60, 16}, {60, 32}, {28, 32}, {120, 16}, {28, 16}};
 
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous kernel on the stream finishes; it waits for it with
+// griddepcontrol.wait before touching that kernel's output.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <typename R, int BX, int BY>
 void down_one(const DownMaps &maps, const LevelK<R> &L, int zero_mode, typename Cx<R>::T *v_out,
               typename Cx<R>::T *fc, typename Cx<R>::T cs, typename Cx<R>::T omega,
               int kconst, const Lay &lc, int batch, const SolveState *st, double *partials,
               int *err, cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
-  k_down2d<R, BX, BY><<<grid, 256, Down2D<R, BX, BY>::smem, s>>>(
-      maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, st, partials, err);
+  launch_pdl(k_down2d<R, BX, BY>, grid, dim3(256), Down2D<R, BX, BY>::smem, s, maps, L,
+             zero_mode, v_out, fc, cs, omega, kconst, lc, st, partials, err);
 }
 
 template <typename R, int BX, int BY>
@@ -28,8 +47,8 @@ void up_one(const UpMaps &maps, const LevelK<R> &L, typename Cx<R>::T *u_out,
             typename Cx<R>::T omega, int kconst, int batch, const SolveState *st, int *err,
             cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
-  k_up2d<R, BX, BY><<<grid, 256, Up2D<R, BX, BY>::smem, s>>>(maps, L, u_out, omega, kconst,
-                                                             st, err);
+  launch_pdl(k_up2d<R, BX, BY>, grid, dim3(256), Up2D<R, BX, BY>::smem, s, maps, L, u_out, omega,
+             kconst, st, err);
 }
 
 // Dynamic shared memory limits, and the maximum shared-memory carveout for
@@ -251,7 +270,10 @@ __global__ void __launch_bounds__(256) k_tail_apply(const float2 *__restrict__ T
                                                     const SolveState *st) {
   constexpr int Q = kTailOpMaxS / 32;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (i >= N * N) return;
+  if (i >= N * N) {
+    griddep_wait();
+    return;
+  }
   float2 t[Q];
   unsigned live = 0;                      // columns inside the level (not padding)
   const float2 *row = T + (size_t)i * S;
@@ -263,6 +285,9 @@ __global__ void __launch_bounds__(256) k_tail_apply(const float2 *__restrict__ T
     t[q] = in ? x : make_float2(0.f, 0.f);
     live |= (in ? 1u : 0u) << q;
   }
+  // the row of T is constant: it is loaded before the dependency wait
+  griddep_wait();
+  griddep_launch_dependents();
   const int iy = i / N, ix = i - iy * N;
   for (int b = 0; b < batch; ++b) {
     if (st && !st[b].active) continue;
@@ -305,7 +330,7 @@ void launch_tail_gather(const double2 *U, float2 *T, int N, int P, int S, cudaSt
 void launch_tail_apply(const float2 *T, int N, int P, int S, const float2 *f, float2 *u,
                        int batch, const SolveState *st, cudaStream_t s) {
   const int M = N * N;
-  k_tail_apply<<<(M + 7) / 8, 256, 0, s>>>(T, N, P, S, f, u, batch, st);
+  launch_pdl(k_tail_apply, dim3((M + 7) / 8), dim3(256), 0, s, T, N, P, S, f, u, batch, st);
 }
 
 int tile_parts(int variant, int N) {

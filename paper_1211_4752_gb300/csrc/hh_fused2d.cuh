@@ -315,6 +315,28 @@ k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
   const int N = L.N;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
   R acc = R(0);
+  // Prologue, independent of the previous kernel's output (it overlaps that
+  // kernel's tail under programmatic dependent launch): the mbarrier, the
+  // tensor maps, the tile class and, off the uniform region, the coefficient
+  // tables.
+  const bool inner = tile_in(L, x0 - 2, x0 + BX + 2, N, false) &&
+                     tile_in(L, y0 - 2, y0 + BY + 2, N, false);
+  const bool fast = inner && tile_in(L, x0 - 2, x0 + BX + 2, N, true) &&
+                    tile_in(L, y0 - 2, y0 + BY + 2, N, true);
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    mbar_fence_init();
+    prefetch_tensor_map(&maps.u);
+    prefetch_tensor_map(&maps.f);
+    if (!kconst) prefetch_tensor_map(&maps.k);
+  }
+  C *s_cx = reinterpret_cast<C *>(base + S::oT);
+  if (!fast) {
+    if (inner) load_tables<R, false>(L, s_cx, s_cx + 3 * S::VW, S::VW, S::VH, x0, y0);
+    else load_tables<R, true>(L, s_cx, s_cx + 3 * S::VW, S::VW, S::VH, x0, y0);
+  }
+  griddep_wait();
+  griddep_launch_dependents();
   // One right-hand side: thread 0 starts the tile copies before the solver
   // state is read, so the state's load latency overlaps them (u is fetched
   // even where the state may say it is zero).  Batches read the state first,
@@ -323,8 +345,6 @@ k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
   const bool loadu = zero_mode == ZERO_NONE || (spec && zero_mode == ZERO_FLAG);
   auto issue = [&](bool withu) {
     if (threadIdx.x == 0) {
-      mbar_init(mbar, 1);
-      mbar_fence_init();
       mbar_expect_tx(mbar, (withu ? S::bU : 0u) + S::bF + (kconst ? 0u : S::bK));
       if (withu) tma_load_3d(base + S::oU, &maps.u, 2 * (x0 - 2), y0 - 2, b, mbar);
       tma_load_3d(base + S::oF, &maps.f, 2 * (x0 - 2), y0 - 1, b, mbar);
@@ -340,15 +360,6 @@ k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
     issue(!zero);
   }
   {
-    const bool inner = tile_in(L, x0 - 2, x0 + BX + 2, N, false) &&
-                       tile_in(L, y0 - 2, y0 + BY + 2, N, false);
-    const bool fast = inner && tile_in(L, x0 - 2, x0 + BX + 2, N, true) &&
-                      tile_in(L, y0 - 2, y0 + BY + 2, N, true);
-    C *s_cx = reinterpret_cast<C *>(base + S::oT);
-    if (!fast && act) {
-      if (inner) load_tables<R, false>(L, s_cx, s_cx + 3 * S::VW, S::VW, S::VH, x0, y0);
-      else load_tables<R, true>(L, s_cx, s_cx + 3 * S::VW, S::VW, S::VH, x0, y0);
-    }
     __syncthreads();   // barrier initialised (and tables written) before any wait
     const bool ok = mbar_wait_bounded(mbar, 0);
     if (__syncthreads_or(!ok)) {
@@ -495,12 +506,29 @@ k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__re
   uint64_t *mbar = reinterpret_cast<uint64_t *>(base + S::oB);
   const int N = L.N;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  // prologue before the dependency wait (see k_down2d)
+  const bool inner = tile_in(L, x0 - 1, x0 + BX, N, false) && tile_in(L, y0 - 1, y0 + BY, N, false);
+  const bool fast = inner && tile_in(L, x0 - 1, x0 + BX, N, true) &&
+                    tile_in(L, y0 - 1, y0 + BY, N, true);
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    mbar_fence_init();
+    prefetch_tensor_map(&maps.v);
+    prefetch_tensor_map(&maps.e);
+    prefetch_tensor_map(&maps.f);
+    if (!kconst) prefetch_tensor_map(&maps.k);
+  }
+  C *s_cx = reinterpret_cast<C *>(base + S::oT);
+  if (!fast) {
+    if (inner) load_tables<R, false>(L, s_cx, s_cx + 3 * S::WW, S::WW, S::WH, x0, y0);
+    else load_tables<R, true>(L, s_cx, s_cx + 3 * S::WW, S::WW, S::WH, x0, y0);
+  }
+  griddep_wait();
+  griddep_launch_dependents();
   // one right-hand side: copies started before the state is read (see k_down2d)
   const bool spec = gridDim.z == 1;
   if (!spec && st && !st[b].active) return;
   if (threadIdx.x == 0) {
-    mbar_init(mbar, 1);
-    mbar_fence_init();
     mbar_expect_tx(mbar, S::bV + S::bE + S::bF + (kconst ? 0u : S::bK));
     tma_load_3d(base + S::oV, &maps.v, 2 * (x0 - 2), y0 - 1, b, mbar);
     tma_load_3d(base + S::oE, &maps.e, 2 * (x0 / 2 - 2), y0 / 2 - 1, b, mbar);
@@ -508,14 +536,6 @@ k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__re
     if (!kconst) tma_load_2d(base + S::oK, &maps.k, x0, y0, mbar);
   }
   const bool act = !(st && !st[b].active);
-  const bool inner = tile_in(L, x0 - 1, x0 + BX, N, false) && tile_in(L, y0 - 1, y0 + BY, N, false);
-  const bool fast = inner && tile_in(L, x0 - 1, x0 + BX, N, true) &&
-                    tile_in(L, y0 - 1, y0 + BY, N, true);
-  C *s_cx = reinterpret_cast<C *>(base + S::oT);
-  if (!fast && act) {
-    if (inner) load_tables<R, false>(L, s_cx, s_cx + 3 * S::WW, S::WW, S::WH, x0, y0);
-    else load_tables<R, true>(L, s_cx, s_cx + 3 * S::WW, S::WW, S::WH, x0, y0);
-  }
   __syncthreads();
   const bool ok = mbar_wait_bounded(mbar, 0);
   if (__syncthreads_or(!ok)) {
