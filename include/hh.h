@@ -105,8 +105,10 @@ typedef struct {
                                 (default 20000; counts inner cycles in MIXED) */
   double div_limit;          /* rho_k above this is divergence (default 1e3) */
   double inner_tol;          /* MIXED: relative residual reduction of the
-                                complex64 cycles per refinement (default 1e-3) */
-  int max_inner;             /* MIXED: inner cycles per refinement (default 4000) */
+                                complex64 cycles per refinement (default 1e-3);
+                                a refinement's cycles also stop once their
+                                residual is below tol/2 * ||f|| */
+  int max_inner;             /* MIXED: inner cycles per refinement (default 20000) */
 } hh_options;
 
 typedef struct {

@@ -1120,7 +1120,7 @@ void hh_default_options(hh_options *o) {
   o->max_cycles = 20000;
   o->div_limit = 1e3;
   o->inner_tol = 1e-3;
-  o->max_inner = 4000;
+  o->max_inner = 20000;
 }
 
 const char *hh_last_error(void) { return g_err.c_str(); }

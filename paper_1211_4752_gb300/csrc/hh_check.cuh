@@ -27,7 +27,10 @@ __device__ __forceinline__ void update_cycle(SolveState &s, double r2, const Sol
 }
 
 // Inner complex64 loop of the refinement: r2 is the inner residual of the
-// current correction e_k (k = 0: e = 0, r = the inner right-hand side).
+// current correction e_k (k = 0: e = 0, r = the inner right-hand side).  The
+// loop ends when that residual has fallen by inner_tol, or below half the
+// outer target (tol/2 * ||f||): the outer residual after u += e equals the
+// inner one up to complex64 rounding, so more inner cycles cannot be needed.
 __device__ __forceinline__ void update_inner(SolveState &s, double r2, const SolveParams *P) {
   if (s.zero) {
     s.ref2 = r2;
@@ -42,7 +45,8 @@ __device__ __forceinline__ void update_inner(SolveState &s, double r2, const Sol
   s.rin2 = r2;
   if (!(rho <= P->div_limit)) {
     s.status = HH_ERR_DIVERGED; s.active = 0; s.done = 1;
-  } else if (rho <= P->inner_tol || s.inner >= P->max_inner || s.cycles >= P->max_cycles) {
+  } else if (rho <= P->inner_tol || r2 <= 0.25 * P->tol * P->tol * s.fnorm2 ||
+             s.inner >= P->max_inner || s.cycles >= P->max_cycles) {
     s.active = 0;
   } else {
     s.inner += 1;

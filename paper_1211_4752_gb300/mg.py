@@ -37,7 +37,7 @@ class HelmholtzMG:
                  form="csl", theta_max=math.pi / 6, p=0, thetas=None, c=None,
                  omega=0.8, nu1=1, nu2=1, precision="fp64", coarsest=4,
                  max_cycles=20000, div_limit=1e3, inner_tol=1e-3,
-                 max_inner=4000, max_batch=1, device=None):
+                 max_inner=20000, max_batch=1, device=None):
         L = B.lib()
         self.n, self.dim, self.N = int(n), int(dim), int(n) - 1
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
