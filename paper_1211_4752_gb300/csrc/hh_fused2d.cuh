@@ -71,6 +71,24 @@ template <typename R, int BX, int BY> struct Up2D {
                             bF = sizeof(C) * BX * BY, bK = sizeof(R) * BX * BY;
 };
 
+// Block sum of one value per thread (256 threads) in the kernel's own
+// precision, fixed order; the result is valid in thread 0.  (A complex64
+// block's |r|^2 terms need no FP64 here: the stop test's tolerance is far
+// above the FP32 rounding of a sum of 256 positive terms, and the partial
+// sums of the blocks are added in FP64.)
+template <typename R> __device__ __forceinline__ R block_sum_r(R v) {
+  __shared__ R ws[8];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  R s = R(0);
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < 8 ? ws[threadIdx.x] : R(0);
+    for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
 __device__ __forceinline__ unsigned char *align_smem128(unsigned char *p) {
   const uint32_t a = smem_u32(p);
   return p + ((128u - (a & 127u)) & 127u);
@@ -290,9 +308,13 @@ __device__ __forceinline__ void down_compute(
     const int cxl = w.x, cyl = w.y;
     if (!CHECK || (x0 / 2 + cxl < Nc && y0 / 2 + cyl < Nc)) {
       const int j = (2 * cyl + 1) * RW + 2 * cxl + 1;   // centre (2c+1) in s_r
-      C a = cscale(s_r[j], R(4));
-      a = cadd(a, cscale(cadd(cadd(s_r[j - 1], s_r[j + 1]), cadd(s_r[j - RW], s_r[j + RW])), R(2)));
-      a = cadd(a, cadd(cadd(s_r[j - RW - 1], s_r[j - RW + 1]), cadd(s_r[j + RW - 1], s_r[j + RW + 1])));
+      // [1 2 1] x [1 2 1] stencil: corners + 2 edges + 4 centre
+      const C e = cadd(cadd(s_r[j - 1], s_r[j + 1]), cadd(s_r[j - RW], s_r[j + RW]));
+      const C k = cadd(cadd(s_r[j - RW - 1], s_r[j - RW + 1]), cadd(s_r[j + RW - 1], s_r[j + RW + 1]));
+      const C m = s_r[j];
+      C a;
+      a.x = fmaf_any(R(4), m.x, fmaf_any(R(2), e.x, k.x));
+      a.y = fmaf_any(R(4), m.y, fmaf_any(R(2), e.y, k.y));
       fco[cyl * Pc + cxl] = cmul(csc, a);
     }
   }
@@ -378,7 +400,7 @@ k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
     }
   }
   if (partials) {
-    const double s = block_sum_d((double)acc);
+    const double s = (double)block_sum_r(acc);
     const int nblk = gridDim.x * gridDim.y;
     if (act && threadIdx.x == 0) partials[(size_t)b * nblk + blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
