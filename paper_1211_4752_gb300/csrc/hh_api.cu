@@ -120,6 +120,10 @@ struct hh_handle {
   long long fixed_kernels = 0;      // other kernels of the current solve
   long long last_kernels = -1;      // kernels of the last completed solve
   float2 *tailop[2] = {nullptr, nullptr};  // tail operator per direction (mixed)
+  int mid = 0;                      // complex64 cycles: cluster kernel for the
+  int mid0 = 0, midt = 0, midcl = 0;  // levels mid0 .. midt-1 (cluster of midcl CTAs)
+  float2 *tailop_mid[2] = {nullptr, nullptr};  // tail operator from level midt
+  MidArgs<float> margs[2];          // per direction
   DownMaps dmap[MAXL];              // tensor maps of the fused kernels, per level
   UpMaps umap[MAXL];
   std::vector<void *> allocs;
@@ -339,12 +343,13 @@ hh_status make_maps(hh_handle *h, int l, int variant, DownMaps *dm, UpMaps *um) 
   return HH_OK;
 }
 
-template <typename R> TailArgs<R> tail_args(hh_handle *h, int dir) {
+// Tail kernel arguments for the levels start .. coarsest.
+template <typename R> TailArgs<R> tail_args_from(hh_handle *h, int dir, int start) {
   Work<R> &W = work<R>(h);
   TailArgs<R> a{};
-  a.nl = h->L - h->tail0;
+  a.nl = h->L - start;
   for (int i = 0; i < a.nl; ++i) {
-    const int l = h->tail0 + i;
+    const int l = start + i;
     a.lv[i].K = levelk<R>(h, l, dir);
     a.lv[i].f = W.f[l];
     a.lv[i].v = W.u_pre[l];
@@ -355,7 +360,7 @@ template <typename R> TailArgs<R> tail_args(hh_handle *h, int dir) {
   using C = typename Cx<R>::T;
   int off = 0, koff = 0, Ns[kMaxTail];
   for (int i = 0; i < a.nl; ++i) {
-    const int N = h->lv[h->tail0 + i].N;
+    const int N = h->lv[start + i].N;
     Ns[i] = N;
     a.off[i] = off;
     off += 3 * N * N + 6 * N;
@@ -370,6 +375,9 @@ template <typename R> TailArgs<R> tail_args(hh_handle *h, int dir) {
   a.m = h->m;
   a.omega = omega<R>(h, dir);
   return a;
+}
+template <typename R> TailArgs<R> tail_args(hh_handle *h, int dir) {
+  return tail_args_from<R>(h, dir, h->tail0);
 }
 
 
@@ -413,7 +421,10 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
   Work<R> &W = work<R>(h);
   const SolveState *st = check != CHECK_NONE ? h->st : nullptr;
   const auto om = omega<R>(h, dir);
-  const int T = h->tail0;
+  // complex64 cycles with the cluster kernel: per-level kernels above mid0
+  bool mid = false;
+  if constexpr (std::is_same<R, float>::value) mid = h->mid != 0;
+  const int T = mid ? h->mid0 : h->tail0;
   for (int l = 0; l < T; ++l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
     const bool norm = l == 0 && check != CHECK_NONE;
@@ -422,7 +433,12 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
                      norm ? h->partials : nullptr, h->err, s);
     if (norm) fork_check(h, check, cond, s);
   }
-  enqueue_tail<R>(h, dir, batch, st, s);
+  if (mid) {
+    if constexpr (std::is_same<R, float>::value)
+      launch_mid2d<float>(h->margs[dir], h->midcl, batch, st, s);
+  } else {
+    enqueue_tail<R>(h, dir, batch, st, s);
+  }
   for (int l = T - 1; l >= 0; --l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
     // the level-0 up pass is the one kernel of the cycle that writes the
@@ -685,6 +701,11 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
   const auto om = omega<R>(h, 0);
   const bool two = h->dim == 2;
   if (kernel == 4) {
+    if constexpr (std::is_same<R, float>::value)
+      if (h->mid) {
+        launch_mid2d<float>(h->margs[0], h->midcl, batch, nullptr, s);
+        return;
+      }
     enqueue_tail<R>(h, 0, batch, nullptr, s);
     return;
   }
@@ -799,8 +820,8 @@ template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, 
 // right-hand sides of level tail0 (one block each), the responses gathered
 // into rows of T and rounded to complex64.  The two N^2 x S scratch arrays
 // live only during setup.
-hh_status build_tail_op(hh_handle *h, int dir, cudaStream_t s) {
-  const LevelHost &v = h->lv[h->tail0];
+hh_status build_tail_op(hh_handle *h, int dir, int start, float2 **out, cudaStream_t s) {
+  const LevelHost &v = h->lv[start];
   const int N = v.N, P = v.P, S = (int)v.S, M = N * N;
   const size_t n = (size_t)M * S;
   double2 *F = nullptr, *U = nullptr;
@@ -810,14 +831,14 @@ hh_status build_tail_op(hh_handle *h, int dir, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemsetAsync(U, 0, n * sizeof(double2), s);
   hh_status r = HH_OK;
   if (e == cudaSuccess) {
-    r = dev_alloc_n(h, &h->tailop[dir], n);
+    r = dev_alloc_n(h, out, n);
     if (r == HH_OK) {
       launch_unit_rhs(F, N, P, S, s);
-      TailArgs<double> a = tail_args<double>(h, dir);
+      TailArgs<double> a = tail_args_from<double>(h, dir, start);
       a.lv[0].f = F;
       a.lv[0].u = U;
       launch_tail2d<double>(a, M, nullptr, s);
-      launch_tail_gather(U, h->tailop[dir], N, P, S, s);
+      launch_tail_gather(U, *out, N, P, S, s);
       e = cudaStreamSynchronize(s);
       if (e == cudaSuccess) e = cudaGetLastError();
     }
@@ -833,6 +854,90 @@ hh_status build_tail_op(hh_handle *h, int dir, cudaStream_t s) {
   return HH_OK;
 }
 
+// Shared-memory layout of the cluster kernel's levels (see MidLevel): rows of
+// stride N + 1 (a power of two), (N + 1) / cl rows per CTA.
+int ilog2(int v) {
+  int r = 0;
+  while ((1 << (r + 1)) <= v) ++r;
+  return r;
+}
+hh_status mid_layout(hh_handle *h, int m0, int t, int cl, int dir, MidArgs<float> *a) {
+  *a = MidArgs<float>{};
+  a->nl = t - m0;
+  if (a->nl < 1 || a->nl > kMaxMid) return fail(HH_ERR_UNSUPPORTED, "mid levels");
+  int off = 0;
+  for (int i = 0; i < a->nl; ++i) {
+    const int l = m0 + i;
+    const int N = h->lv[l].N, NX = N + 1, rp = NX / cl;
+    if (rp < 1 || (NX & (NX - 1))) return fail(HH_ERR_UNSUPPORTED, "mid level size");
+    MidLevel<float> &M = a->lv[i];
+    M.K = levelk<float>(h, l, dir);
+    M.c = cscal<float>(h, l, dir);
+    M.rp = rp;
+    M.lrp = ilog2(rp);
+    M.lnx = ilog2(NX);
+    M.off_tab = off; off += 6 * N;
+    M.off_d = off; off += (rp + 3) * NX;
+    M.off_wt = off; off += (rp + 3) * NX;
+    M.off_f = off; off += rp * NX;
+    M.off_v = off; off += (rp + 3) * NX;
+    M.off_t = off; off += (rp + 1) * NX;
+    M.off_w = off; off += (rp + 2) * NX;
+  }
+  const LevelHost &vt = h->lv[t];
+  if (vt.N != 15 || vt.P != 16) return fail(HH_ERR_UNSUPPORTED, "tail level");
+  a->Nt = vt.N;
+  a->Pt = vt.P;
+  a->St = (int)vt.S;
+  const int rpt = 16 / cl;
+  a->lrpt = ilog2(rpt);
+  a->off_ft = off; off += rpt * 16;
+  a->off_ut = off; off += rpt * 16;
+  a->off_fg = off; off += a->St;
+  a->smem_bytes = off * (int)sizeof(float2);
+  a->f0 = h->w32.f[m0];
+  a->u0 = h->w32.u_post[m0];
+  a->P0 = h->lv[m0].P;
+  a->S0 = h->lv[m0].S;
+  a->T = h->tailop_mid[dir];
+  a->omega = omega<float>(h, dir);
+  return HH_OK;
+}
+
+// Complex64 cycles, opt-in (HH_MID=1 in the environment): run the levels
+// between the first one of at most 127 points per axis and the 15-point level
+// in one cluster kernel (16 CTAs, or 8), the 15-point level and below as a
+// tail operator.  On a GB300 the per-level kernels are faster at 1023^2
+// (12.7 us against 14.5 us for these levels), so they stay the default.
+hh_status setup_mid(hh_handle *h, cudaStream_t s) {
+  const char *me = std::getenv("HH_MID");
+  if (!(me && std::strcmp(me, "1") == 0)) return HH_OK;
+  if (h->dim != 2 || !h->fused) return HH_OK;
+  int t = -1;
+  for (int l = 1; l < h->L; ++l)
+    if (h->lv[l].N == 15) t = l;
+  if (t < 0) return HH_OK;
+  int m0 = 1;
+  while (m0 < t && h->lv[m0].N > 127) ++m0;
+  if (m0 >= t || t - m0 > kMaxMid) return HH_OK;
+  for (int cl : {16, 8}) {
+    MidArgs<float> a;
+    if (mid_layout(h, m0, t, cl, 0, &a) != HH_OK) { g_err.clear(); continue; }
+    if (a.smem_bytes > 227 * 1024) continue;
+    if (init_mid2d<float>(cl) != cudaSuccess) { cudaGetLastError(); continue; }
+    if (mid2d_max_clusters<float>(cl, a.smem_bytes) < 1) continue;
+    for (int dir = 0; dir < 2; ++dir)
+      HH_TRY(build_tail_op(h, dir, t, &h->tailop_mid[dir], s));
+    for (int dir = 0; dir < 2; ++dir) HH_TRY(mid_layout(h, m0, t, cl, dir, &h->margs[dir]));
+    h->mid = 1;
+    h->mid0 = m0;
+    h->midt = t;
+    h->midcl = cl;
+    return HH_OK;
+  }
+  return HH_OK;
+}
+
 hh_status autotune(hh_handle *h, cudaStream_t s) {
   const char *force = std::getenv("HH_TILE_VARIANT");
   if (force) {
@@ -841,7 +946,8 @@ hh_status autotune(hh_handle *h, cudaStream_t s) {
     for (int l = 0; l < h->tail0; ++l) h->variant[l] = v;
     return HH_OK;
   }
-  for (int l = 0; l < h->tail0; ++l) {
+  const int tuned = h->mid ? h->mid0 : h->tail0;   // levels with per-level kernels
+  for (int l = 0; l < tuned; ++l) {
     if (h->opt.precision == HH_MIXED) HH_TRY(tune_level<float>(h, l, s, &h->variant[l]));
     else HH_TRY(tune_level<double>(h, l, s, &h->variant[l]));
   }
@@ -1075,7 +1181,8 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
     const char *te = std::getenv("HH_TAIL");
     const bool op = !(te && std::strcmp(te, "kernel") == 0);
     if (op && h->opt.precision == HH_MIXED && h->lv[h->tail0].S <= kTailOpMaxS)
-      for (int dir = 0; dir < 2; ++dir) HH_TRY(build_tail_op(h, dir, s));
+      for (int dir = 0; dir < 2; ++dir) HH_TRY(build_tail_op(h, dir, h->tail0, &h->tailop[dir], s));
+    if (op && h->opt.precision == HH_MIXED) HH_TRY(setup_mid(h, s));
     HH_TRY(autotune(h, s));
     for (int l = 0; l < h->tail0; ++l) {
       if (h->opt.precision == HH_FP64) HH_TRY(make_maps<double>(h, l, h->variant[l], &h->dmap[l], &h->umap[l]));
@@ -1186,7 +1293,8 @@ int hh_level_points(const hh_handle *h, int level) {
 
 int hh_cycle_kernels(const hh_handle *h) {
   if (!h) return 0;
-  if (h->fused) return 2 * h->tail0 + 2;   // down passes, stop test, tail, up passes
+  if (h->fused)   // down passes, stop test, tail (or cluster kernel), up passes
+    return 2 * (h->mid && h->opt.precision == HH_MIXED ? h->mid0 : h->tail0) + 2;
   // per level nu1 sweeps, residual + restriction, nu2 sweeps; stop test; LU
   return (h->L - 1) * (h->opt.nu1 + 1 + h->opt.nu2) + 2;
 }

@@ -84,6 +84,48 @@ void launch_tail2d(const TailArgs<R> &a, int batch, const SolveState *st, cudaSt
 // N x N), column j = pitched position j (0 <= j < S = N * P); the padding
 // columns (j % P >= N) are zero.
 constexpr int kTailOpMaxS = 1024;    // S <= 32 * 32: one register tile per lane
+
+// Middle levels of a complex64 cycle in one thread-block cluster per
+// right-hand side (hh_mid2d.cu).  Levels m0 .. t-1 are distributed over the
+// cluster's CTAs by rows (CTA q owns rows [q rp, (q+1) rp) of a level with rp
+// rows per CTA) and live in shared memory; neighbours' rows are read through
+// distributed shared memory; phases are separated by cluster barriers.
+// Level t (15 interior points per axis) and everything coarser is the tail
+// operator T_t applied as a dense product.
+constexpr int kMaxMid = 6;
+template <typename R> struct MidLevel {
+  LevelK<R> K;               // operator (coefficient tables in global memory)
+  typename Cx<R>::T c;       // scale of the residual restricted from this level
+  int rp, lrp;               // rows per CTA (a power of two) and its log2
+  int lnx;                   // log2 of the row length rounded up (N + 1)
+  // offsets (complex elements) in shared memory; "rows a..b" are global row
+  // indices relative to the CTA's first own row r0
+  int off_tab;               // 6N coefficient tables
+  int off_d, off_wt;         // D and omega / D on rows r0-1 .. r1+1 (rp + 3 rows)
+  int off_f;                 // f on the own rows (rp)
+  int off_v;                 // v on rows r0-1 .. r1+1 (rp + 3)
+  int off_t;                 // r on rows r0 .. r1 (rp + 1), later u on the own rows
+  int off_w;                 // w on rows r0-1 .. r1 (rp + 2)
+};
+template <typename R> struct MidArgs {
+  int nl;                          // levels m0 .. t-1
+  MidLevel<R> lv[kMaxMid];
+  const typename Cx<R>::T *f0;     // level m0 right-hand side (pitched)
+  typename Cx<R>::T *u0;           // level m0 result (pitched)
+  int P0;
+  long long S0;
+  int Nt, Pt, St, lrpt;            // tail level: points (15), pitch (16), S = Nt Pt,
+                                   // log2 of its rows per CTA
+  int off_ft, off_ut, off_fg;      // tail f, u (own rows, pitch 16), gathered f (St)
+  const float2 *T;                 // tail operator, Nt^2 rows x St columns
+  typename Cx<R>::T omega;
+  int smem_bytes;
+};
+template <typename R> cudaError_t init_mid2d(int cl);
+template <typename R>
+cudaError_t launch_mid2d(const MidArgs<R> &a, int cl, int batch, const SolveState *st,
+                         cudaStream_t s);
+template <typename R> int mid2d_max_clusters(int cl, int smem_bytes);
 void launch_unit_rhs(double2 *F, int N, int P, int S, cudaStream_t s);
 void launch_tail_gather(const double2 *U, float2 *T, int N, int P, int S, cudaStream_t s);
 void launch_tail_apply(const float2 *T, int N, int P, int S, const float2 *f, float2 *u,
