@@ -923,8 +923,8 @@ hh_status setup_mid(hh_handle *h, cudaStream_t s) {
   for (int cl : {16, 8}) {
     MidArgs<float> a;
     if (mid_layout(h, m0, t, cl, 0, &a) != HH_OK) { g_err.clear(); continue; }
-    if (a.smem_bytes > 227 * 1024) continue;
-    if (init_mid2d<float>(cl) != cudaSuccess) { cudaGetLastError(); continue; }
+    if (a.smem_bytes > 226 * 1024) continue;
+    if (init_mid2d<float>(cl, a.smem_bytes) != cudaSuccess) { cudaGetLastError(); continue; }
     if (mid2d_max_clusters<float>(cl, a.smem_bytes) < 1) continue;
     for (int dir = 0; dir < 2; ++dir)
       HH_TRY(build_tail_op(h, dir, t, &h->tailop_mid[dir], s));

@@ -121,7 +121,7 @@ template <typename R> struct MidArgs {
   typename Cx<R>::T omega;
   int smem_bytes;
 };
-template <typename R> cudaError_t init_mid2d(int cl);
+template <typename R> cudaError_t init_mid2d(int cl, int smem_bytes);
 template <typename R>
 cudaError_t launch_mid2d(const MidArgs<R> &a, int cl, int batch, const SolveState *st,
                          cudaStream_t s);

@@ -109,7 +109,8 @@ template <typename R>
 __global__ void __launch_bounds__(1024) k_tail2d(TailArgs<R> A, const SolveState *st) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.x;
-  if (st && !st[b].active) return;
+  // one decision per block (the stop test may update the state meanwhile)
+  if (!__syncthreads_and(!(st && !st[b].active))) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *sm = reinterpret_cast<C *>(smem_raw);
   R *skk = reinterpret_cast<R *>(smem_raw + A.kbase);
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(256) k_tail_apply(const float2 *__restrict__ T
   griddep_launch_dependents();
   const int iy = i / N, ix = i - iy * N;
   for (int b = 0; b < batch; ++b) {
-    if (st && !st[b].active) continue;
+    if (!__all_sync(0xffffffffu, !(st && !st[b].active))) continue;   // warp-uniform
     const float2 *fb = f + (size_t)b * S;
     float2 v[Q];
 #pragma unroll

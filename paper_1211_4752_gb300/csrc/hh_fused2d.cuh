@@ -374,9 +374,12 @@ k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
     }
   };
   if (spec) issue(loadu);
-  // blocks of a finished right-hand side skip the work
-  bool act = !(st && !st[b].active);
-  const bool zero = zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero);
+  // blocks of a finished right-hand side skip the work.  The stop test may
+  // update the state while this kernel runs (it runs beside the coarse
+  // levels), so each block takes one decision for all its threads.
+  bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
+  const bool zero =
+      __syncthreads_or(zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero)) != 0;
   if (!spec) {
     if (!act) return;
     issue(!zero);
@@ -547,17 +550,24 @@ k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__re
   }
   griddep_wait();
   griddep_launch_dependents();
-  // one right-hand side: copies started before the state is read (see k_down2d)
+  // one right-hand side: copies started before the state is read (see
+  // k_down2d); one decision per block
   const bool spec = gridDim.z == 1;
-  if (!spec && st && !st[b].active) return;
-  if (threadIdx.x == 0) {
-    mbar_expect_tx(mbar, S::bV + S::bE + S::bF + (kconst ? 0u : S::bK));
-    tma_load_3d(base + S::oV, &maps.v, 2 * (x0 - 2), y0 - 1, b, mbar);
-    tma_load_3d(base + S::oE, &maps.e, 2 * (x0 / 2 - 2), y0 / 2 - 1, b, mbar);
-    tma_load_3d(base + S::oF, &maps.f, 2 * x0, y0, b, mbar);
-    if (!kconst) tma_load_2d(base + S::oK, &maps.k, x0, y0, mbar);
+  auto issue = [&]() {
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(mbar, S::bV + S::bE + S::bF + (kconst ? 0u : S::bK));
+      tma_load_3d(base + S::oV, &maps.v, 2 * (x0 - 2), y0 - 1, b, mbar);
+      tma_load_3d(base + S::oE, &maps.e, 2 * (x0 / 2 - 2), y0 / 2 - 1, b, mbar);
+      tma_load_3d(base + S::oF, &maps.f, 2 * x0, y0, b, mbar);
+      if (!kconst) tma_load_2d(base + S::oK, &maps.k, x0, y0, mbar);
+    }
+  };
+  if (spec) issue();
+  const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
+  if (!spec) {
+    if (!act) return;
+    issue();
   }
-  const bool act = !(st && !st[b].active);
   __syncthreads();
   const bool ok = mbar_wait_bounded(mbar, 0);
   if (__syncthreads_or(!ok)) {

@@ -103,7 +103,7 @@ k_smooth(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in,
          const SolveState *__restrict__ st, double *__restrict__ partials) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
-  if (st && !st[b].active) return;
+  if (!__syncthreads_and(!(st && !st[b].active))) return;   // one decision per block
   const bool zero = zero_mode == ZERO_ALL ||
                     (zero_mode == ZERO_FLAG && st && st[b].zero);
   const int N = L.N, P = L.P;
@@ -149,7 +149,7 @@ k_resid_restrict(LevelK<R> L, const typename Cx<R>::T *__restrict__ u,
                  const SolveState *__restrict__ st) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
-  if (st && !st[b].active) return;
+  if (!__syncthreads_and(!(st && !st[b].active))) return;   // one decision per block
   u += (size_t)b * L.S;
   f += (size_t)b * L.S;
   fc += (size_t)b * lc.S;
@@ -224,7 +224,7 @@ k_correct_smooth(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in,
                  typename Cx<R>::T omega, const SolveState *__restrict__ st) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
-  if (st && !st[b].active) return;
+  if (!__syncthreads_and(!(st && !st[b].active))) return;   // one decision per block
   const int N = L.N, P = L.P;
   const C *u = u_in + (size_t)b * L.S;
   const C *ec = e + (size_t)b * lc.S;
@@ -285,7 +285,7 @@ k_refine(LevelK<double> L, const double2 *__restrict__ u_in, int u_zero,
   const size_t pts = npts<DIM>(N);
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t p0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (st && st[b].done) {
+  if (__syncthreads_or(st && st[b].done)) {   // one decision per block
     if (u_out)
       for (size_t p = p0; p < pts; p += stride) {
         int x, y, z;
@@ -387,7 +387,7 @@ __global__ void k_coarse_solve(const double2 *__restrict__ lu,
                                const SolveState *__restrict__ st) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.x;
-  if (st && !st[b].active) return;
+  if (!__syncthreads_and(!(st && !st[b].active))) return;   // one decision per block
   const int N = lay.N, m = (int)npts<DIM>(N), i = threadIdx.x;
   const C *fb = f + (size_t)b * lay.S;
   double2 y = make_double2(0.0, 0.0);

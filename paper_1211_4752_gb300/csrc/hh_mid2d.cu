@@ -69,7 +69,17 @@ k_mid2d(const __grid_constant__ MidArgs<R> A, const SolveState *__restrict__ st)
   }
   griddep_wait();
   griddep_launch_dependents();
-  if (st && !st[b].active) return;   // the whole cluster shares b
+  // The stop test may update the state while this kernel runs (it runs
+  // beside the coarse levels): every CTA of the cluster must take the same
+  // decision, so rank 0's reading is shared through distributed memory.
+  {
+    __shared__ int s_act;
+    if (tid == 0) s_act = !(st && !st[b].active);
+    cluster.sync();
+    const int act = *cluster.map_shared_rank(&s_act, 0);
+    cluster.sync();   // rank 0's flag is read before any CTA leaves
+    if (!act) return;
+  }
 
   // level m0: own rows of the right-hand side from global memory
   {
@@ -267,9 +277,9 @@ template <typename K> void mid_attrs(K kern, int cl, size_t smem, cudaError_t *e
 
 }  // namespace
 
-template <typename R> cudaError_t init_mid2d(int cl) {
+template <typename R> cudaError_t init_mid2d(int cl, int smem_bytes) {
   cudaError_t e = cudaSuccess;
-  const size_t smem = 227 * 1024;
+  const size_t smem = (size_t)smem_bytes;
   if (cl == 8) mid_attrs(k_mid2d<R, 8>, 8, smem, &e);
   else if (cl == 16) mid_attrs(k_mid2d<R, 16>, 16, smem, &e);
   else e = cudaErrorInvalidValue;
@@ -322,7 +332,7 @@ cudaError_t launch_mid2d(const MidArgs<R> &a, int cl, int batch, const SolveStat
   return cudaErrorInvalidValue;
 }
 
-template cudaError_t init_mid2d<float>(int);
+template cudaError_t init_mid2d<float>(int, int);
 template int mid2d_max_clusters<float>(int, int);
 template cudaError_t launch_mid2d<float>(const MidArgs<float> &, int, int, const SolveState *,
                                          cudaStream_t);
