@@ -42,7 +42,8 @@ import numpy as np
 
 __all__ = [
     "Level", "Hierarchy", "ecs_coordinate", "level_spacings", "laplacian_1d",
-    "apply_operator", "operator_diagonal", "jacobi", "restrict_fw", "prolong",
+    "apply_operator", "operator_diagonal", "jacobi", "gmres_smooth", "smooth",
+    "restrict_fw", "prolong",
     "dense_matrix", "lu_factor", "lu_solve", "build_hierarchy",
     "adjoint_hierarchy", "vcycle", "solve", "residual_norm",
     "symmetrizer_weights", "adjoint_solve_symmetrized", "grad_k2",
@@ -134,6 +135,8 @@ class Hierarchy:
     nu1: int = 1
     nu2: int = 1
     lu: tuple = None      # (factors, pivots) of the coarsest operator
+    smoother: str = "jacobi"   # or "gmres": GMRES(m) smoothing (Sec. 3.2)
+    m: int = 3                 # GMRES degree
     info: dict = field(default_factory=dict)
 
 
@@ -183,6 +186,45 @@ def jacobi(lv: Level, u, f, omega):
     """One weighted-Jacobi sweep u <- u + omega D^{-1}(f - A u), Eq. (wjacobi);
     every point uses the old iterate."""
     return u + omega * (f - apply_operator(lv, u)) / operator_diagonal(lv)
+
+
+def gmres_smooth(lv: Level, u, f, m=3):
+    """One GMRES(m) smoothing step (Sec. 3.2, the smoother the paper uses):
+    u + z, where z minimises ||f - A (u + z)||_2 over the Krylov space
+    K_m(A, r0) = span{r0, A r0, ..., A^{m-1} r0}, r0 = f - A u.  Arnoldi with
+    modified Gram-Schmidt builds an orthonormal basis V and the (m+1) x m
+    Hessenberg matrix H with A V_m = V_{m+1} H; y minimises ||beta e1 - H y||
+    (a small least-squares solve) and z = V_m y.  If the space has dimension
+    j < m (A V_j lies in span V_j), the exact minimiser on it is taken."""
+    r0 = f - apply_operator(lv, u)
+    beta = np.linalg.norm(r0)
+    if beta == 0.0:
+        return u
+    V = [r0 / beta]
+    H = np.zeros((m + 1, m), dtype=np.complex128)
+    k = m
+    for j in range(m):
+        w = apply_operator(lv, V[j])
+        for i in range(j + 1):
+            H[i, j] = np.vdot(V[i], w)
+            w = w - H[i, j] * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j] == 0.0:
+            k = j + 1
+            break
+        V.append(w / H[j + 1, j])
+    e1 = np.zeros(k + 1, dtype=np.complex128)
+    e1[0] = beta
+    y = np.linalg.lstsq(H[:k + 1, :k], e1, rcond=None)[0]
+    z = sum(y[j] * V[j] for j in range(k))
+    return u + z
+
+
+def smooth(hier, lv: Level, u, f):
+    """One smoothing step with the hierarchy's smoother."""
+    if hier.smoother == "gmres":
+        return gmres_smooth(lv, u, f, hier.m)
+    return jacobi(lv, u, f, hier.omega)
 
 
 # --------------------------------------------------------------------------
@@ -286,7 +328,8 @@ def lu_solve(lu, b):
 
 def build_hierarchy(n, dim, k2, layers=0, gamma=math.pi / 6,
                     theta_max=math.pi / 6, p=None, form="csl", c=None,
-                    omega=0.8, nu1=1, nu2=1, coarsest=4, thetas=None):
+                    omega=0.8, nu1=1, nu2=1, coarsest=4, thetas=None,
+                    smoother="jacobi", m=3):
     """Level-dependent hierarchy for (-Delta - k^2) u = f on the unit square
     (cube) with n = 2^P intervals per dimension.
 
@@ -337,7 +380,9 @@ def build_hierarchy(n, dim, k2, layers=0, gamma=math.pi / 6,
         k2_l = k2_l[inj]
     if c is None:
         c = [1.0 + 0j] * (len(levels) - 1)
-    hier = Hierarchy(levels, list(c), omega, nu1, nu2)
+    if smoother not in ("jacobi", "gmres"):
+        raise ValueError(smoother)
+    hier = Hierarchy(levels, list(c), omega, nu1, nu2, smoother=smoother, m=m)
     hier.lu = lu_factor(dense_matrix(levels[-1]))
     hier.info = dict(dtheta=dtheta, p=p, a=a, b=b, gamma=gamma, form=form)
     return hier
@@ -362,7 +407,7 @@ def adjoint_hierarchy(hier: Hierarchy):
         levels.append(Level(lv.n, lv.dim, lo, dg, up, np.conj(lv.alpha),
                             np.conj(lv.beta), lv.k2))
     adj = Hierarchy(levels, [np.conj(x) for x in hier.c], np.conj(hier.omega),
-                    hier.nu1, hier.nu2)
+                    hier.nu1, hier.nu2, smoother=hier.smoother, m=hier.m)
     adj.lu = lu_factor(dense_matrix(levels[-1]))
     adj.info = dict(hier.info, adjoint=True)
     return adj
@@ -378,7 +423,7 @@ def vcycle(hier: Hierarchy, l, u, f):
     guess; LU on the coarsest level), interpolated correction, post-smooth."""
     lv = hier.levels[l]
     for _ in range(hier.nu1):
-        u = jacobi(lv, u, f, hier.omega)
+        u = smooth(hier, lv, u, f)
     r = f - apply_operator(lv, u)
     fc = hier.c[l] * restrict_fw(r)
     if l + 1 == len(hier.levels) - 1:
@@ -387,7 +432,7 @@ def vcycle(hier: Hierarchy, l, u, f):
         ec = vcycle(hier, l + 1, np.zeros_like(fc), fc)
     u = u + prolong(ec)
     for _ in range(hier.nu2):
-        u = jacobi(lv, u, f, hier.omega)
+        u = smooth(hier, lv, u, f)
     return u
 
 

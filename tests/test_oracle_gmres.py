@@ -1,0 +1,99 @@
+"""Pins of the oracle's GMRES(m) smoother (Sec. 3.2) and of the cycle built
+on it: the minimal-residual property against an independent least-squares
+solve on the monomial Krylov basis, exactness when the Krylov space is the
+whole space, monotone residuals, and the cycle counts of Tables 1 and 2."""
+
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1211_4752_gb300 import workloads as W
+
+GOLDEN = Path(__file__).resolve().parent / "golden"
+
+
+def _level(n, dim, k2, layers):
+    return O.build_hierarchy(n, dim, k2, layers=layers).levels
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_gmres_step_minimises_residual_over_krylov_space(m):
+    lv = _level(16, 2, 300.0, 3)[1]           # 7 x 7 level with a shift and ECS
+    rng = np.random.default_rng(m)
+    shape = lv.shape
+    u = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    f = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    got = O.gmres_smooth(lv, u, f, m)
+    # independent: least squares on [A r0, A^2 r0, ...] (monomial basis)
+    r0 = (f - O.apply_operator(lv, u)).ravel()
+    K, AK = [], []
+    q = r0
+    for _ in range(m):
+        K.append(q)
+        q = O.apply_operator(lv, q.reshape(shape)).ravel()
+        AK.append(q)
+    y = np.linalg.lstsq(np.stack(AK, 1), r0, rcond=None)[0]
+    ref = u + (np.stack(K, 1) @ y).reshape(shape)
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+    r_new = np.linalg.norm(f - O.apply_operator(lv, got))
+    assert r_new <= np.linalg.norm(r0) * (1 + 1e-14)
+
+
+def test_gmres_three_steps_solve_a_three_unknown_system():
+    lv = _level(4, 1, 7.0, 0)[0]              # 1-D, 3 interior points
+    f = np.array([1.0, -2.0 + 1j, 0.5])
+    u = O.gmres_smooth(lv, np.zeros(3, complex), f, 3)
+    assert np.linalg.norm(f - O.apply_operator(lv, u)) <= 1e-12 * np.linalg.norm(f)
+
+
+def test_gmres_cycle_converges_where_jacobi_diverges():
+    """The 511^2 bump medium at kh = 0.5 makes the Jacobi cycle diverge
+    (Sec. 3.2); a smaller copy (127^2, same kh) with GMRES(3) smoothing
+    converges to the direct solution."""
+    w = W.bump(n=128, layers=4, nsrc=1)
+    H = O.build_hierarchy(128, 2, w["k2"], layers=4, smoother="gmres")
+    f = w["rhs"][0]
+    res = O.solve(H, f, tol=1e-8, max_cycles=200)
+    Hj = O.build_hierarchy(128, 2, w["k2"], layers=4)
+    with pytest.raises(O.DivergedError):
+        O.solve(Hj, f, tol=1e-8, max_cycles=200)
+    lv = H.levels[0]
+    from scipy.sparse import diags, identity, kron
+    def op1(ax):
+        N = lv.n - 1
+        return diags([-lv.lo[ax][1:], lv.dg[ax], -lv.up[ax][:-1]], [-1, 0, 1], shape=(N, N))
+    N = lv.n - 1
+    A = (kron(identity(N), op1(0)) + kron(op1(1), identity(N))) * lv.alpha \
+        - diags(lv.beta * lv.k2.ravel())
+    from scipy.sparse.linalg import spsolve
+    ref = spsolve(A.tocsc(), f.ravel()).reshape(f.shape)
+    assert np.linalg.norm(res.u - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_cycle_counts_follow_tables_1_and_2():
+    """GMRES(3)-smoothed V(1,1) cycles to 1e-7 for the constant-k model: at
+    128^2 and 256^2 within a factor 2 of the counts the paper prints, more
+    cycles for k = 80 than for k = 40, and the 64^2 grid at k = 80 (kh = 1.25)
+    far slower than 128^2.  Exact agreement is not expected: the paper gives
+    neither the ECS angle nor where its layer lies (our readings: pi/6, inside
+    the unit square)."""
+    table = {}
+    for line in (GOLDEN / "table12_gmres_cycles.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            k, n, c = map(int, line.split())
+            table[(k, n)] = c
+    got = {}
+    for k in (40, 80):
+        for n in (64, 128, 256):
+            H = O.build_hierarchy(n, 2, float(k * k), layers=n // 4, smoother="gmres")
+            f = W.point_sources(n, 2, [(n // 2 - 1, n // 2 - 1)])[0]
+            got[(k, n)] = O.solve(H, f, tol=1e-7, max_cycles=400).cycles
+    for k in (40, 80):
+        for n in (128, 256):
+            assert table[(k, n)] / 2 <= got[(k, n)] <= table[(k, n)] * 2, (k, n, got)
+        for n in (64, 128, 256):
+            assert got[(80, n)] > got[(40, n)]
+    assert got[(80, 64)] >= 2 * got[(80, 128)]
