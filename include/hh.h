@@ -74,6 +74,10 @@ enum { HH_FP64 = 0,       /* complex128 everywhere                        */
 /* hh_solve flags. */
 enum { HH_USE_GUESS = 1 };  /* u holds the initial guess (else u_0 = 0)  */
 
+/* Smoother of every level (Sec. 3.2). */
+enum { HH_SMOOTH_JACOBI = 0,  /* weighted Jacobi, Eq. (wjacobi) (default)    */
+       HH_SMOOTH_GMRES = 1 }; /* GMRES(m) steps, the paper's smoother        */
+
 typedef struct {
   int dim;          /* 2 or 3 */
   int n;            /* intervals per axis on the finest level: a power of
@@ -109,6 +113,10 @@ typedef struct {
                                 a refinement's cycles also stop once their
                                 residual is below tol/2 * ||f|| */
   int max_inner;             /* MIXED: inner cycles per refinement (default 20000) */
+  int smoother;              /* HH_SMOOTH_JACOBI (default) or HH_SMOOTH_GMRES;
+                                GMRES needs max_batch <= 64 and runs the
+                                per-step kernels (no fused 2-D path) */
+  int gmres_m;               /* GMRES(m) Krylov dimension, 1..3 (default 3) */
 } hh_options;
 
 typedef struct {

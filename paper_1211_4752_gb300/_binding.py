@@ -28,6 +28,8 @@ HH_FORM_CSG = 1
 HH_FP64 = 0
 HH_MIXED = 1
 HH_USE_GUESS = 1
+HH_SMOOTH_JACOBI = 0
+HH_SMOOTH_GMRES = 1
 
 
 class HHGrid(ct.Structure):
@@ -46,7 +48,7 @@ class HHOptions(ct.Structure):
                 ("nu1", ct.c_int), ("nu2", ct.c_int), ("precision", ct.c_int),
                 ("coarsest", ct.c_int), ("max_cycles", ct.c_int),
                 ("div_limit", ct.c_double), ("inner_tol", ct.c_double),
-                ("max_inner", ct.c_int)]
+                ("max_inner", ct.c_int), ("smoother", ct.c_int), ("gmres_m", ct.c_int)]
 
 
 class HHSolveInfo(ct.Structure):

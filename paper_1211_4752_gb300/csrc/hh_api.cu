@@ -9,6 +9,7 @@
 #include "../../include/hh.h"
 #include "hh_internal.h"
 #include "hh_cycle.h"
+#include "hh_gmres.h"
 
 #include <cudaTypedefs.h>
 
@@ -59,6 +60,8 @@ template <typename R> struct Work {
   C *u_post[MAXL] = {};
   C *f[MAXL] = {};
   C *tmp[MAXL] = {};
+  C *gq[MAXL] = {};   // GMRES smoothing: Krylov vectors q_0..q_3 of the level
+  C *gw[MAXL] = {};   // and w = A q_j
 };
 
 struct LevelHost {
@@ -124,6 +127,9 @@ struct hh_handle {
   int mid0 = 0, midt = 0, midcl = 0;  // levels mid0 .. midt-1 (cluster of midcl CTAs)
   float2 *tailop_mid[2] = {nullptr, nullptr};  // tail operator from level midt
   MidArgs<float> margs[2];          // per direction
+  double *gm_parts = nullptr;       // GMRES smoothing: partial sums,
+  unsigned int *gm_counter = nullptr;  // last-block arrival counter,
+  double *gm_gsc = nullptr;         // per right-hand side scalars
   DownMaps dmap[MAXL];              // tensor maps of the fused kernels, per level
   UpMaps umap[MAXL];
   std::vector<void *> allocs;
@@ -229,9 +235,74 @@ enum { CHECK_NONE = 0, CHECK_CYCLE = 1, CHECK_INNER = 2 };
 // scaled full-weighting restriction of the residual, LU on the coarsest level,
 // interpolated correction + post-smoothing.  The level-0 iterate is read from
 // and written to W.u_post[0]; W.f[0] holds the right-hand side.
+template <typename R> GmresWork<R> gmres_work(hh_handle *h, int l) {
+  Work<R> &W = work<R>(h);
+  GmresWork<R> g;
+  g.Q = W.gq[l];
+  g.qs = (size_t)h->lv[l].S * h->max_batch;
+  g.w = W.gw[l];
+  g.parts = h->gm_parts;
+  g.counter = h->gm_counter;
+  g.gsc = h->gm_gsc;
+  return g;
+}
+int partial_blocks_of(const hh_handle *h, int l) {
+  return l == 0 ? h->nparts : partial_blocks(h->lv[l].pts);
+}
+
+// The V-cycle with GMRES(m) smoothing (Sec. 3.2): on each level nu1 GMRES
+// steps, residual + restriction, recursion, correction, nu2 GMRES steps.
+// On level 0 the first step's residual is the stop test's.
+template <typename R, int DIM>
+void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
+                         unsigned long long cond, cudaStream_t s) {
+  Work<R> &W = work<R>(h);
+  const SolveState *st = check != CHECK_NONE ? h->st : nullptr;
+  const int L = h->L, m = h->opt.gmres_m;
+  for (int l = 0; l + 1 < L; ++l) {
+    const LevelK<R> K = levelk<R>(h, l, dir);
+    const GmresWork<R> g = gmres_work<R>(h, l);
+    const int nb = partial_blocks_of(h, l);
+    const typename Cx<R>::T *in = l == 0 ? W.u_post[0] : W.u_pre[l];
+    int zm = l == 0 ? zero0 : ZERO_ALL;
+    for (int j = 0; j < h->opt.nu1; ++j) {
+      const bool norm = l == 0 && j == 0 && check != CHECK_NONE;
+      launch_gmres_start<R, DIM>(K, in, zm, W.f[l], g, batch, st, norm ? h->partials : g.parts, nb, s);
+      if (norm) {
+        if (check == CHECK_CYCLE)
+          launch_check_cycle(h->st, h->partials, h->params, h->flag, cond, h->copies, h->err, s);
+        else
+          launch_check_inner(h->st, h->partials, h->params, h->flag, cond, h->copies, h->err, s);
+      }
+      launch_gmres_rest<R, DIM>(K, in, zm, W.u_pre[l], g, m, batch, st, nb, s);
+      in = W.u_pre[l];
+      zm = ZERO_NONE;
+    }
+    launch_resid_restrict<R, DIM>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
+                                  cscal<R>(h, l, dir), batch, st, s);
+  }
+  launch_coarse_solve<R, DIM>(h->lu[dir], h->piv[dir], lay_of(h, L - 1), W.f[L - 1],
+                              W.u_post[L - 1], batch, st, s);
+  for (int l = L - 2; l >= 0; --l) {
+    const LevelK<R> K = levelk<R>(h, l, dir);
+    const GmresWork<R> g = gmres_work<R>(h, l);
+    const int nb = partial_blocks_of(h, l);
+    launch_gmres_correct<R, DIM>(K, W.u_pre[l], W.u_post[l + 1], lay_of(h, l + 1), W.u_post[l],
+                                 batch, st, s);
+    for (int j = 0; j < h->opt.nu2; ++j) {
+      launch_gmres_start<R, DIM>(K, W.u_post[l], ZERO_NONE, W.f[l], g, batch, st, g.parts, nb, s);
+      launch_gmres_rest<R, DIM>(K, W.u_post[l], ZERO_NONE, W.u_post[l], g, m, batch, st, nb, s);
+    }
+  }
+}
+
 template <typename R, int DIM>
 void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
                    unsigned long long cond, cudaStream_t s) {
+  if (h->opt.smoother == HH_SMOOTH_GMRES) {
+    enqueue_cycle_gmres<R, DIM>(h, dir, batch, zero0, check, cond, s);
+    return;
+  }
   Work<R> &W = work<R>(h);
   const SolveState *st = check != CHECK_NONE ? h->st : nullptr;
   const auto om = omega<R>(h, dir);
@@ -1115,7 +1186,30 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   h->kconst = k2_dev ? 0 : 1;
   h->k2c = k2_dev ? 0.0 : k2_const;
   h->fused = 0;
-  if (dim == 2 && h->opt.nu1 == 1 && h->opt.nu2 == 1) {
+  if (h->opt.smoother == HH_SMOOTH_GMRES) {
+    // Krylov vectors per level (cycle precision), partial sums for up to six
+    // quantities per block, the arrival counter and the per-RHS scalars
+    for (int l = 0; l + 1 < L; ++l) {
+      const size_t np = (size_t)h->lv[l].S * B;
+      if (h->opt.precision == HH_FP64) {
+        HH_TRY(dev_alloc_n(h, &h->w64.gq[l], 4 * np));
+        HH_TRY(dev_alloc_n(h, &h->w64.gw[l], np));
+        HH_CK(cudaMemsetAsync(h->w64.gq[l], 0, 4 * np * sizeof(double2), s));
+        HH_CK(cudaMemsetAsync(h->w64.gw[l], 0, np * sizeof(double2), s));
+      } else {
+        HH_TRY(dev_alloc_n(h, &h->w32.gq[l], 4 * np));
+        HH_TRY(dev_alloc_n(h, &h->w32.gw[l], np));
+        HH_CK(cudaMemsetAsync(h->w32.gq[l], 0, 4 * np * sizeof(float2), s));
+        HH_CK(cudaMemsetAsync(h->w32.gw[l], 0, np * sizeof(float2), s));
+      }
+    }
+    HH_TRY(dev_alloc_n(h, &h->gm_parts, (size_t)2 * 152 * 6 * B));
+    HH_TRY(dev_alloc_n(h, &h->gm_counter, 1));
+    HH_CK(cudaMemsetAsync(h->gm_counter, 0, sizeof(unsigned int), s));
+    HH_TRY(dev_alloc_n(h, &h->gm_gsc, (size_t)kGmresScalars * B));
+    HH_CK(cudaMemsetAsync(h->gm_gsc, 0, (size_t)kGmresScalars * B * sizeof(double), s));
+  }
+  if (dim == 2 && h->opt.nu1 == 1 && h->opt.nu2 == 1 && h->opt.smoother == HH_SMOOTH_JACOBI) {
     // first level whose tail (it and every coarser level) fits in shared memory
     int t0 = 1;
     auto tail_bytes = [&](int t) {
@@ -1228,6 +1322,8 @@ void hh_default_options(hh_options *o) {
   o->div_limit = 1e3;
   o->inner_tol = 1e-3;
   o->max_inner = 20000;
+  o->smoother = HH_SMOOTH_JACOBI;
+  o->gmres_m = 3;
 }
 
 const char *hh_last_error(void) { return g_err.c_str(); }
@@ -1261,6 +1357,11 @@ hh_status hh_setup(const hh_grid *grid, const double *k2_dev, double k2_const,
   if (o.max_cycles < 1 || o.max_inner < 1) return fail(HH_ERR_ARG, "max_cycles and max_inner must be >= 1");
   if (!(o.div_limit > 0) || !(o.inner_tol > 0 && o.inner_tol < 1)) return fail(HH_ERR_ARG, "bad div_limit or inner_tol");
   if (!std::isfinite(o.omega_re) || !std::isfinite(o.omega_im)) return fail(HH_ERR_ARG, "bad omega");
+  if (o.smoother != HH_SMOOTH_JACOBI && o.smoother != HH_SMOOTH_GMRES) return fail(HH_ERR_ARG, "bad smoother");
+  if (o.smoother == HH_SMOOTH_GMRES && (o.gmres_m < 1 || o.gmres_m > 3))
+    return fail(HH_ERR_ARG, "gmres_m must be in 1..3");
+  if (o.smoother == HH_SMOOTH_GMRES && max_batch > kGmresMaxBatch)
+    return fail(HH_ERR_ARG, "GMRES smoothing supports at most 64 right-hand sides per handle");
   if (!std::isfinite(k2_const)) return fail(HH_ERR_ARG, "k2_const must be finite");
 
   hh_handle *h = new hh_handle();
@@ -1295,6 +1396,8 @@ int hh_cycle_kernels(const hh_handle *h) {
   if (!h) return 0;
   if (h->fused)   // down passes, stop test, tail (or cluster kernel), up passes
     return 2 * (h->mid && h->opt.precision == HH_MIXED ? h->mid0 : h->tail0) + 2;
+  if (h->opt.smoother == HH_SMOOTH_GMRES)   // per level: steps of 2m + 2 kernels,
+    return (h->L - 1) * ((h->opt.nu1 + h->opt.nu2) * (2 * h->opt.gmres_m + 2) + 2) + 2;
   // per level nu1 sweeps, residual + restriction, nu2 sweeps; stop test; LU
   return (h->L - 1) * (h->opt.nu1 + 1 + h->opt.nu2) + 2;
 }

@@ -1,0 +1,43 @@
+// GMRES(m) smoothing kernels (hh_gmres.cu): workspace and launchers.
+#pragma once
+#include "hh_internal.h"
+
+namespace hh {
+
+constexpr int kGmresMaxBatch = 64;   // right-hand sides per handle with GMRES smoothing
+constexpr int kGmresScalars = 32;    // FP64 scalars per right-hand side
+
+// Workspace of one level: Krylov vectors q_0..q_3 (at stride qs = S * batch
+// capacity), w = A q_j, per-block partial sums (up to 6 per right-hand side),
+// the last-block arrival counter (starts at 0; the last block resets it) and
+// the per-right-hand-side FP64 scalars.
+template <typename R> struct GmresWork {
+  typename Cx<R>::T *Q;
+  size_t qs;
+  typename Cx<R>::T *w;
+  double *parts;
+  unsigned int *counter;
+  double *gsc;
+};
+
+// q_0 = f - A u and |q_0|^2; parts (layout [b][block], nblk blocks) may be the
+// stop test's partial sums on level 0.
+template <typename R, int DIM>
+void launch_gmres_start(const LevelK<R> &L, const typename Cx<R>::T *u, int zero_mode,
+                        const typename Cx<R>::T *f, const GmresWork<R> &g, int batch,
+                        const SolveState *st, double *parts, int nblk, cudaStream_t s);
+
+// The m Arnoldi steps, the least-squares solve and u_out = u_in + V y (u_in
+// read as zero where the start kernel took it as zero).
+template <typename R, int DIM>
+void launch_gmres_rest(const LevelK<R> &L, const typename Cx<R>::T *u_in, int zero_mode,
+                       typename Cx<R>::T *u_out, const GmresWork<R> &g, int m, int batch,
+                       const SolveState *st, int nblk, cudaStream_t s);
+
+// u_out = u_in + P e (coarse-grid correction without smoothing).
+template <typename R, int DIM>
+void launch_gmres_correct(const LevelK<R> &L, const typename Cx<R>::T *u_in,
+                          const typename Cx<R>::T *e, const Lay &lc, typename Cx<R>::T *u_out,
+                          int batch, const SolveState *st, cudaStream_t s);
+
+}  // namespace hh

@@ -37,7 +37,8 @@ class HelmholtzMG:
                  form="csl", theta_max=math.pi / 6, p=0, thetas=None, c=None,
                  omega=0.8, nu1=1, nu2=1, precision="fp64", coarsest=4,
                  max_cycles=20000, div_limit=1e3, inner_tol=1e-3,
-                 max_inner=20000, max_batch=1, device=None):
+                 max_inner=20000, max_batch=1, device=None, smoother="jacobi",
+                 gmres_m=3):
         L = B.lib()
         self.n, self.dim, self.N = int(n), int(dim), int(n) - 1
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -75,6 +76,10 @@ class HelmholtzMG:
         o.div_limit = float(div_limit)
         o.inner_tol = float(inner_tol)
         o.max_inner = int(max_inner)
+        if smoother not in ("jacobi", "gmres"):
+            raise ValueError("smoother must be 'jacobi' or 'gmres'")
+        o.smoother = B.HH_SMOOTH_GMRES if smoother == "gmres" else B.HH_SMOOTH_JACOBI
+        o.gmres_m = int(gmres_m)
         self.k2_const = 0.0
         k2_ptr = ct.c_void_p(0)
         if isinstance(k2, torch.Tensor):

@@ -7,6 +7,7 @@ the CUDA path.  Usage:
     python tests/golden/make_oracle_samples.py ecs_const  [out.json]
     python tests/golden/make_oracle_samples.py layered    [out.json]
     python tests/golden/make_oracle_samples.py --divergence layered
+    python tests/golden/make_oracle_samples.py --gmres bump
 """
 
 import json
@@ -50,10 +51,15 @@ def main():
         w = getattr(workloads, sys.argv[2])()
         divergence(w, Path(__file__).with_name(w["name"] + "_divergence.json"))
         return
+    smoother = "jacobi"
+    if which == "--gmres":      # GMRES(3) smoothing (Sec. 3.2)
+        smoother = "gmres"
+        which = sys.argv[2]
     w = getattr(workloads, which)()
-    out = Path(sys.argv[2]) if len(sys.argv) > 2 else Path(__file__).with_name(w["name"] + ".json")
+    suffix = "_gmres" if smoother == "gmres" else ""
+    out = Path(__file__).with_name(w["name"] + suffix + ".json")
     t0 = time.time()
-    H = oracle.build_hierarchy(w["n"], w["dim"], w["k2"], layers=w["layers"])
+    H = oracle.build_hierarchy(w["n"], w["dim"], w["k2"], layers=w["layers"], smoother=smoother)
     f = w["rhs"][0]
     res = oracle.solve(H, f, tol=1e-6, max_cycles=20000)
     u = res.u
@@ -69,8 +75,10 @@ def main():
                 history_every50=res.history[::50], u_norm=float(np.linalg.norm(u)),
                 u_maxabs=float(np.abs(u).max()), sample_index=idx,
                 sample_value=vals, seconds=time.time() - t0,
-                note="FP64 oracle, V(1,1) weighted Jacobi 0.8, CSL shifts "
-                     "theta_l = l (pi/6)/log2(n), coarsest 3x3 interior, u0 = 0")
+                smoother=smoother,
+                note="FP64 oracle, V(1,1) cycles (" + ("GMRES(3)" if smoother == "gmres" else
+                     "weighted Jacobi 0.8") + "), CSL shifts theta_l = l (pi/6)/log2(n), "
+                     "coarsest 3^dim interior, u0 = 0")
     out.write_text(json.dumps(data))
     print(out, res.cycles, res.history[-1], data["seconds"])
 

@@ -1,0 +1,133 @@
+"""GMRES(m) smoothing (Sec. 3.2) on the GPU against the oracle's GMRES cycle.
+
+The GPU builds the Krylov basis with classical Gram-Schmidt on unnormalised
+vectors and solves the small least-squares problem by Givens rotations; the
+oracle uses modified Gram-Schmidt and a library least-squares solve.  Both
+compute the same minimiser, so iterates agree to rounding."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1211_4752_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relerr(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(np.ravel(b))
+
+
+CASES = [
+    dict(n=64, dim=2, k2=("field", 30.0, 36.0), layers=4, form="csl", m=3),
+    dict(n=128, dim=2, k2=("const", 6400.0), layers=(8, 12), form="csg", m=3),
+    dict(n=64, dim=2, k2=("const", 1600.0), layers=8, form="csl", m=2),
+    dict(n=16, dim=3, k2=("field", 5.0, 9.0), layers=2, form="csl", m=3),
+    dict(n=32, dim=3, k2=("const", 300.0), layers=(2, 3), form="csg", m=1),
+]
+
+
+def _pair(case, precision="fp64", batch=2):
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n, dim = case["n"], case["dim"]
+    spec = case["k2"]
+    k2 = spec[1] if spec[0] == "const" else W.smooth_k2(n, dim, 4, spec[1], spec[2])
+    P = int(round(math.log2(n)))
+    c = [np.exp(-1j * (math.pi / 6) / P)] * (P - 2) if case["form"] == "csg" else None
+    H = O.build_hierarchy(n, dim, k2, layers=case["layers"], form=case["form"], c=c,
+                          smoother="gmres", m=case["m"])
+    k2_t = dev(k2) if isinstance(k2, np.ndarray) else float(k2)
+    mg = HelmholtzMG(n, dim=dim, k2=k2_t, layers=case["layers"], form=case["form"], c=c,
+                     precision=precision, max_batch=batch, smoother="gmres", gmres_m=case["m"])
+    return H, mg
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c['dim']}d-n{c['n']}-m{c['m']}")
+def test_gmres_cycles_match_oracle(case):
+    H, mg = _pair(case)
+    f = W.random_field((2,) + H.levels[0].shape, 31)
+    got = host(mg.cycles(dev(f), dev(np.zeros_like(f)), 2))
+    for b in range(2):
+        u = np.zeros_like(f[b])
+        for _ in range(2):
+            u = O.vcycle(H, 0, u, f[b])
+        assert relerr(got[b], u) < 1e-9, b
+    mg.close()
+    # complex64 cycles on the same hierarchy
+    H, mg = _pair(case, precision="mixed")
+    got = host(mg.cycles(dev(f), dev(np.zeros_like(f)), 2))
+    u = np.zeros_like(f[0])
+    for _ in range(2):
+        u = O.vcycle(H, 0, u, f[0])
+    assert relerr(got[0], u) < 1e-4
+    mg.close()
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_gmres_solve_matches_oracle_constant_k(n):
+    """The constant-k model of Table 1 (k = 40, centre source, ECS n/4):
+    FP64 cycle for cycle against the oracle, mixed to the same residual."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    H = O.build_hierarchy(n, 2, 1600.0, layers=n // 4, smoother="gmres")
+    f = W.point_sources(n, 2, [(n // 2 - 1, n // 2 - 1)])
+    ref = O.solve(H, f[0], tol=1e-7, max_cycles=400)
+    mg = HelmholtzMG(n, k2=1600.0, layers=n // 4, smoother="gmres")
+    u, info = mg.solve(dev(f), tol=1e-7)
+    assert info[0]["status"] == "OK"
+    assert abs(info[0]["cycles"] - ref.cycles) <= 1
+    assert relerr(host(u)[0], ref.u) < 1e-8
+    mg.close()
+    mg = HelmholtzMG(n, k2=1600.0, layers=n // 4, smoother="gmres", precision="mixed")
+    u, info = mg.solve(dev(f), tol=1e-7)
+    assert info[0]["status"] == "OK"
+    rho = np.linalg.norm(f[0] - O.apply_operator(H.levels[0], host(u)[0])) / np.linalg.norm(f[0])
+    assert rho <= 1e-7
+    assert relerr(host(u)[0], ref.u) < 1e-5
+    mg.close()
+
+
+def test_gmres_adjoint_and_gradient():
+    """Adjoint solve with GMRES-smoothed cycles on the conjugate-transposed
+    hierarchy, and the gradient, against the oracle, on a medium where the
+    Jacobi cycle diverges (kh = 0.5)."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    w = W.bump(n=64, layers=4, nsrc=2)
+    k2 = w["k2"]
+    H = O.build_hierarchy(64, 2, k2, layers=4, smoother="gmres")
+    Ha = O.adjoint_hierarchy(H)
+    mg = HelmholtzMG(64, k2=dev(k2), layers=4, max_batch=2, smoother="gmres")
+    f = w["rhs"]
+    g = W.random_field(f.shape, 41)
+    u, iu = mg.solve(dev(f), tol=1e-10)
+    lam, il = mg.adjoint(dev(g), tol=1e-10)
+    assert all(i["status"] == "OK" for i in iu + il)
+    u_ref = np.stack([O.solve(H, f[b], tol=1e-10).u for b in range(2)])
+    lam_ref = np.stack([O.solve(Ha, g[b], tol=1e-10).u for b in range(2)])
+    assert relerr(host(u), u_ref) < 1e-8
+    assert relerr(host(lam), lam_ref) < 1e-8
+    grad = host(mg.grad_k2(u, lam))
+    gref = O.grad_k2(u_ref, lam_ref)
+    assert np.abs(grad - gref).max() <= 1e-7 * np.abs(gref).max()
+    mg.close()
+
+
+def test_gmres_options_are_checked():
+    from paper_1211_4752_gb300 import HelmholtzMG
+    from paper_1211_4752_gb300._binding import HHError
+    with pytest.raises(HHError):
+        HelmholtzMG(64, k2=100.0, smoother="gmres", gmres_m=4)
+    with pytest.raises(HHError):
+        HelmholtzMG(64, k2=100.0, smoother="gmres", max_batch=65)
