@@ -179,3 +179,49 @@ def test_gmres_solves_match_oracle_full_size(name):
             assert rho <= 1e-6
             assert relerr(uh[idx], ref) < 1e-5
         mg.close()
+
+
+def test_bump_gradient_full_size_against_central_differences():
+    """The differentiable workload at full size: 511^2, kh = 0.5 background
+    with a 10 % Gaussian bump in k^2, 16 sources on the first physical row,
+    loss = 1/2 ||u on the last physical row - d||^2.  With GMRES(3) smoothing
+    (the Jacobi cycle diverges on this medium), d loss / d k^2 from the adjoint
+    solve (torch.autograd) against central differences of the loss at
+    seeded points of the physical region, and d loss / d f along a direction."""
+    from paper_1211_4752_gb300 import helmholtz_solve
+    w = W.bump()
+    n, layers = w["n"], w["layers"]
+    k2 = torch.from_numpy(w["k2"]).cuda().requires_grad_(True)
+    f = torch.from_numpy(w["rhs"]).cuda().requires_grad_(True)
+    rows = torch.from_numpy(w["receiver_rows"]).cuda()
+    cols = torch.from_numpy(w["receiver_cols"]).cuda()
+    d = torch.from_numpy(w["data"]).cuda()
+    kw = dict(n=n, layers=layers, smoother="gmres", precision="mixed")
+
+    def loss_of(k2v, fv):
+        u = helmholtz_solve(k2v, fv, tol=1e-10, **kw)
+        return 0.5 * (u[:, rows, cols] - d).abs().pow(2).sum()
+
+    L0 = loss_of(k2, f)
+    L0.backward()
+    gk = k2.grad.detach().cpu().numpy()
+    gf = f.grad.detach().cpu().numpy()
+    k2n = k2.detach().cpu().numpy()
+    rng = np.random.default_rng(7)
+    pts = [tuple(rng.integers(layers + 8, n - 1 - layers - 8, size=2)) for _ in range(6)]
+    with torch.no_grad():
+        for (i, j) in pts:
+            # a point perturbation moves the loss by ~1e-10 of itself: a step
+            # of 1e-3 k^2 keeps that above the solves' rounding, while the
+            # central difference's own error stays O(step^2)
+            dk = 1e-3 * k2n[i, j]
+            kp = k2.detach().clone(); kp[i, j] += dk
+            km = k2.detach().clone(); km[i, j] -= dk
+            fd = (loss_of(kp, f.detach()) - loss_of(km, f.detach())).item() / (2 * dk)
+            assert abs(fd - gk[i, j]) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(gk).max()), (i, j, fd, gk[i, j])
+        v = torch.from_numpy(W.random_field(tuple(f.shape), 8)).cuda()
+        eps = 1e-3
+        fd = (loss_of(k2.detach(), f.detach() + eps * v)
+              - loss_of(k2.detach(), f.detach() - eps * v)).item() / (2 * eps)
+        pred = np.real(np.vdot(gf, v.cpu().numpy()))
+        assert abs(fd - pred) <= 1e-4 * abs(fd)
