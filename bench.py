@@ -230,21 +230,28 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     kconst = not isinstance(k2, np.ndarray)
     kt = {}
-    for kid in (0, 2, 4) + ((3,) if mixed else ()):
+    fused = mg.tile_shape(0) is not None
+    for kid in ((0, 2, 4) if fused else ()) + ((3,) if mixed else ()):
         ms = ct.c_double()
         B.check(B.lib().hh_time_kernel(mg._h, kid, 0, 1, 50, ct.byref(ms),
                                        ct.c_void_p(stream.cuda_stream)))
         kt[kid] = ms.value
-    dom = max((0, 2), key=lambda k: kt[k])
-    name = KERNELS[dom]
-    bpp = kernel_bytes(dom, kconst, mixed)
-    achieved = bpp * pts / (kt[dom] * 1e-3) / 1e9
-    traffic = None
-    tf = ROOT / "profiles" / "traffic.json"
-    if tf.exists():
-        d = json.loads(tf.read_text())
-        key = f"{w['name']}:{args.precision}:{name}"
-        traffic = d.get(key)
+    roofline = None
+    if fused:
+        dom = max((0, 2), key=lambda k: kt[k])
+        name = KERNELS[dom]
+        bpp = kernel_bytes(dom, kconst, mixed)
+        achieved = bpp * pts / (kt[dom] * 1e-3) / 1e9
+        traffic = None
+        tf = ROOT / "profiles" / "traffic.json"
+        if tf.exists():
+            d = json.loads(tf.read_text())
+            traffic = d.get(f"{w['name']}:{args.precision}:{name}")
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "bytes_per_point": bpp,
+                    "tile_level0": mg.tile_shape(0),
+                    "launch_ms": {KERNELS[k]: v for k, v in kt.items()}}
 
     fp64 = None
     if mixed and args.compare_fp64:
@@ -285,11 +292,7 @@ def run_ours(args):
                       "rel_residual": last["rel_residual"], "all_ok": ok},
             "e2e": {"value": pts * args.steps * world / e2e_total / 1e6, "unit": "MDOF/s",
                     "h2d_bytes_per_step": pts * 16, "d2h_bytes_per_step": pts * 16},
-            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "bytes_per_point": bpp,
-                         "tile_level0": mg.tile_shape(0),
-                         "launch_ms": {KERNELS[k]: v for k, v in kt.items()}},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "fp64_gpu": fp64,
             "gpu_launches": launches,
