@@ -131,3 +131,18 @@ def test_gmres_options_are_checked():
         HelmholtzMG(64, k2=100.0, smoother="gmres", gmres_m=4)
     with pytest.raises(HHError):
         HelmholtzMG(64, k2=100.0, smoother="gmres", max_batch=65)
+
+
+def test_theta_sweep_matches_oracle():
+    """Table 5's experiment (k = 30, n = 128, GMRES(3), theta_max from pi/15
+    to pi/4): the GPU's cycle counts equal the oracle's at every rotation."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n = 128
+    f = W.point_sources(n, 2, [(n // 2 - 1, n // 2 - 1)])
+    for d in (15, 12, 10, 8, 6, 5, 4):
+        H = O.build_hierarchy(n, 2, 900.0, layers=n // 4, smoother="gmres", theta_max=math.pi / d)
+        ref = O.solve(H, f[0], tol=1e-7, max_cycles=400).cycles
+        mg = HelmholtzMG(n, k2=900.0, layers=n // 4, smoother="gmres", theta_max=math.pi / d)
+        _, info = mg.solve(dev(f), tol=1e-7)
+        assert info[0]["status"] == "OK" and abs(info[0]["cycles"] - ref) <= 1, (d, info, ref)
+        mg.close()

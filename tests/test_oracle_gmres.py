@@ -97,3 +97,36 @@ def test_cycle_counts_follow_tables_1_and_2():
         for n in (64, 128, 256):
             assert got[(80, n)] > got[(40, n)]
     assert got[(80, 64)] >= 2 * got[(80, 128)]
+
+
+def _table5():
+    rows = []
+    for line in (GOLDEN / "table5_theta_sweep.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            d, c = map(int, line.split())
+            rows.append((d, c))
+    return rows
+
+
+def theta_sweep_cycles(d_values, n=128, k=30.0):
+    f = W.point_sources(n, 2, [(n // 2 - 1, n // 2 - 1)])[0]
+    out = []
+    for d in d_values:
+        H = O.build_hierarchy(n, 2, k * k, layers=n // 4, smoother="gmres",
+                              theta_max=math.pi / d)
+        out.append(O.solve(H, f, tol=1e-7, max_cycles=400).cycles)
+    return out
+
+
+def test_theta_sweep_follows_table_5():
+    """Cycles as a function of theta_max (Table 5, k = 30, n = 128): within a
+    factor 2 of the printed counts, falling from the smallest rotation to a
+    minimum at pi/8 .. pi/5 and rising again at pi/4 (too small a shift leaves
+    coarse spectra near zero; too large a one corrupts the smooth modes)."""
+    table = _table5()
+    got = theta_sweep_cycles([d for d, _ in table])
+    for (d, c), g in zip(table, got):
+        assert c / 2 <= g <= c * 2, (d, g, c)
+    i_min = int(np.argmin(got))
+    assert [d for d, _ in table][i_min] in (8, 6, 5)
+    assert got[0] > got[i_min] and got[-1] > got[i_min]
