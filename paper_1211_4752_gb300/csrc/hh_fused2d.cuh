@@ -386,10 +386,12 @@ k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
   }
   {
     __syncthreads();   // barrier initialised (and tables written) before any wait
-    const bool ok = mbar_wait_bounded(mbar, 0);
+    // one warp waits for the copies; the others sleep at the block barrier
+    // (that also carries the copies' visibility to them) instead of spinning
+    const bool ok = threadIdx.x >= 32 || mbar_wait_bounded(mbar, 0);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicExch(err, (int)HH_ERR_TIMEOUT);
-      mbar_wait_bounded(mbar, 0);   // let copies still in flight land
+      if (threadIdx.x < 32) mbar_wait_bounded(mbar, 0);   // let copies still in flight land
       act = false;
     } else if (act) {
       C *vb = v_out + (size_t)b * L.S;
@@ -569,10 +571,10 @@ k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__re
     issue();
   }
   __syncthreads();
-  const bool ok = mbar_wait_bounded(mbar, 0);
+  const bool ok = threadIdx.x >= 32 || mbar_wait_bounded(mbar, 0);   // one warp waits
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) atomicExch(err, (int)HH_ERR_TIMEOUT);
-    mbar_wait_bounded(mbar, 0);
+    if (threadIdx.x < 32) mbar_wait_bounded(mbar, 0);
     return;
   }
   if (!act) return;
