@@ -46,7 +46,7 @@ __all__ = [
     "restrict_fw", "prolong",
     "dense_matrix", "lu_factor", "lu_solve", "build_hierarchy",
     "adjoint_hierarchy", "vcycle", "solve", "residual_norm",
-    "symmetrizer_weights", "adjoint_solve_symmetrized", "grad_k2",
+    "symmetrizer_weights", "adjoint_solve_symmetrized", "grad_k2", "fgmres",
     "SolveResult", "DivergedError", "NotConvergedError",
 ]
 
@@ -474,6 +474,62 @@ def solve(hier: Hierarchy, f, tol=1e-6, max_cycles=20000, u0=None,
 # --------------------------------------------------------------------------
 # Adjoint and gradient
 # --------------------------------------------------------------------------
+
+def fgmres(hier: Hierarchy, f, tol=1e-6, m=10, max_iter=2000, u0=None, precond=None,
+           strict=True):
+    """Right-preconditioned flexible GMRES(m) (Saad 1993) for A_0 u = f, the
+    preconditioner being one level-dependent V-cycle from a zero initial
+    guess on the residual equation (the use of the cycle in Table 3 of the
+    paper; flexible because a GMRES-smoothed cycle is not a fixed linear
+    map).  Modified Gram-Schmidt Arnoldi; stops when the least-squares
+    residual estimate falls to tol * ||f||.  Returns a SolveResult whose
+    `cycles` counts the preconditioner applications (= iterations).
+    `precond(v)` replaces the V-cycle (for the pins); with strict=False the
+    iterate reached after max_iter iterations is returned instead of raising."""
+    if precond is None:
+        precond = lambda v: vcycle(hier, 0, np.zeros_like(v), v)
+    lv = hier.levels[0]
+    nf = np.linalg.norm(f)
+    u = np.zeros_like(f) if u0 is None else u0.copy()
+    hist = []
+    it = 0
+    while True:
+        r = f - apply_operator(lv, u)
+        beta = np.linalg.norm(r)
+        hist.append(beta / nf)
+        if beta <= tol * nf:
+            return SolveResult(u, it, hist)
+        if it >= max_iter:
+            if not strict:
+                return SolveResult(u, it, hist)
+            raise NotConvergedError(f"no convergence in {it} iterations")
+        V = [r / beta]
+        Z = []
+        H = np.zeros((m + 1, m), dtype=np.complex128)
+        e1 = np.zeros(m + 1, dtype=np.complex128)
+        e1[0] = beta
+        k = 0
+        for j in range(m):
+            Z.append(precond(V[j]))
+            w = apply_operator(lv, Z[j])
+            for i in range(j + 1):
+                H[i, j] = np.vdot(V[i], w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            it += 1
+            k = j + 1
+            y, *_ = np.linalg.lstsq(H[:k + 1, :k], e1[:k + 1], rcond=None)
+            est = np.linalg.norm(e1[:k + 1] - H[:k + 1, :k] @ y)
+            if H[j + 1, j] == 0.0 or est <= tol * nf or it >= max_iter:
+                break
+            V.append(w / H[j + 1, j])
+        y, *_ = np.linalg.lstsq(H[:k + 1, :k], e1[:k + 1], rcond=None)
+        u = u + sum(y[i] * Z[i] for i in range(k))
+        if est <= tol * nf:
+            r = f - apply_operator(lv, u)
+            hist.append(np.linalg.norm(r) / nf)
+            return SolveResult(u, it, hist)
+
 
 def symmetrizer_weights(hier: Hierarchy):
     """W = prod over axes of (h_{i-1} + h_i)/2 on the finest level.  W A_0 is
