@@ -156,6 +156,33 @@ hh_status hh_setup(const hh_grid *grid, const double *k2_dev, double k2_const,
 hh_status hh_solve(hh_handle *h, const void *rhs_dev, void *u_dev, int batch,
                    double tol, int flags, hh_solve_info *info, void *stream);
 
+/* Flexible GMRES(restart) for A_0 u_b = f_b, right-preconditioned by one
+ * level-dependent V-cycle per iteration from a zero initial guess: the use
+ * of the cycle as a preconditioner in Sec. 4.1 (Table 3, LVL-MG-FGMRES;
+ * flexible GMRES because a cycle with GMRES smoothing is not a fixed linear
+ * map).  The cycle is the handle's (precision, smoother, shift schedule);
+ * the Krylov vectors, inner products and the least-squares problem are
+ * complex128 / FP64 in either precision.
+ *   rhs_dev   device, complex128[batch][N^dim], read only.
+ *   u_dev     device, complex128[batch][N^dim]: initial guess if
+ *             flags & HH_USE_GUESS (else ignored), solution on return.
+ *   tol       a right-hand side stops when its least-squares residual
+ *             estimate, or its true residual at a restart, is <= tol ||f_b||.
+ *   restart   m in 1..32: Arnoldi columns per restart cycle.
+ *   max_iter  iterations (= V-cycles) per right-hand side; 0 takes the
+ *             options' max_cycles.
+ *   info      host, batch entries, or NULL: cycles = iterations,
+ *             refinements = restarts, rel_residual = ||f - A_0 u|| / ||f|| of
+ *             the returned u (evaluated at the final restart check), status.
+ * Workspace: 2 restart + 5 level-0 vectors per right-hand side, allocated by
+ * the first call (and again when restart or batch grows), freed by
+ * hh_destroy.  Returns as hh_solve (HH_ERR_OOM if the workspace does not
+ * fit); the residual of a minimal-residual method does not grow, so
+ * HH_ERR_DIVERGED here means a non-finite value (div_limit is not used).
+ * Synchronises `stream` once per restart cycle. */
+hh_status hh_fgmres(hh_handle *h, const void *rhs_dev, void *u_dev, int batch, double tol,
+                    int restart, int max_iter, int flags, hh_solve_info *info, void *stream);
+
 /* hh_solve on HOST arrays: copies rhs in, solves, copies u out (the copies
  * are part of the call).  Same layout and semantics as hh_solve. */
 hh_status hh_solve_host(hh_handle *h, const void *rhs_host, void *u_host,

@@ -68,6 +68,7 @@ SIGNATURES = {
     "hh_solve": (_I, [_P, _P, _P, _I, _D, _I, ct.POINTER(HHSolveInfo), _P]),
     "hh_solve_host": (_I, [_P, _P, _P, _I, _D, _I, ct.POINTER(HHSolveInfo), _P]),
     "hh_adjoint": (_I, [_P, _P, _P, _I, _D, _I, ct.POINTER(HHSolveInfo), _P]),
+    "hh_fgmres": (_I, [_P, _P, _P, _I, _D, _I, _I, _I, ct.POINTER(HHSolveInfo), _P]),
     "hh_grad_k2": (_I, [_P, _P, _P, _I, _P, _P]),
     "hh_apply": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "hh_cycles": (_I, [_P, _P, _P, _I, _I, _P]),

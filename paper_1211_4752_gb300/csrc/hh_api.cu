@@ -10,6 +10,7 @@
 #include "hh_internal.h"
 #include "hh_cycle.h"
 #include "hh_gmres.h"
+#include "hh_krylov.h"
 
 #include <cudaTypedefs.h>
 
@@ -130,6 +131,10 @@ struct hh_handle {
   double *gm_parts = nullptr;       // GMRES smoothing: partial sums,
   unsigned int *gm_counter = nullptr;  // last-block arrival counter,
   double *gm_gsc = nullptr;         // per right-hand side scalars
+  KrylovWork kw;                    // flexible GMRES: workspace (first use),
+  int kw_m = 0, kw_b = 0, kw_sms = 0;  // its restart length, batch capacity, SMs,
+  std::vector<void *> kw_mem;       // its allocations and iteration graphs
+  std::map<std::tuple<int, int, int>, GraphEntry> kw_graphs;  // (precision, m, batch)
   DownMaps dmap[MAXL];              // tensor maps of the fused kernels, per level
   UpMaps umap[MAXL];
   std::vector<void *> allocs;
@@ -229,7 +234,11 @@ template <typename R> typename Cx<R>::T omega(const hh_handle *h, int dir) {
   return w;
 }
 
-enum { CHECK_NONE = 0, CHECK_CYCLE = 1, CHECK_INNER = 2 };
+// Stop test of a cycle: none (every right-hand side runs), the plain loop's,
+// the refinement's inner loop's, or none with the right-hand sides masked by
+// SolveState::active (the cycle as a preconditioner).
+enum { CHECK_NONE = 0, CHECK_CYCLE = 1, CHECK_INNER = 2, CHECK_MASK = 3 };
+inline bool stop_test(int check) { return check == CHECK_CYCLE || check == CHECK_INNER; }
 
 // One level-dependent V(nu1,nu2)-cycle (Sec. 3.1): per level pre-smoothing,
 // scaled full-weighting restriction of the residual, LU on the coarsest level,
@@ -266,7 +275,7 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
     const typename Cx<R>::T *in = l == 0 ? W.u_post[0] : W.u_pre[l];
     int zm = l == 0 ? zero0 : ZERO_ALL;
     for (int j = 0; j < h->opt.nu1; ++j) {
-      const bool norm = l == 0 && j == 0 && check != CHECK_NONE;
+      const bool norm = l == 0 && j == 0 && stop_test(check);
       launch_gmres_start<R, DIM>(K, in, zm, W.f[l], g, batch, st, norm ? h->partials : g.parts, nb, s);
       if (norm) {
         if (check == CHECK_CYCLE)
@@ -313,7 +322,7 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
     for (int j = 0; j < h->opt.nu1; ++j) {
       typename Cx<R>::T *out = ((h->opt.nu1 - 1 - j) % 2 == 0) ? W.u_pre[l] : W.tmp[l];
       const int zm = j == 0 ? (l == 0 ? zero0 : ZERO_ALL) : ZERO_NONE;
-      const bool norm = (l == 0 && j == 0 && check != CHECK_NONE);
+      const bool norm = l == 0 && j == 0 && stop_test(check);
       launch_smooth<R, DIM>(K, in, zm, W.f[l], out, om, batch, st,
                             norm ? h->partials : nullptr, h->nparts, s);
       if (norm) {
@@ -498,7 +507,7 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
   const int T = mid ? h->mid0 : h->tail0;
   for (int l = 0; l < T; ++l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
-    const bool norm = l == 0 && check != CHECK_NONE;
+    const bool norm = l == 0 && stop_test(check);
     launch_down2d<R>(h->variant[l], h->dmap[l], K, l == 0 ? zero0 : ZERO_ALL, W.u_pre[l],
                      W.f[l + 1], cscal<R>(h, l, dir), om, h->kconst, lay_of(h, l + 1), batch, st,
                      norm ? h->partials : nullptr, h->err, s);
@@ -514,7 +523,7 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
     const LevelK<R> K = levelk<R>(h, l, dir);
     // the level-0 up pass is the one kernel of the cycle that writes the
     // level-0 iterate: it waits for the stop test
-    if (l == 0 && check != CHECK_NONE) cudaStreamWaitEvent(s, h->ev_join, 0);
+    if (l == 0 && stop_test(check)) cudaStreamWaitEvent(s, h->ev_join, 0);
     launch_up2d<R>(h->variant[l], h->umap[l], K, W.u_post[l], om, h->kconst, batch, st,
                    h->err, s);
   }
@@ -827,7 +836,20 @@ hh_status ensure_device(const hh_handle *h) {
   return HH_OK;
 }
 
+void free_krylov(hh_handle *h) {
+  for (auto &kv : h->kw_graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  h->kw_graphs.clear();
+  for (void *p : h->kw_mem) cudaFree(p);
+  h->kw_mem.clear();
+  h->kw = KrylovWork();
+  h->kw_m = h->kw_b = h->kw_sms = 0;
+}
+
 void destroy_impl(hh_handle *h) {
+  free_krylov(h);
   for (auto &kv : h->graphs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
@@ -1287,6 +1309,204 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   return HH_OK;
 }
 
+// ---- flexible GMRES(m) with the cycle as preconditioner (Sec. 4.1, Table 3)
+
+// Workspace for restart length m and `batch` right-hand sides: m + 1 basis
+// vectors, m preconditioned vectors and w in the cycle's precision; A u, F
+// and U in complex128 (all zeroed, so the padding column stays zero);
+// partial sums, counters, scalars, the column index.  Kept for later calls;
+// a larger request reallocates it and drops the iteration graphs, which hold
+// its pointers.
+hh_status ensure_krylov(hh_handle *h, int m, int batch, cudaStream_t s) {
+  if (m <= h->kw_m && batch <= h->kw_b) return HH_OK;
+  const int M = std::max(m, h->kw_m), B = std::max(batch, h->kw_b);
+  HH_CK(cudaStreamSynchronize(s));
+  free_krylov(h);
+  HH_CK(krylov_init());
+  auto alloc = [&](void **p, size_t bytes) -> hh_status {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HH_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                  " bytes) for the Krylov workspace: " + cudaGetErrorString(e));
+    }
+    h->kw_mem.push_back(*p);
+    return HH_OK;
+  };
+  KrylovWork k;
+  k.S = h->lv[0].S;
+  k.vs = (size_t)k.S * B;
+  int sms = 0;
+  HH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  size_t nparts = 0;   // partial sums of the largest grid over batch sizes 1..B
+  for (int b = 1; b <= B; ++b) {
+    long long c;
+    krylov_grid(k.S, b, sms, &k.nblk, &c);
+    nparts = std::max(nparts, (size_t)b * k.nblk);
+  }
+  const size_t esz = h->opt.precision == HH_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t kbytes = (2 * (size_t)M + 2) * k.vs * esz, dbytes = 3 * k.vs * sizeof(double2);
+  char *kv = nullptr;
+  double2 *dv = nullptr;
+  HH_TRY(alloc((void **)&kv, kbytes));
+  HH_CK(cudaMemsetAsync(kv, 0, kbytes, s));
+  HH_TRY(alloc((void **)&dv, dbytes));
+  HH_CK(cudaMemsetAsync(dv, 0, dbytes, s));
+  k.V = kv;
+  k.Z = kv + (size_t)(M + 1) * k.vs * esz;
+  k.w = kv + (size_t)(2 * M + 1) * k.vs * esz;
+  k.au = dv;
+  k.F = dv + k.vs;
+  k.U = dv + 2 * k.vs;
+  HH_TRY(alloc((void **)&k.parts, nparts * (kKrylovMaxRestart + 1) * sizeof(double2)));
+  HH_TRY(alloc((void **)&k.counter, (size_t)B * sizeof(unsigned int)));
+  HH_CK(cudaMemsetAsync(k.counter, 0, (size_t)B * sizeof(unsigned int), s));
+  HH_TRY(alloc((void **)&k.rhs, (size_t)B * sizeof(KrylovRhs)));
+  HH_CK(cudaMemsetAsync(k.rhs, 0, (size_t)B * sizeof(KrylovRhs), s));
+  HH_TRY(alloc((void **)&k.j, sizeof(int)));
+  h->kw = k;
+  h->kw_m = M;
+  h->kw_b = B;
+  h->kw_sms = sms;
+  return HH_OK;
+}
+
+// The workspace with the grid of a call on `batch` right-hand sides.
+KrylovWork krylov_for(const hh_handle *h, int batch) {
+  KrylovWork k = h->kw;
+  krylov_grid(k.S, batch, h->kw_sms, &k.nblk, &k.chunk);
+  return k;
+}
+
+// One FGMRES iteration in the cycle's precision R: the cycle on v_j (staged
+// in the cycle's right-hand side), z_j, w = A z_j, two Gram-Schmidt passes,
+// the Givens step, v_{j+1}, j += 1.  cond: the WHILE node's handle (0: none).
+template <typename R>
+void enqueue_fgmres_iteration(hh_handle *h, int m, int batch, unsigned long long cond,
+                              cudaStream_t s) {
+  const KrylovWork k = krylov_for(h, batch);
+  Work<R> &W = work<R>(h);
+  cycle_dispatch<R>(h, 0, batch, ZERO_ALL, CHECK_MASK, 0, s);
+  launch_fg_stash<R>(k, W.u_post[0], h->st, batch, s);
+  const LevelK<R> K0 = levelk<R>(h, 0, 0);
+  using C = typename Cx<R>::T;
+  if (h->dim == 2) launch_apply<R, 2>(K0, W.u_post[0], static_cast<C *>(k.w), batch, s);
+  else launch_apply<R, 3>(K0, W.u_post[0], static_cast<C *>(k.w), batch, s);
+  for (int pass = 0; pass < 2; ++pass) {
+    launch_fg_dot<R>(k, pass, h->st, batch, s);
+    launch_fg_axpy<R>(k, pass, m, h->st, h->params, batch, s);
+  }
+  launch_fg_scale<R>(k, 0, W.f[0], h->st, batch, s);
+  launch_fg_next(k, h->st, m, batch, cond, h->copies, s);
+}
+
+// Kernels of one FGMRES iteration (the cycle has no stop test here).
+int fgmres_iteration_kernels(const hh_handle *h) { return hh_cycle_kernels(h) - 1 + 8; }
+
+// The iterations of one restart: a WHILE node whose body is one iteration
+// (runs while a right-hand side is active and j < m), or with HH_LOOP=host
+// a plain graph of one iteration that the host launches m times.
+template <typename R>
+hh_status get_fgmres_graph(hh_handle *h, int m, int batch, cudaGraphExec_t *out) {
+  const bool plain = host_loop();
+  auto key = std::make_tuple(plain ? 1 : 0, m, batch);
+  auto it = h->kw_graphs.find(key);
+  if (it != h->kw_graphs.end()) {
+    *out = it->second.exec;
+    return HH_OK;
+  }
+  GraphEntry g;
+  if (plain) {
+    HH_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    enqueue_fgmres_iteration<R>(h, m, batch, 0, h->cap);
+    HH_CK(cudaStreamEndCapture(h->cap, &g.graph));
+  } else {
+    HH_CK(cudaGraphCreate(&g.graph, 0));
+    cudaGraphConditionalHandle cond;
+    HH_CK(cudaGraphConditionalHandleCreate(&cond, g.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    HH_CK(cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &cp));
+    HH_CK(cudaStreamBeginCaptureToGraph(h->cap, cp.conditional.phGraph_out[0], nullptr, nullptr,
+                                        0, cudaStreamCaptureModeThreadLocal));
+    enqueue_fgmres_iteration<R>(h, m, batch, (unsigned long long)cond, h->cap);
+    cudaGraph_t captured = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(h->cap, &captured);
+    if (ec != cudaSuccess) {
+      cudaGraphDestroy(g.graph);
+      return fail(HH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    }
+  }
+  HH_CK(cudaGraphInstantiate(&g.exec, g.graph, 0));
+  h->kw_graphs[key] = g;
+  *out = g.exec;
+  return HH_OK;
+}
+
+// FGMRES(m) solve of A_0 u = f in the cycle's precision R.  rhs, u: dense
+// device complex128 arrays (u holds the initial guess when `guess`).  Per
+// restart: A u and r = f - A u in FP64, the restart decision, v_0 = r / ||r||,
+// one host read of "any active", the iteration graph, u += Z y.
+template <typename R>
+hh_status fgmres_core(hh_handle *h, const double2 *rhs, double2 *u, int guess, int batch,
+                      double tol, int m, int max_iter, hh_solve_info *info, cudaStream_t s) {
+  HH_TRY(ensure_krylov(h, m, batch, s));
+  const KrylovWork k = krylov_for(h, batch);
+  const Lay l0 = lay_of(h, 0), d0 = lay_dense(h, 0);
+  const int trust_est = std::is_same<R, double>::value ? 1 : 0;
+  HH_TRY(copy_to_pitched(h, 0, k.F, rhs, batch, sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  if (guess)
+    HH_TRY(copy_to_pitched(h, 0, k.U, u, batch, sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  else
+    HH_CK(cudaMemsetAsync(k.U, 0, (size_t)l0.S * batch * sizeof(double2), s));
+  SolveParams &P = *h->params_h;
+  P.tol = tol;
+  P.div_limit = h->opt.div_limit;
+  P.inner_tol = h->opt.inner_tol;
+  P.max_cycles = max_iter;
+  P.max_inner = h->opt.max_inner;
+  P.batch = batch;
+  P.nparts = k.nblk;
+  HH_CK(cudaMemcpyAsync(h->params, h->params_h, sizeof(SolveParams), cudaMemcpyHostToDevice, s));
+  HH_CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+  HH_CK(cudaMemsetAsync(h->copies, 0, sizeof(unsigned int), s));
+  cudaGraphExec_t ex;
+  HH_TRY(get_fgmres_graph<R>(h, m, batch, &ex));
+  const bool plain = host_loop();
+  const LevelK<double> K0 = levelk<double>(h, 0, 0);
+  long long fixed = 0;
+  for (int r = 0; r <= max_iter + 1; ++r) {
+    const int first = r == 0;
+    const int au_zero = first && !guess;
+    if (!au_zero) {
+      if (h->dim == 2) launch_apply<double, 2>(K0, k.U, k.au, batch, s);
+      else launch_apply<double, 3>(K0, k.U, k.au, batch, s);
+      ++fixed;
+    }
+    HH_CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    launch_fg_restart<R>(k, au_zero, first, trust_est, h->st, h->params, h->flag, batch, s);
+    launch_fg_scale<R>(k, 1, work<R>(h).f[0], h->st, batch, s);
+    fixed += 2;
+    HH_CK(cudaMemcpyAsync(h->flag_h, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HH_CK(cudaStreamSynchronize(s));
+    if (*h->flag_h == 0) break;
+    HH_CK(cudaMemsetAsync(k.j, 0, sizeof(int), s));
+    for (int i = 0; i < (plain ? m : 1); ++i) HH_CK(cudaGraphLaunch(ex, s));
+    launch_fg_update<R>(k, h->st, batch, s);
+    ++fixed;
+  }
+  launch_finish(h->st, k.U, l0, u, d0, h->dim, batch, s);
+  HH_CK(cudaGetLastError());
+  h->fixed_kernels = fixed + 1;
+  const hh_status st = read_info(h, batch, info, s);
+  h->last_kernels = (long long)*h->copies_h * fgmres_iteration_kernels(h) + h->fixed_kernels;
+  return st;
+}
+
 }  // namespace
 
 namespace hh {
@@ -1436,6 +1656,26 @@ hh_status hh_solve(hh_handle *h, const void *rhs_dev, void *u_dev, int batch,
   const double2 *guess = (flags & HH_USE_GUESS) ? (const double2 *)u_dev : nullptr;
   return solve_core(h, 0, (const double2 *)rhs_dev, guess, (double2 *)u_dev,
                     batch, tol, info, (cudaStream_t)stream);
+}
+
+hh_status hh_fgmres(hh_handle *h, const void *rhs_dev, void *u_dev, int batch, double tol,
+                    int restart, int max_iter, int flags, hh_solve_info *info, void *stream) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(check_batch(h, batch));
+  if (!rhs_dev || !u_dev) return fail(HH_ERR_ARG, "rhs and u must not be NULL");
+  if (!(tol > 0 && tol < 1)) return fail(HH_ERR_ARG, "tol must be in (0, 1)");
+  if (restart < 1 || restart > kKrylovMaxRestart)
+    return fail(HH_ERR_ARG, "restart must be in 1.." + std::to_string(kKrylovMaxRestart));
+  if (max_iter < 0) return fail(HH_ERR_ARG, "max_iter must be >= 0");
+  HH_TRY(ensure_device(h));
+  const int guess = (flags & HH_USE_GUESS) != 0;
+  const int iters = max_iter > 0 ? max_iter : h->opt.max_cycles;
+  if (h->opt.precision == HH_MIXED)
+    return fgmres_core<float>(h, (const double2 *)rhs_dev, (double2 *)u_dev, guess, batch, tol,
+                              restart, iters, info, (cudaStream_t)stream);
+  return fgmres_core<double>(h, (const double2 *)rhs_dev, (double2 *)u_dev, guess, batch, tol,
+                             restart, iters, info, (cudaStream_t)stream);
 }
 
 hh_status hh_adjoint(hh_handle *h, const void *g_dev, void *lambda_dev,

@@ -13,17 +13,22 @@
 
 namespace hh {
 
+// (x, y, z) of interior point p of one right-hand side.  A right-hand side
+// has fewer than 2^32 points (setup bounds n), so 32-bit unsigned division
+// suffices (64-bit division is a long software sequence).
 template <int DIM>
 __device__ __forceinline__ void coords(size_t p, int N, int &x, int &y,
                                        int &z) {
-  x = (int)(p % N);
-  size_t q = p / N;
+  const unsigned pp = (unsigned)p, n = (unsigned)N;
+  const unsigned q = pp / n;
+  x = (int)(pp - q * n);
   if (DIM == 2) {
     y = (int)q;
     z = 0;
   } else {
-    y = (int)(q % N);
-    z = (int)(q / N);
+    const unsigned r = q / n;
+    y = (int)(q - r * n);
+    z = (int)r;
   }
 }
 

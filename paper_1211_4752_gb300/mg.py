@@ -166,6 +166,14 @@ class HelmholtzMG:
         """lambda = A_0^{-H} g by V-cycles on the conjugate-transposed hierarchy."""
         return self._solve(B.lib().hh_adjoint, g, tol, lam0, raise_on_fail)
 
+    def fgmres(self, f, tol=1e-6, restart=10, max_iter=0, u0=None, raise_on_fail=False):
+        """u = A_0^{-1} f by flexible GMRES(restart) with one V-cycle of this
+        handle as the preconditioner per iteration (Table 3's LVL-MG-FGMRES).
+        info: cycles = iterations, refinements = restarts."""
+        def fn(h, fp, up, nb, t, flags, info, s):
+            return B.lib().hh_fgmres(h, fp, up, nb, t, int(restart), int(max_iter), flags, info, s)
+        return self._solve(fn, f, tol, u0, raise_on_fail)
+
     def solve_host(self, f_host, u_host, tol=1e-6, use_guess=False):
         """Solve with HOST (ideally pinned) complex128 tensors; the copies
         are part of the call.  u_host is overwritten with the solution."""
