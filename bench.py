@@ -270,6 +270,25 @@ def run_ours(args):
                 "status": i64[0]["status"], "ms_per_solve": s64 * 1e3}
         mg64.close()
 
+    # the same problem by flexible GMRES with one cycle per iteration as the
+    # preconditioner (Table 3's LVL-MG-FGMRES), timed once after a warm-up
+    fg = None
+    if args.fgmres_restart > 0:
+        mg.fgmres(f, tol=args.tol, restart=args.fgmres_restart)
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, ifg = mg.fgmres(f, tol=args.tol, restart=args.fgmres_restart)
+        e1.record(stream)
+        e1.synchronize()
+        sfg = e0.elapsed_time(e1) / 1e3
+        fg = {"value": pts / sfg / 1e6, "unit": "MDOF/s", "ms_per_solve": sfg * 1e3,
+              "restart": args.fgmres_restart, "iterations": ifg[0]["cycles"],
+              "restarts": ifg[0]["refinements"], "rel_residual": ifg[0]["rel_residual"],
+              "status": ifg[0]["status"], "kernels": mg.solve_kernels}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args, last["cycles"])
@@ -295,6 +314,7 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "fp64_gpu": fp64,
+            "fgmres": fg,
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -386,6 +406,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_fgmres(args):
+    """One FGMRES(restart) solve of the workload capped at --fgmres-iterations
+    iterations, then exit: the target of launch-list captures of the Krylov
+    kernels (run with HH_LOOP=host so that ncu sees the iteration kernels)."""
+    import numpy as np
+    import torch
+    from paper_1211_4752_gb300 import HelmholtzMG, workloads as W
+    w = getattr(W, args.workload)()
+    k2 = w["k2"]
+    k2_t = torch.from_numpy(k2).cuda() if isinstance(k2, np.ndarray) else float(k2)
+    mg = HelmholtzMG(w["n"], dim=w["dim"], k2=k2_t, layers=w["layers"],
+                     precision=args.precision, max_batch=1, smoother=args.smoother)
+    f = torch.from_numpy(w["rhs"][:1].copy()).cuda()
+    _, info = mg.fgmres(f, tol=args.tol, restart=args.fgmres_restart,
+                        max_iter=args.fgmres_iterations)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": "fgmres", "workload": w["name"], "restart": args.fgmres_restart,
+                      "info": info[0], "kernels": mg.solve_kernels}))
+    mg.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,15 +438,22 @@ def main():
     ap.add_argument("--smoother", choices=["jacobi", "gmres"], default="jacobi",
                     help="jacobi: the benchmarked configuration; gmres: the paper's GMRES(3)")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--fgmres-restart", type=int, default=32,
+                    help="also time FGMRES(m) with the cycle as preconditioner (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-cycles", type=int, default=4)
-    ap.add_argument("--kernel", choices=sorted(KERNELS.values()),
-                    help="launch one level-0 kernel of the workload and exit (for ncu)")
+    ap.add_argument("--kernel", choices=sorted(KERNELS.values()) + ["fgmres"],
+                    help="launch one level-0 kernel of the workload (or one capped FGMRES "
+                         "solve) and exit (for ncu)")
+    ap.add_argument("--fgmres-iterations", type=int, default=40,
+                    help="iteration cap of --kernel fgmres")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.kernel == "fgmres":
+        profile_fgmres(args)
     elif args.kernel:
         profile_one(args)
     else:
