@@ -183,6 +183,30 @@ hh_status hh_solve(hh_handle *h, const void *rhs_dev, void *u_dev, int batch,
 hh_status hh_fgmres(hh_handle *h, const void *rhs_dev, void *u_dev, int batch, double tol,
                     int restart, int max_iter, int flags, hh_solve_info *info, void *stream);
 
+/* One problem of a group solve: a handle (its grid size, medium and
+ * options), its right-hand sides and solutions (device, layout of
+ * hh_solve), batch, flags (HH_USE_GUESS) and per-RHS info (host, batch
+ * entries, or NULL). */
+typedef struct {
+  hh_handle *h;
+  const void *rhs_dev;
+  void *u_dev;
+  int batch;
+  int flags;
+  hh_solve_info *info;
+} hh_group_item;
+
+/* Solve `count` independent problems of possibly different grid sizes in one
+ * call (the batching of Sec. 4.1's many-source experiments over uneven grid
+ * sizes): each problem runs hh_solve on a stream of its handle, from its own
+ * host thread, forked from and joined back to `stream`, so the problems'
+ * kernels run concurrently on the device (the small grids' latency-bound
+ * coarse levels overlap the large grids' work).  Results are identical to
+ * separate hh_solve calls.  The handles must be distinct and on the current
+ * device.  Returns the worst status over all right-hand sides (as hh_solve);
+ * HH_ERR_ARG (nothing enqueued) for an invalid item.  Synchronises `stream`. */
+hh_status hh_solve_group(const hh_group_item *items, int count, double tol, void *stream);
+
 /* hh_solve on HOST arrays: copies rhs in, solves, copies u out (the copies
  * are part of the call).  Same layout and semantics as hh_solve. */
 hh_status hh_solve_host(hh_handle *h, const void *rhs_host, void *u_host,

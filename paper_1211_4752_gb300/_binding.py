@@ -56,6 +56,12 @@ class HHSolveInfo(ct.Structure):
                 ("rel_residual", ct.c_double), ("status", ct.c_int)]
 
 
+class HHGroupItem(ct.Structure):
+    _fields_ = [("h", ct.c_void_p), ("rhs_dev", ct.c_void_p), ("u_dev", ct.c_void_p),
+                ("batch", ct.c_int), ("flags", ct.c_int),
+                ("info", ct.POINTER(HHSolveInfo))]
+
+
 # name -> (restype, argtypes); every symbol include/hh.h declares.
 _P = ct.c_void_p
 _I = ct.c_int
@@ -69,6 +75,7 @@ SIGNATURES = {
     "hh_solve_host": (_I, [_P, _P, _P, _I, _D, _I, ct.POINTER(HHSolveInfo), _P]),
     "hh_adjoint": (_I, [_P, _P, _P, _I, _D, _I, ct.POINTER(HHSolveInfo), _P]),
     "hh_fgmres": (_I, [_P, _P, _P, _I, _D, _I, _I, _I, ct.POINTER(HHSolveInfo), _P]),
+    "hh_solve_group": (_I, [ct.POINTER(HHGroupItem), _I, _D, _P]),
     "hh_grad_k2": (_I, [_P, _P, _P, _I, _P, _P]),
     "hh_apply": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "hh_cycles": (_I, [_P, _P, _P, _I, _I, _P]),

@@ -23,6 +23,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -117,6 +118,8 @@ struct hh_handle {
   int variant[MAXL] = {};           // tile shape per fused level (autotuned)
   int parts_cap = 0;                // capacity of `partials` per RHS
   cudaStream_t side = nullptr;      // branch of the stop test in the fused cycle
+  cudaStream_t grp = nullptr;       // this handle's stream in a group solve (lazy)
+  cudaEvent_t ev_grp = nullptr;     // its join event
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int *err = nullptr;               // device status word of bounded waits
   unsigned int *copies = nullptr;   // cycles launched by the current solve
@@ -355,15 +358,16 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
 }
 
 // cuTensorMapEncodeTiled from the driver (no link-time dependency on it).
+// (Looked up once, thread-safely: handles may be set up from several threads.)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess && q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -863,6 +867,8 @@ void destroy_impl(hh_handle *h) {
   if (h->st_h) cudaFreeHost(h->st_h);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->grp) cudaStreamDestroy(h->grp);
+  if (h->ev_grp) cudaEventDestroy(h->ev_grp);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
@@ -1676,6 +1682,68 @@ hh_status hh_fgmres(hh_handle *h, const void *rhs_dev, void *u_dev, int batch, d
                               restart, iters, info, (cudaStream_t)stream);
   return fgmres_core<double>(h, (const double2 *)rhs_dev, (double2 *)u_dev, guess, batch, tol,
                              restart, iters, info, (cudaStream_t)stream);
+}
+
+hh_status hh_solve_group(const hh_group_item *items, int count, double tol, void *stream) {
+  g_err.clear();
+  if (count < 0 || (count > 0 && !items)) return fail(HH_ERR_ARG, "items must hold count entries");
+  if (!(tol > 0 && tol < 1)) return fail(HH_ERR_ARG, "tol must be in (0, 1)");
+  for (int i = 0; i < count; ++i) {
+    const hh_group_item &it = items[i];
+    HH_TRY(check_handle(it.h));
+    HH_TRY(check_batch(it.h, it.batch));
+    if (!it.rhs_dev || !it.u_dev) return fail(HH_ERR_ARG, "rhs and u must not be NULL");
+    HH_TRY(ensure_device(it.h));
+    for (int j = 0; j < i; ++j)
+      if (items[j].h == it.h) return fail(HH_ERR_ARG, "a handle appears twice in the group");
+  }
+  if (count == 0) return HH_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < count; ++i) {
+    hh_handle *h = items[i].h;
+    if (!h->grp) HH_CK(cudaStreamCreateWithFlags(&h->grp, cudaStreamNonBlocking));
+    if (!h->ev_grp) HH_CK(cudaEventCreateWithFlags(&h->ev_grp, cudaEventDisableTiming));
+  }
+  // fork: every problem's stream waits for the work already on `stream`
+  cudaEvent_t fork = items[0].h->ev_grp;
+  HH_CK(cudaEventRecord(fork, s));
+  for (int i = 0; i < count; ++i) HH_CK(cudaStreamWaitEvent(items[i].h->grp, fork, 0));
+  std::vector<hh_status> res(count, HH_OK);
+  std::vector<std::string> msg(count);
+  auto run = [&](int i) {
+    const hh_group_item &it = items[i];
+    hh_handle *h = it.h;
+    if (cudaSetDevice(h->device) != cudaSuccess) {
+      res[i] = HH_ERR_CUDA;
+      msg[i] = "cudaSetDevice failed in a group worker";
+      return;
+    }
+    const double2 *guess = (it.flags & HH_USE_GUESS) ? (const double2 *)it.u_dev : nullptr;
+    res[i] = solve_core(h, 0, (const double2 *)it.rhs_dev, guess, (double2 *)it.u_dev, it.batch,
+                        tol, it.info, h->grp);
+    msg[i] = g_err;
+  };
+  std::vector<std::thread> workers;
+  for (int i = 1; i < count; ++i) workers.emplace_back(run, i);
+  run(0);
+  for (auto &t : workers) t.join();
+  // join: `stream` waits for every problem's stream
+  for (int i = 0; i < count; ++i) {
+    HH_CK(cudaEventRecord(items[i].h->ev_grp, items[i].h->grp));
+    HH_CK(cudaStreamWaitEvent(s, items[i].h->ev_grp, 0));
+  }
+  HH_CK(cudaStreamSynchronize(s));
+  hh_status worst = HH_OK;
+  for (int i = 0; i < count; ++i) {
+    if (res[i] == HH_OK) continue;
+    const bool soft = res[i] == HH_ERR_NOT_CONVERGED || res[i] == HH_ERR_DIVERGED;
+    const bool wsoft = worst == HH_OK || worst == HH_ERR_NOT_CONVERGED;
+    if (worst == HH_OK || (!soft && wsoft) || (res[i] == HH_ERR_DIVERGED && wsoft)) {
+      worst = res[i];
+      g_err = "group item " + std::to_string(i) + ": " + msg[i];
+    }
+  }
+  return worst;
 }
 
 hh_status hh_adjoint(hh_handle *h, const void *g_dev, void *lambda_dev,

@@ -294,3 +294,29 @@ class HelmholtzSolve(torch.autograd.Function):
 def helmholtz_solve(k2, f, tol=1e-6, **mg_kwargs):
     """Differentiable solve: u = A_0(k2)^{-1} f (see HelmholtzSolve)."""
     return HelmholtzSolve.apply(k2, f, mg_kwargs, tol)
+
+
+def solve_group(problems, tol=1e-6):
+    """Solve independent problems of possibly different grid sizes in one call
+    (hh_solve_group): `problems` is a list of (HelmholtzMG, f) or
+    (HelmholtzMG, f, u0) with distinct handles; the problems run
+    concurrently on the device.  Returns [(u, info), ...] in order."""
+    items = (B.HHGroupItem * len(problems))()
+    outs, keep = [], []
+    for i, p in enumerate(problems):
+        mg, f = p[0], p[1]
+        u0 = p[2] if len(p) > 2 else None
+        f = mg._vec(f, "rhs")
+        nb = f.shape[0]
+        u = torch.empty_like(f) if u0 is None else mg._vec(u0, "u0").clone()
+        info = (B.HHSolveInfo * nb)()
+        items[i] = B.HHGroupItem(mg._h, _ptr(f), _ptr(u), nb,
+                                 B.HH_USE_GUESS if u0 is not None else 0, info)
+        outs.append((u, info, nb))
+        keep.append(f)
+    dev = problems[0][0].device if problems else torch.device("cuda")
+    with torch.cuda.device(dev):
+        st = B.lib().hh_solve_group(items, len(problems), float(tol), _stream())
+    if st not in (B.HH_OK, B.HH_ERR_NOT_CONVERGED, B.HH_ERR_DIVERGED):
+        B.check(st)
+    return [(u, HelmholtzMG._infos(info, nb)) for u, info, nb in outs]

@@ -90,6 +90,8 @@ def test_calls_with_null_handle_fail_cleanly(hh):
     assert L.hh_solve(None, None, None, 1, 1e-6, 0, info, None) == hh.HH_ERR_ARG
     assert L.hh_adjoint(None, None, None, 1, 1e-6, 0, info, None) == hh.HH_ERR_ARG
     assert L.hh_fgmres(None, None, None, 1, 1e-6, 10, 0, 0, info, None) == hh.HH_ERR_ARG
+    assert L.hh_solve_group(None, 1, 1e-6, None) == hh.HH_ERR_ARG
+    assert L.hh_solve_group(None, 0, 1e-6, None) == hh.HH_OK
     assert L.hh_destroy(None) == hh.HH_OK
     assert L.hh_num_levels(None) == 0
     assert L.hh_cycle_kernels(None) == 0
