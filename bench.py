@@ -129,7 +129,7 @@ def profile_one(args):
     import ctypes as ct
     from paper_1211_4752_gb300 import HelmholtzMG, workloads as W
     from paper_1211_4752_gb300 import _binding as B
-    w = getattr(W, args.workload)()
+    w = getattr(W, args.workload)(**({"n": args.kernel_n} if args.kernel_n else {}))
     k2 = w["k2"]
     k2_t = torch.from_numpy(k2).cuda() if isinstance(k2, np.ndarray) else float(k2)
     mg = HelmholtzMG(w["n"], dim=w["dim"], k2=k2_t, layers=w["layers"],
@@ -253,6 +253,34 @@ def run_ours(args):
                     "tile_level0": mg.tile_shape(0),
                     "launch_ms": {KERNELS[k]: v for k, v in kt.items()}}
 
+    # the same level-0 kernels on a grid whose arrays exceed the 129 MB L2
+    # (constant k, kh = 0.625, ECS n/32): the HBM-bound figure
+    roofline_large = None
+    if fused and args.large_n > 0:
+        wl = W.ecs_const(n=args.large_n)
+        mgl = HelmholtzMG(wl["n"], k2=wl["k2"], layers=wl["layers"], precision=args.precision,
+                          max_batch=1)
+        ptsl = (wl["n"] - 1) ** 2
+        ktl = {}
+        for kid in (0, 2):
+            ms = ct.c_double()
+            B.check(B.lib().hh_time_kernel(mgl._h, kid, 0, 1, 20, ct.byref(ms),
+                                           ct.c_void_p(stream.cuda_stream)))
+            ktl[kid] = ms.value
+        dom = max((0, 2), key=lambda k: ktl[k])
+        bpp = kernel_bytes(dom, True, mixed)
+        achieved = bpp * ptsl / (ktl[dom] * 1e-3) / 1e9
+        traffic = None
+        tf = ROOT / "profiles" / "traffic.json"
+        if tf.exists():
+            traffic = json.loads(tf.read_text()).get(f"{wl['name']}:{args.precision}:{KERNELS[dom]}")
+        roofline_large = {"bound": "hbm", "kernel": KERNELS[dom], "workload": wl["name"],
+                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                          "bytes_per_point": bpp, "tile_level0": mgl.tile_shape(0),
+                          "launch_ms": {KERNELS[k]: v for k, v in ktl.items()}}
+        mgl.close()
+
     fp64 = None
     if mixed and args.compare_fp64:
         mg64 = HelmholtzMG(n, dim=dim, k2=k2_t, layers=w["layers"], precision="fp64", max_batch=1,
@@ -312,6 +340,7 @@ def run_ours(args):
             "e2e": {"value": pts * args.steps * world / e2e_total / 1e6, "unit": "MDOF/s",
                     "h2d_bytes_per_step": pts * 16, "d2h_bytes_per_step": pts * 16},
             "roofline": roofline,
+            "roofline_large": roofline_large,
             "cpu_baseline": cpu,
             "fp64_gpu": fp64,
             "fgmres": fg,
@@ -520,6 +549,8 @@ def main():
     ap.add_argument("--smoother", choices=["jacobi", "gmres"], default="jacobi",
                     help="jacobi: the benchmarked configuration; gmres: the paper's GMRES(3)")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--large-n", type=int, default=4096,
+                    help="also time the level-0 kernels on an (n-1)^2 grid beyond L2 (0: skip)")
     ap.add_argument("--fgmres-restart", type=int, default=32,
                     help="also time FGMRES(m) with the cycle as preconditioner (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -529,6 +560,8 @@ def main():
     ap.add_argument("--kernel", choices=sorted(KERNELS.values()) + ["fgmres"],
                     help="launch one level-0 kernel of the workload (or one capped FGMRES "
                          "solve) and exit (for ncu)")
+    ap.add_argument("--kernel-n", type=int, default=0,
+                    help="grid size n of the workload for --kernel (0: the workload's own)")
     ap.add_argument("--fgmres-iterations", type=int, default=40,
                     help="iteration cap of --kernel fgmres")
     args = ap.parse_args()

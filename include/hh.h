@@ -203,7 +203,8 @@ typedef struct {
  * kernels run concurrently on the device (the small grids' latency-bound
  * coarse levels overlap the large grids' work).  Results are identical to
  * separate hh_solve calls.  The handles must be distinct and on the current
- * device.  Returns the worst status over all right-hand sides (as hh_solve);
+ * device.  (A group with a handle whose cycle is one cooperative launch,
+ * HH_PERSIST=1 at setup, runs its problems one after another on `stream`.)  Returns the worst status over all right-hand sides (as hh_solve);
  * HH_ERR_ARG (nothing enqueued) for an invalid item.  Synchronises `stream`. */
 hh_status hh_solve_group(const hh_group_item *items, int count, double tol, void *stream);
 

@@ -131,6 +131,9 @@ struct hh_handle {
   int mid0 = 0, midt = 0, midcl = 0;  // levels mid0 .. midt-1 (cluster of midcl CTAs)
   float2 *tailop_mid[2] = {nullptr, nullptr};  // tail operator from level midt
   MidArgs<float> margs[2];          // per direction
+  int persist = 0, persist_grid = 0;  // complex64 cycles as one cooperative launch
+  PersistArgs pargs[2];             // its arguments per direction (per-call fields filled at launch)
+  unsigned int *pbar = nullptr;     // its grid barrier (arrivals, generation)
   double *gm_parts = nullptr;       // GMRES smoothing: partial sums,
   unsigned int *gm_counter = nullptr;  // last-block arrival counter,
   double *gm_gsc = nullptr;         // per right-hand side scalars
@@ -502,6 +505,23 @@ void enqueue_tail(hh_handle *h, int dir, int batch, const SolveState *st, cudaSt
 template <typename R>
 void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
                          unsigned long long cond, cudaStream_t s) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (h->persist) {   // the whole cycle in one cooperative launch
+      PersistArgs a = h->pargs[dir];
+      a.zero0 = zero0;
+      a.batch = batch;
+      a.check = check == CHECK_CYCLE ? 1 : (check == CHECK_INNER ? 2 : 0);
+      a.st = check != CHECK_NONE ? h->st : nullptr;
+      a.partials = h->partials;
+      a.P = h->params;
+      a.flag = h->flag;
+      a.cond = cond;
+      a.copies = h->copies;
+      a.err = h->err;
+      launch_vcycle2d(a, h->persist_grid, s);
+      return;
+    }
+  }
   Work<R> &W = work<R>(h);
   const SolveState *st = check != CHECK_NONE ? h->st : nullptr;
   const auto om = omega<R>(h, dir);
@@ -1037,6 +1057,62 @@ hh_status setup_mid(hh_handle *h, cudaStream_t s) {
   return HH_OK;
 }
 
+// Complex64 cycles as one cooperative launch (k_vcycle2d, 60 x 16 tiles on
+// every fused level, the tail operator below them): HH_PERSIST=1 in the
+// environment turns it on where it applies (2-D fused path, tail operator
+// built, at most kPersistMaxLevels fused levels, the device holds the grid).
+hh_status setup_persist(hh_handle *h, cudaStream_t s) {
+  const char *pe = std::getenv("HH_PERSIST");
+  if (!(pe && std::strcmp(pe, "1") == 0)) return HH_OK;
+  if (h->dim != 2 || !h->fused || h->opt.precision != HH_MIXED || h->mid) return HH_OK;
+  if (!h->tailop[0] || !h->tailop[1] || h->tail0 < 1 || h->tail0 > kPersistMaxLevels)
+    return HH_OK;
+  int v0 = -1;
+  for (int v = 0; v < kNumTileVariants; ++v)
+    if (tile_bx(v) == kPersistBX && tile_by(v) == kPersistBY) v0 = v;
+  if (v0 < 0) return HH_OK;
+  int bps = 0, sms = 0;
+  if (init_vcycle2d(&bps) != cudaSuccess || bps < 1) {
+    cudaGetLastError();
+    return HH_OK;
+  }
+  HH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  HH_TRY(dev_alloc_n(h, &h->pbar, 2));
+  HH_CK(cudaMemsetAsync(h->pbar, 0, 2 * sizeof(unsigned int), s));
+  Work<float> &W = h->w32;
+  for (int dir = 0; dir < 2; ++dir) {
+    PersistArgs &a = h->pargs[dir];
+    std::memset(&a, 0, sizeof(a));
+    a.T = h->tail0;
+    for (int l = 0; l < h->tail0; ++l) {
+      PersistLevel &p = a.lv[l];
+      p.K = levelk<float>(h, l, dir);
+      HH_TRY(make_maps<float>(h, l, v0, &p.dm, &p.um));
+      p.v = W.u_pre[l];
+      p.fc = W.f[l + 1];
+      p.u = W.u_post[l];
+      p.f = W.f[l];
+      p.cs = cscal<float>(h, l, dir);
+      p.lc = lay_of(h, l + 1);
+      p.ntx = (h->lv[l].N + kPersistBX - 1) / kPersistBX;
+      p.nty = (h->lv[l].N + kPersistBY - 1) / kPersistBY;
+    }
+    a.omega = omega<float>(h, dir);
+    a.kconst = h->kconst;
+    const LevelHost &tv = h->lv[h->tail0];
+    a.Top = h->tailop[dir];
+    a.tN = tv.N;
+    a.tP = tv.P;
+    a.tS = (int)tv.S;
+    a.tf = W.f[h->tail0];
+    a.tu = W.u_post[h->tail0];
+    a.bar = h->pbar;
+  }
+  h->persist = 1;
+  h->persist_grid = bps * sms;
+  return HH_OK;
+}
+
 hh_status autotune(hh_handle *h, cudaStream_t s) {
   const char *force = std::getenv("HH_TILE_VARIANT");
   if (force) {
@@ -1310,6 +1386,7 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
       if (h->opt.precision == HH_FP64) HH_TRY(make_maps<double>(h, l, h->variant[l], &h->dmap[l], &h->umap[l]));
       else HH_TRY(make_maps<float>(h, l, h->variant[l], &h->dmap[l], &h->umap[l]));
     }
+    if (op) HH_TRY(setup_persist(h, s));
   }
   h->nparts = h->fused ? tile_parts(h->variant[0], h->lv[0].N) : partial_blocks(h->lv[0].pts);
   return HH_OK;
@@ -1407,7 +1484,10 @@ void enqueue_fgmres_iteration(hh_handle *h, int m, int batch, unsigned long long
 }
 
 // Kernels of one FGMRES iteration (the cycle has no stop test here).
-int fgmres_iteration_kernels(const hh_handle *h) { return hh_cycle_kernels(h) - 1 + 8; }
+int fgmres_iteration_kernels(const hh_handle *h) {
+  const bool one = h->persist && h->opt.precision == HH_MIXED;   // no stop test inside
+  return (one ? 1 : hh_cycle_kernels(h) - 1) + 8;
+}
 
 // The iterations of one restart: a WHILE node whose body is one iteration
 // (runs while a right-hand side is active and j < m), or with HH_LOOP=host
@@ -1620,6 +1700,7 @@ int hh_level_points(const hh_handle *h, int level) {
 
 int hh_cycle_kernels(const hh_handle *h) {
   if (!h) return 0;
+  if (h->persist && h->opt.precision == HH_MIXED) return 1;   // one cooperative launch
   if (h->fused)   // down passes, stop test, tail (or cluster kernel), up passes
     return 2 * (h->mid && h->opt.precision == HH_MIXED ? h->mid0 : h->tail0) + 2;
   if (h->opt.smoother == HH_SMOOTH_GMRES)   // per level: steps of 2m + 2 kernels,
@@ -1699,6 +1780,27 @@ hh_status hh_solve_group(const hh_group_item *items, int count, double tol, void
   }
   if (count == 0) return HH_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  // A handle whose cycle is one cooperative launch (all of its blocks
+  // resident) must not share the device with another problem's kernels:
+  // such a group runs its problems one after another on `stream`.
+  bool serial = false;
+  for (int i = 0; i < count; ++i) serial = serial || items[i].h->persist;
+  if (serial) {
+    hh_status worst = HH_OK;
+    std::string msg;
+    for (int i = 0; i < count; ++i) {
+      const hh_group_item &it = items[i];
+      const double2 *guess = (it.flags & HH_USE_GUESS) ? (const double2 *)it.u_dev : nullptr;
+      const hh_status r = solve_core(it.h, 0, (const double2 *)it.rhs_dev, guess,
+                                     (double2 *)it.u_dev, it.batch, tol, it.info, s);
+      if (r != HH_OK && worst == HH_OK) {
+        worst = r;
+        msg = "group item " + std::to_string(i) + ": " + g_err;
+      }
+    }
+    g_err = msg;
+    return worst;
+  }
   for (int i = 0; i < count; ++i) {
     hh_handle *h = items[i].h;
     if (!h->grp) HH_CK(cudaStreamCreateWithFlags(&h->grp, cudaStreamNonBlocking));

@@ -126,6 +126,51 @@ template <typename R>
 cudaError_t launch_mid2d(const MidArgs<R> &a, int cl, int batch, const SolveState *st,
                          cudaStream_t s);
 template <typename R> int mid2d_max_clusters(int cl, int smem_bytes);
+// One complex64 V-cycle (2-D) in one cooperative launch (hh_vcycle2d.cu):
+// the fused down passes of levels 0 .. T-1, the tail operator of level T and
+// the up passes, every block working through the tiles of a level and then
+// meeting the others at a grid barrier (bounded; a timeout sets the status
+// word).  The stop test of level 0 runs in the last block while the others
+// start level 1.
+constexpr int kPersistMaxLevels = 9;
+struct PersistLevel {
+  LevelK<float> K;
+  DownMaps dm;
+  UpMaps um;
+  float2 *v;       // pre-smoothed iterate (down output, up input)
+  float2 *fc;      // restricted right-hand side (level l + 1)
+  float2 *u;       // result of the up pass
+  float2 *f;       // right-hand side of this level
+  float2 cs;       // scale of the restricted residual
+  Lay lc;          // layout of level l + 1
+  int ntx, nty;    // tiles per axis
+};
+struct PersistArgs {
+  int T;                          // fused levels 0 .. T-1
+  PersistLevel lv[kPersistMaxLevels];
+  float2 omega;
+  int kconst;
+  int zero0;                      // ZERO_* mode of the level-0 iterate
+  int batch;
+  int check;                      // 0: none, 1: plain loop, 2: refinement's inner loop
+  const float2 *Top;              // tail operator of level T (rows N^2, columns S)
+  int tN, tP, tS;
+  const float2 *tf;               // right-hand side of level T
+  float2 *tu;                     // its result
+  SolveState *st;                 // per right-hand side state (null: all active)
+  double *partials;               // level-0 stop-test partial sums [b][tile]
+  const SolveParams *P;
+  int *flag;
+  unsigned long long cond;        // WHILE-node condition handle (0: none)
+  unsigned int *copies;           // cycles run (counted by the stop test)
+  int *err;                       // status word of bounded waits
+  unsigned int *bar;              // grid barrier: arrival count, generation
+};
+constexpr int kPersistBX = 60, kPersistBY = 16;
+size_t vcycle2d_smem();
+cudaError_t init_vcycle2d(int *blocks_per_sm);
+cudaError_t launch_vcycle2d(const PersistArgs &a, int grid, cudaStream_t s);
+
 void launch_unit_rhs(double2 *F, int N, int P, int S, cudaStream_t s);
 void launch_tail_gather(const double2 *U, float2 *T, int N, int P, int S, cudaStream_t s);
 void launch_tail_apply(const float2 *T, int N, int P, int S, const float2 *f, float2 *u,

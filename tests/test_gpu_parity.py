@@ -194,6 +194,55 @@ def test_cluster_mid_levels_match_per_level_kernels(n, monkeypatch):
     mg0.close()
 
 
+@pytest.mark.parametrize("n,batch", [(64, 2), (256, 3), (1024, 1)])
+def test_persistent_cycle_matches_per_level_kernels(n, batch, monkeypatch):
+    """complex64 cycles in one cooperative launch (HH_PERSIST=1) against the
+    per-level kernels: iterates to complex64 rounding (the tile shapes differ,
+    so the summation order does), solves cycle for cycle, forward and adjoint,
+    on a heterogeneous medium with ECS layers; FGMRES on top of it."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    k2 = W.smooth_k2(n, 2, 9, 0.55 * n, 0.62 * n)
+    kw = dict(k2=dev(k2), layers=n // 16, max_batch=batch, precision="mixed")
+    monkeypatch.setenv("HH_PERSIST", "1")
+    mg = HelmholtzMG(n, **kw)
+    monkeypatch.delenv("HH_PERSIST")
+    mg0 = HelmholtzMG(n, **kw)
+    assert mg.cycle_kernels == 1 < mg0.cycle_kernels
+    f = rnd((batch, n - 1, n - 1), 31)
+    z = np.zeros_like(f)
+    a = host(mg.cycles(dev(f), dev(z), 3))
+    b = host(mg0.cycles(dev(f), dev(z), 3))
+    assert relerr(a, b) < 2e-6
+    mg.close()
+    mg0.close()
+    # solves on the constant-k model (k = 40 with ECS n/4 at 64, else kh =
+    # 0.625 with ECS n/32), where the Jacobi cycle converges
+    kc, lay = (1600.0, 16) if n == 64 else ((0.625 * n) ** 2, n // 32)
+    kw = dict(k2=kc, layers=lay, max_batch=batch, precision="mixed")
+    monkeypatch.setenv("HH_PERSIST", "1")
+    mg = HelmholtzMG(n, **kw)
+    monkeypatch.delenv("HH_PERSIST")
+    mg0 = HelmholtzMG(n, **kw)
+    assert mg.cycle_kernels == 1
+    src = np.zeros_like(f)
+    for j in range(batch):
+        src[j] = W.point_sources(n, 2, [(n // 2 - 1 + 3 * j, n // 2 - 1)])[0]
+    ua, ia = mg.solve(dev(src), tol=1e-6)
+    ub, ib = mg0.solve(dev(src), tol=1e-6)
+    assert all(i["status"] == "OK" for i in ia)
+    assert [i["cycles"] for i in ia] == [i["cycles"] for i in ib]
+    assert relerr(host(ua), host(ub)) < 1e-5
+    la, il = mg.adjoint(dev(src), tol=1e-6)
+    assert all(i["status"] == "OK" for i in il)
+    rho = np.linalg.norm((host(mg.apply(la, adjoint=True)) - src).reshape(batch, -1), axis=1)
+    assert np.all(rho <= 1e-6 * np.linalg.norm(src.reshape(batch, -1), axis=1))
+    uf, jf = mg.fgmres(dev(src), tol=1e-6, restart=16)
+    assert all(i["status"] == "OK" for i in jf)
+    assert relerr(host(uf), host(ub)) < 1e-5
+    mg.close()
+    mg0.close()
+
+
 def test_adjoint_mixed_matches_oracle():
     """Mixed-precision adjoint solve (adjoint tail operator) vs the oracle."""
     from paper_1211_4752_gb300 import HelmholtzMG
