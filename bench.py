@@ -317,9 +317,12 @@ def run_ours(args):
               "restarts": ifg[0]["refinements"], "rel_residual": ifg[0]["rel_residual"],
               "status": ifg[0]["status"], "kernels": mg.solve_kernels}
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args, last["cycles"])
+        if args.cpu_all_cores:
+            cyc = int(cpu["sample"].split(" scaled to ")[1].split(" cycles")[0])
+            cpu_all = cpu_baseline_all_cores(w, args, cyc)
     if rank == 0:
         line = {
             "metric": "finest-grid MDOF/s solved to 1e-6 rel. residual",
@@ -342,6 +345,7 @@ def run_ours(args):
             "roofline": roofline,
             "roofline_large": roofline_large,
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "fp64_gpu": fp64,
             "fgmres": fg,
             "gpu_launches": launches,
@@ -388,6 +392,56 @@ def cpu_baseline(w, args, cycles_hint):
             "kind": "oracle",
             "sample": f"{ncyc} V-cycles of {w['name']} ({s_per_cycle:.3f} s/cycle, numpy FP64, "
                       f"1 thread) scaled to {cycles} cycles ({src}); setup {t1 - t0:.1f} s"}
+
+
+def _oracle_cycles_worker(task):
+    """One host core: build the oracle hierarchy of the workload and time
+    V-cycles for about `seconds` (a process of a spawn pool)."""
+    name, seconds, smoother = task
+    import numpy as np
+
+    import oracle as O
+    from paper_1211_4752_gb300 import workloads as W
+    w = getattr(W, name)()
+    H = O.build_hierarchy(w["n"], w["dim"], w["k2"], layers=w["layers"], smoother=smoother)
+    f = w["rhs"][0]
+    u = np.zeros_like(f)
+    t1 = time.perf_counter()
+    ncyc = 0
+    while True:
+        u = O.vcycle(H, 0, u, f)
+        O.residual_norm(H, u, f)
+        ncyc += 1
+        el = time.perf_counter() - t1
+        if el > seconds or ncyc >= 200:
+            return ncyc, el
+
+
+def cpu_baseline_all_cores(w, args, cycles):
+    """The oracle on every host core at once: one independent solve per core
+    (a spawn pool, one numpy thread each), each timed on a bounded sample of
+    V-cycles and scaled to `cycles`; the value is their summed throughput."""
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ["OMP_NUM_THREADS"] = os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    try:
+        with mp.get_context("spawn").Pool(ncores) as pool:
+            res = pool.map(_oracle_cycles_worker,
+                           [(args.workload, args.cpu_seconds, args.smoother)] * ncores)
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    pts = (w["n"] - 1) ** w["dim"]
+    value = sum(pts / (el / nc * cycles) / 1e6 for nc, el in res)
+    per = sum(el / nc for nc, el in res) / len(res)
+    return {"value": value, "unit": "MDOF/s", "cores": ncores, "kind": "oracle",
+            "sample": f"{ncores} processes x {min(nc for nc, _ in res)}+ V-cycles of {w['name']} "
+                      f"({per:.3f} s/cycle per core, numpy FP64, 1 thread each), one independent "
+                      f"solve per core scaled to {cycles} cycles, throughputs summed"}
 
 
 def run_reference(args):
@@ -554,6 +608,8 @@ def main():
     ap.add_argument("--fgmres-restart", type=int, default=32,
                     help="also time FGMRES(m) with the cycle as preconditioner (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", dest="cpu_all_cores", action="store_false",
+                    help="skip the oracle timed on every host core at once")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-cycles", type=int, default=4)
