@@ -157,7 +157,7 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = getattr(W, args.workload)()
+    w = getattr(W, args.workload)(*args.workload_arg)
     n, dim = w["n"], w["dim"]
     pts = (n - 1) ** dim
     k2 = w["k2"]
@@ -330,7 +330,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64+f64" if mixed else "c128",
-            "data": "synthetic (seeded point sources; " + ("k^2 field" if isinstance(w["k2"], np.ndarray) else "constant k") + ")",
+            "data": ("synthetic (the analytic coefficient and source of the ionization model)"
+                     if w["name"].startswith("ionization") else
+                     "synthetic (seeded point sources; " + ("k^2 field" if isinstance(w["k2"], np.ndarray) else "constant k") + ")"),
             "config": {"workload": w["name"], "n": n, "interior": n - 1, "dim": dim,
                        "k2": float(k2) if not isinstance(k2, np.ndarray) else "field",
                        "ecs_layer": w["layers"], "precision": args.precision,
@@ -397,12 +399,12 @@ def cpu_baseline(w, args, cycles_hint):
 def _oracle_cycles_worker(task):
     """One host core: build the oracle hierarchy of the workload and time
     V-cycles for about `seconds` (a process of a spawn pool)."""
-    name, seconds, smoother = task
+    name, wargs, seconds, smoother = task
     import numpy as np
 
     import oracle as O
     from paper_1211_4752_gb300 import workloads as W
-    w = getattr(W, name)()
+    w = getattr(W, name)(*wargs)
     H = O.build_hierarchy(w["n"], w["dim"], w["k2"], layers=w["layers"], smoother=smoother)
     f = w["rhs"][0]
     u = np.zeros_like(f)
@@ -428,7 +430,8 @@ def cpu_baseline_all_cores(w, args, cycles):
     try:
         with mp.get_context("spawn").Pool(ncores) as pool:
             res = pool.map(_oracle_cycles_worker,
-                           [(args.workload, args.cpu_seconds, args.smoother)] * ncores)
+                           [(args.workload, tuple(args.workload_arg), args.cpu_seconds,
+                             args.smoother)] * ncores)
     finally:
         for k, v in env.items():
             if v is None:
@@ -449,7 +452,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_1211_4752_gb300 import workloads as W
-    w = getattr(W, args.workload)()
+    w = getattr(W, args.workload)(*args.workload_arg)
     import numpy as np
 
     import oracle as O
@@ -578,7 +581,7 @@ def profile_fgmres(args):
     import numpy as np
     import torch
     from paper_1211_4752_gb300 import HelmholtzMG, workloads as W
-    w = getattr(W, args.workload)()
+    w = getattr(W, args.workload)(*args.workload_arg)
     k2 = w["k2"]
     k2_t = torch.from_numpy(k2).cuda() if isinstance(k2, np.ndarray) else float(k2)
     mg = HelmholtzMG(w["n"], dim=w["dim"], k2=k2_t, layers=w["layers"],
@@ -599,6 +602,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ecs_const")
+    ap.add_argument("--workload-arg", type=int, nargs="*", default=[],
+                    help="positional arguments of the workload (e.g. k0 of ionization)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--smoother", choices=["jacobi", "gmres"], default="jacobi",
                     help="jacobi: the benchmarked configuration; gmres: the paper's GMRES(3)")

@@ -18,6 +18,12 @@ interior point i at coordinate (i + 1) / n):
 * ``bump``              511^2, kh = 0.5 background with a 10 % Gaussian bump
   in k^2, ECS 16, 16 sources on the first physical row.
 * ``cube``              127^3, k = 80 (kh = 0.625), ECS 16, centre source.
+* ``ionization``        the quantum-mechanical ionization model of Sec. 4.3 on
+  (0, r)^2, r = 50: coefficient e^{-x^2} + e^{-y^2} + k0^2 of u, source
+  e^{-(x^2+y^2)}, u = 0 on x = 0 and y = 0, ECS on the sides x = r, y = r;
+  grid sizes of Table 8 (k0 = 1 .. 5: 128^2, 256^2, 256^2, 512^2, 512^2).
+  Mapped to the unit square by x = r xi: the coefficient and the source are
+  multiplied by r^2.
 """
 
 from __future__ import annotations
@@ -138,6 +144,24 @@ def cube(n=128, k=80.0, layers=16):
     c = n // 2 - 1
     return dict(name=f"cube_{n-1}^3_k{k:g}_ecs{layers}", n=n, dim=3, k2=k * k,
                 layers=layers, rhs=point_sources(n, 3, [(c, c, c)]))
+
+
+ION_GRIDS = {1: 128, 2: 256, 3: 256, 4: 512, 5: 512}   # Table 8
+
+
+def ionization(k0=1, n=None, r=50.0, layer_frac=8):
+    """Sec. 4.3's ionization model (see the module docstring).  The ECS layer
+    takes the last n / layer_frac cells next to x = r and y = r inside the
+    grid; the sides x = 0 and y = 0 have no layer (homogeneous Dirichlet).
+    Arrays are [y][x] over the interior points (i + 1) r / n."""
+    n = ION_GRIDS[k0] if n is None else n
+    x = interior_coords(n) * r
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    k2 = r * r * (np.exp(-X * X) + np.exp(-Y * Y) + float(k0) ** 2)
+    rhs = (r * r * np.exp(-(X * X + Y * Y)))[None].astype(np.complex128)
+    layers = n // layer_frac
+    return dict(name=f"ionization_{n-1}x{n-1}_k0{k0:g}_ecs0-{layers}", n=n, dim=2, k2=k2,
+                layers=(0, layers), rhs=rhs)
 
 
 def random_field(shape, seed, complex_=True, scale=1.0):

@@ -8,6 +8,7 @@ the CUDA path.  Usage:
     python tests/golden/make_oracle_samples.py layered    [out.json]
     python tests/golden/make_oracle_samples.py --divergence layered
     python tests/golden/make_oracle_samples.py --gmres bump
+    python tests/golden/make_oracle_samples.py --gmres ionization 4   (k0 = 4)
 """
 
 import json
@@ -55,7 +56,8 @@ def main():
     if which == "--gmres":      # GMRES(3) smoothing (Sec. 3.2)
         smoother = "gmres"
         which = sys.argv[2]
-    w = getattr(workloads, which)()
+    extra = [int(a) for a in sys.argv[3 if smoother == "gmres" else 2:] if a.isdigit()]
+    w = getattr(workloads, which)(*extra)
     suffix = "_gmres" if smoother == "gmres" else ""
     out = Path(__file__).with_name(w["name"] + suffix + ".json")
     t0 = time.time()

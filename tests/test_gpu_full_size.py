@@ -151,9 +151,13 @@ def test_gmres_layered_first_cycles_match_oracle():
     mg.close()
 
 
-@pytest.mark.parametrize("name", ["bump", "cube"])
+@pytest.mark.parametrize("name", ["bump", "cube", "ionization:4", "ionization:5"])
 def test_gmres_solves_match_oracle_full_size(name):
-    w = getattr(W, name)()
+    """GMRES(3)-smoothed solves to 1e-6 against the oracle's fixtures: the
+    511^2 bump medium, the 127^3 cube, and the ionization model of Sec. 4.3
+    (Table 8) at k0 = 4 and 5 on 511^2."""
+    base, _, arg = name.partition(":")
+    w = getattr(W, base)(*([int(arg)] if arg else []))
     fx = GOLDEN / f"{w['name']}_gmres.json"
     if not fx.exists():
         pytest.skip(f"fixture {fx.name} not written")

@@ -146,3 +146,37 @@ def test_theta_sweep_matches_oracle():
         _, info = mg.solve(dev(f), tol=1e-7)
         assert info[0]["status"] == "OK" and abs(info[0]["cycles"] - ref) <= 1, (d, info, ref)
         mg.close()
+
+
+@pytest.mark.parametrize("k0", [1, 2, 3])
+def test_ionization_model_matches_oracle(k0):
+    """Sec. 4.3's ionization model (Table 8 grid sizes, Dirichlet on x = 0 and
+    y = 0, ECS on the other sides, space-dependent coefficient and source):
+    FP64 cycle for cycle against the oracle to 1e-7, mixed to the same
+    residual; the Jacobi cycle diverges on both sides."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    w = W.ionization(k0)
+    n = w["n"]
+    H = O.build_hierarchy(n, 2, w["k2"], layers=w["layers"], smoother="gmres")
+    ref = O.solve(H, w["rhs"][0], tol=1e-7, max_cycles=600)
+    f = dev(w["rhs"])
+    mg = HelmholtzMG(n, k2=dev(w["k2"]), layers=w["layers"], smoother="gmres")
+    u, info = mg.solve(f, tol=1e-7)
+    assert info[0]["status"] == "OK" and abs(info[0]["cycles"] - ref.cycles) <= 1, (info, ref.cycles)
+    assert relerr(host(u)[0], ref.u) < 1e-8
+    mg.close()
+    mg = HelmholtzMG(n, k2=dev(w["k2"]), layers=w["layers"], smoother="gmres", precision="mixed")
+    u, info = mg.solve(f, tol=1e-7)
+    assert info[0]["status"] == "OK"
+    rho = np.linalg.norm(w["rhs"][0] - O.apply_operator(H.levels[0], host(u)[0])) / np.linalg.norm(w["rhs"][0])
+    assert rho <= 1e-7
+    assert relerr(host(u)[0], ref.u) < 1e-5
+    mg.close()
+    if k0 == 1:
+        Hj = O.build_hierarchy(n, 2, w["k2"], layers=w["layers"])
+        with pytest.raises(O.DivergedError):
+            O.solve(Hj, w["rhs"][0], tol=1e-7, max_cycles=600)
+        mg = HelmholtzMG(n, k2=dev(w["k2"]), layers=w["layers"])
+        _, info = mg.solve(f, tol=1e-7)
+        assert info[0]["status"] == "ERR_DIVERGED"
+        mg.close()

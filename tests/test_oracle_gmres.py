@@ -130,3 +130,34 @@ def test_theta_sweep_follows_table_5():
     i_min = int(np.argmin(got))
     assert [d for d, _ in table][i_min] in (8, 6, 5)
     assert got[0] > got[i_min] and got[-1] > got[i_min]
+
+
+def _table8():
+    rows = {}
+    for line in (GOLDEN / "table8_ionization.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            k0, n, c = map(int, line.split())
+            rows[k0] = (n, c)
+    return rows
+
+
+def test_ionization_model_matches_table8():
+    """Sec. 4.3's ionization model (Dirichlet on two sides, ECS on the others,
+    a space-dependent coefficient and source; the layer reading n/8 cells):
+    the oracle's GMRES(3)-smoothed cycle counts fall within 25 % of the
+    LVL-MG row of Table 8 for k0 = 1, 2, 3 and grow with k0, and the
+    weighted-Jacobi cycle diverges on this medium (the instability of
+    Eq. (jacstab))."""
+    table = _table8()
+    got = {}
+    for k0 in (1, 2, 3):
+        w = W.ionization(k0)
+        assert w["n"] == table[k0][0]
+        H = O.build_hierarchy(w["n"], 2, w["k2"], layers=w["layers"], smoother="gmres")
+        got[k0] = O.solve(H, w["rhs"][0], tol=1e-7, max_cycles=600).cycles
+        assert 0.75 * table[k0][1] <= got[k0] <= 1.25 * table[k0][1], (k0, got)
+    assert got[1] < got[2] < got[3]
+    w = W.ionization(1)
+    H = O.build_hierarchy(w["n"], 2, w["k2"], layers=w["layers"])
+    with pytest.raises(O.DivergedError):
+        O.solve(H, w["rhs"][0], tol=1e-7, max_cycles=600)
