@@ -85,7 +85,7 @@ def level_spacings(n_l, a, b, gamma):
     return np.diff(ecs_coordinate(x, a, b, gamma))
 
 
-def laplacian_1d(h):
+def laplacian_1d(h, sommerfeld_k=None, ends=(True, True)):
     """Three-point second difference on a (complex, non-uniform) grid, as the
     coefficients of -D2 at the n-1 interior nodes:
 
@@ -94,12 +94,31 @@ def laplacian_1d(h):
         dg_i = lo_i + up_i = 2/(h_{i-1} h_i).
 
     On the uniform real grid this is (-u_{i-1} + 2u_i - u_{i+1})/h^2, the
-    Laplacian of Eq. (HH)."""
+    Laplacian of Eq. (HH).  The end nodes are u = 0 (Dirichlet), or, with
+    sommerfeld_k = k, at the ends selected by `ends` (low, high), carry the
+    radiating condition du/dn = i k u of Table 4's model, discretised to
+    second order by the one-sided difference on the two end cells (uniform
+    spacing h there): (3 u_b - 4 u_{b-1} + u_{b-2}) / (2 h) = i k u_b, and
+    eliminated, u_b = (4 u_{b-1} - u_{b-2}) / (3 - 2 i k h).  The row next
+    to the end then couples to its two inner neighbours only: at the high
+    end dg -= 4 up / (3 - 2ikh) and lo -= up / (3 - 2ikh); mirrored at the
+    low end."""
     hm = h[:-1]
     hp = h[1:]
     lo = 2.0 / ((hm + hp) * hm)
     up = 2.0 / ((hm + hp) * hp)
-    return lo, lo + up, up
+    dg = lo + up
+    if sommerfeld_k is not None:
+        lo, dg, up = (x.astype(np.complex128) for x in (lo, dg, up))
+        if ends[0]:
+            d = 3.0 - 2j * sommerfeld_k * h[0]
+            dg[0] -= 4.0 * lo[0] / d
+            up[0] -= lo[0] / d
+        if ends[1]:
+            d = 3.0 - 2j * sommerfeld_k * h[-1]
+            dg[-1] -= 4.0 * up[-1] / d
+            lo[-1] -= up[-1] / d
+    return lo, dg, up
 
 
 # --------------------------------------------------------------------------
@@ -329,7 +348,7 @@ def lu_solve(lu, b):
 def build_hierarchy(n, dim, k2, layers=0, gamma=math.pi / 6,
                     theta_max=math.pi / 6, p=None, form="csl", c=None,
                     omega=0.8, nu1=1, nu2=1, coarsest=4, thetas=None,
-                    smoother="jacobi", m=3):
+                    smoother="jacobi", m=3, sommerfeld=False):
     """Level-dependent hierarchy for (-Delta - k^2) u = f on the unit square
     (cube) with n = 2^P intervals per dimension.
 
@@ -342,7 +361,10 @@ def build_hierarchy(n, dim, k2, layers=0, gamma=math.pi / 6,
     default 1.  `layers` is the ECS layer width in fine-grid points, one
     number for every side or a (lo, hi) pair; gamma is the ECS angle.
     k2 is the real fine-grid k^2 field (array of the interior shape) or a
-    constant; coarse levels inject it."""
+    constant; coarse levels inject it.  sommerfeld=True replaces the
+    Dirichlet condition at every end without an ECS layer by the radiating
+    condition of Table 4 (laplacian_1d; constant k only), on every level with
+    that level's spacing and the unshifted k."""
     P = int(round(math.log2(n)))
     if 2 ** P != n:
         raise ValueError("n must be a power of two")
@@ -354,6 +376,11 @@ def build_hierarchy(n, dim, k2, layers=0, gamma=math.pi / 6,
     a = layers[0] / n
     b = 1.0 - layers[1] / n
     k2 = np.asarray(k2, dtype=np.float64)
+    ksom = None
+    if sommerfeld:
+        if k2.ndim != 0:
+            raise ValueError("the radiating condition needs a constant k")
+        ksom = math.sqrt(float(k2))
     if k2.ndim == 0:
         k2 = np.full((n - 1,) * dim, float(k2))
     levels = []
@@ -362,7 +389,7 @@ def build_hierarchy(n, dim, k2, layers=0, gamma=math.pi / 6,
     k2_l = k2
     while True:
         h = level_spacings(n_l, a, b, gamma)
-        lo, dg, up = laplacian_1d(h)
+        lo, dg, up = laplacian_1d(h, ksom, (layers[0] == 0, layers[1] == 0))
         theta = thetas[l] if thetas is not None else l * dtheta
         if form == "csl":
             alpha, beta = 1.0 + 0j, np.exp(1j * theta)
@@ -384,7 +411,8 @@ def build_hierarchy(n, dim, k2, layers=0, gamma=math.pi / 6,
         raise ValueError(smoother)
     hier = Hierarchy(levels, list(c), omega, nu1, nu2, smoother=smoother, m=m)
     hier.lu = lu_factor(dense_matrix(levels[-1]))
-    hier.info = dict(dtheta=dtheta, p=p, a=a, b=b, gamma=gamma, form=form)
+    hier.info = dict(dtheta=dtheta, p=p, a=a, b=b, gamma=gamma, form=form,
+                     sommerfeld=bool(sommerfeld))
     return hier
 
 
@@ -547,7 +575,11 @@ def symmetrizer_weights(hier: Hierarchy):
 
 def adjoint_solve_symmetrized(hier: Hierarchy, g, tol=1e-6, max_cycles=20000):
     """A_0^H lambda = g through the forward solver:
-    lambda = conj(W y) with A_0 y = W^{-1} conj(g)."""
+    lambda = conj(W y) with A_0 y = W^{-1} conj(g).  (W A_0 is complex
+    symmetric for Dirichlet and ECS ends; the eliminated radiating condition
+    couples the end row to a second neighbour, which breaks that symmetry.)"""
+    if hier.info.get("sommerfeld"):
+        raise ValueError("the symmetrizer route needs Dirichlet or ECS ends")
     W = symmetrizer_weights(hier)
     res = solve(hier, np.conj(g) / W, tol=tol, max_cycles=max_cycles)
     return np.conj(W * res.u), res

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from paper_1211_4752_gb300 import workloads as W
 
 RTOL = 1e-12
 
@@ -400,3 +401,59 @@ def test_gradient_against_central_differences():
     eps = 1e-4 * np.abs(k2).max() / np.abs(v).max()
     fd = (loss_and_u(k2 + eps * v)[0] - loss_and_u(k2 - eps * v)[0]) / (2 * eps)
     assert abs(fd - np.sum(grad * v)) <= 1e-4 * abs(fd)
+
+
+# ---- Radiating (Sommerfeld) condition of Table 4 --------------------------
+
+def _reflection_1d(n, k):
+    """|B/A| of u_j = A lam^j + B lam^-j fitted to the 1-D solution of a
+    centre point source between two radiating ends, lam = e^{i kap h} the
+    discrete outgoing wave (cos kap h = 1 - k^2 h^2 / 2): the amplitude the
+    ends reflect."""
+    h = 1.0 / n
+    kap = math.acos(1 - k * k * h * h / 2) / h
+    lam = np.exp(1j * kap * h)
+    H = O.build_hierarchy(n, 1, k * k, sommerfeld=True)
+    j0 = n // 2 - 1
+    f = np.zeros(n - 1, dtype=np.complex128)
+    f[j0] = 1.0
+    u = np.linalg.solve(O.dense_matrix(H.levels[0]), f)
+    j1 = j0 + n // 8
+    M = np.array([[lam ** j1, lam ** (-j1)], [lam ** (j1 + 1), lam ** (-(j1 + 1))]])
+    a, b = np.linalg.solve(M, u[j1:j1 + 2])
+    return abs(b / a)
+
+
+def test_radiating_condition_reflects_at_second_order():
+    """The eliminated one-sided radiating condition lets the outgoing wave
+    leave: the reflected amplitude is below (kh)^2 and falls four-fold when h
+    halves (a sign error in i k, or a first-order difference, fails this)."""
+    k = 40.0
+    r = [_reflection_1d(n, k) for n in (128, 256, 512)]
+    for n, rr in zip((128, 256, 512), r):
+        assert rr < (k / n) ** 2, (n, r)
+    assert 3.0 < r[0] / r[1] < 5.0 and 3.0 < r[1] / r[2] < 5.0, r
+
+
+def test_radiating_condition_table4_cycles():
+    """Table 4 (constant k, radiating conditions on all sides, GMRES(3)
+    smoothing, centre source, tol 1e-7): the oracle's cycle counts are within
+    30 % of the printed LVL-MG row for k = 20, 40, 80 and grow with k."""
+    table = {20: (32, 23), 40: (64, 36), 80: (128, 64)}
+    got = {}
+    for k, (n, c) in table.items():
+        H = O.build_hierarchy(n, 2, float(k * k), sommerfeld=True, smoother="gmres")
+        f = W.point_sources(n, 2, [(n // 2 - 1, n // 2 - 1)])[0]
+        got[k] = O.solve(H, f, tol=1e-7, max_cycles=600).cycles
+        assert 0.7 * c <= got[k] <= 1.3 * c, (k, got)
+    assert got[20] < got[40] < got[80]
+
+
+def test_radiating_condition_converged_solution_matches_direct_solve():
+    H = O.build_hierarchy(32, 2, 300.0, sommerfeld=True, smoother="gmres")
+    f = W.random_field((31, 31), 8)
+    res = O.solve(H, f, tol=1e-12, max_cycles=2000)
+    ref = np.linalg.solve(O.dense_matrix(H.levels[0]), f.ravel()).reshape(f.shape)
+    assert np.linalg.norm(res.u - ref) <= 1e-9 * np.linalg.norm(ref)
+    with pytest.raises(ValueError):
+        O.adjoint_solve_symmetrized(H, f)
