@@ -86,6 +86,13 @@ typedef struct {
                        axis; 0 = plain homogeneous Dirichlet at that end */
   int layer_hi;     /* same at the high end; layer_lo + layer_hi < n */
   double ecs_angle; /* ECS rotation angle gamma in radians, 0 <= gamma < pi/2 */
+  int sommerfeld;   /* 1: every axis end without an ECS layer carries the
+                       radiating condition du/dn = i k u of Table 4 instead of
+                       u = 0, discretised to second order by the one-sided
+                       difference (3 u_b - 4 u_{b-1} + u_{b-2}) / (2 h) = i k u_b
+                       with the boundary node eliminated, on every level with
+                       its own h and the unshifted k; needs a constant k
+                       (k2_dev NULL).  0: Dirichlet (default) */
 } hh_grid;
 
 typedef struct {

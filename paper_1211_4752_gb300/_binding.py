@@ -34,7 +34,7 @@ HH_SMOOTH_GMRES = 1
 
 class HHGrid(ct.Structure):
     _fields_ = [("dim", ct.c_int), ("n", ct.c_int), ("layer_lo", ct.c_int),
-                ("layer_hi", ct.c_int), ("ecs_angle", ct.c_double)]
+                ("layer_hi", ct.c_int), ("ecs_angle", ct.c_double), ("sommerfeld", ct.c_int)]
 
 
 class HHShift(ct.Structure):

@@ -178,9 +178,14 @@ cd ecs_z(double x, double a, double b, double gamma) {
 }
 
 // -D2 on a level with n_l intervals: lo/dg/up at the n_l - 1 interior nodes of
-// the three-point formula on the non-uniform complex grid.
-void lap1d(int n_l, double a, double b, double gamma, std::vector<cd> &lo,
-           std::vector<cd> &dg, std::vector<cd> &up) {
+// the three-point formula on the non-uniform complex grid.  ksom > 0: at the
+// ends selected by som_lo / som_hi the end node carries the radiating
+// condition du/dn = i ksom u (Table 4), discretised to second order by the
+// one-sided difference on the two end cells, (3 u_b - 4 u_{b-1} + u_{b-2}) /
+// (2 h) = i k u_b, and eliminated: u_b = (4 u_{b-1} - u_{b-2}) / (3 - 2ikh),
+// which changes dg and the inner coupling of the row next to that end.
+void lap1d(int n_l, double a, double b, double gamma, double ksom, bool som_lo, bool som_hi,
+           std::vector<cd> &lo, std::vector<cd> &dg, std::vector<cd> &up) {
   std::vector<cd> h(n_l);
   cd zp = ecs_z(0.0, a, b, gamma);
   for (int i = 0; i < n_l; ++i) {
@@ -197,6 +202,17 @@ void lap1d(int n_l, double a, double b, double gamma, std::vector<cd> &lo,
     lo[i] = 2.0 / ((hm + hp) * hm);
     up[i] = 2.0 / ((hm + hp) * hp);
     dg[i] = lo[i] + up[i];
+  }
+  const cd I(0.0, 1.0);
+  if (ksom > 0.0 && som_lo) {
+    const cd d = 3.0 - 2.0 * I * ksom * h[0];
+    dg[0] -= 4.0 * lo[0] / d;
+    up[0] -= lo[0] / d;
+  }
+  if (ksom > 0.0 && som_hi) {
+    const cd d = 3.0 - 2.0 * I * ksom * h[n_l - 1];
+    dg[N - 1] -= 4.0 * up[N - 1] / d;
+    lo[N - 1] -= up[N - 1] / d;
   }
 }
 
@@ -1179,7 +1195,8 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
     cd c(1.0, 0.0);
     if (sh.c && l + 1 < L) c = cd(sh.c[2 * l], sh.c[2 * l + 1]);
     std::vector<cd> lo, dg, up;
-    lap1d(v.n, a, b, g.ecs_angle, lo, dg, up);
+    const double ksom = g.sommerfeld ? std::sqrt(k2_const) : 0.0;
+    lap1d(v.n, a, b, g.ecs_angle, ksom, g.layer_lo == 0, g.layer_hi == 0, lo, dg, up);
     const int N = v.N;
     std::vector<double2> t64[2];
     std::vector<float2> t32[2];
@@ -1648,6 +1665,13 @@ hh_status hh_setup(const hh_grid *grid, const double *k2_dev, double k2_const,
     return fail(HH_ERR_ARG, "ECS layers must be >= 0 with layer_lo + layer_hi < n");
   if (!(g.ecs_angle >= 0.0 && g.ecs_angle < M_PI / 2))
     return fail(HH_ERR_ARG, "ecs_angle must be in [0, pi/2)");
+  if (g.sommerfeld != 0 && g.sommerfeld != 1) return fail(HH_ERR_ARG, "sommerfeld must be 0 or 1");
+  if (g.sommerfeld && (k2_dev || !(k2_const > 0.0)))
+    return fail(HH_ERR_ARG, "the radiating condition needs a constant k^2 > 0 (k2_dev NULL)");
+  if (g.sommerfeld && (g.layer_lo > 0 && g.layer_hi > 0))
+    return fail(HH_ERR_ARG, "the radiating condition needs an end without an ECS layer");
+  if (g.sommerfeld && ((g.layer_lo == 0 && g.n < 4) || (g.layer_hi == 0 && g.n < 4)))
+    return fail(HH_ERR_ARG, "grid too small for the radiating condition");
   if (max_batch < 1 || max_batch > 4096) return fail(HH_ERR_ARG, "max_batch must be in 1..4096");
   hh_shift sh;
   hh_default_shift(&sh);

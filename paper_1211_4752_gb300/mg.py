@@ -31,14 +31,15 @@ class HelmholtzMG:
     (real tensor of the interior shape, any device) or a float; layers: ECS
     layer width in fine cells, one int or (lo, hi); form: 'csl' | 'csg';
     thetas / c: optional per-level angles / per-transfer residual scales;
-    precision: 'fp64' | 'mixed'."""
+    precision: 'fp64' | 'mixed'; sommerfeld: the radiating condition of
+    Table 4 at the ends without an ECS layer (constant k only)."""
 
     def __init__(self, n, dim=2, k2=0.0, layers=0, ecs_angle=math.pi / 6,
                  form="csl", theta_max=math.pi / 6, p=0, thetas=None, c=None,
                  omega=0.8, nu1=1, nu2=1, precision="fp64", coarsest=4,
                  max_cycles=20000, div_limit=1e3, inner_tol=1e-3,
                  max_inner=20000, max_batch=1, device=None, smoother="jacobi",
-                 gmres_m=3):
+                 gmres_m=3, sommerfeld=False):
         L = B.lib()
         self.n, self.dim, self.N = int(n), int(dim), int(n) - 1
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -46,7 +47,7 @@ class HelmholtzMG:
         self.max_batch = int(max_batch)
         self.precision = precision
         lo, hi = (layers, layers) if isinstance(layers, int) else tuple(layers)
-        g = B.HHGrid(self.dim, self.n, int(lo), int(hi), float(ecs_angle))
+        g = B.HHGrid(self.dim, self.n, int(lo), int(hi), float(ecs_angle), int(bool(sommerfeld)))
         sh = B.HHShift()
         L.hh_default_shift(ct.byref(sh))
         sh.form = B.HH_FORM_CSL if form == "csl" else B.HH_FORM_CSG

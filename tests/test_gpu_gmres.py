@@ -180,3 +180,57 @@ def test_ionization_model_matches_oracle(k0):
         _, info = mg.solve(f, tol=1e-7)
         assert info[0]["status"] == "ERR_DIVERGED"
         mg.close()
+
+
+@pytest.mark.parametrize("k,n", [(20, 32), (40, 64), (80, 128), (160, 256)])
+def test_radiating_condition_matches_oracle(k, n):
+    """Table 4's model (constant k, the radiating condition on every side, no
+    ECS layer, centre source): GMRES(3)-smoothed solves cycle for cycle
+    against the oracle (FP64) and to the same residual (mixed); the adjoint
+    against the oracle's conjugate-transposed hierarchy; weighted-Jacobi
+    cycles (the fused kernels and the tail operator) iterate for iterate."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    k2 = float(k * k)
+    f = W.point_sources(n, 2, [(n // 2 - 1, n // 2 - 1)])
+    H = O.build_hierarchy(n, 2, k2, sommerfeld=True, smoother="gmres")
+    ref = O.solve(H, f[0], tol=1e-7, max_cycles=600)
+    mg = HelmholtzMG(n, k2=k2, sommerfeld=True, smoother="gmres")
+    u, info = mg.solve(dev(f), tol=1e-7)
+    assert info[0]["status"] == "OK" and abs(info[0]["cycles"] - ref.cycles) <= 1, (info, ref.cycles)
+    assert relerr(host(u)[0], ref.u) < 1e-8
+    g = W.random_field(f.shape, 61)
+    lam, il = mg.adjoint(dev(g), tol=1e-7)
+    lref = O.solve(O.adjoint_hierarchy(H), g[0], tol=1e-7, max_cycles=600)
+    assert il[0]["status"] == "OK" and abs(il[0]["cycles"] - lref.cycles) <= 1
+    assert relerr(host(lam)[0], lref.u) < 1e-8
+    mg.close()
+    mg = HelmholtzMG(n, k2=k2, sommerfeld=True, smoother="gmres", precision="mixed")
+    u, info = mg.solve(dev(f), tol=1e-7)
+    assert info[0]["status"] == "OK"
+    rho = np.linalg.norm(f[0] - O.apply_operator(H.levels[0], host(u)[0])) / np.linalg.norm(f[0])
+    assert rho <= 1e-7 and relerr(host(u)[0], ref.u) < 1e-5
+    mg.close()
+    Hj = O.build_hierarchy(n, 2, k2, sommerfeld=True)
+    uj = np.zeros_like(f[0])
+    for _ in range(3):
+        uj = O.vcycle(Hj, 0, uj, f[0])
+    for precision, tol in (("fp64", 1e-10), ("mixed", 1e-5)):
+        mg = HelmholtzMG(n, k2=k2, sommerfeld=True, precision=precision)
+        got = host(mg.cycles(dev(f), dev(np.zeros_like(f)), 3))
+        assert relerr(got[0], uj) < tol, precision
+        mg.close()
+
+
+def test_radiating_condition_3d_cycles_match_oracle():
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n, k2 = 16, 64.0
+    f = W.random_field((1, 15, 15, 15), 62)
+    for sm in ("jacobi", "gmres"):
+        H = O.build_hierarchy(n, 3, k2, sommerfeld=True, smoother=sm)
+        u = np.zeros_like(f[0])
+        for _ in range(2):
+            u = O.vcycle(H, 0, u, f[0])
+        mg = HelmholtzMG(n, dim=3, k2=k2, sommerfeld=True, smoother=sm)
+        got = host(mg.cycles(dev(f), dev(np.zeros_like(f)), 2))
+        assert relerr(got[0], u) < 1e-10, sm
+        mg.close()

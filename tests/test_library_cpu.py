@@ -107,3 +107,14 @@ def test_python_layer_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         B.lib()
+
+
+def test_setup_rejects_bad_radiating_condition(hh):
+    L = hh.lib()
+    h = ct.c_void_p()
+    for grid, field, k2 in ((hh.HHGrid(2, 64, 8, 8, 0.5, 1), None, 100.0),   # no end without a layer
+                            (hh.HHGrid(2, 64, 0, 0, 0.5, 2), None, 100.0),   # bad flag
+                            (hh.HHGrid(2, 64, 0, 0, 0.5, 1), None, 0.0),     # k = 0
+                            (hh.HHGrid(2, 64, 0, 0, 0.5, 1), ct.c_void_p(8), 100.0)):  # k^2 field
+        assert L.hh_setup(ct.byref(grid), field, k2, None, None, 1, None, ct.byref(h)) == hh.HH_ERR_ARG
+        assert h.value is None
