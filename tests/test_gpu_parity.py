@@ -443,3 +443,32 @@ def test_max_cycles_and_divergence_status():
     mg2 = HelmholtzMG(n, k2=400.0, layers=4, max_cycles=5)
     u, info = mg2.solve(dev(point_rhs(n, 2, 1, 3)), tol=1e-10)
     assert info[0]["status"] == "ERR_NOT_CONVERGED" and info[0]["cycles"] == 5
+
+
+OMEGAS = [0.8, 0.8 + 0.2j, 0.8 - 0.2j, 0.7 + 0.3j, 0.7 - 0.3j, 0.6 - 0.4j, 1.0 - 0.3j,
+          0.5 + 0.5j]
+
+
+@pytest.mark.parametrize("layers", [16, 8])
+def test_complex_omega_jacobi_ablation_matches_oracle(layers):
+    """The weighted-Jacobi cycle with complex weights omega (Eq. (wjacobi)) on
+    Table 1's constant-k model (k = 40, 63^2, centre source, ECS n/4 and
+    n/8): cycle counts to 1e-6, or the cycle at which rho passes the
+    divergence limit, equal the oracle's (+-1) for every weight.  No fixed
+    weight converges where the real one diverges, the instability of fixed
+    Jacobi weights on the shifted levels (Eq. (jacstab)) that motivates GMRES
+    smoothing."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n, k2 = 64, 1600.0
+    f = W.point_sources(n, 2, [(n // 2 - 1, n // 2 - 1)])
+    for om in OMEGAS:
+        H = O.build_hierarchy(n, 2, k2, layers=layers, omega=om)
+        try:
+            ref = O.solve(H, f[0], tol=1e-6, max_cycles=3000)
+            want, cyc = "OK", ref.cycles
+        except O.DivergedError as e:
+            want, cyc = "ERR_DIVERGED", int(str(e).split("cycle ")[1].split(":")[0])
+        mg = HelmholtzMG(n, k2=k2, layers=layers, omega=om)
+        _, info = mg.solve(dev(f), tol=1e-6)
+        assert info[0]["status"] == want and abs(info[0]["cycles"] - cyc) <= 1, (om, info, want, cyc)
+        mg.close()
