@@ -59,6 +59,23 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over the ranks of the process group (x without one):
+    the job's time is the slowest replica's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mdofs(points_per_rank, steps, world, seconds):
+    """Whole-job throughput of `world` replicas (each solving points_per_rank
+    per step for `steps` steps) over the slowest replica's time."""
+    return points_per_rank * steps * world / seconds / 1e6
+
+
 def measured_peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -195,15 +212,12 @@ def run_ours(args):
         launches += mg.solve_kernels
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total = sum(times)
+    total = max_over_ranks(sum(times), dist, "cuda")
     if dist:
-        t = torch.tensor([total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
         dist.barrier()
     last = infos[-1]
     ok = all(i["status"] == "OK" for i in infos)
-    value = pts * args.steps * world / total / 1e6
+    value = job_mdofs(pts, args.steps, world, total)
 
     # end to end through the host-buffer C-ABI call (pinned host memory)
     fh = torch.from_numpy(w["rhs"][:1].copy()).pin_memory()
@@ -219,11 +233,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e_times.append(e0.elapsed_time(e1) / 1e3)
-    e2e_total = sum(e_times)
-    if dist:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e_times), dist, "cuda")
 
     # dominant kernel, timed live on this stream (level 0, back to back)
     import ctypes as ct
@@ -342,7 +352,7 @@ def run_ours(args):
                        "setup_s": setup_s},
             "solve": {"cycles": last["cycles"], "refinements": last["refinements"],
                       "rel_residual": last["rel_residual"], "all_ok": ok},
-            "e2e": {"value": pts * args.steps * world / e2e_total / 1e6, "unit": "MDOF/s",
+            "e2e": {"value": job_mdofs(pts, args.steps, world, e2e_total), "unit": "MDOF/s",
                     "h2d_bytes_per_step": pts * 16, "d2h_bytes_per_step": pts * 16},
             "roofline": roofline,
             "roofline_large": roofline_large,
