@@ -461,7 +461,7 @@ template <typename R> TailArgs<R> tail_args_from(hh_handle *h, int dir, int star
     a.lv[i].c = cscal<R>(h, l, dir);
   }
   using C = typename Cx<R>::T;
-  int off = 0, koff = 0, Ns[kMaxTail];
+  int off = 0, koff = 0, Ns[kMaxTail] = {};
   for (int i = 0; i < a.nl; ++i) {
     const int N = h->lv[start + i].N;
     Ns[i] = N;
@@ -1335,7 +1335,7 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
     // first level whose tail (it and every coarser level) fits in shared memory
     int t0 = 1;
     auto tail_bytes = [&](int t) {
-      int Ns[MAXL];
+      int Ns[MAXL] = {};
       for (int l = t; l < L; ++l) Ns[l - t] = h->lv[l].N;
       return h->opt.precision == HH_FP64 ? tail_smem_bytes<double>(Ns, L - t)
                                          : tail_smem_bytes<float>(Ns, L - t);
