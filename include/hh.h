@@ -44,6 +44,8 @@
 #ifndef HH_H
 #define HH_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -59,7 +61,10 @@ typedef enum {
   HH_ERR_OOM = 3,           /* device allocation failed */
   HH_ERR_NOT_CONVERGED = 4, /* max_cycles reached; best iterate left in u */
   HH_ERR_DIVERGED = 5,      /* rho_k > div_limit or not finite */
-  HH_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+  HH_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (a TMA tile copy
+                               or a grid barrier of the opt-in cooperative
+                               cycle); the iterate is not usable, the handle
+                               is, and the next solve starts afresh */
   HH_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
 } hh_status;
 
@@ -124,6 +129,29 @@ typedef struct {
                                 GMRES needs max_batch <= 64 and runs the
                                 per-step kernels (no fused 2-D path) */
   int gmres_m;               /* GMRES(m) Krylov dimension, 1..3 (default 3) */
+  const char *tuner_cache;   /* path of the autotuner's cache file, or NULL
+                                (default).  hh_setup looks up this handle's
+                                tuner key (hh_tuner_key) there; if present it
+                                takes the recorded tile shapes instead of
+                                timing them, else it times them and adds the
+                                key to the file (rewritten through a temporary
+                                file and a rename).  The same key then gives
+                                the same kernels, so identical inputs give
+                                bit-identical iterates and cycle counts across
+                                handles and processes.  HH_ERR_ARG if the file
+                                cannot be read or written.  The string is read
+                                during hh_setup only. */
+  void *(*dev_alloc)(size_t bytes, void *ctx);
+                             /* optional device allocator for the handle's
+                                workspace (NULL: cudaMalloc), e.g. a caching
+                                allocator of the calling framework; it must
+                                return memory of the handle's device aligned
+                                to 256 bytes, or NULL on failure (HH_ERR_OOM) */
+  void (*dev_free)(void *ptr, void *ctx);
+                             /* its release function (set both or neither);
+                                hh_destroy synchronizes the device first, so
+                                no kernel of the handle uses the memory */
+  void *alloc_ctx;           /* passed to dev_alloc / dev_free */
 } hh_options;
 
 typedef struct {
@@ -167,9 +195,12 @@ hh_status hh_solve(hh_handle *h, const void *rhs_dev, void *u_dev, int batch,
  * level-dependent V-cycle per iteration from a zero initial guess: the use
  * of the cycle as a preconditioner in Sec. 4.1 (Table 3, LVL-MG-FGMRES;
  * flexible GMRES because a cycle with GMRES smoothing is not a fixed linear
- * map).  The cycle is the handle's (precision, smoother, shift schedule);
- * the Krylov vectors, inner products and the least-squares problem are
- * complex128 / FP64 in either precision.
+ * map).  The cycle is the handle's (precision, smoother, shift schedule).
+ * HH_FP64 handles keep the whole Krylov process in complex128 / FP64.
+ * HH_MIXED handles keep the Krylov basis (V, Z, w) and its vector arithmetic
+ * in complex64 (block partial sums, the Hessenberg matrix, the Givens
+ * rotations and y in FP64), and every restart is an FP64 refinement step:
+ * A u, f - A u, u += Z y and the residual that ends a solve are complex128.
  *   rhs_dev   device, complex128[batch][N^dim], read only.
  *   u_dev     device, complex128[batch][N^dim]: initial guess if
  *             flags & HH_USE_GUESS (else ignored), solution on return.
@@ -285,6 +316,14 @@ hh_status hh_coarse_solve(hh_handle *h, const void *f_dev, void *e_dev,
 hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
                          int reps, double *ms, void *stream);
 
+/* The autotuner's key of this handle: the quantities its tile choices
+ * depend on (dimension, grid size, precision, ECS layers, constant or
+ * variable k^2, radiating ends, SM count and device name), as a string.
+ * Writes at most `len` bytes including the terminating zero into buf and
+ * returns the key's full length (without the zero), or -1 for a NULL
+ * handle. */
+int hh_tuner_key(const hh_handle *h, char *buf, int len);
+
 /* Hierarchy queries. */
 int hh_num_levels(const hh_handle *h);
 int hh_level_points(const hh_handle *h, int level); /* N_l per axis */
@@ -306,8 +345,8 @@ long long hh_solve_kernels(const hh_handle *h);
  * no fused kernel (3-D, nu1 or nu2 > 1, or the tail levels). */
 int hh_tile_shape(const hh_handle *h, int level, int *bx, int *by);
 
-/* Relative residuals rho_b = ||f_b - A_0 u_b||_2 / ||f_b||_2 (the quantity of
- * the stop test, Sec. 4.1) of caller arrays, with no allocation of any kind:
+/* Relative residuals rho_b = ||f_b - A_0 u_b||_2 / ||f_b||_2 of caller
+ * arrays (A_0 the finest, unshifted operator), with no allocation of any kind:
  * the block partial sums live in a fixed 1 MiB device array inside the
  * library (64 right-hand sides x 1024 blocks x 2 sums of FP64).  The paper
  * has no counterpart; it serves callers that must not allocate device memory
@@ -317,13 +356,24 @@ int hh_tile_shape(const hh_handle *h, int level, int *bx, int *by);
  *   rho_dev: device, batch doubles (out); 0 where f_b and r_b are zero,
  *   +inf where only f_b is zero.
  *   batch: 1..64, else HH_ERR_ARG.  Asynchronous on `stream`.
- * The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * outside any stream capture.  The array is shared by every handle on the
- * device: calls that overlap in time race, so order them (same stream, or
- * synchronize).  Nothing in it needs clearing between calls. */
+ * hh_setup looks up the array's device address (cudaGetSymbolAddress,
+ * with the handle's device current) and keeps it in the handle, so this
+ * call does no lookup and may be enqueued anywhere the handle may be used.
+ * The array is shared by every handle on the device: calls that overlap in
+ * time race, so order them (same stream, or synchronize).  Nothing in it
+ * needs clearing between calls: each call writes every slot it reads. */
 hh_status hh_rel_residual_static(hh_handle *h, const void *u_dev, const void *f_dev,
                                  int batch, double *rho_dev, void *stream);
+
+/* Test hook for the failure path of bounded device waits (no fault is
+ * involved).  With on != 0, every later solve on this handle makes one block
+ * of the opt-in cooperative cycle (HH_PERSIST=1 in the environment at
+ * hh_setup) leave without arriving at its first grid barrier; the other
+ * blocks' waits give up after about a second, the loop ends, and the solve
+ * returns HH_ERR_TIMEOUT with an unusable iterate.  on = 0 restores normal
+ * solves; the handle stays valid throughout.  HH_ERR_UNSUPPORTED for a handle
+ * without the cooperative cycle.  Synchronous. */
+hh_status hh_test_barrier_timeout(hh_handle *h, int on);
 
 /* Release the handle and its workspace (NULL is allowed). */
 hh_status hh_destroy(hh_handle *h);

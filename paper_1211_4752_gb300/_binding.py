@@ -48,7 +48,15 @@ class HHOptions(ct.Structure):
                 ("nu1", ct.c_int), ("nu2", ct.c_int), ("precision", ct.c_int),
                 ("coarsest", ct.c_int), ("max_cycles", ct.c_int),
                 ("div_limit", ct.c_double), ("inner_tol", ct.c_double),
-                ("max_inner", ct.c_int), ("smoother", ct.c_int), ("gmres_m", ct.c_int)]
+                ("max_inner", ct.c_int), ("smoother", ct.c_int), ("gmres_m", ct.c_int),
+                ("tuner_cache", ct.c_char_p),
+                ("dev_alloc", ct.c_void_p), ("dev_free", ct.c_void_p),
+                ("alloc_ctx", ct.c_void_p)]
+
+
+# allocator callbacks of hh_options (void *(size_t, void *), void (void *, void *))
+DEV_ALLOC = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p)
+DEV_FREE = ct.CFUNCTYPE(None, ct.c_void_p, ct.c_void_p)
 
 
 class HHSolveInfo(ct.Structure):
@@ -90,6 +98,8 @@ SIGNATURES = {
     "hh_solve_kernels": (ct.c_longlong, [_P]),
     "hh_rel_residual_static": (_I, [_P, _P, _P, _I, _P, _P]),
     "hh_tile_shape": (_I, [_P, _I, ct.POINTER(_I), ct.POINTER(_I)]),
+    "hh_tuner_key": (_I, [_P, ct.c_char_p, _I]),
+    "hh_test_barrier_timeout": (_I, [_P, _I]),
     "hh_destroy": (_I, [_P]),
     "hh_last_error": (ct.c_char_p, []),
 }

@@ -21,11 +21,21 @@
 #include <type_traits>
 #include <cstdlib>
 #include <cstring>
+#include <cctype>
+#include <unistd.h>
 #include <map>
 #include <string>
 #include <thread>
 #include <tuple>
 #include <vector>
+
+namespace hh {
+// hh_noalloc.cu: relative residuals with partial sums in a fixed device array
+hh_status rel_residual_static(const LevelK<double> &L, int dim, double *parts,
+                              const double2 *u, const double2 *f, int batch, double *rho,
+                              cudaStream_t s, std::string *msg);
+cudaError_t static_scratch_address(double **out);
+}  // namespace hh
 
 using cd = std::complex<double>;
 using namespace hh;
@@ -108,6 +118,7 @@ struct hh_handle {
   SolveParams *params = nullptr;
   int *flag = nullptr;
   int *flag_h = nullptr;           // pinned
+  int *err_h = nullptr;            // pinned copy of the status word
   SolveParams *params_h = nullptr;  // pinned
   SolveState *st_h = nullptr;       // pinned
   cudaStream_t cap = nullptr;       // private stream for graph capture
@@ -134,6 +145,7 @@ struct hh_handle {
   int persist = 0, persist_grid = 0;  // complex64 cycles as one cooperative launch
   PersistArgs pargs[2];             // its arguments per direction (per-call fields filled at launch)
   unsigned int *pbar = nullptr;     // its grid barrier (arrivals, generation)
+  int *pskip = nullptr;             // its test hook word (hh_test_barrier_timeout)
   double *gm_parts = nullptr;       // GMRES smoothing: partial sums,
   unsigned int *gm_counter = nullptr;  // last-block arrival counter,
   double *gm_gsc = nullptr;         // per right-hand side scalars
@@ -145,18 +157,44 @@ struct hh_handle {
   UpMaps umap[MAXL];
   std::vector<void *> allocs;
   std::map<std::tuple<int, int, int>, GraphEntry> graphs;
+  std::string tuner_path;           // autotuner cache file ("" = none)
+  double *static_scratch = nullptr;  // device address of the fixed array of
+                                     // hh_rel_residual_static (looked up at setup)
 
   double2 omega64() const { return make_double2(opt.omega_re, opt.omega_im); }
 };
 
 namespace {
 
+// Device memory of a handle: the caller's allocator where hh_options gives
+// one (e.g. a framework's caching allocator), else cudaMalloc.
+cudaError_t raw_alloc(const hh_handle *h, void **p, size_t bytes) {
+  if (h->opt.dev_alloc) {
+    *p = h->opt.dev_alloc(bytes, h->opt.alloc_ctx);
+    if (!*p) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(*p) % 256 != 0) {
+      h->opt.dev_free(*p, h->opt.alloc_ctx);
+      *p = nullptr;
+      return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+  }
+  return cudaMalloc(p, bytes);
+}
+void raw_free(const hh_handle *h, void *p) {
+  if (!p) return;
+  if (h->opt.dev_free) h->opt.dev_free(p, h->opt.alloc_ctx);
+  else cudaFree(p);
+}
+
 hh_status dev_alloc(hh_handle *h, void **p, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = raw_alloc(h, p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(HH_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+    if (e == cudaErrorInvalidValue)
+      return fail(HH_ERR_ARG, "the device allocator returned memory not aligned to 256 bytes");
+    return fail(HH_ERR_OOM, std::string("device allocation (") + std::to_string(bytes) +
                                 " bytes): " + cudaGetErrorString(e));
   }
   h->allocs.push_back(*p);
@@ -776,6 +814,9 @@ hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
   HH_TRY(set_params(h, batch, tol, s));
   HH_CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
   HH_CK(cudaMemsetAsync(h->copies, 0, sizeof(unsigned int), s));
+  // the cooperative cycle's grid barrier starts from zero arrivals (a wait
+  // that gave up in an earlier solve leaves a partial count behind)
+  if (h->pbar) HH_CK(cudaMemsetAsync(h->pbar, 0, 2 * sizeof(unsigned int), s));
   h->fixed_kernels = 3;   // norm of f, state init, final copy
   launch_norm2(h->w64.f[0], (size_t)l0.S, batch, h->partials, h->nparts, s);
   launch_state_init(h->st, h->partials, h->params, h->flag, s);
@@ -801,8 +842,9 @@ hh_status solve_core(hh_handle *h, int dir, const double2 *rhs,
   h->fixed_kernels += 2;
   for (int it = 0; it < h->opt.max_cycles + 2; ++it) {
     HH_CK(cudaMemcpyAsync(h->flag_h, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HH_CK(cudaMemcpyAsync(h->err_h, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     HH_CK(cudaStreamSynchronize(s));
-    if (*h->flag_h == 0) break;
+    if (*h->flag_h == 0 || *h->err_h) break;   // done, or a bounded wait gave up
     HH_TRY(run_loop(h, HH_MIXED, dir, batch, s));
     refine_dispatch(h, dir, h->u64[cur], 0, h->w32.u_post[0], h->u64[1 - cur], batch, s);
     cur = 1 - cur;
@@ -883,22 +925,26 @@ void free_krylov(hh_handle *h) {
     if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
   }
   h->kw_graphs.clear();
-  for (void *p : h->kw_mem) cudaFree(p);
+  for (void *p : h->kw_mem) raw_free(h, p);
   h->kw_mem.clear();
   h->kw = KrylovWork();
   h->kw_m = h->kw_b = h->kw_sms = 0;
 }
 
 void destroy_impl(hh_handle *h) {
+  // memory going back to a caller's allocator may be handed out again at
+  // once: no kernel of this handle may still use it
+  if (h->opt.dev_free) cudaDeviceSynchronize();
   free_krylov(h);
   for (auto &kv : h->graphs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
   }
   h->graphs.clear();
-  for (void *p : h->allocs) cudaFree(p);
+  for (void *p : h->allocs) raw_free(h, p);
   h->allocs.clear();
   if (h->flag_h) cudaFreeHost(h->flag_h);
+  if (h->err_h) cudaFreeHost(h->err_h);
   if (h->copies_h) cudaFreeHost(h->copies_h);
   if (h->params_h) cudaFreeHost(h->params_h);
   if (h->st_h) cudaFreeHost(h->st_h);
@@ -961,8 +1007,8 @@ hh_status build_tail_op(hh_handle *h, int dir, int start, float2 **out, cudaStre
   const int N = v.N, P = v.P, S = (int)v.S, M = N * N;
   const size_t n = (size_t)M * S;
   double2 *F = nullptr, *U = nullptr;
-  cudaError_t e = cudaMalloc(&F, n * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMalloc(&U, n * sizeof(double2));
+  cudaError_t e = raw_alloc(h, reinterpret_cast<void **>(&F), n * sizeof(double2));
+  if (e == cudaSuccess) e = raw_alloc(h, reinterpret_cast<void **>(&U), n * sizeof(double2));
   if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, n * sizeof(double2), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(U, 0, n * sizeof(double2), s);
   hh_status r = HH_OK;
@@ -979,8 +1025,9 @@ hh_status build_tail_op(hh_handle *h, int dir, int start, float2 **out, cudaStre
       if (e == cudaSuccess) e = cudaGetLastError();
     }
   }
-  if (F) cudaFree(F);
-  if (U) cudaFree(U);
+  if (F || U) cudaStreamSynchronize(s);   // (done above unless an allocation failed)
+  raw_free(h, F);
+  raw_free(h, U);
   if (r != HH_OK) return r;
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1096,6 +1143,8 @@ hh_status setup_persist(hh_handle *h, cudaStream_t s) {
   HH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   HH_TRY(dev_alloc_n(h, &h->pbar, 2));
   HH_CK(cudaMemsetAsync(h->pbar, 0, 2 * sizeof(unsigned int), s));
+  HH_TRY(dev_alloc_n(h, &h->pskip, 1));
+  HH_CK(cudaMemsetAsync(h->pskip, 0, sizeof(int), s));
   Work<float> &W = h->w32;
   for (int dir = 0; dir < 2; ++dir) {
     PersistArgs &a = h->pargs[dir];
@@ -1124,9 +1173,107 @@ hh_status setup_persist(hh_handle *h, cudaStream_t s) {
     a.tf = W.f[h->tail0];
     a.tu = W.u_post[h->tail0];
     a.bar = h->pbar;
+    a.skip = h->pskip;
   }
   h->persist = 1;
   h->persist_grid = bps * sms;
+  return HH_OK;
+}
+
+// ---- autotuner cache ------------------------------------------------------
+// A JSON object whose keys are tuner keys and whose values are the chosen
+// tile-shape indices, one per tuned level:
+//   {
+//    "v1 dim=2 n=1024 prec=mixed ...": [0, 0, 0, 3, 0],
+//    ...
+//   }
+// The format tag at the start of a key changes whenever the tuned set does,
+// so a file from another build is never misread.
+constexpr const char *kTunerFormat = "v1";
+
+std::string tuner_key(const hh_handle *h) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  cudaDeviceProp prop;
+  std::string dev = "unknown";
+  if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) dev = prop.name;
+  for (char &c : dev)
+    if (c == '"' || c == '\\' || (unsigned char)c < 32) c = '_';
+  char b[512];
+  std::snprintf(b, sizeof b, "%s dim=%d n=%d prec=%s layers=%d,%d k2=%s sommerfeld=%d sms=%d dev=%s",
+                kTunerFormat, h->dim, h->n, h->opt.precision == HH_MIXED ? "mixed" : "fp64",
+                h->grid.layer_lo, h->grid.layer_hi, h->kconst ? "const" : "field",
+                h->grid.sommerfeld, sms, dev.c_str());
+  return b;
+}
+
+// Read the cache file into m (a missing file is an empty cache).
+hh_status read_tuner_cache(const std::string &path, std::map<std::string, std::vector<int>> *m) {
+  m->clear();
+  FILE *fp = std::fopen(path.c_str(), "rb");
+  if (!fp) return HH_OK;
+  std::string t;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof buf, fp)) > 0) t.append(buf, got);
+  std::fclose(fp);
+  size_t i = t.find('{');
+  if (i == std::string::npos) return fail(HH_ERR_ARG, "tuner cache " + path + ": not a JSON object");
+  ++i;
+  auto skip = [&]() { while (i < t.size() && std::isspace((unsigned char)t[i])) ++i; };
+  for (;;) {
+    skip();
+    if (i < t.size() && t[i] == '}') return HH_OK;
+    if (i >= t.size() || t[i] != '"') break;
+    const size_t e = t.find('"', i + 1);
+    if (e == std::string::npos) break;
+    const std::string key = t.substr(i + 1, e - i - 1);
+    i = e + 1;
+    skip();
+    if (i >= t.size() || t[i] != ':') break;
+    ++i;
+    skip();
+    if (i >= t.size() || t[i] != '[') break;
+    ++i;
+    std::vector<int> v;
+    bool ok = false;
+    for (;;) {
+      skip();
+      if (i < t.size() && t[i] == ']') { ++i; ok = true; break; }
+      char *end = nullptr;
+      const long x = std::strtol(t.c_str() + i, &end, 10);
+      if (end == t.c_str() + i) break;
+      v.push_back((int)x);
+      i = end - t.c_str();
+      skip();
+      if (i < t.size() && t[i] == ',') ++i;
+    }
+    if (!ok) break;
+    (*m)[key] = v;
+    skip();
+    if (i < t.size() && t[i] == ',') ++i;
+  }
+  return fail(HH_ERR_ARG, "tuner cache " + path + ": malformed");
+}
+
+hh_status write_tuner_cache(const std::string &path, const std::map<std::string, std::vector<int>> &m) {
+  const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+  FILE *fp = std::fopen(tmp.c_str(), "wb");
+  if (!fp) return fail(HH_ERR_ARG, "tuner cache " + path + ": cannot write " + tmp);
+  std::fputs("{\n", fp);
+  size_t k = 0;
+  for (const auto &kv : m) {
+    std::fprintf(fp, " \"%s\": [", kv.first.c_str());
+    for (size_t j = 0; j < kv.second.size(); ++j) std::fprintf(fp, j ? ", %d" : "%d", kv.second[j]);
+    std::fputs(++k < m.size() ? "],\n" : "]\n", fp);
+  }
+  std::fputs("}\n", fp);
+  const bool ok = std::fflush(fp) == 0;
+  std::fclose(fp);
+  if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0) {
+    std::remove(tmp.c_str());
+    return fail(HH_ERR_ARG, "tuner cache " + path + ": cannot write");
+  }
   return HH_OK;
 }
 
@@ -1139,6 +1286,18 @@ hh_status autotune(hh_handle *h, cudaStream_t s) {
     return HH_OK;
   }
   const int tuned = h->mid ? h->mid0 : h->tail0;   // levels with per-level kernels
+  const std::string key = tuner_key(h);
+  std::map<std::string, std::vector<int>> cache;
+  if (!h->tuner_path.empty()) {
+    HH_TRY(read_tuner_cache(h->tuner_path, &cache));
+    const auto it = cache.find(key);
+    if (it != cache.end() && (int)it->second.size() == tuned &&
+        std::all_of(it->second.begin(), it->second.end(),
+                    [](int v) { return v >= 0 && v < kNumTileVariants; })) {
+      for (int l = 0; l < tuned; ++l) h->variant[l] = it->second[l];
+      return HH_OK;
+    }
+  }
   for (int l = 0; l < tuned; ++l) {
     if (h->opt.precision == HH_MIXED) HH_TRY(tune_level<float>(h, l, s, &h->variant[l]));
     else HH_TRY(tune_level<double>(h, l, s, &h->variant[l]));
@@ -1152,6 +1311,12 @@ hh_status autotune(hh_handle *h, cudaStream_t s) {
       HH_CK(cudaMemsetAsync(p, 0, np * sizeof(float2), s));
   }
   HH_CK(cudaStreamSynchronize(s));
+  if (!h->tuner_path.empty()) {
+    // merge into the file as it is now (another handle may have added keys)
+    HH_TRY(read_tuner_cache(h->tuner_path, &cache));
+    cache[key] = std::vector<int>(h->variant, h->variant + tuned);
+    HH_TRY(write_tuner_cache(h->tuner_path, cache));
+  }
   return HH_OK;
 }
 
@@ -1173,11 +1338,13 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   const double dtheta = sh.theta_max / p;
 
   HH_CK(cudaGetDevice(&h->device));
+  HH_CK(static_scratch_address(&h->static_scratch));
   HH_CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   HH_CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
   HH_CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   HH_CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   HH_CK(cudaMallocHost(&h->flag_h, sizeof(int)));
+  HH_CK(cudaMallocHost(&h->err_h, sizeof(int)));
   HH_CK(cudaMallocHost(&h->params_h, sizeof(SolveParams)));
   HH_CK(cudaMallocHost(&h->st_h, sizeof(SolveState) * h->max_batch));
 
@@ -1425,10 +1592,10 @@ hh_status ensure_krylov(hh_handle *h, int m, int batch, cudaStream_t s) {
   free_krylov(h);
   HH_CK(krylov_init());
   auto alloc = [&](void **p, size_t bytes) -> hh_status {
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = raw_alloc(h, p, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return fail(HH_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+      return fail(HH_ERR_OOM, std::string("device allocation (") + std::to_string(bytes) +
                                   " bytes) for the Krylov workspace: " + cudaGetErrorString(e));
     }
     h->kw_mem.push_back(*p);
@@ -1613,12 +1780,6 @@ hh_status fgmres_core(hh_handle *h, const double2 *rhs, double2 *u, int guess, i
 
 }  // namespace
 
-namespace hh {
-// hh_noalloc.cu: relative residuals with partial sums in a fixed device array
-hh_status rel_residual_static(const LevelK<double> &L, int dim, int device, const double2 *u,
-                              const double2 *f, int batch, double *rho, cudaStream_t s,
-                              std::string *msg);
-}  // namespace hh
 
 // ===========================================================================
 // C ABI
@@ -1694,10 +1855,14 @@ hh_status hh_setup(const hh_grid *grid, const double *k2_dev, double k2_const,
   if (o.smoother == HH_SMOOTH_GMRES && max_batch > kGmresMaxBatch)
     return fail(HH_ERR_ARG, "GMRES smoothing supports at most 64 right-hand sides per handle");
   if (!std::isfinite(k2_const)) return fail(HH_ERR_ARG, "k2_const must be finite");
+  if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
+    return fail(HH_ERR_ARG, "dev_alloc and dev_free must both be set or both be NULL");
 
   hh_handle *h = new hh_handle();
   h->grid = g;
   h->opt = o;
+  if (o.tuner_cache) h->tuner_path = o.tuner_cache;
+  h->opt.tuner_cache = nullptr;   // the caller's string is not kept
   h->max_batch = max_batch;
   const hh_status st = setup_impl(h, k2_dev, k2_const, sh, (cudaStream_t)stream);
   if (st != HH_OK) {
@@ -1741,14 +1906,37 @@ hh_status hh_rel_residual_static(hh_handle *h, const void *u_dev, const void *f_
   if (!u_dev || !f_dev || !rho_dev) return fail(HH_ERR_ARG, "u, f and rho must not be NULL");
   HH_TRY(ensure_device(h));
   std::string msg;
-  const hh_status st = rel_residual_static(levelk_dense<double>(h, 0, 0), h->dim, h->device,
-                                           (const double2 *)u_dev, (const double2 *)f_dev,
-                                           batch, rho_dev, (cudaStream_t)stream, &msg);
+  const hh_status st = rel_residual_static(levelk_dense<double>(h, 0, 0), h->dim,
+                                           h->static_scratch, (const double2 *)u_dev,
+                                           (const double2 *)f_dev, batch, rho_dev,
+                                           (cudaStream_t)stream, &msg);
   if (st != HH_OK) return fail(st, msg);
   return HH_OK;
 }
 
 long long hh_solve_kernels(const hh_handle *h) { return h ? h->last_kernels : -1; }
+
+int hh_tuner_key(const hh_handle *h, char *buf, int len) {
+  if (!h) return -1;
+  const std::string k = tuner_key(h);
+  if (buf && len > 0) {
+    const size_t n = std::min(k.size(), (size_t)len - 1);
+    std::memcpy(buf, k.data(), n);
+    buf[n] = 0;
+  }
+  return (int)k.size();
+}
+
+hh_status hh_test_barrier_timeout(hh_handle *h, int on) {
+  g_err.clear();
+  HH_TRY(check_handle(h));
+  HH_TRY(ensure_device(h));
+  if (!h->persist || !h->pskip)
+    return fail(HH_ERR_UNSUPPORTED, "the handle has no cooperative cycle (HH_PERSIST=1 at setup)");
+  const int v = on ? 1 : 0;
+  HH_CK(cudaMemcpy(h->pskip, &v, sizeof(int), cudaMemcpyHostToDevice));
+  return HH_OK;
+}
 
 int hh_tile_shape(const hh_handle *h, int level, int *bx, int *by) {
   const bool ok = h && h->fused && level >= 0 && level < h->tail0;

@@ -165,6 +165,10 @@ struct PersistArgs {
   unsigned int *copies;           // cycles run (counted by the stop test)
   int *err;                       // status word of bounded waits
   unsigned int *bar;              // grid barrier: arrival count, generation
+  const int *skip;                // test hook (device word, normally 0): when
+                                  // set, the last block returns instead of
+                                  // arriving at the first grid barrier, so the
+                                  // others' bounded waits run out
 };
 constexpr int kPersistBX = 60, kPersistBY = 16;
 size_t vcycle2d_smem();

@@ -17,7 +17,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 #include <algorithm>
 
@@ -86,41 +85,34 @@ __global__ void k_rel_residual_finish(const double *parts, int nparts, int batch
   }
 }
 
-// Device address of the scratch array, looked up once per device (with that
-// device current) and kept for the life of the process.
-constexpr int kMaxDevices = 64;
-std::mutex g_addr_mu;
-double *g_addr[kMaxDevices] = {};
+}  // namespace
 
-cudaError_t scratch_address(int device, double **out) {
-  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[device]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_rel_residual_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[device] = static_cast<double *>(p);
-  }
-  *out = g_addr[device];
+// Device address of the scratch array on the current device.  Host code may
+// not pass the array's name to a kernel (on the host it names a stand-in, not
+// device memory), so hh_setup looks the address up here, with the handle's
+// device current, and keeps it in the handle.  A handle is only valid in the
+// context it was set up in, so the kept address cannot outlive its context
+// (a device reset ends the handle too; a new hh_setup looks it up again).
+cudaError_t static_scratch_address(double **out) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_rel_residual_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double *>(p);
   return cudaSuccess;
 }
 
-}  // namespace
-
-hh_status rel_residual_static(const LevelK<double> &L, int dim, int device, const double2 *u,
-                              const double2 *f, int batch, double *rho, cudaStream_t s,
-                              std::string *msg) {
+hh_status rel_residual_static(const LevelK<double> &L, int dim, double *parts,
+                              const double2 *u, const double2 *f, int batch, double *rho,
+                              cudaStream_t s, std::string *msg) {
   if (batch < 1 || batch > kStaticMaxBatch) {
     *msg = "batch must be in 1..64 for hh_rel_residual_static";
     return HH_ERR_ARG;
   }
-  double *parts = nullptr;
-  cudaError_t e = scratch_address(device, &parts);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    *msg = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-    return HH_ERR_CUDA;
+  if (!parts) {
+    *msg = "the handle holds no scratch address";
+    return HH_ERR_ARG;
   }
+  cudaError_t e;
   const size_t pts = dim == 2 ? (size_t)L.N * L.N : (size_t)L.N * L.N * L.N;
   const int nparts = (int)std::min<size_t>(kStaticParts, (pts + 255) / 256);
   if (dim == 2)

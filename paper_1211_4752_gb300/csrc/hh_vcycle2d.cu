@@ -23,7 +23,10 @@
 // way before the next copy overwrites them.
 //
 // Every wait is bounded (about a second); a timeout sets the status word and
-// ends the block's work, and the blocks still waiting time out in turn.
+// ends the block's work, and the blocks still waiting time out in turn.  A
+// block that gives up also clears the loop condition, and a launch that
+// finds the status word already set returns at once, so a solve whose wait
+// ran out ends after at most one second per launch with HH_ERR_TIMEOUT.
 //
 // Opt-in (HH_PERSIST=1): on a GB300 at 1023^2 its ten grid barriers over the
 // resident blocks (3 per SM at this kernel's 80 registers) cost more than the
@@ -100,6 +103,14 @@ __device__ bool tile_wait(uint64_t *mbar, unsigned phase, int *err) {
   return true;
 }
 
+// End the cycle loop after a wait gave up (the stop test will not run).
+__device__ void give_up(const PersistArgs &A) {
+  if (threadIdx.x == 0) {
+    *A.flag = 0;
+    if (A.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)A.cond, 0u);
+  }
+}
+
 // The level-0 stop test (k_check's body for the in-kernel cycle): one warp
 // per right-hand side adds its tiles' partial sums in order.
 __device__ void stop_test(const PersistArgs &A, int per0) {
@@ -138,6 +149,11 @@ __global__ void __launch_bounds__(256, 3) k_vcycle2d(const __grid_constant__ Per
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *base = align_smem128(smem_raw);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(base + kOB);
+  // an earlier launch of this solve gave up: nothing to do (block-uniform)
+  if (*(volatile const int *)A.err) {
+    if (blockIdx.x == 0) give_up(A);
+    return;
+  }
   if (threadIdx.x == 0) {
     mbar_init(mbar, 1);
     mbar_fence_init();
@@ -175,7 +191,7 @@ __global__ void __launch_bounds__(256, 3) k_vcycle2d(const __grid_constant__ Per
         if (!A.kconst) tma_load_2d(base + SD::oK, &Lv.dm.k, x0 - 4, y0 - 1, mbar);
       }
       __syncthreads();
-      if (!tile_wait(mbar, phase, A.err)) return;
+      if (!tile_wait(mbar, phase, A.err)) { give_up(A); return; }
       phase ^= 1u;
       float acc = 0.f;
       C *vb = Lv.v + (size_t)b * L.S;
@@ -191,7 +207,10 @@ __global__ void __launch_bounds__(256, 3) k_vcycle2d(const __grid_constant__ Per
         if (threadIdx.x == 0) A.partials[(size_t)b * per0 + r] = s;
       }
     }
-    if (!grid_sync(A.bar, A.err)) return;
+    // test hook: the last block leaves without arriving (its tile copies have
+    // all landed; the decision is block-uniform)
+    if (l == 0 && A.skip && *(volatile const int *)A.skip && blockIdx.x == gridDim.x - 1) return;
+    if (!grid_sync(A.bar, A.err)) { give_up(A); return; }
     if (l == 0 && A.check && blockIdx.x == gridDim.x - 1) stop_test(A, per0);
   }
 
@@ -226,7 +245,7 @@ __global__ void __launch_bounds__(256, 3) k_vcycle2d(const __grid_constant__ Per
       }
     }
   }
-  if (!grid_sync(A.bar, A.err)) return;
+  if (!grid_sync(A.bar, A.err)) { give_up(A); return; }
 
   // ---- up passes ----
   for (int l = A.T - 1; l >= 0; --l) {
@@ -254,14 +273,14 @@ __global__ void __launch_bounds__(256, 3) k_vcycle2d(const __grid_constant__ Per
         if (!A.kconst) tma_load_2d(base + SU::oK, &Lv.um.k, x0, y0, mbar);
       }
       __syncthreads();
-      if (!tile_wait(mbar, phase, A.err)) return;
+      if (!tile_wait(mbar, phase, A.err)) { give_up(A); return; }
       phase ^= 1u;
       C *ob = Lv.u + (size_t)b * L.S;
       if (fast) up_compute<float, BX, BY, false, true>(L, ob, A.omega, A.kconst, x0, y0, base);
       else if (inner) up_compute<float, BX, BY, false, false>(L, ob, A.omega, A.kconst, x0, y0, base);
       else up_compute<float, BX, BY, true, false>(L, ob, A.omega, A.kconst, x0, y0, base);
     }
-    if (l > 0 && !grid_sync(A.bar, A.err)) return;
+    if (l > 0 && !grid_sync(A.bar, A.err)) { give_up(A); return; }
   }
 }
 

@@ -32,14 +32,17 @@ class HelmholtzMG:
     layer width in fine cells, one int or (lo, hi); form: 'csl' | 'csg';
     thetas / c: optional per-level angles / per-transfer residual scales;
     precision: 'fp64' | 'mixed'; sommerfeld: the radiating condition of
-    Table 4 at the ends without an ECS layer (constant k only)."""
+    Table 4 at the ends without an ECS layer (constant k only);
+    tuner_cache: path of the autotuner's cache file (hh_options.tuner_cache);
+    allocator: None (the library's cudaMalloc) or 'torch' (the handle's
+    workspace comes from torch's caching allocator on the handle's device)."""
 
     def __init__(self, n, dim=2, k2=0.0, layers=0, ecs_angle=math.pi / 6,
                  form="csl", theta_max=math.pi / 6, p=0, thetas=None, c=None,
                  omega=0.8, nu1=1, nu2=1, precision="fp64", coarsest=4,
                  max_cycles=20000, div_limit=1e3, inner_tol=1e-3,
                  max_inner=20000, max_batch=1, device=None, smoother="jacobi",
-                 gmres_m=3, sommerfeld=False):
+                 gmres_m=3, sommerfeld=False, tuner_cache=None, allocator=None):
         L = B.lib()
         self.n, self.dim, self.N = int(n), int(dim), int(n) - 1
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -81,6 +84,27 @@ class HelmholtzMG:
             raise ValueError("smoother must be 'jacobi' or 'gmres'")
         o.smoother = B.HH_SMOOTH_GMRES if smoother == "gmres" else B.HH_SMOOTH_JACOBI
         o.gmres_m = int(gmres_m)
+        if tuner_cache is not None:
+            self._tuner_path = str(tuner_cache).encode()
+            o.tuner_cache = self._tuner_path
+        self._alloc_cbs = None
+        if allocator == "torch":
+            dev_index = self.device.index if self.device.index is not None else torch.cuda.current_device()
+
+            def _alloc(nbytes, ctx):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev_index)
+                except RuntimeError:
+                    return None
+
+            def _free(ptr, ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cbs = (B.DEV_ALLOC(_alloc), B.DEV_FREE(_free))
+            o.dev_alloc = ct.cast(self._alloc_cbs[0], ct.c_void_p)
+            o.dev_free = ct.cast(self._alloc_cbs[1], ct.c_void_p)
+        elif allocator is not None:
+            raise ValueError("allocator must be None or 'torch'")
         self.k2_const = 0.0
         k2_ptr = ct.c_void_p(0)
         if isinstance(k2, torch.Tensor):
@@ -121,6 +145,14 @@ class HelmholtzMG:
     def solve_kernels(self):
         """Kernels launched by the last completed solve (-1 before one)."""
         return B.lib().hh_solve_kernels(self._h)
+
+    @property
+    def tuner_key(self):
+        """The autotuner's key of this handle (hh_tuner_key)."""
+        n = B.lib().hh_tuner_key(self._h, None, 0)
+        buf = ct.create_string_buffer(n + 1)
+        B.lib().hh_tuner_key(self._h, buf, n + 1)
+        return buf.value.decode()
 
     def tile_shape(self, level):
         """(bx, by) of the fused 2-D kernels on `level`, or None."""
@@ -198,6 +230,13 @@ class HelmholtzMG:
         with torch.cuda.device(self.device):
             B.check(B.lib().hh_grad_k2(self._h, _ptr(u), _ptr(lam), u.shape[0], _ptr(g), _stream()))
         return g
+
+    def test_barrier_timeout(self, on):
+        """Test hook of the bounded device waits (handles set up with
+        HH_PERSIST=1 only): while on, solves return HH_ERR_TIMEOUT after
+        about a second instead of converging; off restores normal solves."""
+        with torch.cuda.device(self.device):
+            B.check(B.lib().hh_test_barrier_timeout(self._h, int(bool(on))))
 
     # ---- step API (complex128, FP64 tables) ------------------------------
     def rel_residual_static(self, u, f):

@@ -472,3 +472,109 @@ def test_complex_omega_jacobi_ablation_matches_oracle(layers):
         _, info = mg.solve(dev(f), tol=1e-6)
         assert info[0]["status"] == want and abs(info[0]["cycles"] - cyc) <= 1, (om, info, want, cyc)
         mg.close()
+
+
+def test_bounded_wait_timeout_returns_status_and_handle_recovers(monkeypatch):
+    """The failure path of the bounded device waits, without a fault: with the
+    test hook on, one block of the cooperative cycle leaves without arriving
+    at its first grid barrier; the others' waits give up after about a
+    second, the solve returns HH_ERR_TIMEOUT, and the next solve on the same
+    handle (hook off) converges to the same iterate as before."""
+    import time
+    from paper_1211_4752_gb300 import HelmholtzMG
+    from paper_1211_4752_gb300 import _binding as B
+    n = 64
+    kw = dict(k2=1600.0, layers=16, max_batch=1, precision="mixed")
+    monkeypatch.setenv("HH_PERSIST", "1")
+    mg = HelmholtzMG(n, **kw)
+    monkeypatch.delenv("HH_PERSIST")
+    assert mg.cycle_kernels == 1          # the cooperative cycle is in use
+    src = dev(W.point_sources(n, 2, [(31, 31)]))
+    u0, i0 = mg.solve(src, tol=1e-6)
+    assert i0[0]["status"] == "OK"
+    mg.test_barrier_timeout(True)
+    t0 = time.perf_counter()
+    with pytest.raises(B.HHError) as ei:
+        mg.solve(src, tol=1e-6)
+    assert ei.value.status == B.HH_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    mg.test_barrier_timeout(False)
+    u1, i1 = mg.solve(src, tol=1e-6)
+    assert i1[0]["status"] == "OK" and i1[0]["cycles"] == i0[0]["cycles"]
+    assert torch.equal(u0, u1)
+    la, il = mg.adjoint(src, tol=1e-6)
+    assert il[0]["status"] == "OK"
+    mg.close()
+    plain = HelmholtzMG(n, **kw)          # no cooperative cycle: the hook is refused
+    with pytest.raises(B.HHError) as ei:
+        plain.test_barrier_timeout(True)
+    assert ei.value.status == B.HH_ERR_UNSUPPORTED
+    plain.close()
+
+
+def test_tuner_cache_gives_identical_handles(tmp_path):
+    """hh_options.tuner_cache: the first handle times the tile shapes and
+    records them under its key; a second handle built from the same file
+    takes them without timing, so the two give bit-identical solutions and
+    cycle counts.  A recorded choice is used as written; a malformed file is
+    an argument error."""
+    import json
+    from paper_1211_4752_gb300 import HelmholtzMG
+    from paper_1211_4752_gb300 import _binding as B
+    n = 256
+    path = tmp_path / "tuner.json"
+    kw = dict(k2=(0.625 * n) ** 2, layers=8, max_batch=2, precision="mixed", tuner_cache=path)
+    a = HelmholtzMG(n, **kw)
+    data = json.loads(path.read_text())
+    key = a.tuner_key
+    assert key in data and key.startswith("v1 dim=2 n=256 prec=mixed")
+    levels = [l for l in range(a.levels) if a.tile_shape(l) is not None]
+    assert len(data[key]) == len(levels)
+    b = HelmholtzMG(n, **kw)
+    assert [a.tile_shape(l) for l in levels] == [b.tile_shape(l) for l in levels]
+    src = np.stack([W.point_sources(n, 2, [(127, 127)])[0], W.point_sources(n, 2, [(90, 160)])[0]])
+    ua, ia = a.solve(dev(src), tol=1e-6)
+    ub, ib = b.solve(dev(src), tol=1e-6)
+    assert all(i["status"] == "OK" for i in ia)
+    assert [i["cycles"] for i in ia] == [i["cycles"] for i in ib]
+    assert torch.equal(ua, ub)
+    a.close()
+    b.close()
+    data[key] = [4] * len(levels)             # shape 4 is 28 x 16
+    path.write_text(json.dumps(data))
+    c = HelmholtzMG(n, **kw)
+    assert all(c.tile_shape(l) == (28, 16) for l in levels)
+    c.close()
+    path.write_text("{ not json")
+    with pytest.raises(B.HHError) as ei:
+        HelmholtzMG(n, **kw)
+    assert ei.value.status == B.HH_ERR_ARG
+
+
+def test_torch_caching_allocator_serves_the_workspace(tmp_path):
+    """hh_options.dev_alloc / dev_free: with allocator='torch' the whole
+    workspace (levels, tail operator, FGMRES vectors) comes from torch's
+    caching allocator and goes back to it on close; solutions equal those of
+    a handle on the library's own allocations (same tuner cache)."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n = 128
+    kw = dict(k2=(0.625 * n) ** 2, layers=4, max_batch=2, precision="mixed",
+              tuner_cache=tmp_path / "t.json")
+    ref = HelmholtzMG(n, **kw)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    mg = HelmholtzMG(n, allocator="torch", **kw)
+    during = torch.cuda.memory_allocated()
+    assert during - before > 6 * (n - 1) * n * 8   # at least the level-0 arrays
+    src = dev(np.stack([W.point_sources(n, 2, [(63, 63)])[0], W.point_sources(n, 2, [(40, 80)])[0]]))
+    u1, i1 = mg.solve(src, tol=1e-6)
+    u0, i0 = ref.solve(src, tol=1e-6)
+    assert all(i["status"] == "OK" for i in i1)
+    assert torch.equal(u0, u1)
+    g1, j1 = mg.fgmres(src, tol=1e-6, restart=8)
+    assert all(i["status"] == "OK" for i in j1)
+    assert torch.cuda.memory_allocated() > during   # the Krylov workspace
+    mg.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
+    ref.close()

@@ -1,9 +1,9 @@
-"""hh_rel_residual_static, whose partial sums live in a fixed device array
-(no allocation), against the existing entry points: the residual that
-hh_solve reports for the iterate it returns, and f - hh_apply(u).
-
-The file name sorts last so that it also runs after every other test in the
-same process (the scratch array is shared process-wide)."""
+"""hh_rel_residual_static keeps its partial sums in a fixed device array
+inside the library instead of allocating.  Its residuals are checked against
+the existing entry points: the residual hh_solve reports for the iterate it
+returns, and f - hh_apply(u) evaluated here.  The array is shared by every
+call in the process, so the tests fill it on purpose with a full 64-RHS call
+first and then check that smaller calls read only what they wrote."""
 
 import numpy as np
 import pytest
@@ -21,10 +21,25 @@ def _apply_residuals(mg, u, f):
     return np.array([np.linalg.norm(r[b]) / np.linalg.norm(fn[b]) for b in range(f.shape[0])])
 
 
-def test_static_residual_matches_solve_and_apply_on_consecutive_calls():
+def _fill_scratch():
+    """One call at the 64-RHS limit on a 1023^2 grid (all 1024 block slots
+    of every right-hand side written with nonzero sums)."""
     from paper_1211_4752_gb300 import HelmholtzMG
+    n = 1024
+    mg = HelmholtzMG(n, k2=(0.625 * n) ** 2, layers=32, max_batch=1)
+    u = torch.from_numpy(W.random_field((1, n - 1, n - 1), 11)).cuda().expand(64, -1, -1).contiguous()
+    f = torch.from_numpy(W.random_field((1, n - 1, n - 1), 12)).cuda().expand(64, -1, -1).contiguous()
+    rho = mg.rel_residual_static(u, f).cpu().numpy()
+    assert np.all(np.isfinite(rho)) and np.all(rho > 0)
+    mg.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_static_residual_matches_solve_and_apply_on_consecutive_calls(precision):
+    from paper_1211_4752_gb300 import HelmholtzMG
+    _fill_scratch()
     n, k, layers = 64, 40.0, 4
-    mg = HelmholtzMG(n, k2=k * k, layers=layers, max_batch=3)
+    mg = HelmholtzMG(n, k2=k * k, layers=layers, max_batch=3, precision=precision)
     rng = np.random.default_rng(5)
     pos = [tuple(rng.integers(n // 4, 3 * n // 4, size=2)) for _ in range(3)]
     f = torch.from_numpy(W.point_sources(n, 2, pos) + 0.1 * W.random_field((3, n - 1, n - 1), 6)).cuda()
@@ -41,9 +56,22 @@ def test_static_residual_matches_solve_and_apply_on_consecutive_calls():
         assert np.allclose(rho, ref, rtol=1e-10, atol=1e-13)
         seen.append(rho)
     assert np.all(seen[1] < 1e-9) and np.all(seen[0] > 1e-9)
-    # a smaller batch right after a larger one reads only what it wrote
+    # a smaller batch after larger ones reads only what it wrote
     one = mg.rel_residual_static(u[:1].contiguous(), f[:1].contiguous()).cpu().numpy()
     assert abs(one[0] - seen[1][0]) <= 1e-12 * seen[1][0]
+    mg.close()
+
+
+def test_static_residual_3d():
+    from paper_1211_4752_gb300 import HelmholtzMG
+    _fill_scratch()
+    n = 16
+    mg = HelmholtzMG(n, dim=3, k2=100.0, layers=2, max_batch=2)
+    u = torch.from_numpy(W.random_field((2, n - 1, n - 1, n - 1), 21)).cuda()
+    f = torch.from_numpy(W.random_field((2, n - 1, n - 1, n - 1), 22)).cuda()
+    for _ in range(2):                    # two calls in a row
+        rho = mg.rel_residual_static(u, f).cpu().numpy()
+        assert np.allclose(rho, _apply_residuals(mg, u, f), rtol=1e-12, atol=0.0)
     mg.close()
 
 
