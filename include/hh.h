@@ -324,6 +324,14 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
  * handle. */
 int hh_tuner_key(const hh_handle *h, char *buf, int len);
 
+/* The coarse schedule of the fused 2-D path, as chosen at setup: levels
+ * 1 .. T-1 (T the first level of the small-level kernel) run as consecutive
+ * groups, one launch per group and direction; a group of J > 1 levels runs
+ * the multi-level passes, a group of one the per-level kernels.  Writes the
+ * group sizes J in order into levels (at most cap entries) and returns the
+ * number of groups (0 where the path is not used; -1 for a NULL handle). */
+int hh_coarse_schedule(const hh_handle *h, int *levels, int cap);
+
 /* Hierarchy queries. */
 int hh_num_levels(const hh_handle *h);
 int hh_level_points(const hh_handle *h, int level); /* N_l per axis */
@@ -342,7 +350,8 @@ long long hh_solve_kernels(const hh_handle *h);
 
 /* Tile shape (fine points, x by y) of the fused 2-D kernels on level l, as
  * chosen at setup; returns 1, or 0 with *bx = *by = 0 where the level runs
- * no fused kernel (3-D, nu1 or nu2 > 1, or the tail levels). */
+ * no per-level fused kernel (3-D, nu1 or nu2 > 1, the tail levels, or a
+ * level inside a multi-level group of hh_coarse_schedule). */
 int hh_tile_shape(const hh_handle *h, int level, int *bx, int *by);
 
 /* Relative residuals rho_b = ||f_b - A_0 u_b||_2 / ||f_b||_2 of caller

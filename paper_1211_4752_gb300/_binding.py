@@ -99,6 +99,7 @@ SIGNATURES = {
     "hh_rel_residual_static": (_I, [_P, _P, _P, _I, _P, _P]),
     "hh_tile_shape": (_I, [_P, _I, ct.POINTER(_I), ct.POINTER(_I)]),
     "hh_tuner_key": (_I, [_P, ct.c_char_p, _I]),
+    "hh_coarse_schedule": (_I, [_P, ct.POINTER(_I), _I]),
     "hh_test_barrier_timeout": (_I, [_P, _I]),
     "hh_destroy": (_I, [_P]),
     "hh_last_error": (ct.c_char_p, []),

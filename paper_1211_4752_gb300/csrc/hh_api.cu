@@ -22,6 +22,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cctype>
+#include <functional>
 #include <unistd.h>
 #include <map>
 #include <string>
@@ -127,6 +128,13 @@ struct hh_handle {
   int kconst = 0;                   // k^2 constant: kernels use LevelK::kc
   double k2c = 0.0;                 // that constant
   int variant[MAXL] = {};           // tile shape per fused level (autotuned)
+  // schedule of the fused levels 1 .. tail0-1: consecutive groups of J levels
+  // run by one launch per direction (J = 1: the per-level kernels; J > 1:
+  // the multi-level kernels with tiles b (down, on level a+J) and B (up, on
+  // level a)); chosen by the autotuner
+  struct CoarseGroup { int a, J, b, B; };
+  int ngroups = 0;
+  CoarseGroup groups[MAXL];
   int parts_cap = 0;                // capacity of `partials` per RHS
   cudaStream_t side = nullptr;      // branch of the stop test in the fused cycle
   cudaStream_t grp = nullptr;       // this handle's stream in a group solve (lazy)
@@ -553,6 +561,75 @@ void enqueue_tail(hh_handle *h, int dir, int batch, const SolveState *st, cudaSt
   launch_tail2d<R>(tail_args<R>(h, dir), batch, st, s);
 }
 
+template <typename R, int J>
+CoarseDownArgs<R, J> coarse_down_args(hh_handle *h, int dir, const hh_handle::CoarseGroup &G) {
+  Work<R> &W = work<R>(h);
+  CoarseDownArgs<R, J> a{};
+  for (int j = 0; j < J; ++j) {
+    a.K[j] = levelk<R>(h, G.a + j, dir);
+    a.v[j] = W.u_pre[G.a + j];
+    a.cs[j] = cscal<R>(h, G.a + j, dir);
+  }
+  for (int j = 0; j <= J; ++j) {
+    a.f[j] = W.f[G.a + j];
+    a.lay[j] = lay_of(h, G.a + j);
+  }
+  a.f0 = W.f[G.a];
+  a.omega = omega<R>(h, dir);
+  a.b = G.b;
+  a.kconst = h->kconst;
+  return a;
+}
+template <typename R, int J>
+CoarseUpArgs<R, J> coarse_up_args(hh_handle *h, int dir, const hh_handle::CoarseGroup &G) {
+  Work<R> &W = work<R>(h);
+  CoarseUpArgs<R, J> a{};
+  for (int j = 0; j < J; ++j) {
+    a.K[j] = levelk<R>(h, G.a + j, dir);
+    a.v[j] = W.u_pre[G.a + j];
+    a.f[j] = W.f[G.a + j];
+  }
+  for (int j = 0; j <= J; ++j) a.lay[j] = lay_of(h, G.a + j);
+  a.e = W.u_post[G.a + J];
+  a.u = W.u_post[G.a];
+  a.omega = omega<R>(h, dir);
+  a.B = G.B;
+  a.kconst = h->kconst;
+  return a;
+}
+
+// Down passes of the levels 1 .. tail0-1 by the handle's coarse schedule
+// (every one of these levels starts from a zero initial guess).
+template <typename R>
+void enqueue_coarse_down(hh_handle *h, int dir, int batch, const SolveState *st, cudaStream_t s) {
+  Work<R> &W = work<R>(h);
+  for (int g = 0; g < h->ngroups; ++g) {
+    const hh_handle::CoarseGroup &G = h->groups[g];
+    if (G.J == 1)
+      launch_down2d<R>(h->variant[G.a], h->dmap[G.a], levelk<R>(h, G.a, dir), ZERO_ALL,
+                       W.u_pre[G.a], W.f[G.a + 1], cscal<R>(h, G.a, dir), omega<R>(h, dir),
+                       h->kconst, lay_of(h, G.a + 1), batch, st, nullptr, h->err, s);
+    else if (G.J == 2)
+      launch_down2d_multi<R, 2>(coarse_down_args<R, 2>(h, dir, G), batch, st, s);
+    else
+      launch_down2d_multi<R, 3>(coarse_down_args<R, 3>(h, dir, G), batch, st, s);
+  }
+}
+template <typename R>
+void enqueue_coarse_up(hh_handle *h, int dir, int batch, const SolveState *st, cudaStream_t s) {
+  Work<R> &W = work<R>(h);
+  for (int g = h->ngroups - 1; g >= 0; --g) {
+    const hh_handle::CoarseGroup &G = h->groups[g];
+    if (G.J == 1)
+      launch_up2d<R>(h->variant[G.a], h->umap[G.a], levelk<R>(h, G.a, dir), W.u_post[G.a],
+                     omega<R>(h, dir), h->kconst, batch, st, h->err, s);
+    else if (G.J == 2)
+      launch_up2d_multi<R, 2>(coarse_up_args<R, 2>(h, dir, G), batch, st, s);
+    else
+      launch_up2d_multi<R, 3>(coarse_up_args<R, 3>(h, dir, G), batch, st, s);
+  }
+}
+
 // The same V-cycle with the fused 2-D kernels: one down pass per level
 // (pre-smoothing + residual + restriction), one kernel for every level from
 // tail0 to the coarsest, one up pass per level (correction + post-smoothing).
@@ -582,7 +659,8 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
   // complex64 cycles with the cluster kernel: per-level kernels above mid0
   bool mid = false;
   if constexpr (std::is_same<R, float>::value) mid = h->mid != 0;
-  const int T = mid ? h->mid0 : h->tail0;
+  // levels 1 .. T-1 run per level (cluster path) or by the coarse schedule
+  const int T = mid ? h->mid0 : (h->ngroups ? 1 : h->tail0);
   for (int l = 0; l < T; ++l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
     const bool norm = l == 0 && stop_test(check);
@@ -595,7 +673,9 @@ void enqueue_cycle_fused(hh_handle *h, int dir, int batch, int zero0, int check,
     if constexpr (std::is_same<R, float>::value)
       launch_mid2d<float>(h->margs[dir], h->midcl, batch, st, s);
   } else {
+    enqueue_coarse_down<R>(h, dir, batch, st, s);
     enqueue_tail<R>(h, dir, batch, st, s);
+    enqueue_coarse_up<R>(h, dir, batch, st, s);
   }
   for (int l = T - 1; l >= 0; --l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
@@ -1189,7 +1269,7 @@ hh_status setup_persist(hh_handle *h, cudaStream_t s) {
 //   }
 // The format tag at the start of a key changes whenever the tuned set does,
 // so a file from another build is never misread.
-constexpr const char *kTunerFormat = "v1";
+constexpr const char *kTunerFormat = "v2";
 
 std::string tuner_key(const hh_handle *h) {
   int sms = 0;
@@ -1277,44 +1357,201 @@ hh_status write_tuner_cache(const std::string &path, const std::map<std::string,
   return HH_OK;
 }
 
+// Candidate coarse schedules for levels 1 .. n: every composition of n into
+// groups of 1 .. kMaxMulti levels, each multi-level group with one of its tile
+// options ((b, B) = (8, 32) or (4, 16) for two levels, (4, 16) for three).
+// The first candidate is the default (groups of two from level 1).
+void coarse_candidates(int n, std::vector<std::vector<hh_handle::CoarseGroup>> *out) {
+  out->clear();
+  std::vector<hh_handle::CoarseGroup> def;
+  for (int a = 1; a <= n; a += 2) def.push_back({a, std::min(2, n - a + 1), 8, 32});
+  out->push_back(def);
+  std::vector<hh_handle::CoarseGroup> cur;
+  std::function<void(int)> rec = [&](int a) {
+    if (a > n) {
+      bool same = cur.size() == def.size();
+      for (size_t i = 0; same && i < cur.size(); ++i)
+        same = cur[i].J == def[i].J && cur[i].b == def[i].b && cur[i].B == def[i].B;
+      if (!same) out->push_back(cur);
+      return;
+    }
+    for (int J = 1; J <= kMaxMulti && a + J - 1 <= n; ++J) {
+      const int opts = J == 2 ? 2 : 1;
+      for (int o = 0; o < opts; ++o) {
+        const int b = (J == 2 && o == 0) ? 8 : 4, B = (J == 2 && o == 0) ? 32 : 16;
+        cur.push_back({a, J, b, B});
+        rec(a + J);
+        cur.pop_back();
+      }
+    }
+  };
+  rec(1);
+}
+
+// Time the coarse part of a cycle (down groups, tail, up groups) under the
+// schedule in h->groups: a captured graph of that part, best of three trials
+// of ten replays.
+template <typename R> hh_status time_coarse(hh_handle *h, cudaStream_t s, float *ms) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  HH_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  enqueue_coarse_down<R>(h, 0, 1, nullptr, h->cap);
+  enqueue_tail<R>(h, 0, 1, nullptr, h->cap);
+  enqueue_coarse_up<R>(h, 0, 1, nullptr, h->cap);
+  HH_CK(cudaStreamEndCapture(h->cap, &g));
+  const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  HH_CK(ei);
+  cudaEvent_t e0, e1;
+  HH_CK(cudaEventCreate(&e0));
+  HH_CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  HH_CK(cudaGraphLaunch(ex, s));
+  for (int trial = 0; trial < 3; ++trial) {
+    HH_CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < 10; ++r) HH_CK(cudaGraphLaunch(ex, s));
+    HH_CK(cudaEventRecord(e1, s));
+    HH_CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    HH_CK(cudaEventElapsedTime(&t, e0, e1));
+    best = std::min(best, t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ex);
+  HH_CK(cudaGetLastError());
+  *ms = best / 10.f;
+  return HH_OK;
+}
+
+template <typename R> hh_status tune_schedule(hh_handle *h, cudaStream_t s) {
+  std::vector<std::vector<hh_handle::CoarseGroup>> cand;
+  coarse_candidates(h->tail0 - 1, &cand);
+  float tbest = 1e30f;
+  size_t best = 0;
+  for (size_t c = 0; c < cand.size(); ++c) {
+    h->ngroups = (int)cand[c].size();
+    std::copy(cand[c].begin(), cand[c].end(), h->groups);
+    float t = 0.f;
+    HH_TRY(time_coarse<R>(h, s, &t));
+    if (t < 0.97f * tbest) { tbest = t; best = c; }   // a later one must win by 3 %
+  }
+  h->ngroups = (int)cand[best].size();
+  std::copy(cand[best].begin(), cand[best].end(), h->groups);
+  return HH_OK;
+}
+
+// A schedule given as "J1,J2,..." (HH_COARSE in the environment; multi-level
+// groups take their first tile option).
+bool parse_schedule(const char *txt, int n, hh_handle *h) {
+  std::vector<hh_handle::CoarseGroup> g;
+  int a = 1;
+  for (const char *p = txt; *p;) {
+    char *end = nullptr;
+    const long J = std::strtol(p, &end, 10);
+    if (end == p || J < 1 || J > kMaxMulti) return false;
+    g.push_back({a, (int)J, J == 2 ? 8 : 4, J == 2 ? 32 : 16});
+    a += (int)J;
+    p = *end == ',' ? end + 1 : end;
+    if (*end && *end != ',') return false;
+  }
+  if (a != n + 1) return false;
+  h->ngroups = (int)g.size();
+  std::copy(g.begin(), g.end(), h->groups);
+  return true;
+}
+
+// Cached schedule: ngroups, then (J, b, B) per group, after the variants.
+bool schedule_from(const std::vector<int> &v, size_t at, int n, hh_handle *h) {
+  if (at >= v.size()) return false;
+  const int ng = v[at];
+  if (ng < 0 || v.size() != at + 1 + 3 * (size_t)ng) return false;
+  std::vector<hh_handle::CoarseGroup> g;
+  int a = 1;
+  for (int i = 0; i < ng; ++i) {
+    const int J = v[at + 1 + 3 * i], b = v[at + 2 + 3 * i], B = v[at + 3 + 3 * i];
+    if (J < 1 || J > kMaxMulti || b < 1 || b > 64 || B < 1 || B > 128 ||
+        (J > 1 && B % (2 << J) != 0))
+      return false;
+    g.push_back({a, J, b, B});
+    a += J;
+  }
+  if (ng > 0 && a != n + 1) return false;
+  h->ngroups = ng;
+  std::copy(g.begin(), g.end(), h->groups);
+  return true;
+}
+
+// Setup-time tuning of the fused 2-D path: the tile shape of every level's
+// per-level kernels, their tensor maps, and the coarse schedule.  Choices
+// come from (in order) HH_TILE_VARIANT / HH_COARSE in the environment, the
+// tuner cache, or timing.
 hh_status autotune(hh_handle *h, cudaStream_t s) {
+  const int tuned = h->mid ? h->mid0 : h->tail0;   // levels with per-level kernels
+  const std::string key = tuner_key(h);
+  std::map<std::string, std::vector<int>> cache;
+  const std::vector<int> *hit = nullptr;
+  if (!h->tuner_path.empty()) {
+    HH_TRY(read_tuner_cache(h->tuner_path, &cache));
+    const auto it = cache.find(key);
+    if (it != cache.end() && (int)it->second.size() > tuned &&
+        std::all_of(it->second.begin(), it->second.begin() + tuned,
+                    [](int v) { return v >= 0 && v < kNumTileVariants; }))
+      hit = &it->second;
+  }
+  bool timed = false;
   const char *force = std::getenv("HH_TILE_VARIANT");
   if (force) {
     const int v = std::atoi(force);
     if (v < 0 || v >= kNumTileVariants) return fail(HH_ERR_ARG, "HH_TILE_VARIANT out of range");
     for (int l = 0; l < h->tail0; ++l) h->variant[l] = v;
-    return HH_OK;
+  } else if (hit) {
+    for (int l = 0; l < tuned; ++l) h->variant[l] = (*hit)[l];
+  } else {
+    for (int l = 0; l < tuned; ++l) {
+      if (h->opt.precision == HH_MIXED) HH_TRY(tune_level<float>(h, l, s, &h->variant[l]));
+      else HH_TRY(tune_level<double>(h, l, s, &h->variant[l]));
+    }
+    timed = true;
   }
-  const int tuned = h->mid ? h->mid0 : h->tail0;   // levels with per-level kernels
-  const std::string key = tuner_key(h);
-  std::map<std::string, std::vector<int>> cache;
-  if (!h->tuner_path.empty()) {
-    HH_TRY(read_tuner_cache(h->tuner_path, &cache));
-    const auto it = cache.find(key);
-    if (it != cache.end() && (int)it->second.size() == tuned &&
-        std::all_of(it->second.begin(), it->second.end(),
-                    [](int v) { return v >= 0 && v < kNumTileVariants; })) {
-      for (int l = 0; l < tuned; ++l) h->variant[l] = it->second[l];
-      return HH_OK;
+  for (int l = 0; l < h->tail0; ++l) {
+    if (h->opt.precision == HH_FP64) HH_TRY(make_maps<double>(h, l, h->variant[l], &h->dmap[l], &h->umap[l]));
+    else HH_TRY(make_maps<float>(h, l, h->variant[l], &h->dmap[l], &h->umap[l]));
+  }
+  h->ngroups = 0;
+  if (!h->mid && h->tail0 > 1) {
+    const char *ce = std::getenv("HH_COARSE");
+    if (ce) {
+      if (!parse_schedule(ce, h->tail0 - 1, h))
+        return fail(HH_ERR_ARG, "HH_COARSE must list group sizes 1..3 covering the coarse levels");
+    } else if (!(hit && !force && schedule_from(*hit, tuned, h->tail0 - 1, h))) {
+      if (h->opt.precision == HH_MIXED) HH_TRY(tune_schedule<float>(h, s));
+      else HH_TRY(tune_schedule<double>(h, s));
+      timed = true;
     }
   }
-  for (int l = 0; l < tuned; ++l) {
-    if (h->opt.precision == HH_MIXED) HH_TRY(tune_level<float>(h, l, s, &h->variant[l]));
-    else HH_TRY(tune_level<double>(h, l, s, &h->variant[l]));
+  if (timed) {
+    // the tuning runs overwrote workspace: clear it again
+    for (int l = 0; l < h->L; ++l) {
+      const size_t np = (size_t)h->lv[l].S * h->max_batch;
+      for (double2 *p : {h->w64.u_pre[l], h->w64.u_post[l], h->w64.f[l]})
+        HH_CK(cudaMemsetAsync(p, 0, np * sizeof(double2), s));
+      for (float2 *p : {h->w32.u_pre[l], h->w32.u_post[l], h->w32.f[l]})
+        HH_CK(cudaMemsetAsync(p, 0, np * sizeof(float2), s));
+    }
+    HH_CK(cudaStreamSynchronize(s));
   }
-  // the tuning runs overwrote workspace: clear it again
-  for (int l = 0; l < h->L; ++l) {
-    const size_t np = (size_t)h->lv[l].S * h->max_batch;
-    for (double2 *p : {h->w64.u_pre[l], h->w64.u_post[l], h->w64.f[l]})
-      HH_CK(cudaMemsetAsync(p, 0, np * sizeof(double2), s));
-    for (float2 *p : {h->w32.u_pre[l], h->w32.u_post[l], h->w32.f[l]})
-      HH_CK(cudaMemsetAsync(p, 0, np * sizeof(float2), s));
-  }
-  HH_CK(cudaStreamSynchronize(s));
-  if (!h->tuner_path.empty()) {
+  if (!h->tuner_path.empty() && timed && !force) {
     // merge into the file as it is now (another handle may have added keys)
     HH_TRY(read_tuner_cache(h->tuner_path, &cache));
-    cache[key] = std::vector<int>(h->variant, h->variant + tuned);
+    std::vector<int> v(h->variant, h->variant + tuned);
+    v.push_back(h->ngroups);
+    for (int g = 0; g < h->ngroups; ++g) {
+      v.push_back(h->groups[g].J);
+      v.push_back(h->groups[g].b);
+      v.push_back(h->groups[g].B);
+    }
+    cache[key] = v;
     HH_TRY(write_tuner_cache(h->tuner_path, cache));
   }
   return HH_OK;
@@ -1526,6 +1763,10 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
       }
       HH_CK(init_cycle2d<float>());
       HH_CK(init_cycle2d<double>());
+      HH_CK((init_multi2d<float, 2>()));
+      HH_CK((init_multi2d<float, 3>()));
+      HH_CK((init_multi2d<double, 2>()));
+      HH_CK((init_multi2d<double, 3>()));
     }
   }
   h->parts_cap = partial_blocks(h->lv[0].pts);
@@ -1567,10 +1808,6 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
       for (int dir = 0; dir < 2; ++dir) HH_TRY(build_tail_op(h, dir, h->tail0, &h->tailop[dir], s));
     if (op && h->opt.precision == HH_MIXED) HH_TRY(setup_mid(h, s));
     HH_TRY(autotune(h, s));
-    for (int l = 0; l < h->tail0; ++l) {
-      if (h->opt.precision == HH_FP64) HH_TRY(make_maps<double>(h, l, h->variant[l], &h->dmap[l], &h->umap[l]));
-      else HH_TRY(make_maps<float>(h, l, h->variant[l], &h->dmap[l], &h->umap[l]));
-    }
     if (op) HH_TRY(setup_persist(h, s));
   }
   h->nparts = h->fused ? tile_parts(h->variant[0], h->lv[0].N) : partial_blocks(h->lv[0].pts);
@@ -1891,8 +2128,10 @@ int hh_level_points(const hh_handle *h, int level) {
 int hh_cycle_kernels(const hh_handle *h) {
   if (!h) return 0;
   if (h->persist && h->opt.precision == HH_MIXED) return 1;   // one cooperative launch
-  if (h->fused)   // down passes, stop test, tail (or cluster kernel), up passes
-    return 2 * (h->mid && h->opt.precision == HH_MIXED ? h->mid0 : h->tail0) + 2;
+  if (h->fused) {  // down passes, stop test, tail (or cluster kernel), up passes
+    if (h->mid && h->opt.precision == HH_MIXED) return 2 * h->mid0 + 2;
+    return 2 * (1 + h->ngroups) + 2;
+  }
   if (h->opt.smoother == HH_SMOOTH_GMRES)   // per level: steps of 2m + 2 kernels,
     return (h->L - 1) * ((h->opt.nu1 + h->opt.nu2) * (2 * h->opt.gmres_m + 2) + 2) + 2;
   // per level nu1 sweeps, residual + restriction, nu2 sweeps; stop test; LU
@@ -1915,6 +2154,13 @@ hh_status hh_rel_residual_static(hh_handle *h, const void *u_dev, const void *f_
 }
 
 long long hh_solve_kernels(const hh_handle *h) { return h ? h->last_kernels : -1; }
+
+int hh_coarse_schedule(const hh_handle *h, int *levels, int cap) {
+  if (!h) return -1;
+  for (int g = 0; g < h->ngroups && g < cap; ++g)
+    if (levels) levels[g] = h->groups[g].J;
+  return h->ngroups;
+}
 
 int hh_tuner_key(const hh_handle *h, char *buf, int len) {
   if (!h) return -1;
@@ -1939,7 +2185,10 @@ hh_status hh_test_barrier_timeout(hh_handle *h, int on) {
 }
 
 int hh_tile_shape(const hh_handle *h, int level, int *bx, int *by) {
-  const bool ok = h && h->fused && level >= 0 && level < h->tail0;
+  bool ok = h && h->fused && level >= 0 && level < h->tail0;
+  for (int g = 0; ok && g < h->ngroups; ++g)   // levels of a multi-level pass
+    if (h->groups[g].J > 1 && level >= h->groups[g].a && level < h->groups[g].a + h->groups[g].J)
+      ok = false;
   if (bx) *bx = ok ? tile_bx(h->variant[level]) : 0;
   if (by) *by = ok ? tile_by(h->variant[level]) : 0;
   return ok ? 1 : 0;

@@ -175,6 +175,61 @@ size_t vcycle2d_smem();
 cudaError_t init_vcycle2d(int *blocks_per_sm);
 cudaError_t launch_vcycle2d(const PersistArgs &a, int grid, cudaStream_t s);
 
+// Fused passes over J consecutive coarse levels a .. a+J-1 (hh_coarse2d.cu),
+// all starting from a zero initial guess.
+// Down: from f_a, writes v_{a+j} (j < J) and f_{a+j} (1 <= j <= J); blocks own
+// b x b tiles of level a+J.
+template <typename R, int J> struct CoarseDownArgs {
+  LevelK<R> K[J];                  // operators of levels a .. a+J-1
+  const typename Cx<R>::T *f0;     // f_a
+  typename Cx<R>::T *v[J];         // v_{a+j} (pre-smoothed iterates)
+  typename Cx<R>::T *f[J + 1];     // f_{a+j}, j >= 1 (f[0] unused)
+  Lay lay[J + 1];                  // layouts of levels a .. a+J
+  typename Cx<R>::T cs[J];         // restriction scales c_{a+j}
+  typename Cx<R>::T omega;
+  int b;                           // tile width on level a+J
+  int kconst;
+};
+// Up: from u_{a+J}, v_{a+j}, f_{a+j}, writes u_a; blocks own B x B tiles of
+// level a (B a multiple of 2^(J+1)).
+template <typename R, int J> struct CoarseUpArgs {
+  LevelK<R> K[J];
+  const typename Cx<R>::T *e;      // u_{a+J}
+  const typename Cx<R>::T *v[J];
+  const typename Cx<R>::T *f[J];
+  typename Cx<R>::T *u;            // u_a
+  Lay lay[J + 1];
+  typename Cx<R>::T omega;
+  int B;
+  int kconst;
+};
+constexpr int kMaxMulti = 3;       // levels per fused coarse pass
+constexpr int kMultiMaxPts = 12 * 256;   // largest region of a multi-level pass (points)
+template <int J> int multi_max_pts(int b, int B);
+
+// Per-axis regions of the up pass for a tile [x0, x0 + B) of level a:
+// o[j], w[j] = origin and width of U_j (j = 0 .. J); W_j is U_j widened by
+// one point at each end.  Shared by the kernel and the host's size query.
+__host__ __device__ inline void up_multi_regions(int x0, int B, int J, int *o, int *w) {
+  o[0] = x0;
+  w[0] = B;
+  for (int j = 0; j < J; ++j) {
+    const int lo = o[j] - 1, hi = o[j] + w[j];    // W_j, inclusive
+    o[j + 1] = ((lo + 1) >> 1) - 1;               // ceil(lo / 2) - 1 (lo >= -1)
+    w[j + 1] = (hi >> 1) - o[j + 1] + 1;          // .. floor(hi / 2)
+  }
+}
+
+template <typename R, int J> size_t down2d_multi_smem(int b, int kconst);
+template <typename R, int J> size_t up2d_multi_smem(int B, int kconst);
+template <typename R, int J> cudaError_t init_multi2d();
+template <typename R, int J>
+void launch_down2d_multi(const CoarseDownArgs<R, J> &a, int batch, const SolveState *st,
+                         cudaStream_t s);
+template <typename R, int J>
+void launch_up2d_multi(const CoarseUpArgs<R, J> &a, int batch, const SolveState *st,
+                       cudaStream_t s);
+
 void launch_unit_rhs(double2 *F, int N, int P, int S, cudaStream_t s);
 void launch_tail_gather(const double2 *U, float2 *T, int N, int P, int S, cudaStream_t s);
 void launch_tail_apply(const float2 *T, int N, int P, int S, const float2 *f, float2 *u,

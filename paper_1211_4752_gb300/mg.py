@@ -147,6 +147,14 @@ class HelmholtzMG:
         return B.lib().hh_solve_kernels(self._h)
 
     @property
+    def coarse_schedule(self):
+        """Group sizes of the fused coarse passes (levels 1 .. T-1), [] if none."""
+        n = B.lib().hh_coarse_schedule(self._h, None, 0)
+        arr = (ct.c_int * max(n, 1))()
+        B.lib().hh_coarse_schedule(self._h, arr, n)
+        return [arr[i] for i in range(max(n, 0))]
+
+    @property
     def tuner_key(self):
         """The autotuner's key of this handle (hh_tuner_key)."""
         n = B.lib().hh_tuner_key(self._h, None, 0)

@@ -527,10 +527,14 @@ def test_tuner_cache_gives_identical_handles(tmp_path):
     a = HelmholtzMG(n, **kw)
     data = json.loads(path.read_text())
     key = a.tuner_key
-    assert key in data and key.startswith("v1 dim=2 n=256 prec=mixed")
+    assert key in data and key.startswith("v2 dim=2 n=256 prec=mixed")
+    sched = a.coarse_schedule
+    tuned = 1 + sum(sched)                    # levels 0 .. T-1 carry a tile shape
+    assert data[key][tuned] == len(sched)     # then the schedule: groups, (J, b, B) each
+    assert data[key][tuned + 1::3] == sched
     levels = [l for l in range(a.levels) if a.tile_shape(l) is not None]
-    assert len(data[key]) == len(levels)
     b = HelmholtzMG(n, **kw)
+    assert b.coarse_schedule == sched
     assert [a.tile_shape(l) for l in levels] == [b.tile_shape(l) for l in levels]
     src = np.stack([W.point_sources(n, 2, [(127, 127)])[0], W.point_sources(n, 2, [(90, 160)])[0]])
     ua, ia = a.solve(dev(src), tol=1e-6)
@@ -540,10 +544,11 @@ def test_tuner_cache_gives_identical_handles(tmp_path):
     assert torch.equal(ua, ub)
     a.close()
     b.close()
-    data[key] = [4] * len(levels)             # shape 4 is 28 x 16
+    data[key] = [4] * tuned + [1, tuned - 1, 4, 16]   # shape 4 is 28 x 16; one group
     path.write_text(json.dumps(data))
     c = HelmholtzMG(n, **kw)
-    assert all(c.tile_shape(l) == (28, 16) for l in levels)
+    assert c.coarse_schedule == [tuned - 1]
+    assert c.tile_shape(0) == (28, 16)
     c.close()
     path.write_text("{ not json")
     with pytest.raises(B.HHError) as ei:
@@ -560,21 +565,28 @@ def test_torch_caching_allocator_serves_the_workspace(tmp_path):
     n = 128
     kw = dict(k2=(0.625 * n) ** 2, layers=4, max_batch=2, precision="mixed",
               tuner_cache=tmp_path / "t.json")
+    import gc
     ref = HelmholtzMG(n, **kw)
+    src = dev(np.stack([W.point_sources(n, 2, [(63, 63)])[0], W.point_sources(n, 2, [(40, 80)])[0]]))
+    gc.collect()          # earlier tests' garbage must not be freed while we count
+    gc.disable()
     torch.cuda.synchronize()
     before = torch.cuda.memory_allocated()
     mg = HelmholtzMG(n, allocator="torch", **kw)
     during = torch.cuda.memory_allocated()
     assert during - before > 6 * (n - 1) * n * 8   # at least the level-0 arrays
-    src = dev(np.stack([W.point_sources(n, 2, [(63, 63)])[0], W.point_sources(n, 2, [(40, 80)])[0]]))
     u1, i1 = mg.solve(src, tol=1e-6)
     u0, i0 = ref.solve(src, tol=1e-6)
     assert all(i["status"] == "OK" for i in i1)
     assert torch.equal(u0, u1)
     g1, j1 = mg.fgmres(src, tol=1e-6, restart=8)
     assert all(i["status"] == "OK" for i in j1)
-    assert torch.cuda.memory_allocated() > during   # the Krylov workspace
+    results = sum(t.numel() * t.element_size() for t in (u0, u1, g1))
+    assert torch.cuda.memory_allocated() > during + results   # the Krylov workspace
     mg.close()
+    del u0, u1, g1
     torch.cuda.synchronize()
-    assert torch.cuda.memory_allocated() == before
+    after = torch.cuda.memory_allocated()
+    gc.enable()
+    assert after == before
     ref.close()
