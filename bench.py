@@ -188,9 +188,16 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    fgm = args.solver == "fgmres"
+
+    def solve_once(rhs):
+        if fgm:
+            return mg.fgmres(rhs, tol=args.tol, restart=args.fgmres_restart)
+        return mg.solve(rhs, tol=args.tol)
+
     infos = []
     for _ in range(args.warmup):
-        _, info = mg.solve(f, tol=args.tol)
+        _, info = solve_once(f)
         infos.append(info[0])
     torch.cuda.synchronize()
     if dist:
@@ -204,7 +211,7 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, info = mg.solve(f, tol=args.tol)
+        _, info = solve_once(f)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
@@ -219,17 +226,25 @@ def run_ours(args):
     ok = all(i["status"] == "OK" for i in infos)
     value = job_mdofs(pts, args.steps, world, total)
 
-    # end to end through the host-buffer C-ABI call (pinned host memory)
+    # end to end through the host-buffer C-ABI call (pinned host memory);
+    # FGMRES: pinned copies in and out around the device call
     fh = torch.from_numpy(w["rhs"][:1].copy()).pin_memory()
     uh = torch.empty_like(fh).pin_memory()
-    mg.solve_host(fh, uh, tol=args.tol)
+
+    def e2e_once():
+        if fgm:
+            u_d, _ = solve_once(fh.to("cuda", non_blocking=True))
+            uh.copy_(u_d, non_blocking=True)
+        else:
+            mg.solve_host(fh, uh, tol=args.tol)
+    e2e_once()
     e_times = []
     for _ in range(args.steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        mg.solve_host(fh, uh, tol=args.tol)
+        e2e_once()
         e1.record(stream)
         e1.synchronize()
         e_times.append(e0.elapsed_time(e1) / 1e3)
@@ -295,12 +310,14 @@ def run_ours(args):
     if mixed and args.compare_fp64:
         mg64 = HelmholtzMG(n, dim=dim, k2=k2_t, layers=w["layers"], precision="fp64", max_batch=1,
                            smoother=args.smoother)
-        mg64.solve(f, tol=args.tol)
+        solve64 = ((lambda r: mg64.fgmres(r, tol=args.tol, restart=args.fgmres_restart)) if fgm
+                   else (lambda r: mg64.solve(r, tol=args.tol)))
+        solve64(f)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, i64 = mg64.solve(f, tol=args.tol)
+        _, i64 = solve64(f)
         e1.record(stream)
         e1.synchronize()
         s64 = e0.elapsed_time(e1) / 1e3
@@ -311,7 +328,7 @@ def run_ours(args):
     # the same problem by flexible GMRES with one cycle per iteration as the
     # preconditioner (Table 3's LVL-MG-FGMRES), timed once after a warm-up
     fg = None
-    if args.fgmres_restart > 0:
+    if args.fgmres_restart > 0 and not fgm:
         mg.fgmres(f, tol=args.tol, restart=args.fgmres_restart)
         torch.cuda.synchronize()
         flush.fill_(1.0)
@@ -327,8 +344,14 @@ def run_ours(args):
               "restarts": ifg[0]["refinements"], "rel_residual": ifg[0]["rel_residual"],
               "status": ifg[0]["status"], "kernels": mg.solve_kernels}
 
+    batched = None
+    if args.batched and args.workload == "ecs_const" and not fgm:
+        batched = group_record(args, max(1, min(args.steps, 2)), 1)
+
     cpu = cpu_all = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and fgm:
+        cpu = cpu_baseline_fgmres(w, args, last["cycles"])
+    elif rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args, last["cycles"])
         if args.cpu_all_cores:
             cyc = int(cpu["sample"].split(" scaled to ")[1].split(" cycles")[0])
@@ -347,10 +370,15 @@ def run_ours(args):
                        "k2": float(k2) if not isinstance(k2, np.ndarray) else "field",
                        "ecs_layer": w["layers"], "precision": args.precision,
                        "smoother": "GMRES(3)" if args.smoother == "gmres" else "Jacobi 0.8",
+                       "solver": (f"FGMRES({args.fgmres_restart}), one cycle per iteration as "
+                                  "the preconditioner" if fgm else "V(1,1) cycles"),
                        "tol": args.tol, "parallelism": f"replicas{world}",
                        "l2": "flushed between steps (256 MB write)",
-                       "setup_s": setup_s},
-            "solve": {"cycles": last["cycles"], "refinements": last["refinements"],
+                       "setup_s": setup_s,
+                       "tuner": {"key": mg.tuner_key, "coarse_schedule": mg.coarse_schedule,
+                                 "tile_level0": mg.tile_shape(0)}},
+            "solve": {("iterations" if fgm else "cycles"): last["cycles"],
+                      ("restarts" if fgm else "refinements"): last["refinements"],
                       "rel_residual": last["rel_residual"], "all_ok": ok},
             "e2e": {"value": job_mdofs(pts, args.steps, world, e2e_total), "unit": "MDOF/s",
                     "h2d_bytes_per_step": pts * 16, "d2h_bytes_per_step": pts * 16},
@@ -360,6 +388,7 @@ def run_ours(args):
             "cpu_baseline_all_cores": cpu_all,
             "fp64_gpu": fp64,
             "fgmres": fg,
+            "batched": batched,
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -404,6 +433,42 @@ def cpu_baseline(w, args, cycles_hint):
             "kind": "oracle",
             "sample": f"{ncyc} V-cycles of {w['name']} ({s_per_cycle:.3f} s/cycle, numpy FP64, "
                       f"1 thread) scaled to {cycles} cycles ({src}); setup {t1 - t0:.1f} s"}
+
+
+def cpu_baseline_fgmres(w, args, iters_hint):
+    """The FP64 oracle's FGMRES with the same preconditioning cycle on this
+    host: a bounded number of iterations (one restart cycle, about
+    --cpu-seconds) timed and scaled to one complete solve with the oracle's own
+    iteration count (its golden fixture when present)."""
+    import numpy as np
+
+    import oracle as O
+    n, dim = w["n"], w["dim"]
+    pts = (n - 1) ** dim
+    H = O.build_hierarchy(n, dim, w["k2"], layers=w["layers"], smoother=args.smoother)
+    f = w["rhs"][0]
+    per_cycle = []
+    u = np.zeros_like(f)
+    t1 = time.perf_counter()
+    while time.perf_counter() - t1 < args.cpu_seconds / 2 and len(per_cycle) < 50:
+        t = time.perf_counter()
+        u = O.vcycle(H, 0, np.zeros_like(f), f)
+        per_cycle.append(time.perf_counter() - t)
+    k = max(2, min(args.fgmres_restart, int(args.cpu_seconds / max(min(per_cycle), 1e-6))))
+    t = time.perf_counter()
+    O.fgmres(H, f, tol=1e-300, m=k, max_iter=k, strict=False)
+    s_per_iter = (time.perf_counter() - t) / k
+    gold = ROOT / "tests" / "golden" / f"{w['name']}_fgmres{args.fgmres_restart}_{args.smoother}.json"
+    if gold.exists():
+        iters = json.loads(gold.read_text())["iterations"]
+        src = "oracle iteration count from its golden fixture"
+    else:
+        iters = iters_hint
+        src = "iteration count of this run's solve"
+    return {"value": pts / (s_per_iter * iters) / 1e6, "unit": "MDOF/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{k} FGMRES iterations of {w['name']} ({s_per_iter:.3f} s/iteration, "
+                      f"numpy FP64, 1 thread) scaled to {iters} iterations ({src})"}
 
 
 def _oracle_cycles_worker(task):
@@ -502,17 +567,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_group(args):
+def group_record(args, steps, warmup, stand_alone=False):
     """The many-source workload over uneven grid sizes (64 point sources over
-    255^2, 511^2 and 1023^2 grids) solved by one group call per step
-    (hh_solve_group: the three problems run concurrently).  value = finest-grid
-    points of all right-hand sides / time; `sequential` times the same
-    problems as three separate solves."""
-    import numpy as np
+    255^2, 511^2 and 1023^2 grids, 22/21/21 right-hand sides) solved by one
+    group call per step (hh_solve_group).  Returns MDOF/s (finest-grid points
+    of all right-hand sides / time), e2e (pinned host buffers in and out every
+    step), the same batches solved one after another, and the stated
+    comparison with 64 sequential plain complex128 solves: one plain solve
+    per grid size timed and scaled by that size's count (a projection)."""
     import torch
     from paper_1211_4752_gb300 import HelmholtzMG, solve_group, workloads as W
-    rank, world, local = env_rank()
-    torch.cuda.set_device(local)
     groups = W.batch_sources()
     probs, pts = [], 0
     for g in groups:
@@ -534,18 +598,19 @@ def run_group(args):
         e1.synchronize()
         return e0.elapsed_time(e1) / 1e3, out
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         solve_group(probs, tol=args.tol)
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
+    sampler = ClockSampler(torch.cuda.current_device()) if stand_alone else None
+    if sampler:
+        sampler.start()
     times, ok, launches = [], True, 0
-    for _ in range(args.steps):
+    for _ in range(steps):
         t, res = timed(lambda: solve_group(probs, tol=args.tol))
         times.append(t)
         ok = ok and all(i["status"] == "OK" for _, info in res for i in info)
         launches += sum(mg.solve_kernels for mg, _ in probs)
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     total = sum(times)
     t_seq, _ = timed(lambda: [mg.solve(f, tol=args.tol) for mg, f in probs])
     # end to end: pinned host right-hand sides in, solutions out, every step
@@ -558,30 +623,65 @@ def run_group(args):
         for o, (u, _) in zip(outs, res):
             o.copy_(u, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-    e_times = [timed(e2e)[0] for _ in range(args.steps)]
+    e_times = [timed(e2e)[0] for _ in range(steps)]
     nbytes = sum(h.numel() * 16 for h in hosts)
+    for mg, _ in probs:
+        mg.close()
+    # 64 sequential plain complex128 solves, projected from one per grid size
+    plain, t_plain = [], 0.0
+    for g in groups:
+        mg = HelmholtzMG(g["n"], k2=g["k2"], layers=g["layers"], precision="fp64", max_batch=1,
+                         smoother=args.smoother)
+        f1 = torch.from_numpy(g["rhs"][:1].copy()).cuda()
+        mg.solve(f1, tol=0.5)                  # captures the cycle graph
+        t1, (_, i1) = timed(lambda: mg.solve(f1, tol=args.tol))
+        cnt = int(g["rhs"].shape[0])
+        plain.append({"grid": g["n"] - 1, "ms_per_solve": t1 * 1e3, "cycles": i1[0]["cycles"],
+                      "count": cnt, "status": i1[0]["status"]})
+        t_plain += t1 * cnt
+        mg.close()
+    return {
+        "value": pts * steps / total / 1e6, "unit": "MDOF/s",
+        "ms_per_step": total / steps * 1e3, "steps": steps, "warmup": warmup,
+        "workload": "batch_sources_64rhs_255_511_1023", "rhs": 64,
+        "grids": [g["n"] - 1 for g in groups],
+        "rhs_per_grid": [int(g["rhs"].shape[0]) for g in groups],
+        "precision": args.precision, "all_ok": ok,
+        "sequential_batches": {"value": pts / t_seq / 1e6, "unit": "MDOF/s", "ms": t_seq * 1e3},
+        "sequential_plain_c128": {"value": pts / t_plain / 1e6, "unit": "MDOF/s",
+                                  "ms": t_plain * 1e3, "per_grid": plain,
+                                  "kind": "projection: one plain complex128 solve per grid "
+                                          "size, timed, times that size's count"},
+        "e2e": {"value": pts * steps / sum(e_times) / 1e6, "unit": "MDOF/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+
+
+def run_group(args):
+    """--workload batch_sources: the group record as the bench line."""
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    r = group_record(args, args.steps, args.warmup, stand_alone=True)
     line = {
         "metric": "finest-grid MDOF/s solved to 1e-6 rel. residual",
-        "value": pts * args.steps / total / 1e6, "unit": "MDOF/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+        "value": r["value"], "unit": "MDOF/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64+f64" if args.precision == "mixed" else "c128",
         "data": "synthetic (64 seeded point sources, constant k per grid)",
-        "config": {"workload": "batch_sources_64rhs_255_511_1023", "rhs": 64,
-                   "grids": [g["n"] - 1 for g in groups],
-                   "rhs_per_grid": [int(g["rhs"].shape[0]) for g in groups],
-                   "precision": args.precision, "tol": args.tol, "parallelism": "replicas1",
+        "config": {"workload": r["workload"], "rhs": 64, "grids": r["grids"],
+                   "rhs_per_grid": r["rhs_per_grid"], "precision": args.precision,
+                   "tol": args.tol, "parallelism": "replicas1",
                    "l2": "flushed between steps (256 MB write)"},
-        "all_ok": ok,
-        "sequential": {"value": pts / t_seq / 1e6, "unit": "MDOF/s", "ms": t_seq * 1e3},
-        "e2e": {"value": pts * args.steps / sum(e_times) / 1e6, "unit": "MDOF/s",
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-        "roofline": None, "cpu_baseline": None,
-        "gpu_launches": launches, "clocks": clocks,
+        "all_ok": r["all_ok"],
+        "sequential": r["sequential_batches"],
+        "sequential_plain_c128": r["sequential_plain_c128"],
+        "e2e": r["e2e"], "roofline": None, "cpu_baseline": None,
+        "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
     }
     print(json.dumps(line), flush=True)
-    for mg, _ in probs:
-        mg.close()
 
 
 def profile_fgmres(args):
@@ -622,6 +722,11 @@ def main():
                     help="also time the level-0 kernels on an (n-1)^2 grid beyond L2 (0: skip)")
     ap.add_argument("--fgmres-restart", type=int, default=32,
                     help="also time FGMRES(m) with the cycle as preconditioner (0: skip)")
+    ap.add_argument("--solver", choices=["cycle", "fgmres"], default="cycle",
+                    help="cycle: V-cycles as the solver (the metric's method); fgmres: FGMRES("
+                         "--fgmres-restart) with one cycle per iteration as the preconditioner")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the 64-source group record (255^2/511^2/1023^2) of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-all-cores", dest="cpu_all_cores", action="store_false",
                     help="skip the oracle timed on every host core at once")

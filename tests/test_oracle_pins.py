@@ -457,3 +457,40 @@ def test_radiating_condition_converged_solution_matches_direct_solve():
     assert np.linalg.norm(res.u - ref) <= 1e-9 * np.linalg.norm(ref)
     with pytest.raises(ValueError):
         O.adjoint_solve_symmetrized(H, f)
+
+
+@pytest.mark.parametrize("n,layers", [(64, 8), (128, 12), (256, 48)])
+def test_coarse_level_ecs_placement(n, layers):
+    """The ECS layer keeps its physical position on coarse levels: with every
+    shift angle zero, level 1 of an n-grid hierarchy is exactly the level-0
+    operator of an n/2 grid whose layer is half as many cells wide (k^2
+    injected), and level 2 that of an n/4 grid (layer a quarter as wide)."""
+    k2 = W.smooth_k2(n, 2, 5, 0.4 * n, 0.6 * n)
+    L = int(round(math.log2(n))) - 1
+    Hn = O.build_hierarchy(n, 2, k2, layers=layers, thetas=[0.0] * L)
+    for lev, div in ((1, 2), (2, 4)):
+        if layers % div:
+            continue
+        Hc = O.build_hierarchy(n // div, 2, k2[div - 1::div, div - 1::div], layers=layers // div,
+                               thetas=[0.0] * L)
+        a, b = Hn.levels[lev], Hc.levels[0]
+        for ax in range(2):
+            for t in ("lo", "dg", "up"):
+                assert np.allclose(getattr(a, t)[ax], getattr(b, t)[ax], rtol=1e-14, atol=0)
+        assert np.array_equal(a.k2, b.k2)
+        x = W.random_field(a.shape, 3)
+        assert np.allclose(O.apply_operator(a, x), O.apply_operator(b, x), rtol=1e-13, atol=0)
+
+
+def test_ecs_cell_straddling_the_layer_edge_gets_the_exact_chord():
+    """A coarse cell that contains the layer edge a: its complex length is the
+    chord z(x_{i+1}) - z(x_i) of the complex coordinate, part physical and part
+    rotated.  Layer of 3 fine cells (a = 3/64) on the 32-interval level: the
+    cell [1/32, 2/32] has length (1/64) + (1/64) e^{i gamma}."""
+    g = math.pi / 6
+    a, b = 3 / 64, 1 - 3 / 64
+    h = O.level_spacings(32, a, b, g)
+    expect = (1 / 64) * (1 + np.exp(1j * g))
+    assert abs(h[1] - expect) < 1e-16
+    assert abs(h[0] - (1 / 32) * np.exp(1j * g)) < 1e-16        # wholly inside the layer
+    assert abs(h[2] - 1 / 32) < 1e-16                            # wholly physical
