@@ -246,6 +246,37 @@ typedef struct {
  * HH_ERR_ARG (nothing enqueued) for an invalid item.  Synchronises `stream`. */
 hh_status hh_solve_group(const hh_group_item *items, int count, double tol, void *stream);
 
+/* Work-list group: problems of different grid sizes solved by ONE chain of
+ * launches per V-cycle (the batching of Sec. 4.1's many-source experiments,
+ * organised as a work list).  The levels of all problems are sorted into
+ * size classes (e.g. 1023^2, 511^2, 255^2, ...); each down and up pass of a
+ * cycle is one launch over the tiles of every problem's level of that size
+ * (60 x 16 tiles), the levels from the tail size down are one launch over
+ * every problem's tail operator, and one stop-test kernel serves every
+ * problem; the cycle loop is one captured CUDA graph with a WHILE node
+ * shared by all problems.  Each problem keeps its own FP64 refinement,
+ * stop test and right-hand sides' states, so every right-hand side stops on
+ * its own; results equal separate hh_solve calls up to the tile shape's
+ * summation order.
+ *   handles  count distinct handles (1..8) of the current device: 2-D,
+ *            HH_MIXED, weighted Jacobi with nu1 = nu2 = 1 (the fused path with
+ *            its tail operator), no HH_PERSIST / HH_MID, tail levels of one
+ *            size; else HH_ERR_UNSUPPORTED.
+ *   batch    right-hand sides per problem (fixed for the group).
+ * The handles must outlive the group and must not be used by other calls
+ * while hh_group_solve runs. */
+typedef struct hh_group hh_group;
+hh_status hh_group_create(hh_handle *const *handles, const int *batch, int count,
+                          hh_group **out);
+/* Solve the group: items[i] names handles[i] and batch[i] with its
+ * right-hand sides, solutions (layout of hh_solve), flags (HH_USE_GUESS) and
+ * info; returns the worst status over all right-hand sides.  Synchronises
+ * `stream`. */
+hh_status hh_group_solve(hh_group *g, const hh_group_item *items, double tol, void *stream);
+/* Kernels of this library launched by the last hh_group_solve (-1 before). */
+long long hh_group_kernels(const hh_group *g);
+hh_status hh_group_destroy(hh_group *g);
+
 /* hh_solve on HOST arrays: copies rhs in, solves, copies u out (the copies
  * are part of the call).  Same layout and semantics as hh_solve. */
 hh_status hh_solve_host(hh_handle *h, const void *rhs_host, void *u_host,

@@ -9,7 +9,7 @@ problems" (arXiv 1211.4752).
 """
 
 from ._binding import HHError, lib, lib_path  # noqa: F401
-from .mg import HelmholtzMG, HelmholtzSolve, helmholtz_solve, solve_group  # noqa: F401
+from .mg import HelmholtzGroup, HelmholtzMG, HelmholtzSolve, helmholtz_solve, solve_group  # noqa: F401
 
-__all__ = ["HelmholtzMG", "HelmholtzSolve", "helmholtz_solve", "solve_group", "HHError",
+__all__ = ["HelmholtzGroup", "HelmholtzMG", "HelmholtzSolve", "helmholtz_solve", "solve_group", "HHError",
            "lib", "lib_path"]

@@ -84,6 +84,10 @@ SIGNATURES = {
     "hh_adjoint": (_I, [_P, _P, _P, _I, _D, _I, ct.POINTER(HHSolveInfo), _P]),
     "hh_fgmres": (_I, [_P, _P, _P, _I, _D, _I, _I, _I, ct.POINTER(HHSolveInfo), _P]),
     "hh_solve_group": (_I, [ct.POINTER(HHGroupItem), _I, _D, _P]),
+    "hh_group_create": (_I, [ct.POINTER(_P), ct.POINTER(_I), _I, ct.POINTER(_P)]),
+    "hh_group_solve": (_I, [_P, ct.POINTER(HHGroupItem), _D, _P]),
+    "hh_group_kernels": (ct.c_longlong, [_P]),
+    "hh_group_destroy": (_I, [_P]),
     "hh_grad_k2": (_I, [_P, _P, _P, _I, _P, _P]),
     "hh_apply": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "hh_cycles": (_I, [_P, _P, _P, _I, _I, _P]),

@@ -1814,6 +1814,258 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   return HH_OK;
 }
 
+// ---- work-list groups: problems of different grid sizes in one launch chain
+
+}  // namespace
+
+// A group of mixed-precision 2-D problems (hh_group_create).  The levels of
+// all problems are sorted into size classes (1023^2, 511^2, ...); one cycle
+// launches one down-pass kernel per class over the tiles of every problem's
+// level of that size, one tail kernel over all problems' tail operators, the
+// up passes per class, and one stop-test kernel for all problems.
+struct hh_group {
+  int count = 0;
+  hh_handle *h[kMaxGroup] = {};
+  int batch[kMaxGroup] = {};
+  int device = 0;
+  struct Slot { int p, l; };
+  std::vector<std::vector<Slot>> cls;   // size classes, largest first
+  int chk = 0;                          // class after whose down pass the stop test forks
+  int tiles0[kMaxGroup] = {};           // level-0 tiles (60 x 16) per right-hand side
+  DownMaps dmap[kMaxGroup][MAXL];
+  UpMaps umap[kMaxGroup][MAXL];
+  cudaStream_t cap = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  unsigned int *copies = nullptr, *copies_h = nullptr;
+  int *flags_h = nullptr, *errs_h = nullptr;
+  GraphEntry graph;
+  long long last_kernels = -1;
+};
+
+namespace {
+
+int group_cycle_kernels(const hh_group *g) { return 2 * (int)g->cls.size() + 2; }
+
+void destroy_group(hh_group *g) {
+  if (g->graph.exec) cudaGraphExecDestroy(g->graph.exec);
+  if (g->graph.graph) cudaGraphDestroy(g->graph.graph);
+  if (g->copies) cudaFree(g->copies);
+  if (g->copies_h) cudaFreeHost(g->copies_h);
+  if (g->flags_h) cudaFreeHost(g->flags_h);
+  if (g->errs_h) cudaFreeHost(g->errs_h);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  if (g->side) cudaStreamDestroy(g->side);
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
+  delete g;
+}
+
+// One cycle of every problem of the group (complex64, forward operators,
+// the refinement's inner stop test), enqueued on s.
+void enqueue_group_cycle(hh_group *g, unsigned long long cond, cudaStream_t s) {
+  const int nc = (int)g->cls.size();
+  auto tiles = [](int N, int *ntx) {
+    *ntx = (N + kGroupBX - 1) / kGroupBX;
+    return *ntx * ((N + kGroupBY - 1) / kGroupBY);
+  };
+  for (int c = 0; c < nc; ++c) {
+    DownList L{};
+    int blocks = 0;
+    for (const auto &sl : g->cls[c]) {
+      hh_handle *h = g->h[sl.p];
+      DownEntry &E = L.e[L.n++];
+      E.maps = g->dmap[sl.p][sl.l];
+      E.L = levelk<float>(h, sl.l, 0);
+      E.zero_mode = sl.l == 0 ? ZERO_FLAG : ZERO_ALL;
+      E.v_out = h->w32.u_pre[sl.l];
+      E.fc = h->w32.f[sl.l + 1];
+      E.cs = cscal<float>(h, sl.l, 0);
+      E.omega = omega<float>(h, 0);
+      E.kconst = h->kconst;
+      E.lc = lay_of(h, sl.l + 1);
+      E.st = h->st;
+      E.partials = sl.l == 0 ? h->partials : nullptr;
+      E.err = h->err;
+      E.ntiles = tiles(h->lv[sl.l].N, &E.ntx);
+      E.batch = g->batch[sl.p];
+      E.start = blocks;
+      blocks += E.ntiles * E.batch;
+    }
+    launch_down2d_list(L, blocks, s);
+    if (c == g->chk) {
+      // the stop test of every problem, beside the coarser classes
+      cudaEventRecord(g->ev_fork, s);
+      cudaStreamWaitEvent(g->side, g->ev_fork, 0);
+      CheckList K{};
+      for (int p = 0; p < g->count; ++p) {
+        hh_handle *h = g->h[p];
+        K.e[K.n++] = CheckEntry{h->st, h->partials, h->params, h->flag, h->err};
+      }
+      K.cond = cond;
+      K.copies = g->copies;
+      launch_check_list(K, g->side);
+      cudaEventRecord(g->ev_join, g->side);
+    }
+  }
+  {
+    TailList T{};
+    int blocks = 0;
+    for (int p = 0; p < g->count; ++p) {
+      hh_handle *h = g->h[p];
+      const LevelHost &v = h->lv[h->tail0];
+      TailEntry &E = T.e[T.n++];
+      E.T = h->tailop[0];
+      E.N = v.N;
+      E.P = v.P;
+      E.S = (int)v.S;
+      E.f = h->w32.f[h->tail0];
+      E.u = h->w32.u_post[h->tail0];
+      E.batch = g->batch[p];
+      E.st = h->st;
+      E.start = blocks;
+      blocks += (v.N * v.N + 7) / 8;
+    }
+    launch_tail_list(T, blocks, s);
+  }
+  for (int c = nc - 1; c >= 0; --c) {
+    // the first up pass that writes a level-0 iterate waits for the stop test
+    if (c == g->chk) cudaStreamWaitEvent(s, g->ev_join, 0);
+    UpList U{};
+    int blocks = 0;
+    for (const auto &sl : g->cls[c]) {
+      hh_handle *h = g->h[sl.p];
+      UpEntry &E = U.e[U.n++];
+      E.maps = g->umap[sl.p][sl.l];
+      E.L = levelk<float>(h, sl.l, 0);
+      E.u_out = h->w32.u_post[sl.l];
+      E.omega = omega<float>(h, 0);
+      E.kconst = h->kconst;
+      E.st = h->st;
+      E.err = h->err;
+      E.ntiles = tiles(h->lv[sl.l].N, &E.ntx);
+      E.batch = g->batch[sl.p];
+      E.start = blocks;
+      blocks += E.ntiles * E.batch;
+    }
+    launch_up2d_list(U, blocks, s);
+  }
+}
+
+hh_status group_graph(hh_group *g, cudaGraphExec_t *out) {
+  if (g->graph.exec) {
+    *out = g->graph.exec;
+    return HH_OK;
+  }
+  GraphEntry ge;
+  HH_CK(cudaGraphCreate(&ge.graph, 0));
+  cudaGraphConditionalHandle cond;
+  HH_CK(cudaGraphConditionalHandleCreate(&cond, ge.graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  HH_CK(cudaGraphAddNode(&node, ge.graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  HH_CK(cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal));
+  for (int k = loop_unroll(); k > 0; --k) enqueue_group_cycle(g, (unsigned long long)cond, g->cap);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(g->cap, &captured);
+  if (ec != cudaSuccess) {
+    cudaGraphDestroy(ge.graph);
+    return fail(HH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+  }
+  HH_CK(cudaGraphInstantiate(&ge.exec, ge.graph, 0));
+  g->graph = ge;
+  *out = ge.exec;
+  return HH_OK;
+}
+
+// The solve of a group: per problem the FP64 set-up (norm of f, state,
+// first refinement residual), then rounds of [the group's complex64 cycle
+// loop (every problem whose outer solve is still open), the FP64 refinement
+// of each problem that took part]; per problem the solution and its info.
+hh_status group_solve_impl(hh_group *g, const hh_group_item *items, double tol, cudaStream_t s) {
+  int cur[kMaxGroup];
+  int keep[kMaxGroup];
+  for (int p = 0; p < g->count; ++p) {
+    hh_handle *h = g->h[p];
+    const int B = g->batch[p];
+    keep[p] = h->nparts;
+    h->nparts = g->tiles0[p];   // the group's level-0 tiles carry the stop test's sums
+    const Lay l0 = lay_of(h, 0);
+    HH_TRY(copy_to_pitched(h, 0, h->w64.f[0], items[p].rhs_dev, B, sizeof(double2),
+                           cudaMemcpyDeviceToDevice, s));
+    HH_TRY(set_params(h, B, tol, s));
+    HH_CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+    HH_CK(cudaMemsetAsync(h->copies, 0, sizeof(unsigned int), s));
+    h->fixed_kernels = 5;   // norm, state init, first refinement and its test, final copy
+    launch_norm2(h->w64.f[0], (size_t)l0.S, B, h->partials, h->nparts, s);
+    launch_state_init(h->st, h->partials, h->params, h->flag, s);
+    const bool guess = (items[p].flags & HH_USE_GUESS) != 0;
+    if (guess)
+      HH_TRY(copy_to_pitched(h, 0, h->u64[0], items[p].u_dev, B, sizeof(double2),
+                             cudaMemcpyDeviceToDevice, s));
+    refine_dispatch(h, 0, h->u64[0], guess ? 0 : 1, nullptr, h->u64[1], B, s);
+    launch_check_outer(h->st, h->partials, h->params, h->flag, s);
+    cur[p] = 1;
+  }
+  HH_CK(cudaMemsetAsync(g->copies, 0, sizeof(unsigned int), s));
+  cudaGraphExec_t ex;
+  HH_TRY(group_graph(g, &ex));
+  long long fixed = 0;
+  int maxc = 0;
+  for (int p = 0; p < g->count; ++p) maxc = std::max(maxc, g->h[p]->opt.max_cycles);
+  for (int it = 0; it < maxc + 2; ++it) {
+    for (int p = 0; p < g->count; ++p) {
+      HH_CK(cudaMemcpyAsync(g->flags_h + p, g->h[p]->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      HH_CK(cudaMemcpyAsync(g->errs_h + p, g->h[p]->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    HH_CK(cudaStreamSynchronize(s));
+    bool any = false, err = false;
+    bool act[kMaxGroup];
+    for (int p = 0; p < g->count; ++p) {
+      act[p] = g->flags_h[p] != 0;
+      any = any || act[p];
+      err = err || g->errs_h[p] != 0;
+    }
+    if (!any || err) break;
+    HH_CK(cudaGraphLaunch(ex, s));
+    for (int p = 0; p < g->count; ++p) {
+      if (!act[p]) continue;
+      hh_handle *h = g->h[p];
+      refine_dispatch(h, 0, h->u64[cur[p]], 0, h->w32.u_post[0], h->u64[1 - cur[p]], g->batch[p], s);
+      cur[p] = 1 - cur[p];
+      launch_check_outer(h->st, h->partials, h->params, h->flag, s);
+      fixed += 2;
+    }
+  }
+  hh_status worst = HH_OK;
+  std::string msg;
+  for (int p = 0; p < g->count; ++p) {
+    hh_handle *h = g->h[p];
+    const Lay l0 = lay_of(h, 0), d0 = lay_dense(h, 0);
+    launch_finish(h->st, h->u64[cur[p]], l0, (double2 *)items[p].u_dev, d0, 2, g->batch[p], s);
+  }
+  HH_CK(cudaGetLastError());
+  HH_CK(cudaMemcpyAsync(g->copies_h, g->copies, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+  for (int p = 0; p < g->count; ++p) {
+    hh_handle *h = g->h[p];
+    const hh_status r = read_info(h, g->batch[p], items[p].info, s);
+    h->nparts = keep[p];
+    fixed += h->fixed_kernels;
+    if (r != HH_OK && (worst == HH_OK || r == HH_ERR_TIMEOUT || r == HH_ERR_DIVERGED)) {
+      worst = r;
+      msg = "group item " + std::to_string(p) + ": " + g_err;
+    }
+  }
+  g->last_kernels = (long long)*g->copies_h * group_cycle_kernels(g) + fixed;
+  if (worst != HH_OK) g_err = msg;
+  return worst;
+}
+
 // ---- flexible GMRES(m) with the cycle as preconditioner (Sec. 4.1, Table 3)
 
 // Workspace for restart length m and `batch` right-hand sides: m + 1 basis
@@ -2308,6 +2560,105 @@ hh_status hh_solve_group(const hh_group_item *items, int count, double tol, void
     }
   }
   return worst;
+}
+
+hh_status hh_group_create(hh_handle *const *handles, const int *batch, int count,
+                          hh_group **out) {
+  g_err.clear();
+  if (!handles || !batch || !out) return fail(HH_ERR_ARG, "handles, batch and out must not be NULL");
+  if (count < 1 || count > kMaxGroup)
+    return fail(HH_ERR_ARG, "a group holds 1.." + std::to_string(kMaxGroup) + " problems");
+  int tailN = -1;
+  for (int i = 0; i < count; ++i) {
+    hh_handle *h = handles[i];
+    HH_TRY(check_handle(h));
+    HH_TRY(check_batch(h, batch[i]));
+    HH_TRY(ensure_device(h));
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == h) return fail(HH_ERR_ARG, "a handle appears twice in the group");
+    if (h->dim != 2 || !h->fused || h->opt.precision != HH_MIXED || !h->tailop[0] || h->mid ||
+        h->persist || h->tail0 < 1)
+      return fail(HH_ERR_UNSUPPORTED, "work-list groups take 2-D mixed-precision handles on the "
+                                      "fused path with the tail operator (weighted Jacobi, nu = 1)");
+    if (tailN >= 0 && h->lv[h->tail0].N != tailN)
+      return fail(HH_ERR_UNSUPPORTED, "the problems' tail levels differ in size");
+    tailN = h->lv[h->tail0].N;
+  }
+  hh_group *g = new hh_group();
+  g->count = count;
+  g->device = handles[0]->device;
+  std::vector<int> sizes;
+  for (int p = 0; p < count; ++p) {
+    g->h[p] = handles[p];
+    g->batch[p] = batch[p];
+    for (int l = 0; l < handles[p]->tail0; ++l) sizes.push_back(handles[p]->lv[l].N);
+  }
+  std::sort(sizes.begin(), sizes.end(), std::greater<int>());
+  sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+  g->cls.resize(sizes.size());
+  int lowest0 = 1 << 30;
+  for (int p = 0; p < count; ++p) {
+    hh_handle *h = handles[p];
+    for (int l = 0; l < h->tail0; ++l) {
+      const int c = (int)(std::find(sizes.begin(), sizes.end(), h->lv[l].N) - sizes.begin());
+      g->cls[c].push_back({p, l});
+      if (l == 0) lowest0 = std::min(lowest0, h->lv[0].N);
+    }
+    const int N = h->lv[0].N;
+    g->tiles0[p] = ((N + kGroupBX - 1) / kGroupBX) * ((N + kGroupBY - 1) / kGroupBY);
+  }
+  g->chk = (int)(std::find(sizes.begin(), sizes.end(), lowest0) - sizes.begin());
+  int v0 = -1;
+  for (int v = 0; v < kNumTileVariants; ++v)
+    if (tile_bx(v) == kGroupBX && tile_by(v) == kGroupBY) v0 = v;
+  hh_status st = v0 < 0 ? fail(HH_ERR_UNSUPPORTED, "no 60 x 16 tile shape") : HH_OK;
+  for (int p = 0; st == HH_OK && p < count; ++p)
+    for (int l = 0; st == HH_OK && l < handles[p]->tail0; ++l)
+      st = make_maps<float>(handles[p], l, v0, &g->dmap[p][l], &g->umap[p][l]);
+  cudaError_t e = cudaSuccess;
+  if (st == HH_OK) {
+    if (e == cudaSuccess) e = init_group2d();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&g->copies, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMallocHost(&g->copies_h, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMallocHost(&g->flags_h, kMaxGroup * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&g->errs_h, kMaxGroup * sizeof(int));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      st = fail(e == cudaErrorMemoryAllocation ? HH_ERR_OOM : HH_ERR_CUDA,
+                std::string("group set-up: ") + cudaGetErrorString(e));
+    }
+  }
+  if (st != HH_OK) {
+    destroy_group(g);
+    return st;
+  }
+  *out = g;
+  return HH_OK;
+}
+
+hh_status hh_group_solve(hh_group *g, const hh_group_item *items, double tol, void *stream) {
+  g_err.clear();
+  if (!g || !items) return fail(HH_ERR_ARG, "group and items must not be NULL");
+  if (!(tol > 0 && tol < 1)) return fail(HH_ERR_ARG, "tol must be in (0, 1)");
+  for (int p = 0; p < g->count; ++p) {
+    const hh_group_item &it = items[p];
+    if (it.h != g->h[p] || it.batch != g->batch[p])
+      return fail(HH_ERR_ARG, "item " + std::to_string(p) + " must name the group's handle and batch");
+    if (!it.rhs_dev || !it.u_dev) return fail(HH_ERR_ARG, "rhs and u must not be NULL");
+    HH_TRY(ensure_device(it.h));
+  }
+  return group_solve_impl(g, items, tol, (cudaStream_t)stream);
+}
+
+long long hh_group_kernels(const hh_group *g) { return g ? g->last_kernels : -1; }
+
+hh_status hh_group_destroy(hh_group *g) {
+  if (g) destroy_group(g);
+  return HH_OK;
 }
 
 hh_status hh_adjoint(hh_handle *h, const void *g_dev, void *lambda_dev,

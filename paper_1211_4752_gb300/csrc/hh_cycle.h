@@ -230,6 +230,78 @@ template <typename R, int J>
 void launch_up2d_multi(const CoarseUpArgs<R, J> &a, int batch, const SolveState *st,
                        cudaStream_t s);
 
+// Work lists over several problems (hh_group2d.cu): one launch runs one
+// level of each of up to kMaxGroup problems (different grid sizes, media and
+// batches); block i belongs to the entry whose [start, start + blocks) holds
+// it.  The tile shape (60 x 16) is common to a launch.
+constexpr int kMaxGroup = 8;
+constexpr int kGroupBX = 60, kGroupBY = 16;
+struct DownEntry {
+  DownMaps maps;
+  LevelK<float> L;
+  int zero_mode;
+  float2 *v_out, *fc;
+  float2 cs, omega;
+  int kconst;
+  Lay lc;
+  const SolveState *st;
+  double *partials;           // level 0: the stop test's per-tile sums
+  int *err;
+  int ntx, ntiles, batch;     // tiles per row, per right-hand side; right-hand sides
+  int start;                  // first block of this entry
+};
+struct DownList {
+  int n;
+  DownEntry e[kMaxGroup];
+};
+struct UpEntry {
+  UpMaps maps;
+  LevelK<float> L;
+  float2 *u_out;
+  float2 omega;
+  int kconst;
+  const SolveState *st;
+  int *err;
+  int ntx, ntiles, batch, start;
+};
+struct UpList {
+  int n;
+  UpEntry e[kMaxGroup];
+};
+// tail operators of several problems (rows of N^2 x S each)
+struct TailEntry {
+  const float2 *T;
+  int N, P, S;
+  const float2 *f;
+  float2 *u;
+  int batch;
+  const SolveState *st;
+  int start;                  // first block (8 rows per block)
+};
+struct TailList {
+  int n;
+  TailEntry e[kMaxGroup];
+};
+// stop test of the inner complex64 loops of several problems (one block)
+struct CheckEntry {
+  SolveState *st;
+  const double *partials;
+  const SolveParams *P;
+  int *flag;
+  const int *err;
+};
+struct CheckList {
+  int n;
+  CheckEntry e[kMaxGroup];
+  unsigned long long cond;    // WHILE-node condition (0: none)
+  unsigned int *copies;       // group cycles run
+};
+cudaError_t init_group2d();
+void launch_down2d_list(const DownList &a, int blocks, cudaStream_t s);
+void launch_up2d_list(const UpList &a, int blocks, cudaStream_t s);
+void launch_tail_list(const TailList &a, int blocks, cudaStream_t s);
+void launch_check_list(const CheckList &a, cudaStream_t s);
+
 void launch_unit_rhs(double2 *F, int N, int P, int S, cudaStream_t s);
 void launch_tail_gather(const double2 *U, float2 *T, int N, int P, int S, cudaStream_t s);
 void launch_tail_apply(const float2 *T, int N, int P, int S, const float2 *f, float2 *u,

@@ -320,22 +320,23 @@ __device__ __forceinline__ void down_compute(
   }
 }
 
-// partials (level 0 of a solve): per-block sums of |f - A u|^2, read by the
-// stop test that runs beside the coarser levels.
+// One block's down pass on tile (tx, ty) of right-hand side b (ntx tiles
+// per row, ntiles per right-hand side; spec: the launch has one right-hand
+// side).  partials (level 0 of a solve): per-block sums of |f - A u|^2,
+// read by the stop test that runs beside the coarser levels.
 template <typename R, int BX, int BY>
-__global__ void __launch_bounds__(256)
-k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
-         typename Cx<R>::T *__restrict__ v_out, typename Cx<R>::T *__restrict__ fc,
-         typename Cx<R>::T cs, typename Cx<R>::T omega, int kconst, Lay lc,
-         const SolveState *__restrict__ st, double *__restrict__ partials, int *err) {
+__device__ __forceinline__ void down_pass_tile(
+    const DownMaps &maps, const LevelK<R> &L, int zero_mode, typename Cx<R>::T *__restrict__ v_out,
+    typename Cx<R>::T *__restrict__ fc, typename Cx<R>::T cs, typename Cx<R>::T omega, int kconst,
+    const Lay &lc, const SolveState *__restrict__ st, double *__restrict__ partials, int *err,
+    int tx, int ty, int b, int ntx, int ntiles, bool spec) {
   using C = typename Cx<R>::T;
   using S = Down2D<R, BX, BY>;
-  const int b = blockIdx.z;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *base = align_smem128(smem_raw);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(base + S::oB);
   const int N = L.N;
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int x0 = tx * BX, y0 = ty * BY;
   R acc = R(0);
   // Prologue, independent of the previous kernel's output (it overlaps that
   // kernel's tail under programmatic dependent launch): the mbarrier, the
@@ -363,7 +364,6 @@ k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
   // state is read, so the state's load latency overlaps them (u is fetched
   // even where the state may say it is zero).  Batches read the state first,
   // so blocks of finished right-hand sides fetch nothing.
-  const bool spec = gridDim.z == 1;
   const bool loadu = zero_mode == ZERO_NONE || (spec && zero_mode == ZERO_FLAG);
   auto issue = [&](bool withu) {
     if (threadIdx.x == 0) {
@@ -406,9 +406,19 @@ k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
   }
   if (partials) {
     const double s = (double)block_sum_r(acc);
-    const int nblk = gridDim.x * gridDim.y;
-    if (act && threadIdx.x == 0) partials[(size_t)b * nblk + blockIdx.y * gridDim.x + blockIdx.x] = s;
+    if (act && threadIdx.x == 0) partials[(size_t)b * ntiles + ty * ntx + tx] = s;
   }
+}
+
+template <typename R, int BX, int BY>
+__global__ void __launch_bounds__(256)
+k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
+         typename Cx<R>::T *__restrict__ v_out, typename Cx<R>::T *__restrict__ fc,
+         typename Cx<R>::T cs, typename Cx<R>::T omega, int kconst, Lay lc,
+         const SolveState *__restrict__ st, double *__restrict__ partials, int *err) {
+  down_pass_tile<R, BX, BY>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, st, partials,
+                            err, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x,
+                            gridDim.x * gridDim.y, gridDim.z == 1);
 }
 
 template <typename R, int BX, int BY, bool CHECK, bool FAST>
@@ -521,18 +531,21 @@ __device__ __forceinline__ void up_compute(const LevelK<R> &L, typename Cx<R>::T
   }
 }
 
+// One block's up pass on tile (tx, ty) of right-hand side b (spec: the
+// launch has one right-hand side).
 template <typename R, int BX, int BY>
-__global__ void __launch_bounds__(256)
-k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__restrict__ u_out,
-       typename Cx<R>::T omega, int kconst, const SolveState *__restrict__ st, int *err) {
+__device__ __forceinline__ void up_pass_tile(const UpMaps &maps, const LevelK<R> &L,
+                                             typename Cx<R>::T *__restrict__ u_out,
+                                             typename Cx<R>::T omega, int kconst,
+                                             const SolveState *__restrict__ st, int *err, int tx,
+                                             int ty, int b, bool spec) {
   using C = typename Cx<R>::T;
   using S = Up2D<R, BX, BY>;
-  const int b = blockIdx.z;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *base = align_smem128(smem_raw);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(base + S::oB);
   const int N = L.N;
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int x0 = tx * BX, y0 = ty * BY;
   // prologue before the dependency wait (see k_down2d)
   const bool inner = tile_in(L, x0 - 1, x0 + BX, N, false) && tile_in(L, y0 - 1, y0 + BY, N, false);
   const bool fast = inner && tile_in(L, x0 - 1, x0 + BX, N, true) &&
@@ -554,7 +567,6 @@ k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__re
   griddep_launch_dependents();
   // one right-hand side: copies started before the state is read (see
   // k_down2d); one decision per block
-  const bool spec = gridDim.z == 1;
   auto issue = [&]() {
     if (threadIdx.x == 0) {
       mbar_expect_tx(mbar, S::bV + S::bE + S::bF + (kconst ? 0u : S::bK));
@@ -582,6 +594,14 @@ k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__re
   if (fast) up_compute<R, BX, BY, false, true>(L, ob, omega, kconst, x0, y0, base);
   else if (inner) up_compute<R, BX, BY, false, false>(L, ob, omega, kconst, x0, y0, base);
   else up_compute<R, BX, BY, true, false>(L, ob, omega, kconst, x0, y0, base);
+}
+
+template <typename R, int BX, int BY>
+__global__ void __launch_bounds__(256)
+k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__restrict__ u_out,
+       typename Cx<R>::T omega, int kconst, const SolveState *__restrict__ st, int *err) {
+  up_pass_tile<R, BX, BY>(maps, L, u_out, omega, kconst, st, err, blockIdx.x, blockIdx.y,
+                          blockIdx.z, gridDim.z == 1);
 }
 
 }  // namespace hh

@@ -368,3 +368,61 @@ def solve_group(problems, tol=1e-6):
     if st not in (B.HH_OK, B.HH_ERR_NOT_CONVERGED, B.HH_ERR_DIVERGED):
         B.check(st)
     return [(u, HelmholtzMG._infos(info, nb)) for u, info, nb in outs]
+
+
+class HelmholtzGroup:
+    """A work-list group (hh_group_create): mixed-precision 2-D handles of
+    possibly different grid sizes whose cycles run as ONE chain of launches
+    (one launch per level size over every problem's level of that size, one
+    tail launch, one stop test for all).  `handles` and `batches` are fixed;
+    solve() takes one right-hand-side tensor per handle."""
+
+    def __init__(self, handles, batches):
+        self.handles = list(handles)
+        self.batches = [int(b) for b in batches]
+        n = len(self.handles)
+        hs = (ct.c_void_p * n)(*[mg._h.value if isinstance(mg._h, ct.c_void_p) else mg._h
+                                 for mg in self.handles])
+        bs = (ct.c_int * n)(*self.batches)
+        g = ct.c_void_p()
+        with torch.cuda.device(self.handles[0].device):
+            B.check(B.lib().hh_group_create(hs, bs, n, ct.byref(g)))
+        self._g = g
+
+    @property
+    def kernels(self):
+        """Kernels launched by the last solve (-1 before one)."""
+        return B.lib().hh_group_kernels(self._g)
+
+    def solve(self, rhs, tol=1e-6, u0=None):
+        """rhs: one complex128 tensor per handle ([batch, N, N]); returns
+        [(u, info), ...] in the handles' order."""
+        n = len(self.handles)
+        items = (B.HHGroupItem * n)()
+        outs, keep = [], []
+        for i, (mg, f) in enumerate(zip(self.handles, rhs)):
+            f = mg._vec(f, "rhs")
+            nb = f.shape[0]
+            g0 = None if u0 is None else u0[i]
+            u = torch.empty_like(f) if g0 is None else mg._vec(g0, "u0").clone()
+            info = (B.HHSolveInfo * nb)()
+            items[i] = B.HHGroupItem(mg._h, _ptr(f), _ptr(u), nb,
+                                     B.HH_USE_GUESS if g0 is not None else 0, info)
+            outs.append((u, info, nb))
+            keep.append(f)
+        with torch.cuda.device(self.handles[0].device):
+            st = B.lib().hh_group_solve(self._g, items, float(tol), _stream())
+        if st not in (B.HH_OK, B.HH_ERR_NOT_CONVERGED, B.HH_ERR_DIVERGED):
+            B.check(st)
+        return [(u, HelmholtzMG._infos(info, nb)) for u, info, nb in outs]
+
+    def close(self):
+        if getattr(self, "_g", None):
+            B.lib().hh_group_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
