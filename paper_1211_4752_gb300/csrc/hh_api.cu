@@ -157,6 +157,9 @@ struct hh_handle {
   double *gm_parts = nullptr;       // GMRES smoothing: partial sums,
   unsigned int *gm_counter = nullptr;  // last-block arrival counter,
   double *gm_gsc = nullptr;         // per right-hand side scalars
+  int gtail0 = 0;                   // GMRES smoothing: first level of the one-block tail (0: none)
+  GmTailArgs<float> gta32[2];       // its arguments per direction and precision
+  GmTailArgs<double> gta64[2];
   KrylovWork kw;                    // flexible GMRES: workspace (first use),
   int kw_m = 0, kw_b = 0, kw_sms = 0;  // its restart length, batch capacity, SMs,
   std::vector<void *> kw_mem;       // its allocations and iteration graphs
@@ -336,7 +339,9 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
   Work<R> &W = work<R>(h);
   const SolveState *st = check != CHECK_NONE ? h->st : nullptr;
   const int L = h->L, m = h->opt.gmres_m;
-  for (int l = 0; l + 1 < L; ++l) {
+  // levels gtail0 .. coarsest run in one block per right-hand side
+  const int T = h->gtail0 > 0 ? h->gtail0 : L - 1;
+  for (int l = 0; l < T; ++l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
     const GmresWork<R> g = gmres_work<R>(h, l);
     const int nb = partial_blocks_of(h, l);
@@ -358,9 +363,16 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
     launch_resid_restrict<R, DIM>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
                                   cscal<R>(h, l, dir), batch, st, s);
   }
-  launch_coarse_solve<R, DIM>(h->lu[dir], h->piv[dir], lay_of(h, L - 1), W.f[L - 1],
-                              W.u_post[L - 1], batch, st, s);
-  for (int l = L - 2; l >= 0; --l) {
+  if (h->gtail0 > 0) {
+    if constexpr (std::is_same<R, float>::value)
+      launch_gmres_tail<float, DIM>(h->gta32[dir], batch, st, s);
+    else
+      launch_gmres_tail<double, DIM>(h->gta64[dir], batch, st, s);
+  } else {
+    launch_coarse_solve<R, DIM>(h->lu[dir], h->piv[dir], lay_of(h, L - 1), W.f[L - 1],
+                                W.u_post[L - 1], batch, st, s);
+  }
+  for (int l = T - 1; l >= 0; --l) {
     const LevelK<R> K = levelk<R>(h, l, dir);
     const GmresWork<R> g = gmres_work<R>(h, l);
     const int nb = partial_blocks_of(h, l);
@@ -1557,6 +1569,63 @@ hh_status autotune(hh_handle *h, cudaStream_t s) {
   return HH_OK;
 }
 
+// GMRES smoothing: the one-block tail runs the levels from the first one
+// whose tail (it and all coarser levels) fits kGmTailSmemMax of shared
+// memory (HH_GMTAIL=off in the environment keeps every level per-level).
+template <typename R> hh_status setup_gmres_tail(hh_handle *h) {
+  h->gtail0 = 0;
+  const char *ge = std::getenv("HH_GMTAIL");
+  if (ge && std::strcmp(ge, "off") == 0) return HH_OK;
+  const int L = h->L;
+  int N[MAXL];
+  int t0 = -1;
+  for (int t = 1; t < L; ++t) {
+    if (L - t > kGmTailMax) continue;
+    for (int l = t; l < L; ++l) N[l - t] = h->lv[l].N;
+    const size_t b = h->dim == 2 ? gmres_tail_smem<R, 2>(N, L - t, h->opt.gmres_m)
+                                 : gmres_tail_smem<R, 3>(N, L - t, h->opt.gmres_m);
+    if (b <= kGmTailSmemMax) { t0 = t; break; }
+  }
+  if (t0 < 0) return HH_OK;
+  HH_CK((h->dim == 2 ? init_gmres_tail<R, 2>() : init_gmres_tail<R, 3>()));
+  using C = typename Cx<R>::T;
+  for (int dir = 0; dir < 2; ++dir) {
+    GmTailArgs<R> a{};
+    a.nl = L - t0;
+    a.m = h->opt.gmres_m;
+    a.nu1 = h->opt.nu1;
+    a.nu2 = h->opt.nu2;
+    auto pts = [&](int n) { return h->dim == 2 ? (size_t)n * n : (size_t)n * n * n; };
+    size_t c = 0, r = 0;
+    for (int q = 0; q < 3; ++q) { a.offQ[q] = (int)c; c += pts(h->lv[t0].N); }
+    for (int i = 0; i < a.nl; ++i) {
+      const int l = t0 + i;
+      GmTailLevel<R> &g = a.lv[i];
+      g.K = levelk<R>(h, l, dir);
+      g.c = cscal<R>(h, l, dir);
+      g.offU = (int)c; c += pts(h->lv[l].N);
+      g.offF = (int)c; c += pts(h->lv[l].N);
+      g.offT = (int)c; c += 3 * (size_t)h->dim * h->lv[l].N;
+      g.offK = (int)r; r += pts(h->lv[l].N);
+      N[i] = h->lv[l].N;
+    }
+    a.kbase = (int)((c * sizeof(C) + 15) / 16 * 16);
+    a.lubase = (int)((a.kbase + r * sizeof(R) + 15) / 16 * 16);
+    a.smem_bytes = (int)(h->dim == 2 ? gmres_tail_smem<R, 2>(N, a.nl, a.m)
+                                     : gmres_tail_smem<R, 3>(N, a.nl, a.m));
+    a.f = work<R>(h).f[t0];
+    a.u = work<R>(h).u_post[t0];
+    a.lay = lay_of(h, t0);
+    a.lu = h->lu[dir];
+    a.piv = h->piv[dir];
+    a.mm = h->m;
+    if constexpr (std::is_same<R, float>::value) h->gta32[dir] = a;
+    else h->gta64[dir] = a;
+  }
+  h->gtail0 = t0;
+  return HH_OK;
+}
+
 hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
                      const hh_shift &sh, cudaStream_t s) {
   const hh_grid &g = h->grid;
@@ -1799,6 +1868,10 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   HH_CK(cudaStreamSynchronize(s));
   HH_CK(cudaGetLastError());
   if (info_h[0] || info_h[1]) return fail(HH_ERR_ARG, "singular coarsest-level operator");
+  if (h->opt.smoother == HH_SMOOTH_GMRES) {
+    if (h->opt.precision == HH_MIXED) HH_TRY(setup_gmres_tail<float>(h));
+    else HH_TRY(setup_gmres_tail<double>(h));
+  }
   if (h->fused) {
     // complex64 cycles apply the tail as a dense operator (HH_TAIL=kernel in
     // the environment keeps the tail kernel)
@@ -2384,8 +2457,12 @@ int hh_cycle_kernels(const hh_handle *h) {
     if (h->mid && h->opt.precision == HH_MIXED) return 2 * h->mid0 + 2;
     return 2 * (1 + h->ngroups) + 2;
   }
-  if (h->opt.smoother == HH_SMOOTH_GMRES)   // per level: steps of 2m + 2 kernels,
-    return (h->L - 1) * ((h->opt.nu1 + h->opt.nu2) * (2 * h->opt.gmres_m + 2) + 2) + 2;
+  if (h->opt.smoother == HH_SMOOTH_GMRES) {  // per level: steps of 2m + 2 kernels,
+    // residual + restriction, correction; then the tail (or the coarsest LU)
+    // and the stop test
+    const int T = h->gtail0 > 0 ? h->gtail0 : h->L - 1;
+    return T * ((h->opt.nu1 + h->opt.nu2) * (2 * h->opt.gmres_m + 2) + 2) + 2;
+  }
   // per level nu1 sweeps, residual + restriction, nu2 sweeps; stop test; LU
   return (h->L - 1) * (h->opt.nu1 + 1 + h->opt.nu2) + 2;
 }

@@ -24,6 +24,16 @@ namespace hh {
 
 namespace {
 
+// Scale of q_i in the complex64 per-thread sums: 1 / |q_i|.  The Krylov
+// vectors are not normalised, so A q_J grows like ||A||^(J+1) |q_0|; its
+// square would overflow FP32 on fine grids.  Products s_i q_i . s_J A q_J
+// stay of the order of ||A||, and the block sums (FP64) are divided by
+// s_i s_J again.  complex128 vectors are summed unscaled in FP64.
+template <typename R> __device__ __forceinline__ R kscale(double sq) {
+  if (sizeof(R) == 8) return R(1);
+  return sq > 0.0 ? R(1.0 / sqrt(sq)) : R(0);
+}
+
 // per right-hand side scalars (FP64): |q_i|^2 at 0..3; c_ij (complex) at
 // ci(i, j) for i <= j < 3; z_j (complex) at 16 + 2 j; at 24 whether the
 // step started from a zero iterate; at 25 the Krylov dimension used
@@ -63,13 +73,16 @@ __device__ __forceinline__ void last_block_reduce(unsigned int *counter, const d
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// Block sums of NQ doubles per thread into parts[b][q][blockIdx.x].
-template <int NQ>
-__device__ __forceinline__ void write_partials(const double (&acc)[NQ], bool act, double *parts,
+// Block sums of NQ values per thread into parts[b][q][blockIdx.x] (FP64
+// from the block sum on; the per-thread sums are in the vectors' precision:
+// FP32 for complex64 vectors, whose FP64 accumulation would be bound by the
+// FP64 pipe, FP64 for complex128).
+template <int NQ, typename A>
+__device__ __forceinline__ void write_partials(const A (&acc)[NQ], bool act, double *parts,
                                                int b) {
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const double s = block_sum(acc[q]);
+    const double s = block_sum((double)acc[q]);
     if (act && threadIdx.x == 0) parts[((size_t)b * NQ + q) * gridDim.x + blockIdx.x] = s;
     __syncthreads();
   }
@@ -89,7 +102,7 @@ k_gm_start(LevelK<R> L, const typename Cx<R>::T *__restrict__ u, int zero_mode,
       __syncthreads_or(zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero)) != 0;
   if (act && blockIdx.x == 0 && threadIdx.x == 0)
     gsc[b * kGmresScalars + 24] = zero ? 1.0 : 0.0;   // for the update kernel
-  double acc[1] = {0.0};
+  R acc[1] = {R(0)};
   if (act) {
     const int N = L.N, P = L.P;
     const size_t off = (size_t)b * L.S;
@@ -107,7 +120,7 @@ k_gm_start(LevelK<R> L, const typename Cx<R>::T *__restrict__ u, int zero_mode,
         r = csub(r, Au);
       }
       q0[o] = r;
-      acc[0] += (double)r.x * r.x + (double)r.y * r.y;
+      acc[0] += r.x * r.x + r.y * r.y;
     }
   }
   write_partials<1>(acc, act, parts, b);
@@ -125,9 +138,12 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
   constexpr int NQ = 2 * (J + 1);
   const int b = blockIdx.y;
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
-  double acc[NQ];
+  R acc[NQ];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  for (int q = 0; q < NQ; ++q) acc[q] = R(0);
+  R sc[J + 1];   // kscale of q_0..q_J
+#pragma unroll
+  for (int i = 0; i <= J; ++i) sc[i] = kscale<R>(gsc[b * kGmresScalars + i]);
   if (act) {
     const int N = L.N, P = L.P;
     const size_t off = (size_t)b * L.S;
@@ -141,11 +157,12 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
       C Aq, D, qc;
       stencil<R, DIM>(L, x, y, z, get, Aq, D, qc);
       w[off + o] = Aq;
+      const C a = cscale(Aq, sc[J]);
 #pragma unroll
       for (int i = 0; i <= J; ++i) {
-        const C qi = Q[(size_t)i * qs + off + o];
-        acc[2 * i] += (double)qi.x * Aq.x + (double)qi.y * Aq.y;       // Re conj(q_i) Aq
-        acc[2 * i + 1] += (double)qi.x * Aq.y - (double)qi.y * Aq.x;   // Im
+        const C qi = cscale(Q[(size_t)i * qs + off + o], sc[i]);
+        acc[2 * i] += qi.x * a.x + qi.y * a.y;       // Re conj(q_i) Aq (scaled)
+        acc[2 * i + 1] += qi.x * a.y - qi.y * a.x;   // Im
       }
     }
   }
@@ -153,11 +170,13 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
   last_block_reduce<NQ>(counter, parts, gridDim.x, gridDim.y, st,
                         [&](int bb, const double *v) {
                           double *g = gsc + bb * kGmresScalars;
+                          const double sj = (double)kscale<R>(g[J]);
                           for (int i = 0; i <= J; ++i) {
                             const double s = g[i];
-                            const bool ok = s > 0.0;
-                            g[ci(i, J)] = ok ? v[2 * i] / s : 0.0;
-                            g[ci(i, J) + 1] = ok ? v[2 * i + 1] / s : 0.0;
+                            const double si = (double)kscale<R>(s);
+                            const bool ok = s > 0.0 && si * sj > 0.0;
+                            g[ci(i, J)] = ok ? v[2 * i] / (si * sj) / s : 0.0;
+                            g[ci(i, J) + 1] = ok ? v[2 * i + 1] / (si * sj) / s : 0.0;
                           }
                         });
 }
@@ -232,7 +251,8 @@ k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
-  double acc[1] = {0.0};
+  R acc[1] = {R(0)};
+  const R sj = kscale<R>(gsc[b * kGmresScalars + J]);   // |q_{J+1}| ~ ||A|| |q_J|
   if (act) {
     C c[J + 1];
     const double *g = gsc + b * kGmresScalars;
@@ -249,7 +269,8 @@ k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
 #pragma unroll
       for (int i = 0; i <= J; ++i) v = csub(v, cmul(c[i], Q[(size_t)i * qs + o]));
       Q[(size_t)(J + 1) * qs + o] = v;
-      acc[0] += (double)v.x * v.x + (double)v.y * v.y;
+      const C vs = cscale(v, sj);
+      acc[0] += vs.x * vs.x + vs.y * vs.y;
     }
   }
   write_partials<1>(acc, act, parts, b);
@@ -257,7 +278,8 @@ k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
   last_block_reduce<1>(counter, parts, gridDim.x, gridDim.y, st,
                        [&](int bb, const double *v) {
                          double *g = gsc + bb * kGmresScalars;
-                         g[J + 1] = v[0];
+                         const double s = (double)kscale<R>(g[J]);
+                         g[J + 1] = s > 0.0 ? v[0] / (s * s) : v[0];
                          if (J + 1 == m) gm_lsq(g, m, tiny);
                        });
 }
@@ -312,7 +334,332 @@ k_gm_correct(LevelK<R> L, const typename Cx<R>::T *u_in, const typename Cx<R>::T
   }
 }
 
+// ---------------------------------------------------------------------------
+// The GMRES-smoothed cycle of the small levels in one block per right-hand
+// side.  Shared memory: per level its iterate U, right-hand side F,
+// coefficient tables and k^2 (the level's LevelK is re-pointed at these
+// copies, so the stencil arithmetic is that of the per-level kernels); the
+// Krylov vectors q_0..q_2 are shared by the levels, since a coarser level
+// runs only between a finer level's smoothing steps.  A q_J is not stored:
+// it is recomputed for the inner products and again for the
+// orthogonalisation.  Reductions are FP64 block sums in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int TB = 512;
+
+// Sum NQ doubles per thread over the block (TB / 32 warps; ws holds NQ x 32
+// slots, of which the first TB / 32 of each row are written); valid in
+// red[0..NQ) after it.
+template <int NQ, typename A>
+__device__ __forceinline__ void tail_reduce(A (&acc)[NQ], double *ws, double *red) {
+  static_assert(TB % 32 == 0 && TB / 32 <= 32, "one reduction slot per warp");
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double v = (double)acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) ws[q * 32 + w] = v;
+  }
+  __syncthreads();
+  if (w < NQ) {
+    double v = lane < TB / 32 ? ws[w * 32 + lane] : 0.0;   // one slot per warp of the block
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w] = v;
+  }
+  __syncthreads();
+}
+
+template <typename R, int DIM>
+__device__ __forceinline__ LevelK<R> tail_level(const GmTailArgs<R> &A, typename Cx<R>::T *cm,
+                                                R *km, int i) {
+  LevelK<R> K = A.lv[i].K;
+  const int N = K.N;
+  K.coef = cm + A.lv[i].offT;
+  K.k2 = km + A.lv[i].offK;
+  K.KP = N;
+  K.P = N;
+  K.S = (long long)npts<DIM>(N);
+  return K;
+}
+
+// One GMRES(m) step on level K (iterate U, right-hand side F; zero: U is
+// taken as zero).  g: FP64 scalars in the layout of gm_lsq; ws, red: scratch.
+// Every loop over Krylov indices is unrolled to its bound (m <= 3), so the
+// vectors and coefficients stay in registers.
+template <typename R, int DIM>
+__device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
+                             const typename Cx<R>::T *F, typename Cx<R>::T *Q0,
+                             typename Cx<R>::T *Q1, typename Cx<R>::T *Q2, int m, bool zero,
+                             double *g, double *ws, double *red) {
+  using C = typename Cx<R>::T;
+  const int N = K.N;
+  const int npt = (int)npts<DIM>(N);
+  const double tiny = sizeof(R) == 4 ? 1e-12 : 1e-26;
+  auto Q = [&](int i) { return i == 0 ? Q0 : (i == 1 ? Q1 : Q2); };
+  // q_0 = F - A U, |q_0|^2 (per-thread sums in the vectors' precision)
+  {
+    R acc[1] = {R(0)};
+    auto get = [&](int xx, int yy, int zz) { return U[at<DIM>(xx, yy, zz, N, N)]; };
+    for (int p = threadIdx.x; p < npt; p += TB) {
+      C r = F[p];
+      if (!zero) {
+        int x, y, z;
+        coords<DIM>(p, N, x, y, z);
+        C Au, D, uc;
+        stencil<R, DIM>(K, x, y, z, get, Au, D, uc);
+        r = csub(r, Au);
+      }
+      Q0[p] = r;
+      acc[0] += r.x * r.x + r.y * r.y;
+    }
+    tail_reduce<1>(acc, ws, red);
+    if (threadIdx.x == 0) g[0] = red[0];
+    __syncthreads();   // every thread reads g[0] (the scale of q_0) next
+  }
+#pragma unroll
+  for (int J = 0; J < 3; ++J) {
+    if (J >= m) break;
+    const C *qj = Q(J);
+    auto get = [&](int xx, int yy, int zz) { return qj[at<DIM>(xx, yy, zz, N, N)]; };
+    R sc[3];   // kscale of q_0..q_J (g[0..J] were written before the barrier)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) sc[i] = i <= J ? kscale<R>(g[i]) : R(0);
+    // <q_i, A q_J> for i <= J
+    {
+      R acc[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) acc[i] = R(0);
+      for (int p = threadIdx.x; p < npt; p += TB) {
+        int x, y, z;
+        coords<DIM>(p, N, x, y, z);
+        C Aq, D, qc;
+        stencil<R, DIM>(K, x, y, z, get, Aq, D, qc);
+        const C a = cscale(Aq, sc[J]);
+#pragma unroll
+        for (int i = 0; i <= J; ++i) {
+          const C qi = cscale(Q(i)[p], sc[i]);
+          acc[2 * i] += qi.x * a.x + qi.y * a.y;
+          acc[2 * i + 1] += qi.x * a.y - qi.y * a.x;
+        }
+      }
+      tail_reduce<6>(acc, ws, red);
+      if (threadIdx.x == 0) {
+        const double sj = (double)sc[J];
+        for (int i = 0; i <= J; ++i) {
+          const double sq = g[i];
+          const double si = (double)sc[i];
+          const bool ok = sq > 0.0 && si * sj > 0.0;
+          g[ci(i, J)] = ok ? red[2 * i] / (si * sj) / sq : 0.0;
+          g[ci(i, J) + 1] = ok ? red[2 * i + 1] / (si * sj) / sq : 0.0;
+        }
+      }
+      __syncthreads();
+    }
+    // q_{J+1} = A q_J - sum_i c_iJ q_i (stored below m), |q_{J+1}|^2
+    {
+      C c[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        c[i] = i <= J ? cmk((R)g[ci(i, J)], (R)g[ci(i, J) + 1]) : czero<C>();
+      R acc[1] = {R(0)};
+      C *qn = J + 1 < m ? Q(J + 1) : nullptr;
+      for (int p = threadIdx.x; p < npt; p += TB) {
+        int x, y, z;
+        coords<DIM>(p, N, x, y, z);
+        C v, D, qc;
+        stencil<R, DIM>(K, x, y, z, get, v, D, qc);
+#pragma unroll
+        for (int i = 0; i <= J; ++i) v = csub(v, cmul(c[i], Q(i)[p]));
+        if (qn) qn[p] = v;
+        const C vs = cscale(v, sc[J]);
+        acc[0] += vs.x * vs.x + vs.y * vs.y;
+      }
+      tail_reduce<1>(acc, ws, red);
+      if (threadIdx.x == 0) {
+        const double sj = (double)sc[J];
+        g[J + 1] = sj > 0.0 ? red[0] / (sj * sj) : red[0];
+        if (J + 1 == m) gm_lsq(g, m, tiny);
+      }
+      __syncthreads();
+    }
+  }
+  // U = U + sum_j z_j q_j
+  {
+    const int k = min(m, (int)g[25]);
+    C z[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) z[j] = cmk((R)g[16 + 2 * j], (R)g[17 + 2 * j]);
+    for (int p = threadIdx.x; p < npt; p += TB) {
+      C v = zero ? czero<C>() : U[p];
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        if (j < k) v = cfma(z[j], Q(j)[p], v);
+      U[p] = v;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R, int DIM>
+__global__ void __launch_bounds__(TB) k_gm_tail(const __grid_constant__ GmTailArgs<R> A,
+                                                const SolveState *st) {
+  using C = typename Cx<R>::T;
+  const int b = blockIdx.x;
+  if (!__syncthreads_and(!(st && !st[b].active))) return;   // one decision per block
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *cm = reinterpret_cast<C *>(smem_raw);
+  R *km = reinterpret_cast<R *>(smem_raw + A.kbase);
+  double2 *slu = reinterpret_cast<double2 *>(smem_raw + A.lubase);
+  const int mm = A.mm;
+  int *spiv = reinterpret_cast<int *>(slu + mm * mm);
+  __shared__ double g[kGmresScalars];
+  __shared__ double ws[6 * 32];
+  __shared__ double red[6];
+  C *const Q0 = cm + A.offQ[0], *const Q1 = cm + A.offQ[1], *const Q2 = cm + A.offQ[2];
+  // stage the top right-hand side, every level's tables and k^2, the LU
+  {
+    const int N = A.lv[0].K.N;
+    const C *fb = A.f + (size_t)b * A.lay.S;
+    C *F = cm + A.lv[0].offF;
+    for (int p = threadIdx.x; p < (int)npts<DIM>(N); p += TB) {
+      int x, y, z;
+      coords<DIM>(p, N, x, y, z);
+      F[p] = fb[at<DIM>(x, y, z, N, A.lay.P)];
+    }
+  }
+  for (int i = 0; i < A.nl; ++i) {
+    const LevelK<R> &G = A.lv[i].K;
+    const int N = G.N;
+    C *tab = cm + A.lv[i].offT;
+    for (int j = threadIdx.x; j < 3 * DIM * N; j += TB) tab[j] = G.coef[j];
+    R *kk = km + A.lv[i].offK;
+    for (int p = threadIdx.x; p < (int)npts<DIM>(N); p += TB) {
+      int x, y, z;
+      coords<DIM>(p, N, x, y, z);
+      kk[p] = G.k2[at<DIM>(x, y, z, N, G.KP)];
+    }
+  }
+  for (int j = threadIdx.x; j < mm * mm; j += TB) slu[j] = A.lu[j];
+  for (int j = threadIdx.x; j < mm; j += TB) spiv[j] = A.piv[j];
+  __syncthreads();
+  // way down: smoothing from zero, residual, full weighting
+  for (int i = 0; i + 1 < A.nl; ++i) {
+    const LevelK<R> K = tail_level<R, DIM>(A, cm, km, i);
+    const int N = K.N, Nc = A.lv[i + 1].K.N;
+    C *U = cm + A.lv[i].offU;
+    const C *F = cm + A.lv[i].offF;
+    for (int s = 0; s < A.nu1; ++s)
+      tail_gm_step<R, DIM>(K, U, F, Q0, Q1, Q2, A.m, s == 0, g, ws, red);
+    {
+      auto get = [&](int xx, int yy, int zz) { return U[at<DIM>(xx, yy, zz, N, N)]; };
+      for (int p = threadIdx.x; p < (int)npts<DIM>(N); p += TB) {
+        int x, y, z;
+        coords<DIM>(p, N, x, y, z);
+        C Au, D, uc;
+        stencil<R, DIM>(K, x, y, z, get, Au, D, uc);
+        Q0[p] = csub(F[p], Au);
+      }
+    }
+    __syncthreads();
+    {
+      const C *r = Q0;
+      C *Fc = cm + A.lv[i + 1].offF;
+      const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
+      const R scale = DIM == 3 ? R(1.0 / 64.0) : R(1.0 / 16.0);
+      const C cs = A.lv[i].c;
+      for (int pc = threadIdx.x; pc < (int)npts<DIM>(Nc); pc += TB) {
+        int cx, cy, cz;
+        coords<DIM>(pc, Nc, cx, cy, cz);
+        C acc = czero<C>();
+        for (int dz = zlo; dz <= zhi; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int x = 2 * cx + 1 + dx, y = 2 * cy + 1 + dy;
+              const int z = DIM == 3 ? 2 * cz + 1 + dz : 0;
+              const R w = R((2 - abs(dx)) * (2 - abs(dy)) * (DIM == 3 ? 2 - abs(dz) : 1));
+              acc = cadd(acc, cscale(r[at<DIM>(x, y, z, N, N)], w));
+            }
+        Fc[pc] = cmul(cs, cscale(acc, scale));
+      }
+    }
+    __syncthreads();
+  }
+  // coarsest level: LU substitution (FP64) by one warp, lane i owning row i
+  if (threadIdx.x < 32) {
+    const int i = threadIdx.x;
+    const C *fl = cm + A.lv[A.nl - 1].offF;
+    C *ul = cm + A.lv[A.nl - 1].offU;
+    double2 y = make_double2(0.0, 0.0);
+    if (i < mm) {
+      const C q = fl[spiv[i]];
+      y = make_double2((double)q.x, (double)q.y);
+    }
+    for (int k = 0; k < mm; ++k) {
+      const double2 yk = make_double2(__shfl_sync(0xffffffffu, y.x, k), __shfl_sync(0xffffffffu, y.y, k));
+      if (i > k && i < mm) y = csub(y, cmul(slu[i * mm + k], yk));
+    }
+    for (int k = mm - 1; k >= 0; --k) {
+      if (i == k) y = cmul(y, slu[k * mm + k]);   // the diagonal holds 1 / U_kk
+      const double2 yk = make_double2(__shfl_sync(0xffffffffu, y.x, k), __shfl_sync(0xffffffffu, y.y, k));
+      if (i < k) y = csub(y, cmul(slu[i * mm + k], yk));
+    }
+    if (i < mm) ul[i] = cmk((R)y.x, (R)y.y);
+  }
+  __syncthreads();
+  // way up: interpolated correction, smoothing
+  for (int i = A.nl - 2; i >= 0; --i) {
+    const LevelK<R> K = tail_level<R, DIM>(A, cm, km, i);
+    const int N = K.N, Nc = A.lv[i + 1].K.N;
+    C *U = cm + A.lv[i].offU;
+    const C *F = cm + A.lv[i].offF;
+    const C *E = cm + A.lv[i + 1].offU;
+    const Lay lc{Nc, Nc, (long long)npts<DIM>(Nc)};
+    for (int p = threadIdx.x; p < (int)npts<DIM>(N); p += TB) {
+      int x, y, z;
+      coords<DIM>(p, N, x, y, z);
+      U[p] = cadd(U[p], prolong_at<R, DIM>(E, lc, x, y, z));
+    }
+    __syncthreads();
+    for (int s = 0; s < A.nu2; ++s)
+      tail_gm_step<R, DIM>(K, U, F, Q0, Q1, Q2, A.m, false, g, ws, red);
+  }
+  {
+    const int N = A.lv[0].K.N;
+    C *ub = A.u + (size_t)b * A.lay.S;
+    const C *U = cm + A.lv[0].offU;
+    for (int p = threadIdx.x; p < (int)npts<DIM>(N); p += TB) {
+      int x, y, z;
+      coords<DIM>(p, N, x, y, z);
+      ub[at<DIM>(x, y, z, N, A.lay.P)] = U[p];
+    }
+  }
+}
+
 }  // namespace
+
+template <typename R, int DIM> size_t gmres_tail_smem(const int *N, int nl, int m) {
+  (void)m;
+  using C = typename Cx<R>::T;
+  size_t c = 3 * npts<DIM>(N[0]);          // q_0..q_2
+  size_t r = 0;
+  for (int i = 0; i < nl; ++i) {
+    c += 2 * npts<DIM>(N[i]) + 3 * DIM * (size_t)N[i];
+    r += npts<DIM>(N[i]);
+  }
+  const size_t kb = (c * sizeof(C) + 15) / 16 * 16;
+  const size_t lb = (kb + r * sizeof(R) + 15) / 16 * 16;
+  const size_t mm = npts<DIM>(N[nl - 1]);
+  return lb + mm * mm * sizeof(double2) + mm * sizeof(int);
+}
+
+template <typename R, int DIM> cudaError_t init_gmres_tail() {
+  return cudaFuncSetAttribute(k_gm_tail<R, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kGmTailSmemMax);
+}
+
+template <typename R, int DIM>
+void launch_gmres_tail(const GmTailArgs<R> &a, int batch, const SolveState *st, cudaStream_t s) {
+  k_gm_tail<R, DIM><<<batch, TB, a.smem_bytes, s>>>(a, st);
+}
 
 template <typename R, int DIM>
 void launch_gmres_start(const LevelK<R> &L, const typename Cx<R>::T *u, int zero_mode,
@@ -360,6 +707,15 @@ void launch_gmres_correct(const LevelK<R> &L, const typename Cx<R>::T *u_in,
   template void launch_gmres_correct<R, DIM>(const LevelK<R> &, const Cx<R>::T *,              \
                                              const Cx<R>::T *, const Lay &, Cx<R>::T *, int,   \
                                              const SolveState *, cudaStream_t);
+#define HH_GMTAIL_INST(R, DIM)                                                                 \
+  template size_t gmres_tail_smem<R, DIM>(const int *, int, int);                              \
+  template cudaError_t init_gmres_tail<R, DIM>();                                              \
+  template void launch_gmres_tail<R, DIM>(const GmTailArgs<R> &, int, const SolveState *,      \
+                                          cudaStream_t);
+HH_GMTAIL_INST(float, 2)
+HH_GMTAIL_INST(float, 3)
+HH_GMTAIL_INST(double, 2)
+HH_GMTAIL_INST(double, 3)
 HH_GMRES_INST(float, 2)
 HH_GMRES_INST(float, 3)
 HH_GMRES_INST(double, 2)

@@ -40,4 +40,36 @@ void launch_gmres_correct(const LevelK<R> &L, const typename Cx<R>::T *u_in,
                           const typename Cx<R>::T *e, const Lay &lc, typename Cx<R>::T *u_out,
                           int batch, const SolveState *st, cudaStream_t s);
 
+// The GMRES(m)-smoothed cycle on the small levels t0 .. coarsest in one
+// block of 512 threads per right-hand side, every array in shared memory
+// (hh_gmres.cu): from a zero initial guess, nu1 GMRES steps, residual and
+// full weighting on the way down, the coarsest LU, and interpolated
+// correction plus nu2 GMRES steps on the way up.  Only the right-hand side of
+// level t0 is read from and its correction written to global memory.
+constexpr int kGmTailMax = 8;
+template <typename R> struct GmTailLevel {
+  LevelK<R> K;                 // the level (tables and k^2 in global memory)
+  typename Cx<R>::T c;         // scale of the residual restricted from it
+  int offU, offF, offT;        // complex offsets in shared memory: iterate,
+                               // right-hand side, coefficient tables (3 dim N)
+  int offK;                    // real offset of k^2 (N^dim)
+};
+template <typename R> struct GmTailArgs {
+  int nl, m, nu1, nu2;
+  GmTailLevel<R> lv[kGmTailMax];
+  int offQ[3];                 // Krylov vectors q_0..q_2 (sized for level t0)
+  int kbase, lubase, smem_bytes;
+  const typename Cx<R>::T *f;  // right-hand side of level t0 (library layout lay)
+  typename Cx<R>::T *u;        // its correction
+  Lay lay;
+  const double2 *lu;           // coarsest LU factors (FP64) and pivots
+  const int *piv;
+  int mm;
+};
+template <typename R, int DIM> size_t gmres_tail_smem(const int *N, int nl, int m);
+template <typename R, int DIM> cudaError_t init_gmres_tail();
+template <typename R, int DIM>
+void launch_gmres_tail(const GmTailArgs<R> &a, int batch, const SolveState *st, cudaStream_t s);
+constexpr size_t kGmTailSmemMax = 200 * 1024;
+
 }  // namespace hh
