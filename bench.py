@@ -708,6 +708,28 @@ def run_group(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_cycles(args):
+    """Run --profile-cycles V-cycles of the workload through hh_cycles (every
+    kernel launched directly on the stream, no graph) and exit: the target of
+    launch-list captures of one cycle's kernels."""
+    import numpy as np
+    import torch
+    from paper_1211_4752_gb300 import HelmholtzMG, workloads as W
+    w = getattr(W, args.workload)(*args.workload_arg)
+    k2 = w["k2"]
+    k2_t = torch.from_numpy(k2).cuda() if isinstance(k2, np.ndarray) else float(k2)
+    mg = HelmholtzMG(w["n"], dim=w["dim"], k2=k2_t, layers=w["layers"],
+                     precision=args.precision, max_batch=1, smoother=args.smoother)
+    f = torch.from_numpy(w["rhs"][:1].copy()).cuda()
+    u = mg.cycles(f, torch.zeros_like(f), args.profile_cycles)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": "cycles", "workload": w["name"], "cycles": args.profile_cycles,
+                      "smoother": args.smoother, "precision": args.precision,
+                      "kernels_per_cycle": mg.cycle_kernels,
+                      "unorm": float(u.abs().pow(2).sum().sqrt())}))
+    mg.close()
+
+
 def profile_fgmres(args):
     """One FGMRES(restart) solve of the workload capped at --fgmres-iterations
     iterations, then exit: the target of launch-list captures of the Krylov
@@ -757,7 +779,9 @@ def main():
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-cycles", type=int, default=4)
-    ap.add_argument("--kernel", choices=sorted(KERNELS.values()) + ["fgmres"],
+    ap.add_argument("--profile-cycles", type=int, default=4,
+                    help="V-cycles run by --kernel cycles")
+    ap.add_argument("--kernel", choices=sorted(KERNELS.values()) + ["fgmres", "cycles"],
                     help="launch one level-0 kernel of the workload (or one capped FGMRES "
                          "solve) and exit (for ncu)")
     ap.add_argument("--kernel-n", type=int, default=0,
@@ -771,6 +795,8 @@ def main():
         run_group(args)
     elif args.kernel == "fgmres":
         profile_fgmres(args)
+    elif args.kernel == "cycles":
+        profile_cycles(args)
     elif args.kernel:
         profile_one(args)
     else:

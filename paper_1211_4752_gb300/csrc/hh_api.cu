@@ -1061,7 +1061,7 @@ template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, 
   HH_CK(cudaEventCreate(&e1));
   float tbest = 1e30f;
   *best = 0;
-  for (int v = 0; v < kNumTileVariants; ++v) {
+  for (int v = 0; v < (l == 0 ? kLevel0Variants : kNumTileVariants); ++v) {
     DownMaps dm;
     UpMaps um;
     HH_TRY(make_maps<R>(h, l, v, &dm, &um));
@@ -1281,7 +1281,7 @@ hh_status setup_persist(hh_handle *h, cudaStream_t s) {
 //   }
 // The format tag at the start of a key changes whenever the tuned set does,
 // so a file from another build is never misread.
-constexpr const char *kTunerFormat = "v2";
+constexpr const char *kTunerFormat = "v3";
 
 std::string tuner_key(const hh_handle *h) {
   int sms = 0;
@@ -1508,14 +1508,15 @@ hh_status autotune(hh_handle *h, cudaStream_t s) {
     const auto it = cache.find(key);
     if (it != cache.end() && (int)it->second.size() > tuned &&
         std::all_of(it->second.begin(), it->second.begin() + tuned,
-                    [](int v) { return v >= 0 && v < kNumTileVariants; }))
+                    [](int v) { return v >= 0 && v < kNumTileVariants; }) &&
+        (tuned == 0 || it->second[0] < kLevel0Variants))
       hit = &it->second;
   }
   bool timed = false;
   const char *force = std::getenv("HH_TILE_VARIANT");
   if (force) {
     const int v = std::atoi(force);
-    if (v < 0 || v >= kNumTileVariants) return fail(HH_ERR_ARG, "HH_TILE_VARIANT out of range");
+    if (v < 0 || v >= kLevel0Variants) return fail(HH_ERR_ARG, "HH_TILE_VARIANT out of range");
     for (int l = 0; l < h->tail0; ++l) h->variant[l] = v;
   } else if (hit) {
     for (int l = 0; l < tuned; ++l) h->variant[l] = (*hit)[l];
@@ -1839,7 +1840,7 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
     }
   }
   h->parts_cap = partial_blocks(h->lv[0].pts);
-  for (int v = 0; v < kNumTileVariants; ++v)
+  for (int v = 0; v < kLevel0Variants; ++v)
     h->parts_cap = std::max(h->parts_cap, tile_parts(v, h->lv[0].N));
   HH_TRY(dev_alloc_n(h, &h->partials, (size_t)h->parts_cap * B));
   HH_TRY(dev_alloc_n(h, &h->err, 1));

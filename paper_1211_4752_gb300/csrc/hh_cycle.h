@@ -6,7 +6,9 @@
 
 namespace hh {
 
-constexpr int kNumTileVariants = 5;  // tile shapes of k_down2d / k_up2d
+constexpr int kNumTileVariants = 7;  // tile shapes of k_down2d / k_up2d
+constexpr int kLevel0Variants = 5;   // those tried on level 0 (the small tiles
+                                     // serve the coarse levels only)
 constexpr int kMaxTail = 8;          // levels handled by the tail kernel
 
 // One level of the tail: operator, right-hand side, pre-smoothed iterate v,

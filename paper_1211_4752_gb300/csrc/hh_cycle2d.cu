@@ -11,7 +11,10 @@ namespace hh {
 namespace {
 
 struct Shape { int bx, by; };
-constexpr Shape kShapes[kNumTileVariants] = {{60, 16}, {60, 32}, {28, 32}, {120, 16}, {28, 16}};
+// (the last two are small tiles for the coarse levels, whose launches are
+// bound by one block's chain of copy, phases and stores rather than by bytes)
+constexpr Shape kShapes[kNumTileVariants] = {{60, 16}, {60, 32}, {28, 32}, {120, 16}, {28, 16},
+                                             {28, 8}, {12, 8}};
 
 // Launch with programmatic stream serialization: the kernel may start while
 // the previous kernel on the stream finishes; it waits for it with
@@ -349,6 +352,8 @@ cudaError_t init_cycle2d() {
   if ((e = attr_one<R, 28, 32>()) != cudaSuccess) return e;
   if ((e = attr_one<R, 120, 16>()) != cudaSuccess) return e;
   if ((e = attr_one<R, 28, 16>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 28, 8>()) != cudaSuccess) return e;
+  if ((e = attr_one<R, 12, 8>()) != cudaSuccess) return e;
   return attrs(k_tail2d<R>, kTailSmemMax);
 }
 
@@ -362,7 +367,9 @@ void launch_down2d(int variant, const DownMaps &maps, const LevelK<R> &L, int ze
     case 1: down_one<R, 60, 32>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
     case 2: down_one<R, 28, 32>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
     case 3: down_one<R, 120, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
-    default: down_one<R, 28, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
+    case 4: down_one<R, 28, 16>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
+    case 5: down_one<R, 28, 8>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
+    default: down_one<R, 12, 8>(maps, L, zero_mode, v_out, fc, cs, omega, kconst, lc, batch, st, partials, err, s); break;
   }
 }
 
@@ -375,7 +382,9 @@ void launch_up2d(int variant, const UpMaps &maps, const LevelK<R> &L, typename C
     case 1: up_one<R, 60, 32>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
     case 2: up_one<R, 28, 32>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
     case 3: up_one<R, 120, 16>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
-    default: up_one<R, 28, 16>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
+    case 4: up_one<R, 28, 16>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
+    case 5: up_one<R, 28, 8>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
+    default: up_one<R, 12, 8>(maps, L, u_out, omega, kconst, batch, st, err, s); break;
   }
 }
 

@@ -172,7 +172,7 @@ __device__ __forceinline__ void down_compute(
   {
     constexpr int NS = NT / VW, RS = (VH + NS - 1) / NS;
     const int tx = tid % VW, sg = tid / VW;
-    if (sg < NS) {
+    if (sg < NS && sg * RS < VH) {   // segments that start inside the region
       const int r0 = sg * RS;
       const int gx = x0 - 1 + tx;
       const bool colin = !CHECK || (gx >= 0 && gx < N);
@@ -248,7 +248,7 @@ __device__ __forceinline__ void down_compute(
   {
     constexpr int NS = NT / RW, RS = (RH + NS - 1) / NS;
     const int rx = tid % RW, sg = tid / RW;
-    if (sg < NS) {
+    if (sg < NS && sg * RS < RH) {
       const int q0 = sg * RS;
       const int tx = rx + 1;
       const bool colin = !CHECK || (x0 + rx < N);
@@ -474,7 +474,7 @@ __device__ __forceinline__ void up_compute(const LevelK<R> &L, typename Cx<R>::T
   {
     constexpr int NS = NT / BX, RS = (BY + NS - 1) / NS;
     const int lx = tid % BX, sg = tid / BX;
-    if (sg < NS) {
+    if (sg < NS && sg * RS < BY) {
       const int q0 = sg * RS;
       const int tx = lx + 1;
       const bool colin = !CHECK || (x0 + lx < N);

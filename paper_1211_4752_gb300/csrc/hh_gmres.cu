@@ -29,9 +29,25 @@ namespace {
 // square would overflow FP32 on fine grids.  Products s_i q_i . s_J A q_J
 // stay of the order of ||A||, and the block sums (FP64) are divided by
 // s_i s_J again.  complex128 vectors are summed unscaled in FP64.
+// The scales are formed once, where |q_i|^2 is finalised, and kept as FP32
+// values in the scalar slots 26..27 (four floats: q_0..q_3), so that no
+// thread forms an FP64 square root or division.
 template <typename R> __device__ __forceinline__ R kscale(double sq) {
   if (sizeof(R) == 8) return R(1);
   return sq > 0.0 ? R(1.0 / sqrt(sq)) : R(0);
+}
+__device__ __forceinline__ float *scale_slots(double *g) { return reinterpret_cast<float *>(g + 26); }
+__device__ __forceinline__ const float *scale_slots(const double *g) {
+  return reinterpret_cast<const float *>(g + 26);
+}
+template <typename R> __device__ __forceinline__ R kscale_of(const double *g, int i) {
+  if (sizeof(R) == 8) return R(1);
+  return R(scale_slots(g)[i]);
+}
+// set |q_i|^2 and its scale
+template <typename R> __device__ __forceinline__ void set_norm(double *g, int i, double sq) {
+  g[i] = sq;
+  scale_slots(g)[i] = (float)kscale<R>(sq);
 }
 
 // per right-hand side scalars (FP64): |q_i|^2 at 0..3; c_ij (complex) at
@@ -125,7 +141,7 @@ k_gm_start(LevelK<R> L, const typename Cx<R>::T *__restrict__ u, int zero_mode,
   }
   write_partials<1>(acc, act, parts, b);
   last_block_reduce<1>(counter, parts, gridDim.x, gridDim.y, st,
-                       [&](int bb, const double *v) { gsc[bb * kGmresScalars] = v[0]; });
+                       [&](int bb, const double *v) { set_norm<R>(gsc + bb * kGmresScalars, 0, v[0]); });
 }
 
 // w = A q_J; <q_i, w> for i <= J; c_iJ = <q_i, w> / |q_i|^2.
@@ -141,9 +157,9 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
   R acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[q] = R(0);
-  R sc[J + 1];   // kscale of q_0..q_J
+  R sc[J + 1];   // scales of q_0..q_J
 #pragma unroll
-  for (int i = 0; i <= J; ++i) sc[i] = kscale<R>(gsc[b * kGmresScalars + i]);
+  for (int i = 0; i <= J; ++i) sc[i] = kscale_of<R>(gsc + b * kGmresScalars, i);
   if (act) {
     const int N = L.N, P = L.P;
     const size_t off = (size_t)b * L.S;
@@ -170,10 +186,10 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
   last_block_reduce<NQ>(counter, parts, gridDim.x, gridDim.y, st,
                         [&](int bb, const double *v) {
                           double *g = gsc + bb * kGmresScalars;
-                          const double sj = (double)kscale<R>(g[J]);
+                          const double sj = (double)kscale_of<R>(g, J);
                           for (int i = 0; i <= J; ++i) {
                             const double s = g[i];
-                            const double si = (double)kscale<R>(s);
+                            const double si = (double)kscale_of<R>(g, i);
                             const bool ok = s > 0.0 && si * sj > 0.0;
                             g[ci(i, J)] = ok ? v[2 * i] / (si * sj) / s : 0.0;
                             g[ci(i, J) + 1] = ok ? v[2 * i + 1] / (si * sj) / s : 0.0;
@@ -252,7 +268,7 @@ k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
   const int b = blockIdx.y;
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
   R acc[1] = {R(0)};
-  const R sj = kscale<R>(gsc[b * kGmresScalars + J]);   // |q_{J+1}| ~ ||A|| |q_J|
+  const R sj = kscale_of<R>(gsc + b * kGmresScalars, J);   // |q_{J+1}| ~ ||A|| |q_J|
   if (act) {
     C c[J + 1];
     const double *g = gsc + b * kGmresScalars;
@@ -278,8 +294,8 @@ k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
   last_block_reduce<1>(counter, parts, gridDim.x, gridDim.y, st,
                        [&](int bb, const double *v) {
                          double *g = gsc + bb * kGmresScalars;
-                         const double s = (double)kscale<R>(g[J]);
-                         g[J + 1] = s > 0.0 ? v[0] / (s * s) : v[0];
+                         const double s = (double)kscale_of<R>(g, J);
+                         set_norm<R>(g, J + 1, s > 0.0 ? v[0] / (s * s) : v[0]);
                          if (J + 1 == m) gm_lsq(g, m, tiny);
                        });
 }
@@ -412,17 +428,17 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
       acc[0] += r.x * r.x + r.y * r.y;
     }
     tail_reduce<1>(acc, ws, red);
-    if (threadIdx.x == 0) g[0] = red[0];
-    __syncthreads();   // every thread reads g[0] (the scale of q_0) next
+    if (threadIdx.x == 0) set_norm<R>(g, 0, red[0]);
+    __syncthreads();   // every thread reads the scale of q_0 next
   }
 #pragma unroll
   for (int J = 0; J < 3; ++J) {
     if (J >= m) break;
     const C *qj = Q(J);
     auto get = [&](int xx, int yy, int zz) { return qj[at<DIM>(xx, yy, zz, N, N)]; };
-    R sc[3];   // kscale of q_0..q_J (g[0..J] were written before the barrier)
+    R sc[3];   // scales of q_0..q_J (written before the last barrier)
 #pragma unroll
-    for (int i = 0; i < 3; ++i) sc[i] = i <= J ? kscale<R>(g[i]) : R(0);
+    for (int i = 0; i < 3; ++i) sc[i] = i <= J ? kscale_of<R>(g, i) : R(0);
     // <q_i, A q_J> for i <= J
     {
       R acc[6];
@@ -476,7 +492,7 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
       tail_reduce<1>(acc, ws, red);
       if (threadIdx.x == 0) {
         const double sj = (double)sc[J];
-        g[J + 1] = sj > 0.0 ? red[0] / (sj * sj) : red[0];
+        set_norm<R>(g, J + 1, sj > 0.0 ? red[0] / (sj * sj) : red[0]);
         if (J + 1 == m) gm_lsq(g, m, tiny);
       }
       __syncthreads();

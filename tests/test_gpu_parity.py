@@ -527,7 +527,7 @@ def test_tuner_cache_gives_identical_handles(tmp_path):
     a = HelmholtzMG(n, **kw)
     data = json.loads(path.read_text())
     key = a.tuner_key
-    assert key in data and key.startswith("v2 dim=2 n=256 prec=mixed")
+    assert key in data and key.startswith("v3 dim=2 n=256 prec=mixed")
     sched = a.coarse_schedule
     tuned = 1 + sum(sched)                    # levels 0 .. T-1 carry a tile shape
     assert data[key][tuned] == len(sched)     # then the schedule: groups, (J, b, B) each
