@@ -719,7 +719,8 @@ def profile_cycles(args):
     k2 = w["k2"]
     k2_t = torch.from_numpy(k2).cuda() if isinstance(k2, np.ndarray) else float(k2)
     mg = HelmholtzMG(w["n"], dim=w["dim"], k2=k2_t, layers=w["layers"],
-                     precision=args.precision, max_batch=1, smoother=args.smoother)
+                     precision=args.precision, max_batch=1, smoother=args.smoother,
+                     tuner_cache=args.tuner_cache)
     f = torch.from_numpy(w["rhs"][:1].copy()).cuda()
     u = mg.cycles(f, torch.zeros_like(f), args.profile_cycles)
     torch.cuda.synchronize()
@@ -781,6 +782,9 @@ def main():
     ap.add_argument("--cpu-cycles", type=int, default=4)
     ap.add_argument("--profile-cycles", type=int, default=4,
                     help="V-cycles run by --kernel cycles")
+    ap.add_argument("--tuner-cache", default=None,
+                    help="tuner cache file of --kernel cycles (a second run with the same file "
+                         "launches no tuning kernels)")
     ap.add_argument("--kernel", choices=sorted(KERNELS.values()) + ["fgmres", "cycles"],
                     help="launch one level-0 kernel of the workload (or one capped FGMRES "
                          "solve) and exit (for ncu)")

@@ -349,7 +349,8 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
 
 /* The autotuner's key of this handle: the quantities its tile choices
  * depend on (dimension, grid size, precision, ECS layers, constant or
- * variable k^2, radiating ends, SM count and device name), as a string.
+ * variable k^2, radiating ends, the number of right-hand sides it times
+ * with = min(max_batch, 16), SM count and device name), as a string.
  * Writes at most `len` bytes including the terminating zero into buf and
  * returns the key's full length (without the zero), or -1 for a NULL
  * handle. */

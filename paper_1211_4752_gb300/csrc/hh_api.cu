@@ -1052,8 +1052,14 @@ void destroy_impl(hh_handle *h) {
 // Autotuner: per fused level, time the down and up passes of every tile
 // shape on the workspace (handle's precision, one right-hand side) and keep
 // the fastest, preferring the earlier shape within 3 %.  HH_TILE_VARIANT=<k> in the environment forces shape k.
+// Right-hand sides the autotuner times with: the handle's batch capacity, at
+// most 16 (a shape that suits one right-hand side's latency-bound launches
+// may not suit a batch's bandwidth-bound ones).
+int tune_batch(const hh_handle *h) { return std::min(h->max_batch, 16); }
+
 template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, int *best) {
   Work<R> &W = work<R>(h);
+  const int tb = tune_batch(h);
   const LevelK<R> K = levelk<R>(h, l, 0);
   const auto om = omega<R>(h, 0);
   cudaEvent_t e0, e1;
@@ -1067,8 +1073,8 @@ template <typename R> hh_status tune_level(hh_handle *h, int l, cudaStream_t s, 
     HH_TRY(make_maps<R>(h, l, v, &dm, &um));
     auto run = [&]() {
       launch_down2d<R>(v, dm, K, ZERO_NONE, W.u_pre[l], W.f[l + 1], cscal<R>(h, l, 0), om,
-                       h->kconst, lay_of(h, l + 1), 1, nullptr, nullptr, h->err, s);
-      launch_up2d<R>(v, um, K, W.u_post[l], om, h->kconst, 1, nullptr, h->err, s);
+                       h->kconst, lay_of(h, l + 1), tb, nullptr, nullptr, h->err, s);
+      launch_up2d<R>(v, um, K, W.u_post[l], om, h->kconst, tb, nullptr, h->err, s);
     };
     run();
     float t = 1e30f;   // best of three trials of four down + up passes
@@ -1292,10 +1298,11 @@ std::string tuner_key(const hh_handle *h) {
   for (char &c : dev)
     if (c == '"' || c == '\\' || (unsigned char)c < 32) c = '_';
   char b[512];
-  std::snprintf(b, sizeof b, "%s dim=%d n=%d prec=%s layers=%d,%d k2=%s sommerfeld=%d sms=%d dev=%s",
+  std::snprintf(b, sizeof b,
+                "%s dim=%d n=%d prec=%s layers=%d,%d k2=%s sommerfeld=%d batch=%d sms=%d dev=%s",
                 kTunerFormat, h->dim, h->n, h->opt.precision == HH_MIXED ? "mixed" : "fp64",
                 h->grid.layer_lo, h->grid.layer_hi, h->kconst ? "const" : "field",
-                h->grid.sommerfeld, sms, dev.c_str());
+                h->grid.sommerfeld, tune_batch(h), sms, dev.c_str());
   return b;
 }
 
@@ -1406,10 +1413,11 @@ void coarse_candidates(int n, std::vector<std::vector<hh_handle::CoarseGroup>> *
 template <typename R> hh_status time_coarse(hh_handle *h, cudaStream_t s, float *ms) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
+  const int tb = tune_batch(h);
   HH_CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  enqueue_coarse_down<R>(h, 0, 1, nullptr, h->cap);
-  enqueue_tail<R>(h, 0, 1, nullptr, h->cap);
-  enqueue_coarse_up<R>(h, 0, 1, nullptr, h->cap);
+  enqueue_coarse_down<R>(h, 0, tb, nullptr, h->cap);
+  enqueue_tail<R>(h, 0, tb, nullptr, h->cap);
+  enqueue_coarse_up<R>(h, 0, tb, nullptr, h->cap);
   HH_CK(cudaStreamEndCapture(h->cap, &g));
   const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
