@@ -43,6 +43,13 @@ sys.path.insert(0, str(ROOT))
 #   FP64 refinement: read u64, e32, f64, k2_64; write u64, rhs32 = 72 B
 # complex128 cycles: twice the cycle figures.
 KERNELS = {0: "down_pass", 2: "up_pass", 3: "refine_fp64", 4: "tail_levels"}
+# 3-D (7-point) cycle: the tile-staged level kernels, algorithmic bytes per
+# fine point in complex64 (k^2 field: + 4 B read per pass):
+#   sweep (Jacobi):                 read u, f; write u         = 24 B
+#   residual + restriction:         read u, f; write f_c / 8   = 17 B
+#   correction + sweep:             read u, e / 8, f; write u  = 25 B
+KERNELS3 = {0: "sweep_3d", 1: "resid_restrict_3d", 2: "correct_sweep_3d"}
+BYTES3 = {0: 24.0, 1: 17.0, 2: 25.0}
 
 
 def kernel_bytes(kid, kconst, mixed):
@@ -262,6 +269,21 @@ def run_ours(args):
                                        ct.c_void_p(stream.cuda_stream)))
         kt[kid] = ms.value
     roofline = None
+    if dim == 3 and args.smoother == "jacobi":
+        # the 3-D cycle's level-0 kernels, timed live back to back
+        kt3 = {}
+        for kid in (0, 1, 2):
+            ms = ct.c_double()
+            B.check(B.lib().hh_time_kernel(mg._h, kid, 0, 1, 20, ct.byref(ms),
+                                           ct.c_void_p(stream.cuda_stream)))
+            kt3[kid] = ms.value
+        dom = max(kt3, key=lambda k: kt3[k])
+        bpp = (BYTES3[dom] + (0.0 if kconst else 4.0)) * (1.0 if mixed else 2.0)
+        achieved = bpp * pts / (kt3[dom] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": KERNELS3[dom], "achieved": achieved, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "bytes_per_point": bpp,
+                    "launch_ms": {KERNELS3[k]: v for k, v in kt3.items()}}
     if fused:
         dom = max((0, 2), key=lambda k: kt[k])
         name = KERNELS[dom]

@@ -342,7 +342,9 @@ hh_status hh_coarse_solve(hh_handle *h, const void *f_dev, void *e_dev,
  *   kernel 3: FP64 refinement residual on level 0 (MIXED handles only)
  *   kernel 4: the single-block kernel of the small levels (fused 2-D path)
  *   kernel 5: one whole V-cycle (no stop test), replayed as a CUDA graph
- * Kernels 0-2, 4, 5 run in the handle's precision.  Workspace contents are
+ *   kernel 6: one GMRES(m) smoothing step on `level` from a nonzero iterate
+ *             (its start, m Arnoldi steps and update; GMRES handles only)
+ * Kernels 0-2, 4-6 run in the handle's precision.  Workspace contents are
  * overwritten (the handle stays valid).  For benchmarks and profiles. */
 hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
                          int reps, double *ms, void *stream);

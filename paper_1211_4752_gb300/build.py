@@ -21,7 +21,7 @@ OUT_DIR = PKG / "_lib"
 LIB_NAME = "libhh_gb300.so"
 SOURCES = ["hh_api.cu", "hh_kernels_common.cu", "hh_kernels_2d.cu",
            "hh_kernels_3d.cu", "hh_cycle2d.cu", "hh_mid2d.cu", "hh_gmres.cu", "hh_noalloc.cu",
-           "hh_krylov.cu", "hh_vcycle2d.cu", "hh_coarse2d.cu", "hh_group2d.cu"]
+           "hh_krylov.cu", "hh_vcycle2d.cu", "hh_coarse2d.cu", "hh_group2d.cu", "hh_tiled3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
          "--extended-lambda", "-Xcompiler", "-fPIC", "-I", str(ROOT / "include")]

@@ -11,6 +11,7 @@
 #include "hh_cycle.h"
 #include "hh_gmres.h"
 #include "hh_krylov.h"
+#include "hh_tiled3d.h"
 
 #include <cudaTypedefs.h>
 
@@ -136,6 +137,7 @@ struct hh_handle {
   int ngroups = 0;
   CoarseGroup groups[MAXL];
   int parts_cap = 0;                // capacity of `partials` per RHS
+  int gm_cap = 0;                   // most blocks of a GMRES smoothing kernel
   cudaStream_t side = nullptr;      // branch of the stop test in the fused cycle
   cudaStream_t grp = nullptr;       // this handle's stream in a group solve (lazy)
   cudaEvent_t ev_grp = nullptr;     // its join event
@@ -315,6 +317,16 @@ inline bool stop_test(int check) { return check == CHECK_CYCLE || check == CHECK
 // scaled full-weighting restriction of the residual, LU on the coarsest level,
 // interpolated correction + post-smoothing.  The level-0 iterate is read from
 // and written to W.u_post[0]; W.f[0] holds the right-hand side.
+// 3-D cycles use the tile-staged kernels (hh_tiled3d.cu); HH_POINTWISE3D=1 in
+// the environment selects the point-wise kernels instead (for comparisons).
+bool pointwise3d() {
+  static const bool v = [] {
+    const char *e = std::getenv("HH_POINTWISE3D");
+    return e && std::strcmp(e, "1") == 0;
+  }();
+  return v;
+}
+
 template <typename R> GmresWork<R> gmres_work(hh_handle *h, int l) {
   Work<R> &W = work<R>(h);
   GmresWork<R> g;
@@ -326,8 +338,14 @@ template <typename R> GmresWork<R> gmres_work(hh_handle *h, int l) {
   g.gsc = h->gm_gsc;
   return g;
 }
+// Blocks of the GMRES smoothing kernels on level l (grid-stride loops of 256
+// threads, at most gm_cap; one partial sum per block and quantity).
+int gmres_blocks(const hh_handle *h, int l) {
+  const size_t g = (h->lv[l].pts + 255) / 256;
+  return (int)std::max<size_t>(1, std::min<size_t>(g, (size_t)h->gm_cap));
+}
 int partial_blocks_of(const hh_handle *h, int l) {
-  return l == 0 ? h->nparts : partial_blocks(h->lv[l].pts);
+  return l == 0 ? h->nparts : gmres_blocks(h, l);
 }
 
 // The V-cycle with GMRES(m) smoothing (Sec. 3.2): on each level nu1 GMRES
@@ -360,8 +378,12 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
       in = W.u_pre[l];
       zm = ZERO_NONE;
     }
-    launch_resid_restrict<R, DIM>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
-                                  cscal<R>(h, l, dir), batch, st, s);
+    if (DIM == 3 && !pointwise3d())
+      launch_resid_restrict3d<R>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
+                                 cscal<R>(h, l, dir), batch, st, s);
+    else
+      launch_resid_restrict<R, DIM>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
+                                    cscal<R>(h, l, dir), batch, st, s);
   }
   if (h->gtail0 > 0) {
     if constexpr (std::is_same<R, float>::value)
@@ -403,8 +425,11 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
       typename Cx<R>::T *out = ((h->opt.nu1 - 1 - j) % 2 == 0) ? W.u_pre[l] : W.tmp[l];
       const int zm = j == 0 ? (l == 0 ? zero0 : ZERO_ALL) : ZERO_NONE;
       const bool norm = l == 0 && j == 0 && stop_test(check);
-      launch_smooth<R, DIM>(K, in, zm, W.f[l], out, om, batch, st,
-                            norm ? h->partials : nullptr, h->nparts, s);
+      if (DIM == 3 && !pointwise3d())
+        launch_smooth3d<R>(K, in, zm, W.f[l], out, om, batch, st, norm ? h->partials : nullptr, s);
+      else
+        launch_smooth<R, DIM>(K, in, zm, W.f[l], out, om, batch, st,
+                              norm ? h->partials : nullptr, h->nparts, s);
       if (norm) {
         if (check == CHECK_CYCLE)
           launch_check_cycle(h->st, h->partials, h->params, h->flag, cond, h->copies, h->err, s);
@@ -413,8 +438,12 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
       }
       in = out;
     }
-    launch_resid_restrict<R, DIM>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
-                                  cscal<R>(h, l, dir), batch, st, s);
+    if (DIM == 3 && !pointwise3d())
+      launch_resid_restrict3d<R>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
+                                 cscal<R>(h, l, dir), batch, st, s);
+    else
+      launch_resid_restrict<R, DIM>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
+                                    cscal<R>(h, l, dir), batch, st, s);
   }
   launch_coarse_solve<R, DIM>(h->lu[dir], h->piv[dir], lay_of(h, L - 1), W.f[L - 1],
                          W.u_post[L - 1], batch, st, s);
@@ -423,9 +452,14 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
     const typename Cx<R>::T *in = nullptr;
     for (int j = 0; j < h->opt.nu2; ++j) {
       typename Cx<R>::T *out = ((h->opt.nu2 - 1 - j) % 2 == 0) ? W.u_post[l] : W.tmp[l];
-      if (j == 0)
+      if (j == 0 && DIM == 3 && !pointwise3d())
+        launch_correct_smooth3d<R>(K, W.u_pre[l], W.u_post[l + 1], lay_of(h, l + 1), W.f[l],
+                                   out, om, batch, st, s);
+      else if (j == 0)
         launch_correct_smooth<R, DIM>(K, W.u_pre[l], W.u_post[l + 1], lay_of(h, l + 1), W.f[l],
                                       out, om, batch, st, s);
+      else if (DIM == 3 && !pointwise3d())
+        launch_smooth3d<R>(K, in, ZERO_NONE, W.f[l], out, om, batch, st, nullptr, s);
       else
         launch_smooth<R, DIM>(K, in, ZERO_NONE, W.f[l], out, om, batch, st,
                               nullptr, h->nparts, s);
@@ -955,6 +989,19 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
   const LevelK<R> K = levelk<R>(h, level, 0);
   const auto om = omega<R>(h, 0);
   const bool two = h->dim == 2;
+  if (kernel == 6) {   // one GMRES(m) smoothing step from a nonzero iterate
+    const GmresWork<R> g = gmres_work<R>(h, level);
+    const int nb = partial_blocks_of(h, level), m = h->opt.gmres_m;
+    typename Cx<R>::T *u = W.u_post[level];
+    if (two) {
+      launch_gmres_start<R, 2>(K, u, ZERO_NONE, W.f[level], g, batch, nullptr, g.parts, nb, s);
+      launch_gmres_rest<R, 2>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s);
+    } else {
+      launch_gmres_start<R, 3>(K, u, ZERO_NONE, W.f[level], g, batch, nullptr, g.parts, nb, s);
+      launch_gmres_rest<R, 3>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s);
+    }
+    return;
+  }
   if (kernel == 4) {
     if constexpr (std::is_same<R, float>::value)
       if (h->mid) {
@@ -974,17 +1021,21 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
                      batch, nullptr, h->err, s);
     return;
   }
+  const bool tiled = !two && !pointwise3d();   // the kernels the 3-D cycle runs
   if (kernel == 0) {
     double *parts = level == 0 ? h->partials : nullptr;
     if (two) launch_smooth<R, 2>(K, W.u_post[level], ZERO_NONE, W.f[level], W.u_pre[level], om, batch, nullptr, parts, h->nparts, s);
+    else if (tiled) launch_smooth3d<R>(K, W.u_post[level], ZERO_NONE, W.f[level], W.u_pre[level], om, batch, nullptr, parts, s);
     else launch_smooth<R, 3>(K, W.u_post[level], ZERO_NONE, W.f[level], W.u_pre[level], om, batch, nullptr, parts, h->nparts, s);
   } else if (kernel == 1) {
     const Lay lc = lay_of(h, level + 1);
     if (two) launch_resid_restrict<R, 2>(K, W.u_pre[level], W.f[level], W.f[level + 1], lc, cscal<R>(h, level, 0), batch, nullptr, s);
+    else if (tiled) launch_resid_restrict3d<R>(K, W.u_pre[level], W.f[level], W.f[level + 1], lc, cscal<R>(h, level, 0), batch, nullptr, s);
     else launch_resid_restrict<R, 3>(K, W.u_pre[level], W.f[level], W.f[level + 1], lc, cscal<R>(h, level, 0), batch, nullptr, s);
   } else {
     const Lay lc = lay_of(h, level + 1);
     if (two) launch_correct_smooth<R, 2>(K, W.u_pre[level], W.u_post[level + 1], lc, W.f[level], W.u_post[level], om, batch, nullptr, s);
+    else if (tiled) launch_correct_smooth3d<R>(K, W.u_pre[level], W.u_post[level + 1], lc, W.f[level], W.u_post[level], om, batch, nullptr, s);
     else launch_correct_smooth<R, 3>(K, W.u_pre[level], W.u_post[level + 1], lc, W.f[level], W.u_post[level], om, batch, nullptr, s);
   }
 }
@@ -1807,7 +1858,15 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
         HH_CK(cudaMemsetAsync(h->w32.gw[l], 0, np * sizeof(float2), s));
       }
     }
-    HH_TRY(dev_alloc_n(h, &h->gm_parts, (size_t)2 * 152 * 6 * B));
+    // blocks per kernel: complex64 4 per SM, enough warps to keep the
+    // stencil loads of the grid-stride loops in flight; complex128 2 per SM
+    // (bound by the FP64 pipe, where more blocks only lengthen the last
+    // block's sum over the partials); HH_GMBLOCKS overrides, for tuning
+    int sms = 0;
+    HH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->gm_cap = (h->opt.precision == HH_FP64 ? 2 : 4) * sms;
+    if (const char *e = std::getenv("HH_GMBLOCKS")) h->gm_cap = std::max(1, std::atoi(e));
+    HH_TRY(dev_alloc_n(h, &h->gm_parts, (size_t)h->gm_cap * 6 * B));
     HH_TRY(dev_alloc_n(h, &h->gm_counter, 1));
     HH_CK(cudaMemsetAsync(h->gm_counter, 0, sizeof(unsigned int), s));
     HH_TRY(dev_alloc_n(h, &h->gm_gsc, (size_t)kGmresScalars * B));
@@ -1850,6 +1909,8 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   h->parts_cap = partial_blocks(h->lv[0].pts);
   for (int v = 0; v < kLevel0Variants; ++v)
     h->parts_cap = std::max(h->parts_cap, tile_parts(v, h->lv[0].N));
+  if (dim == 3) h->parts_cap = std::max(h->parts_cap, tiles3d(h->lv[0].N));
+  if (h->gm_cap) h->parts_cap = std::max(h->parts_cap, gmres_blocks(h, 0));
   HH_TRY(dev_alloc_n(h, &h->partials, (size_t)h->parts_cap * B));
   HH_TRY(dev_alloc_n(h, &h->err, 1));
   HH_CK(cudaMemsetAsync(h->err, 0, sizeof(int), s));
@@ -1893,6 +1954,11 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
     if (op) HH_TRY(setup_persist(h, s));
   }
   h->nparts = h->fused ? tile_parts(h->variant[0], h->lv[0].N) : partial_blocks(h->lv[0].pts);
+  // the 3-D weighted-Jacobi cycle's level-0 sweep writes one partial sum per box
+  if (dim == 3 && h->opt.smoother == HH_SMOOTH_JACOBI && !pointwise3d())
+    h->nparts = tiles3d(h->lv[0].N);
+  // the GMRES cycle's level-0 start kernel writes one partial sum per block
+  if (h->opt.smoother == HH_SMOOTH_GMRES) h->nparts = gmres_blocks(h, 0);
   return HH_OK;
 }
 
@@ -2939,7 +3005,9 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
   HH_TRY(check_handle(h));
   HH_TRY(check_batch(h, batch));
   if (!ms || reps < 1) return fail(HH_ERR_ARG, "ms must not be NULL and reps >= 1");
-  if (kernel < 0 || kernel > 5) return fail(HH_ERR_ARG, "kernel must be 0..5");
+  if (kernel < 0 || kernel > 6) return fail(HH_ERR_ARG, "kernel must be 0..6");
+  if (kernel == 6 && h->opt.smoother != HH_SMOOTH_GMRES)
+    return fail(HH_ERR_ARG, "kernel 6 needs GMRES smoothing");
   if (level < 0 || level + 1 >= h->L) return fail(HH_ERR_ARG, "bad level");
   if (kernel == 4 && !h->fused) return fail(HH_ERR_ARG, "kernel 4 needs the fused 2-D path");
   if (kernel == 1 && h->fused && level < h->tail0)

@@ -32,6 +32,7 @@
 // u = (1 - omega) w + (omega / D) (f + neighbour terms of w): only omega / D
 // is needed per point, and it is formed before the dependency wait, while
 // the previous kernel still runs.
+#include "hh_launch.cuh"
 #include "hh_cycle.h"
 #include "hh_complex.cuh"
 
@@ -40,23 +41,6 @@
 namespace hh {
 
 namespace {
-
-// Launch with programmatic stream serialization (see hh_cycle2d.cu).
-template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
 
 constexpr int NT = 256;
 

@@ -2,6 +2,7 @@
 // shapes (picked per level by the setup-time autotuner), and the single-block
 // "tail" kernel that runs every level from the first small one down to the
 // coarsest LU and back up inside one launch per right-hand side.
+#include "hh_launch.cuh"
 #include "hh_cycle.h"
 #include "hh_fused2d.cuh"
 #include "hh_kernels.cuh"
@@ -15,25 +16,6 @@ struct Shape { int bx, by; };
 // bound by one block's chain of copy, phases and stores rather than by bytes)
 constexpr Shape kShapes[kNumTileVariants] = {{60, 16}, {60, 32}, {28, 32}, {120, 16}, {28, 16},
                                              {28, 8}, {12, 8}};
-
-// Launch with programmatic stream serialization: the kernel may start while
-// the previous kernel on the stream finishes; it waits for it with
-// griddepcontrol.wait before touching that kernel's output.
-template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
 
 template <typename R, int BX, int BY>
 void down_one(const DownMaps &maps, const LevelK<R> &L, int zero_mode, typename Cx<R>::T *v_out,

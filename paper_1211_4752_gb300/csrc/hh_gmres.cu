@@ -18,6 +18,8 @@
 // (u + sum z_j q_j).  Right-hand sides whose loop has stopped skip the work
 // but still arrive at the last-block count.
 #include "hh_kernels.cuh"
+#include "hh_launch.cuh"
+#include "hh_tma.cuh"
 #include "hh_gmres.h"
 
 namespace hh {
@@ -89,18 +91,29 @@ __device__ __forceinline__ void last_block_reduce(unsigned int *counter, const d
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// Block sums of NQ values per thread into parts[b][q][blockIdx.x] (FP64
-// from the block sum on; the per-thread sums are in the vectors' precision:
-// FP32 for complex64 vectors, whose FP64 accumulation would be bound by the
-// FP64 pipe, FP64 for complex128).
+// Block sums of NQ values per thread into parts[b][q][blockIdx.x]: each warp
+// adds its lanes' values in their own precision (FP32 for complex64 vectors,
+// whose FP64 accumulation would be bound by the FP64 pipe; FP64 for
+// complex128), thread 0 adds the warp sums in FP64 in warp order.
 template <int NQ, typename A>
 __device__ __forceinline__ void write_partials(const A (&acc)[NQ], bool act, double *parts,
                                                int b) {
+  __shared__ double ws[NQ * 32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const double s = block_sum((double)acc[q]);
-    if (act && threadIdx.x == 0) parts[((size_t)b * NQ + q) * gridDim.x + blockIdx.x] = s;
-    __syncthreads();
+    A v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) ws[q * 32 + w] = (double)v;
+  }
+  __syncthreads();
+  if (act && threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0.0;
+      for (int i = 0; i < nw; ++i) s += ws[q * 32 + i];
+      parts[((size_t)b * NQ + q) * gridDim.x + blockIdx.x] = s;
+    }
   }
 }
 
@@ -113,6 +126,8 @@ k_gm_start(LevelK<R> L, const typename Cx<R>::T *__restrict__ u, int zero_mode,
            const SolveState *st, double *parts, unsigned int *counter, double *gsc) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
+  griddep_wait();   // the previous kernel's output (programmatic launch)
+  griddep_launch_dependents();
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
   const bool zero =
       __syncthreads_or(zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero)) != 0;
@@ -153,6 +168,8 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
   using C = typename Cx<R>::T;
   constexpr int NQ = 2 * (J + 1);
   const int b = blockIdx.y;
+  griddep_wait();   // the previous kernel's output (programmatic launch)
+  griddep_launch_dependents();
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
   R acc[NQ];
 #pragma unroll
@@ -259,13 +276,17 @@ __device__ void gm_lsq(double *g, int m, double tiny) {
 
 // q_{J+1} = w - sum_{i<=J} c_iJ q_i; |q_{J+1}|^2; after the last column the
 // least-squares solve.
+// (at most 64 registers, 4 blocks per SM: the least-squares solve of the
+// last block, which would need more, may spill)
 template <typename R, int DIM, int J>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
           const typename Cx<R>::T *__restrict__ w, const SolveState *st, double *parts,
           unsigned int *counter, double *gsc, int m) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
+  griddep_wait();   // the previous kernel's output (programmatic launch)
+  griddep_launch_dependents();
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
   R acc[1] = {R(0)};
   const R sj = kscale_of<R>(gsc + b * kGmresScalars, J);   // |q_{J+1}| ~ ||A|| |q_J|
@@ -310,6 +331,8 @@ k_gm_update(LevelK<R> L, const typename Cx<R>::T *u_in,
             const SolveState *st, const double *gsc, int m) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
+  griddep_wait();   // the previous kernel's output (programmatic launch)
+  griddep_launch_dependents();
   if (!__syncthreads_and(!(st && !st[b].active))) return;
   const double *g = gsc + b * kGmresScalars;
   const bool zero = g[24] != 0.0;
@@ -337,6 +360,8 @@ k_gm_correct(LevelK<R> L, const typename Cx<R>::T *u_in, const typename Cx<R>::T
              Lay lc, typename Cx<R>::T *u_out, const SolveState *st) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
+  griddep_wait();   // the previous kernel's output (programmatic launch)
+  griddep_launch_dependents();
   if (!__syncthreads_and(!(st && !st[b].active))) return;
   const int N = L.N, P = L.P;
   const size_t off = (size_t)b * L.S;
@@ -362,21 +387,24 @@ k_gm_correct(LevelK<R> L, const typename Cx<R>::T *u_in, const typename Cx<R>::T
 // ---------------------------------------------------------------------------
 constexpr int TB = 512;
 
-// Sum NQ doubles per thread over the block (TB / 32 warps; ws holds NQ x 32
-// slots, of which the first TB / 32 of each row are written); valid in
-// red[0..NQ) after it.
+// Sum the first nq of NQ values per thread over the block (TB / 32 warps;
+// ws holds NQ x 32 slots, of which the first TB / 32 of each row are
+// written): each warp adds its lanes' values in their own precision, the warp
+// sums are added in FP64; valid in red[0..nq) after it.
 template <int NQ, typename A>
-__device__ __forceinline__ void tail_reduce(A (&acc)[NQ], double *ws, double *red) {
+__device__ __forceinline__ void tail_reduce(A (&acc)[NQ], double *ws, double *red,
+                                            int nq = NQ) {
   static_assert(TB % 32 == 0 && TB / 32 <= 32, "one reduction slot per warp");
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    double v = (double)acc[q];
+    if (q >= nq) break;
+    A v = acc[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) ws[q * 32 + w] = v;
+    if (lane == 0) ws[q * 32 + w] = (double)v;
   }
   __syncthreads();
-  if (w < NQ) {
+  if (w < nq) {
     double v = lane < TB / 32 ? ws[w * 32 + lane] : 0.0;   // one slot per warp of the block
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[w] = v;
@@ -457,7 +485,7 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
           acc[2 * i + 1] += qi.x * a.y - qi.y * a.x;
         }
       }
-      tail_reduce<6>(acc, ws, red);
+      tail_reduce<6>(acc, ws, red, 2 * (J + 1));
       if (threadIdx.x == 0) {
         const double sj = (double)sc[J];
         for (int i = 0; i <= J; ++i) {
@@ -681,8 +709,8 @@ template <typename R, int DIM>
 void launch_gmres_start(const LevelK<R> &L, const typename Cx<R>::T *u, int zero_mode,
                         const typename Cx<R>::T *f, const GmresWork<R> &g, int batch,
                         const SolveState *st, double *parts, int nblk, cudaStream_t s) {
-  k_gm_start<R, DIM><<<dim3(nblk, batch), 256, 0, s>>>(L, u, zero_mode, f, g.Q, st, parts,
-                                                        g.counter, g.gsc);
+  launch_pdl(k_gm_start<R, DIM>, dim3(nblk, batch), dim3(256), 0, s, L, u, zero_mode, f, g.Q, st,
+             parts, g.counter, g.gsc);
 }
 
 template <typename R, int DIM>
@@ -692,25 +720,31 @@ void launch_gmres_rest(const LevelK<R> &L, const typename Cx<R>::T *u_in, int ze
   const dim3 grid(nblk, batch);
   for (int j = 0; j < m; ++j) {
     if (j == 0) {
-      k_gm_arnoldi<R, DIM, 0><<<grid, 256, 0, s>>>(L, g.Q, g.qs, g.w, st, g.parts, g.counter, g.gsc);
-      k_gm_orth<R, DIM, 0><<<grid, 256, 0, s>>>(L, g.Q, g.qs, g.w, st, g.parts, g.counter, g.gsc, m);
+      launch_pdl(k_gm_arnoldi<R, DIM, 0>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                 g.counter, g.gsc);
+      launch_pdl(k_gm_orth<R, DIM, 0>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                 g.counter, g.gsc, m);
     } else if (j == 1) {
-      k_gm_arnoldi<R, DIM, 1><<<grid, 256, 0, s>>>(L, g.Q, g.qs, g.w, st, g.parts, g.counter, g.gsc);
-      k_gm_orth<R, DIM, 1><<<grid, 256, 0, s>>>(L, g.Q, g.qs, g.w, st, g.parts, g.counter, g.gsc, m);
+      launch_pdl(k_gm_arnoldi<R, DIM, 1>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                 g.counter, g.gsc);
+      launch_pdl(k_gm_orth<R, DIM, 1>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                 g.counter, g.gsc, m);
     } else {
-      k_gm_arnoldi<R, DIM, 2><<<grid, 256, 0, s>>>(L, g.Q, g.qs, g.w, st, g.parts, g.counter, g.gsc);
-      k_gm_orth<R, DIM, 2><<<grid, 256, 0, s>>>(L, g.Q, g.qs, g.w, st, g.parts, g.counter, g.gsc, m);
+      launch_pdl(k_gm_arnoldi<R, DIM, 2>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                 g.counter, g.gsc);
+      launch_pdl(k_gm_orth<R, DIM, 2>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                 g.counter, g.gsc, m);
     }
   }
-  k_gm_update<R, DIM><<<grid, 256, 0, s>>>(L, u_in, g.Q, g.qs, u_out, st, g.gsc, m);
+  launch_pdl(k_gm_update<R, DIM>, grid, dim3(256), 0, s, L, u_in, g.Q, g.qs, u_out, st, g.gsc, m);
 }
 
 template <typename R, int DIM>
 void launch_gmres_correct(const LevelK<R> &L, const typename Cx<R>::T *u_in,
                           const typename Cx<R>::T *e, const Lay &lc, typename Cx<R>::T *u_out,
                           int batch, const SolveState *st, cudaStream_t s) {
-  k_gm_correct<R, DIM><<<dim3(grid_for(npts<DIM>(L.N)), batch), 256, 0, s>>>(L, u_in, e, lc,
-                                                                            u_out, st);
+  launch_pdl(k_gm_correct<R, DIM>, dim3(grid_for(npts<DIM>(L.N)), batch), dim3(256), 0, s, L, u_in,
+             e, lc, u_out, st);
 }
 
 #define HH_GMRES_INST(R, DIM)                                                                  \

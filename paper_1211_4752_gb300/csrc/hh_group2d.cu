@@ -7,28 +7,13 @@
 // kMaxGroup) start offsets and then runs the same per-tile code as the
 // single-problem kernels (hh_fused2d.cuh), so the results are those of the
 // per-problem cycles bit for bit.
+#include "hh_launch.cuh"
 #include "hh_cycle.h"
 #include "hh_fused2d.cuh"
 
 namespace hh {
 
 namespace {
-
-template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
 
 constexpr int BX = kGroupBX, BY = kGroupBY;
 

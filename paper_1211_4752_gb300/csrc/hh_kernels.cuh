@@ -91,6 +91,24 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;
 }
 
+// Deterministic block sum, valid in thread 0: each warp adds its 32 values
+// in their own precision A (a butterfly), the warp sums are added in FP64 in
+// warp order.  For FP32 values this keeps the FP64 pipe (a small fraction of
+// the FP32 rate) out of all but the last 8..32 additions.
+template <typename A> __device__ __forceinline__ double block_sum_w(A v) {
+  __shared__ double ws[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) ws[w] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) s += ws[i];
+  }
+  return s;
+}
+
 template <int DIM> __host__ __device__ inline size_t npts(int N) {
   return DIM == 2 ? (size_t)N * N : (size_t)N * N * N;
 }
