@@ -284,6 +284,18 @@ def run_ours(args):
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": None, "bytes_per_point": bpp,
                     "launch_ms": {KERNELS3[k]: v for k, v in kt3.items()}}
+    if args.smoother == "gmres":
+        # one level-0 GMRES(3) smoothing step (start, 3 Arnoldi steps, update),
+        # timed live back to back; a k^2 field adds 4 B per operator application
+        ms = ct.c_double()
+        B.check(B.lib().hh_time_kernel(mg._h, 6, 0, 1, 20, ct.byref(ms),
+                                       ct.c_void_p(stream.cuda_stream)))
+        bpp = (GMRES_STEP_BYTES + (0.0 if kconst else 16.0)) * (1.0 if mixed else 2.0)
+        achieved = bpp * pts / (ms.value * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "gmres_step_level0", "achieved": achieved,
+                    "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None, "bytes_per_point": bpp,
+                    "launch_ms": {"gmres_step_level0": ms.value}}
     if fused:
         dom = max((0, 2), key=lambda k: kt[k])
         name = KERNELS[dom]
@@ -370,6 +382,10 @@ def run_ours(args):
     if args.batched and args.workload == "ecs_const" and not fgm:
         batched = group_record(args, max(1, min(args.steps, 2)), 1)
 
+    gmres = None
+    if args.gmres_record and args.workload == "ecs_const" and args.smoother == "jacobi" and not fgm:
+        gmres = gmres_record(w, args, k2_t, f, stream, flush)
+
     cpu = cpu_all = None
     if rank == 0 and not args.no_cpu_baseline and fgm:
         cpu = cpu_baseline_fgmres(w, args, last["cycles"])
@@ -411,6 +427,7 @@ def run_ours(args):
             "fp64_gpu": fp64,
             "fgmres": fg,
             "batched": batched,
+            "gmres": gmres,
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -418,6 +435,58 @@ def run_ours(args):
     mg.close()
     if dist:
         dist.destroy_process_group()
+
+
+# Algorithmic bytes per point of one GMRES(3) smoothing step on a level
+# (complex64 vectors, constant k; each kernel reads and writes its vectors
+# once): start: u, f -> q_0 (24 B); Arnoldi step J: q_0..q_J -> w (8 (J + 2));
+# orthogonalisation J: w, q_0..q_J -> q_{J+1} (8 (J + 3)); update:
+# u, q_0..q_2 -> u (40 B).  Sum over J = 0..2: 232 B.
+GMRES_STEP_BYTES = 232.0
+
+
+def gmres_record(w, args, k2_t, f, stream, flush):
+    """The same workload with GMRES(3) smoothing (the paper's smoother): the
+    cycle's time (captured graph, hh_time_kernel kernel 5), one level-0
+    smoothing step against its algorithmic bytes, and a solve to the tolerance
+    capped at --gmres-max-cycles cycles."""
+    import ctypes as ct
+    import torch
+    from paper_1211_4752_gb300 import HelmholtzMG
+    from paper_1211_4752_gb300 import _binding as B
+    n, dim = w["n"], w["dim"]
+    pts = (n - 1) ** dim
+    mixed = args.precision == "mixed"
+    mg = HelmholtzMG(n, dim=dim, k2=k2_t, layers=w["layers"], precision=args.precision,
+                     max_batch=1, smoother="gmres", max_cycles=args.gmres_max_cycles)
+    sp = ct.c_void_p(stream.cuda_stream)
+    ms = ct.c_double()
+    B.check(B.lib().hh_time_kernel(mg._h, 5, 0, 1, 20, ct.byref(ms), sp))
+    cycle_ms = ms.value
+    B.check(B.lib().hh_time_kernel(mg._h, 6, 0, 1, 20, ct.byref(ms), sp))
+    step_ms = ms.value
+    peak, peak_kind = measured_peaks()
+    bpp = GMRES_STEP_BYTES * (1.0 if mixed else 2.0)
+    achieved = bpp * pts / (step_ms * 1e-3) / 1e9
+    flush.fill_(1.0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, info = mg.solve(f, tol=args.tol)
+    e1.record(stream)
+    e1.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    rec = {"smoother": "GMRES(3)", "cycle_ms": cycle_ms, "kernels_per_cycle": mg.cycle_kernels,
+           "solve": {"value": pts / s / 1e6 if info[0]["status"] == "OK" else None,
+                     "unit": "MDOF/s", "ms": s * 1e3, "cycles": info[0]["cycles"],
+                     "status": info[0]["status"], "rel_residual": info[0]["rel_residual"],
+                     "max_cycles": args.gmres_max_cycles},
+           "roofline": {"bound": "hbm", "kernel": "gmres_step_level0", "achieved": achieved,
+                        "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None, "bytes_per_point": bpp,
+                        "launch_ms": {"gmres_step_level0": step_ms}}}
+    mg.close()
+    return rec
 
 
 def cpu_baseline(w, args, cycles_hint):
@@ -796,6 +865,10 @@ def main():
                          "--fgmres-restart) with one cycle per iteration as the preconditioner")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 64-source group record (255^2/511^2/1023^2) of the default line")
+    ap.add_argument("--no-gmres", dest="gmres_record", action="store_false",
+                    help="skip the GMRES(3)-smoothed cycle record of the default line")
+    ap.add_argument("--gmres-max-cycles", type=int, default=400,
+                    help="cycle cap of the GMRES record's solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-all-cores", dest="cpu_all_cores", action="store_false",
                     help="skip the oracle timed on every host core at once")

@@ -75,7 +75,8 @@ template <typename R> struct Work {
   C *f[MAXL] = {};
   C *tmp[MAXL] = {};
   C *gq[MAXL] = {};   // GMRES smoothing: Krylov vectors q_0..q_3 of the level
-  C *gw[MAXL] = {};   // and w = A q_j
+  C *gw[MAXL] = {};   // and w = A q_j (two buffers)
+  C *gw2[MAXL] = {};
 };
 
 struct LevelHost {
@@ -138,6 +139,7 @@ struct hh_handle {
   CoarseGroup groups[MAXL];
   int parts_cap = 0;                // capacity of `partials` per RHS
   int gm_cap = 0;                   // most blocks of a GMRES smoothing kernel
+  int gm_fuse = 1;                  // fused orthogonalisation + Arnoldi kernels
   cudaStream_t side = nullptr;      // branch of the stop test in the fused cycle
   cudaStream_t grp = nullptr;       // this handle's stream in a group solve (lazy)
   cudaEvent_t ev_grp = nullptr;     // its join event
@@ -333,6 +335,7 @@ template <typename R> GmresWork<R> gmres_work(hh_handle *h, int l) {
   g.Q = W.gq[l];
   g.qs = (size_t)h->lv[l].S * h->max_batch;
   g.w = W.gw[l];
+  g.w2 = W.gw2[l];
   g.parts = h->gm_parts;
   g.counter = h->gm_counter;
   g.gsc = h->gm_gsc;
@@ -374,7 +377,7 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
         else
           launch_check_inner(h->st, h->partials, h->params, h->flag, cond, h->copies, h->err, s);
       }
-      launch_gmres_rest<R, DIM>(K, in, zm, W.u_pre[l], g, m, batch, st, nb, s);
+      launch_gmres_rest<R, DIM>(K, in, zm, W.u_pre[l], g, m, batch, st, nb, s, h->gm_fuse);
       in = W.u_pre[l];
       zm = ZERO_NONE;
     }
@@ -402,7 +405,7 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
                                  batch, st, s);
     for (int j = 0; j < h->opt.nu2; ++j) {
       launch_gmres_start<R, DIM>(K, W.u_post[l], ZERO_NONE, W.f[l], g, batch, st, g.parts, nb, s);
-      launch_gmres_rest<R, DIM>(K, W.u_post[l], ZERO_NONE, W.u_post[l], g, m, batch, st, nb, s);
+      launch_gmres_rest<R, DIM>(K, W.u_post[l], ZERO_NONE, W.u_post[l], g, m, batch, st, nb, s, h->gm_fuse);
     }
   }
 }
@@ -995,10 +998,10 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
     typename Cx<R>::T *u = W.u_post[level];
     if (two) {
       launch_gmres_start<R, 2>(K, u, ZERO_NONE, W.f[level], g, batch, nullptr, g.parts, nb, s);
-      launch_gmres_rest<R, 2>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s);
+      launch_gmres_rest<R, 2>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s, h->gm_fuse);
     } else {
       launch_gmres_start<R, 3>(K, u, ZERO_NONE, W.f[level], g, batch, nullptr, g.parts, nb, s);
-      launch_gmres_rest<R, 3>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s);
+      launch_gmres_rest<R, 3>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s, h->gm_fuse);
     }
     return;
   }
@@ -1849,13 +1852,17 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
       if (h->opt.precision == HH_FP64) {
         HH_TRY(dev_alloc_n(h, &h->w64.gq[l], 4 * np));
         HH_TRY(dev_alloc_n(h, &h->w64.gw[l], np));
+        HH_TRY(dev_alloc_n(h, &h->w64.gw2[l], np));
         HH_CK(cudaMemsetAsync(h->w64.gq[l], 0, 4 * np * sizeof(double2), s));
         HH_CK(cudaMemsetAsync(h->w64.gw[l], 0, np * sizeof(double2), s));
+        HH_CK(cudaMemsetAsync(h->w64.gw2[l], 0, np * sizeof(double2), s));
       } else {
         HH_TRY(dev_alloc_n(h, &h->w32.gq[l], 4 * np));
         HH_TRY(dev_alloc_n(h, &h->w32.gw[l], np));
+        HH_TRY(dev_alloc_n(h, &h->w32.gw2[l], np));
         HH_CK(cudaMemsetAsync(h->w32.gq[l], 0, 4 * np * sizeof(float2), s));
         HH_CK(cudaMemsetAsync(h->w32.gw[l], 0, np * sizeof(float2), s));
+        HH_CK(cudaMemsetAsync(h->w32.gw2[l], 0, np * sizeof(float2), s));
       }
     }
     // blocks per kernel: complex64 4 per SM, enough warps to keep the
@@ -1866,7 +1873,13 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
     HH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     h->gm_cap = (h->opt.precision == HH_FP64 ? 2 : 4) * sms;
     if (const char *e = std::getenv("HH_GMBLOCKS")) h->gm_cap = std::max(1, std::atoi(e));
-    HH_TRY(dev_alloc_n(h, &h->gm_parts, (size_t)h->gm_cap * 6 * B));
+    HH_TRY(dev_alloc_n(h, &h->gm_parts, (size_t)h->gm_cap * kGmresParts * B));
+    // complex64: the orthogonalisation of a step and the next Arnoldi product
+    // in one kernel (fewer launches; complex128 stays unfused, since the
+    // recomputed neighbours' orthogonalisation costs FP64 operations, the
+    // bound of those kernels); HH_GMFUSE=0/1 in the environment overrides
+    h->gm_fuse = h->opt.precision != HH_FP64;
+    if (const char *e = std::getenv("HH_GMFUSE")) h->gm_fuse = std::atoi(e) != 0;
     HH_TRY(dev_alloc_n(h, &h->gm_counter, 1));
     HH_CK(cudaMemsetAsync(h->gm_counter, 0, sizeof(unsigned int), s));
     HH_TRY(dev_alloc_n(h, &h->gm_gsc, (size_t)kGmresScalars * B));
@@ -2532,11 +2545,14 @@ int hh_cycle_kernels(const hh_handle *h) {
     if (h->mid && h->opt.precision == HH_MIXED) return 2 * h->mid0 + 2;
     return 2 * (1 + h->ngroups) + 2;
   }
-  if (h->opt.smoother == HH_SMOOTH_GMRES) {  // per level: steps of 2m + 2 kernels,
+  if (h->opt.smoother == HH_SMOOTH_GMRES) {  // per level: steps of 2m + 2 kernels
+    // (m + 3 with the fused orthogonalisation + Arnoldi kernels, m >= 2),
     // residual + restriction, correction; then the tail (or the coarsest LU)
     // and the stop test
     const int T = h->gtail0 > 0 ? h->gtail0 : h->L - 1;
-    return T * ((h->opt.nu1 + h->opt.nu2) * (2 * h->opt.gmres_m + 2) + 2) + 2;
+    const int m = h->opt.gmres_m;
+    const int step = h->gm_fuse && m >= 2 ? m + 3 : 2 * m + 2;
+    return T * ((h->opt.nu1 + h->opt.nu2) * step + 2) + 2;
   }
   // per level nu1 sweeps, residual + restriction, nu2 sweeps; stop test; LU
   return (h->L - 1) * (h->opt.nu1 + 1 + h->opt.nu2) + 2;

@@ -214,6 +214,89 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
                         });
 }
 
+// Step J's orthogonalisation and step J+1's Arnoldi product in one pass:
+// q_{J+1} = w - sum_{i<=J} c_iJ q_i (w = A q_J) and |q_{J+1}|^2, then
+// A q_{J+1} and <q_i, A q_{J+1}> for i <= J+1.  A q_{J+1} needs q_{J+1} at
+// the stencil's neighbours, which other blocks produce: it is recomputed there
+// from w and q_0..q_J (the same operations in the same order, so the values
+// equal the stored ones), and no grid-wide barrier separates the two steps.
+// w_in (A q_J) and w_out (A q_{J+1}) are different buffers: other blocks
+// still read w_in around this block's points.  The complex64 per-thread sums
+// scale q_{J+1} and A q_{J+1} by s_J, the scale of q_J (q_{J+1}'s own is
+// not known before this pass ends): |s_J q_{J+1}| ~ ||A|| and
+// |s_J A q_{J+1}| ~ ||A||^2 stay far inside the FP32 range.
+template <typename R, int DIM, int J>
+__global__ void __launch_bounds__(256)
+k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
+                  const typename Cx<R>::T *__restrict__ w_in, typename Cx<R>::T *__restrict__ w_out,
+                  const SolveState *st, double *parts, unsigned int *counter, double *gsc) {
+  using C = typename Cx<R>::T;
+  constexpr int NQ = 1 + 2 * (J + 2);   // |q_{J+1}|^2; <q_i, A q_{J+1}>, i <= J+1
+  static_assert(NQ <= kGmresParts, "partial-sum slots");
+  const int b = blockIdx.y;
+  griddep_wait();   // the previous kernel's output (programmatic launch)
+  griddep_launch_dependents();
+  const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
+  R acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = R(0);
+  R sc[J + 1];   // scales of q_0..q_J
+#pragma unroll
+  for (int i = 0; i <= J; ++i) sc[i] = kscale_of<R>(gsc + b * kGmresScalars, i);
+  const R sj = sc[J];
+  if (act) {
+    C c[J + 1];
+    const double *g = gsc + b * kGmresScalars;
+#pragma unroll
+    for (int i = 0; i <= J; ++i) c[i] = cmk((R)g[ci(i, J)], (R)g[ci(i, J) + 1]);
+    const int N = L.N, P = L.P;
+    const size_t off = (size_t)b * L.S;
+    const C *wb = w_in + off;
+    const C *qb = Q + off;
+    auto qnext = [&](int xx, int yy, int zz) {
+      const size_t o = at<DIM>(xx, yy, zz, N, P);
+      C v = wb[o];
+#pragma unroll
+      for (int i = 0; i <= J; ++i) v = csub(v, cmul(c[i], qb[(size_t)i * qs + o]));
+      return v;
+    };
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < npts<DIM>(N);
+         p += (size_t)gridDim.x * blockDim.x) {
+      int x, y, z;
+      coords<DIM>(p, N, x, y, z);
+      const size_t o = at<DIM>(x, y, z, N, P);
+      C Aq, D, qc;
+      stencil<R, DIM>(L, x, y, z, qnext, Aq, D, qc);   // qc = q_{J+1} here
+      Q[(size_t)(J + 1) * qs + off + o] = qc;
+      w_out[off + o] = Aq;
+      const C vs = cscale(qc, sj), a = cscale(Aq, sj);
+      acc[0] += vs.x * vs.x + vs.y * vs.y;
+#pragma unroll
+      for (int i = 0; i <= J; ++i) {
+        const C qi = cscale(qb[(size_t)i * qs + o], sc[i]);
+        acc[1 + 2 * i] += qi.x * a.x + qi.y * a.y;       // Re conj(q_i) A q_{J+1} (scaled)
+        acc[2 + 2 * i] += qi.x * a.y - qi.y * a.x;       // Im
+      }
+      acc[1 + 2 * (J + 1)] += vs.x * a.x + vs.y * a.y;
+      acc[2 + 2 * (J + 1)] += vs.x * a.y - vs.y * a.x;
+    }
+  }
+  write_partials<NQ>(acc, act, parts, b);
+  last_block_reduce<NQ>(counter, parts, gridDim.x, gridDim.y, st,
+                        [&](int bb, const double *v) {
+                          double *g = gsc + bb * kGmresScalars;
+                          const double s2 = (double)kscale_of<R>(g, J);
+                          set_norm<R>(g, J + 1, s2 > 0.0 ? v[0] / (s2 * s2) : v[0]);
+                          for (int i = 0; i <= J + 1; ++i) {
+                            const double sq = g[i];
+                            const double si = i <= J ? (double)kscale_of<R>(g, i) : s2;
+                            const bool ok = sq > 0.0 && si * s2 > 0.0;
+                            g[ci(i, J + 1)] = ok ? v[1 + 2 * i] / (si * s2) / sq : 0.0;
+                            g[ci(i, J + 1) + 1] = ok ? v[2 + 2 * i] / (si * s2) / sq : 0.0;
+                          }
+                        });
+}
+
 // Least squares min ||beta e1 - H y|| for the Krylov dimension k (m columns
 // at most), by complex Givens rotations; z_j = y_j / |q_j|.
 __device__ void gm_lsq(double *g, int m, double tiny) {
@@ -716,27 +799,46 @@ void launch_gmres_start(const LevelK<R> &L, const typename Cx<R>::T *u, int zero
 template <typename R, int DIM>
 void launch_gmres_rest(const LevelK<R> &L, const typename Cx<R>::T *u_in, int zero_mode,
                        typename Cx<R>::T *u_out, const GmresWork<R> &g, int m, int batch,
-                       const SolveState *st, int nblk, cudaStream_t s) {
+                       const SolveState *st, int nblk, cudaStream_t s, int fuse) {
   const dim3 grid(nblk, batch);
-  for (int j = 0; j < m; ++j) {
-    if (j == 0) {
-      launch_pdl(k_gm_arnoldi<R, DIM, 0>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                 g.counter, g.gsc);
-      launch_pdl(k_gm_orth<R, DIM, 0>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                 g.counter, g.gsc, m);
-    } else if (j == 1) {
-      launch_pdl(k_gm_arnoldi<R, DIM, 1>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                 g.counter, g.gsc);
-      launch_pdl(k_gm_orth<R, DIM, 1>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                 g.counter, g.gsc, m);
+  const dim3 blk(256);
+  if (fuse && m >= 2) {
+    // A q_0 -> w; (q_1, A q_1) -> w2; (q_2, A q_2) -> w; orthogonalisation of
+    // the last column (and the least-squares solve) from the latest buffer
+    launch_pdl(k_gm_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+               g.counter, g.gsc);
+    launch_pdl(k_gm_orth_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs,
+               (const typename Cx<R>::T *)g.w, g.w2, st, g.parts, g.counter, g.gsc);
+    if (m == 2) {
+      launch_pdl(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs,
+                 (const typename Cx<R>::T *)g.w2, st, g.parts, g.counter, g.gsc, m);
     } else {
-      launch_pdl(k_gm_arnoldi<R, DIM, 2>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                 g.counter, g.gsc);
-      launch_pdl(k_gm_orth<R, DIM, 2>, grid, dim3(256), 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                 g.counter, g.gsc, m);
+      launch_pdl(k_gm_orth_arnoldi<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs,
+                 (const typename Cx<R>::T *)g.w2, g.w, st, g.parts, g.counter, g.gsc);
+      launch_pdl(k_gm_orth<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs,
+                 (const typename Cx<R>::T *)g.w, st, g.parts, g.counter, g.gsc, m);
+    }
+  } else {
+    for (int j = 0; j < m; ++j) {
+      if (j == 0) {
+        launch_pdl(k_gm_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                   g.counter, g.gsc);
+        launch_pdl(k_gm_orth<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                   g.counter, g.gsc, m);
+      } else if (j == 1) {
+        launch_pdl(k_gm_arnoldi<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                   g.counter, g.gsc);
+        launch_pdl(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                   g.counter, g.gsc, m);
+      } else {
+        launch_pdl(k_gm_arnoldi<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                   g.counter, g.gsc);
+        launch_pdl(k_gm_orth<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                   g.counter, g.gsc, m);
+      }
     }
   }
-  launch_pdl(k_gm_update<R, DIM>, grid, dim3(256), 0, s, L, u_in, g.Q, g.qs, u_out, st, g.gsc, m);
+  launch_pdl(k_gm_update<R, DIM>, grid, blk, 0, s, L, u_in, g.Q, g.qs, u_out, st, g.gsc, m);
 }
 
 template <typename R, int DIM>
@@ -753,7 +855,7 @@ void launch_gmres_correct(const LevelK<R> &L, const typename Cx<R>::T *u_in,
                                            const SolveState *, double *, int, cudaStream_t);   \
   template void launch_gmres_rest<R, DIM>(const LevelK<R> &, const Cx<R>::T *, int,            \
                                           Cx<R>::T *, const GmresWork<R> &, int, int,          \
-                                          const SolveState *, int, cudaStream_t);              \
+                                          const SolveState *, int, cudaStream_t, int);         \
   template void launch_gmres_correct<R, DIM>(const LevelK<R> &, const Cx<R>::T *,              \
                                              const Cx<R>::T *, const Lay &, Cx<R>::T *, int,   \
                                              const SolveState *, cudaStream_t);

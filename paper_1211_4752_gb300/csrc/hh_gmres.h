@@ -6,15 +6,18 @@ namespace hh {
 
 constexpr int kGmresMaxBatch = 64;   // right-hand sides per handle with GMRES smoothing
 constexpr int kGmresScalars = 32;    // FP64 scalars per right-hand side
+constexpr int kGmresParts = 7;       // partial sums per block and right-hand side (at most)
 
 // Workspace of one level: Krylov vectors q_0..q_3 (at stride qs = S * batch
-// capacity), w = A q_j, per-block partial sums (up to 6 per right-hand side),
+// capacity), w = A q_j (two buffers), per-block partial sums (up to 7 per
+// right-hand side),
 // the last-block arrival counter (starts at 0; the last block resets it) and
 // the per-right-hand-side FP64 scalars.
 template <typename R> struct GmresWork {
   typename Cx<R>::T *Q;
   size_t qs;
   typename Cx<R>::T *w;
+  typename Cx<R>::T *w2;   // second buffer of A q_j (the fused steps alternate)
   double *parts;
   unsigned int *counter;
   double *gsc;
@@ -28,11 +31,13 @@ void launch_gmres_start(const LevelK<R> &L, const typename Cx<R>::T *u, int zero
                         const SolveState *st, double *parts, int nblk, cudaStream_t s);
 
 // The m Arnoldi steps, the least-squares solve and u_out = u_in + V y (u_in
-// read as zero where the start kernel took it as zero).
+// read as zero where the start kernel took it as zero).  fuse: the
+// orthogonalisation of step J and the Arnoldi product of step J+1 in one
+// kernel (m + 2 kernels instead of 2 m + 1).
 template <typename R, int DIM>
 void launch_gmres_rest(const LevelK<R> &L, const typename Cx<R>::T *u_in, int zero_mode,
                        typename Cx<R>::T *u_out, const GmresWork<R> &g, int m, int batch,
-                       const SolveState *st, int nblk, cudaStream_t s);
+                       const SolveState *st, int nblk, cudaStream_t s, int fuse = 1);
 
 // u_out = u_in + P e (coarse-grid correction without smoothing).
 template <typename R, int DIM>

@@ -23,4 +23,11 @@ void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// The same launch without the attribute (stream order as usual).
+template <typename... KArgs, typename... Args>
+void launch_plain(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                  Args... args) {
+  kern<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
+}
+
 }  // namespace hh
