@@ -19,7 +19,6 @@
 // but still arrive at the last-block count.
 #include "hh_kernels.cuh"
 #include "hh_launch.cuh"
-#include "hh_tma.cuh"
 #include "hh_gmres.h"
 
 namespace hh {
@@ -126,8 +125,6 @@ k_gm_start(LevelK<R> L, const typename Cx<R>::T *__restrict__ u, int zero_mode,
            const SolveState *st, double *parts, unsigned int *counter, double *gsc) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
-  griddep_wait();   // the previous kernel's output (programmatic launch)
-  griddep_launch_dependents();
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
   const bool zero =
       __syncthreads_or(zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero)) != 0;
@@ -168,8 +165,6 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
   using C = typename Cx<R>::T;
   constexpr int NQ = 2 * (J + 1);
   const int b = blockIdx.y;
-  griddep_wait();   // the previous kernel's output (programmatic launch)
-  griddep_launch_dependents();
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
   R acc[NQ];
 #pragma unroll
@@ -234,8 +229,6 @@ k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
   constexpr int NQ = 1 + 2 * (J + 2);   // |q_{J+1}|^2; <q_i, A q_{J+1}>, i <= J+1
   static_assert(NQ <= kGmresParts, "partial-sum slots");
   const int b = blockIdx.y;
-  griddep_wait();   // the previous kernel's output (programmatic launch)
-  griddep_launch_dependents();
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
   R acc[NQ];
 #pragma unroll
@@ -368,8 +361,6 @@ k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
           unsigned int *counter, double *gsc, int m) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
-  griddep_wait();   // the previous kernel's output (programmatic launch)
-  griddep_launch_dependents();
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
   R acc[1] = {R(0)};
   const R sj = kscale_of<R>(gsc + b * kGmresScalars, J);   // |q_{J+1}| ~ ||A|| |q_J|
@@ -414,8 +405,6 @@ k_gm_update(LevelK<R> L, const typename Cx<R>::T *u_in,
             const SolveState *st, const double *gsc, int m) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
-  griddep_wait();   // the previous kernel's output (programmatic launch)
-  griddep_launch_dependents();
   if (!__syncthreads_and(!(st && !st[b].active))) return;
   const double *g = gsc + b * kGmresScalars;
   const bool zero = g[24] != 0.0;
@@ -443,8 +432,6 @@ k_gm_correct(LevelK<R> L, const typename Cx<R>::T *u_in, const typename Cx<R>::T
              Lay lc, typename Cx<R>::T *u_out, const SolveState *st) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
-  griddep_wait();   // the previous kernel's output (programmatic launch)
-  griddep_launch_dependents();
   if (!__syncthreads_and(!(st && !st[b].active))) return;
   const int N = L.N, P = L.P;
   const size_t off = (size_t)b * L.S;
@@ -792,7 +779,7 @@ template <typename R, int DIM>
 void launch_gmres_start(const LevelK<R> &L, const typename Cx<R>::T *u, int zero_mode,
                         const typename Cx<R>::T *f, const GmresWork<R> &g, int batch,
                         const SolveState *st, double *parts, int nblk, cudaStream_t s) {
-  launch_pdl(k_gm_start<R, DIM>, dim3(nblk, batch), dim3(256), 0, s, L, u, zero_mode, f, g.Q, st,
+  launch_plain(k_gm_start<R, DIM>, dim3(nblk, batch), dim3(256), 0, s, L, u, zero_mode, f, g.Q, st,
              parts, g.counter, g.gsc);
 }
 
@@ -805,47 +792,47 @@ void launch_gmres_rest(const LevelK<R> &L, const typename Cx<R>::T *u_in, int ze
   if (fuse && m >= 2) {
     // A q_0 -> w; (q_1, A q_1) -> w2; (q_2, A q_2) -> w; orthogonalisation of
     // the last column (and the least-squares solve) from the latest buffer
-    launch_pdl(k_gm_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+    launch_plain(k_gm_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
                g.counter, g.gsc);
-    launch_pdl(k_gm_orth_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs,
+    launch_plain(k_gm_orth_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs,
                (const typename Cx<R>::T *)g.w, g.w2, st, g.parts, g.counter, g.gsc);
     if (m == 2) {
-      launch_pdl(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs,
+      launch_plain(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs,
                  (const typename Cx<R>::T *)g.w2, st, g.parts, g.counter, g.gsc, m);
     } else {
-      launch_pdl(k_gm_orth_arnoldi<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs,
+      launch_plain(k_gm_orth_arnoldi<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs,
                  (const typename Cx<R>::T *)g.w2, g.w, st, g.parts, g.counter, g.gsc);
-      launch_pdl(k_gm_orth<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs,
+      launch_plain(k_gm_orth<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs,
                  (const typename Cx<R>::T *)g.w, st, g.parts, g.counter, g.gsc, m);
     }
   } else {
     for (int j = 0; j < m; ++j) {
       if (j == 0) {
-        launch_pdl(k_gm_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+        launch_plain(k_gm_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
                    g.counter, g.gsc);
-        launch_pdl(k_gm_orth<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+        launch_plain(k_gm_orth<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
                    g.counter, g.gsc, m);
       } else if (j == 1) {
-        launch_pdl(k_gm_arnoldi<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+        launch_plain(k_gm_arnoldi<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
                    g.counter, g.gsc);
-        launch_pdl(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+        launch_plain(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
                    g.counter, g.gsc, m);
       } else {
-        launch_pdl(k_gm_arnoldi<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+        launch_plain(k_gm_arnoldi<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
                    g.counter, g.gsc);
-        launch_pdl(k_gm_orth<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+        launch_plain(k_gm_orth<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
                    g.counter, g.gsc, m);
       }
     }
   }
-  launch_pdl(k_gm_update<R, DIM>, grid, blk, 0, s, L, u_in, g.Q, g.qs, u_out, st, g.gsc, m);
+  launch_plain(k_gm_update<R, DIM>, grid, blk, 0, s, L, u_in, g.Q, g.qs, u_out, st, g.gsc, m);
 }
 
 template <typename R, int DIM>
 void launch_gmres_correct(const LevelK<R> &L, const typename Cx<R>::T *u_in,
                           const typename Cx<R>::T *e, const Lay &lc, typename Cx<R>::T *u_out,
                           int batch, const SolveState *st, cudaStream_t s) {
-  launch_pdl(k_gm_correct<R, DIM>, dim3(grid_for(npts<DIM>(L.N)), batch), dim3(256), 0, s, L, u_in,
+  launch_plain(k_gm_correct<R, DIM>, dim3(grid_for(npts<DIM>(L.N)), batch), dim3(256), 0, s, L, u_in,
              e, lc, u_out, st);
 }
 
