@@ -340,7 +340,8 @@ hh_status hh_coarse_solve(hh_handle *h, const void *f_dev, void *e_dev,
  *   kernel 1: residual + full-weighting restriction on `level`
  *   kernel 2: correction + post-smoothing sweep on `level`
  *   kernel 3: FP64 refinement residual on level 0 (MIXED handles only)
- *   kernel 4: the single-block kernel of the small levels (fused 2-D path)
+ *   kernel 4: the single-block kernel of the small levels (fused 2-D path,
+ *             or the one-block tail of GMRES smoothing)
  *   kernel 5: one whole V-cycle (no stop test), replayed as a CUDA graph
  *   kernel 6: one GMRES(m) smoothing step on `level` from a nonzero iterate
  *             (its start, m Arnoldi steps and update; GMRES handles only)

@@ -1005,6 +1005,16 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
     }
     return;
   }
+  if (kernel == 4 && h->opt.smoother == HH_SMOOTH_GMRES) {   // the GMRES one-block tail
+    if constexpr (std::is_same<R, float>::value) {
+      if (two) launch_gmres_tail<float, 2>(h->gta32[0], batch, nullptr, s);
+      else launch_gmres_tail<float, 3>(h->gta32[0], batch, nullptr, s);
+    } else {
+      if (two) launch_gmres_tail<double, 2>(h->gta64[0], batch, nullptr, s);
+      else launch_gmres_tail<double, 3>(h->gta64[0], batch, nullptr, s);
+    }
+    return;
+  }
   if (kernel == 4) {
     if constexpr (std::is_same<R, float>::value)
       if (h->mid) {
@@ -3025,7 +3035,8 @@ hh_status hh_time_kernel(hh_handle *h, int kernel, int level, int batch,
   if (kernel == 6 && h->opt.smoother != HH_SMOOTH_GMRES)
     return fail(HH_ERR_ARG, "kernel 6 needs GMRES smoothing");
   if (level < 0 || level + 1 >= h->L) return fail(HH_ERR_ARG, "bad level");
-  if (kernel == 4 && !h->fused) return fail(HH_ERR_ARG, "kernel 4 needs the fused 2-D path");
+  if (kernel == 4 && !h->fused && !(h->opt.smoother == HH_SMOOTH_GMRES && h->gtail0 > 0))
+    return fail(HH_ERR_ARG, "kernel 4 needs the fused 2-D path or the GMRES one-block tail");
   if (kernel == 1 && h->fused && level < h->tail0)
     return fail(HH_ERR_ARG, "kernel 1 is part of kernel 0 on fused levels");
   if (kernel == 3 && (level != 0 || h->opt.precision != HH_MIXED))

@@ -51,10 +51,84 @@ template <typename R> __device__ __forceinline__ void set_norm(double *g, int i,
   scale_slots(g)[i] = (float)kscale<R>(sq);
 }
 
+// |q_i|^2 and its scale from a per-thread sum of |s_ref q_i|^2 (s_ref: the
+// scale the kernel applied; 1 for q_0).  complex64: without an FP64 square
+// root or division (FP32 reciprocals of scales, which lie far inside the FP32
+// range, and FP64 products): s_i = s_ref / sqrt(sum).
+template <typename R> __device__ __forceinline__ void fin_norm(double *g, int i, double sum,
+                                                               float s_ref) {
+  if (sizeof(R) == 8) {
+    set_norm<R>(g, i, sum);
+    return;
+  }
+  const double inv = s_ref > 0.f ? (double)(1.0f / s_ref) : 1.0;
+  g[i] = sum * inv * inv;
+  const float fs = (float)sum;
+  scale_slots(g)[i] = (sum > 0.0 && fs > 1e-36f && fs < 1e36f) ? s_ref * rsqrtf(fs)
+                                                                 : (float)kscale<R>(g[i]);
+}
+
+// c_ij = <q_i, A q_j> / |q_i|^2 from a sum of s_i q_i . s_ref A q_j (complex64:
+// |q_i|^-2 = s_i^2, so c_ij = sum s_i / s_ref; complex128: the scales are 1).
+template <typename R> __device__ __forceinline__ double fin_coef(const double *g, int i,
+                                                                 double sum, float si,
+                                                                 float s_ref) {
+  if (sizeof(R) == 8) return g[i] > 0.0 ? sum / g[i] : 0.0;
+  if (!(g[i] > 0.0) || !(si > 0.f) || !(s_ref > 0.f)) return 0.0;
+  return sum * (double)(si * (1.0f / s_ref));
+}
+
 // per right-hand side scalars (FP64): |q_i|^2 at 0..3; c_ij (complex) at
 // ci(i, j) for i <= j < 3; z_j (complex) at 16 + 2 j; at 24 whether the
-// step started from a zero iterate; at 25 the Krylov dimension used
+// step started from a zero iterate; at 25 the Krylov dimension used; at
+// 26..27 the FP32 scales.  From 28 on, FP32 copies that every thread reads
+// (a double-to-float conversion per thread would occupy GB300's narrow FP64
+// pipe): c_ij at float 2 (j (j + 1) / 2 + i), z_j at float 12 + 2 j, the
+// zero flag at float 18 and the Krylov dimension at float 19.
 __device__ __forceinline__ int ci(int i, int j) { return 4 + 2 * (j * (j + 1) / 2 + i); }
+__device__ __forceinline__ float *fmirror(double *g) { return reinterpret_cast<float *>(g + 28); }
+__device__ __forceinline__ const float *fmirror(const double *g) {
+  return reinterpret_cast<const float *>(g + 28);
+}
+__device__ __forceinline__ void put_c(double *g, int i, int j, double re, double im) {
+  g[ci(i, j)] = re;
+  g[ci(i, j) + 1] = im;
+  float *f = fmirror(g) + 2 * (j * (j + 1) / 2 + i);
+  f[0] = (float)re;
+  f[1] = (float)im;
+}
+__device__ __forceinline__ void put_z(double *g, int j, double re, double im) {
+  g[16 + 2 * j] = re;
+  g[17 + 2 * j] = im;
+  fmirror(g)[12 + 2 * j] = (float)re;
+  fmirror(g)[13 + 2 * j] = (float)im;
+}
+__device__ __forceinline__ void put_k(double *g, int k) {
+  g[25] = (double)k;
+  fmirror(g)[19] = (float)k;
+}
+__device__ __forceinline__ void put_zero(double *g, bool zero) {
+  g[24] = zero ? 1.0 : 0.0;
+  fmirror(g)[18] = zero ? 1.f : 0.f;
+}
+// c_ij and z_j in the vectors' precision (complex64: from the FP32 copies)
+template <typename R> __device__ __forceinline__ typename Cx<R>::T get_c(const double *g, int i, int j) {
+  if constexpr (sizeof(R) == 4) {
+    const float *f = fmirror(g) + 2 * (j * (j + 1) / 2 + i);
+    return make_float2(f[0], f[1]);
+  } else {
+    return make_double2(g[ci(i, j)], g[ci(i, j) + 1]);
+  }
+}
+template <typename R> __device__ __forceinline__ typename Cx<R>::T get_z(const double *g, int j) {
+  if constexpr (sizeof(R) == 4) {
+    return make_float2(fmirror(g)[12 + 2 * j], fmirror(g)[13 + 2 * j]);
+  } else {
+    return make_double2(g[16 + 2 * j], g[17 + 2 * j]);
+  }
+}
+__device__ __forceinline__ int get_k(const double *g) { return (int)fmirror(g)[19]; }
+__device__ __forceinline__ bool get_zero(const double *g) { return fmirror(g)[18] != 0.f; }
 
 // Called by every block after it wrote its NQ partial sums (layout
 // [b][q][block]): the last block to arrive adds each right-hand side's sums in
@@ -129,7 +203,7 @@ k_gm_start(LevelK<R> L, const typename Cx<R>::T *__restrict__ u, int zero_mode,
   const bool zero =
       __syncthreads_or(zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero)) != 0;
   if (act && blockIdx.x == 0 && threadIdx.x == 0)
-    gsc[b * kGmresScalars + 24] = zero ? 1.0 : 0.0;   // for the update kernel
+    put_zero(gsc + b * kGmresScalars, zero);   // for the update kernel
   R acc[1] = {R(0)};
   if (act) {
     const int N = L.N, P = L.P;
@@ -153,7 +227,7 @@ k_gm_start(LevelK<R> L, const typename Cx<R>::T *__restrict__ u, int zero_mode,
   }
   write_partials<1>(acc, act, parts, b);
   last_block_reduce<1>(counter, parts, gridDim.x, gridDim.y, st,
-                       [&](int bb, const double *v) { set_norm<R>(gsc + bb * kGmresScalars, 0, v[0]); });
+                       [&](int bb, const double *v) { fin_norm<R>(gsc + bb * kGmresScalars, 0, v[0], 1.f); });
 }
 
 // w = A q_J; <q_i, w> for i <= J; c_iJ = <q_i, w> / |q_i|^2.
@@ -198,13 +272,11 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
   last_block_reduce<NQ>(counter, parts, gridDim.x, gridDim.y, st,
                         [&](int bb, const double *v) {
                           double *g = gsc + bb * kGmresScalars;
-                          const double sj = (double)kscale_of<R>(g, J);
+                          const float sj = kscale_of<R>(g, J);
                           for (int i = 0; i <= J; ++i) {
-                            const double s = g[i];
-                            const double si = (double)kscale_of<R>(g, i);
-                            const bool ok = s > 0.0 && si * sj > 0.0;
-                            g[ci(i, J)] = ok ? v[2 * i] / (si * sj) / s : 0.0;
-                            g[ci(i, J) + 1] = ok ? v[2 * i + 1] / (si * sj) / s : 0.0;
+                            const float si = kscale_of<R>(g, i);
+                            put_c(g, i, J, fin_coef<R>(g, i, v[2 * i], si, sj),
+                                  fin_coef<R>(g, i, v[2 * i + 1], si, sj));
                           }
                         });
 }
@@ -241,7 +313,7 @@ k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
     C c[J + 1];
     const double *g = gsc + b * kGmresScalars;
 #pragma unroll
-    for (int i = 0; i <= J; ++i) c[i] = cmk((R)g[ci(i, J)], (R)g[ci(i, J) + 1]);
+    for (int i = 0; i <= J; ++i) c[i] = get_c<R>(g, i, J);
     const int N = L.N, P = L.P;
     const size_t off = (size_t)b * L.S;
     const C *wb = w_in + off;
@@ -278,15 +350,23 @@ k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
   last_block_reduce<NQ>(counter, parts, gridDim.x, gridDim.y, st,
                         [&](int bb, const double *v) {
                           double *g = gsc + bb * kGmresScalars;
-                          const double s2 = (double)kscale_of<R>(g, J);
-                          set_norm<R>(g, J + 1, s2 > 0.0 ? v[0] / (s2 * s2) : v[0]);
-                          for (int i = 0; i <= J + 1; ++i) {
-                            const double sq = g[i];
-                            const double si = i <= J ? (double)kscale_of<R>(g, i) : s2;
-                            const bool ok = sq > 0.0 && si * s2 > 0.0;
-                            g[ci(i, J + 1)] = ok ? v[1 + 2 * i] / (si * s2) / sq : 0.0;
-                            g[ci(i, J + 1) + 1] = ok ? v[2 + 2 * i] / (si * s2) / sq : 0.0;
+                          const float s2 = kscale_of<R>(g, J);
+                          fin_norm<R>(g, J + 1, v[0], s2);
+                          for (int i = 0; i <= J; ++i) {
+                            const float si = kscale_of<R>(g, i);
+                            put_c(g, i, J + 1, fin_coef<R>(g, i, v[1 + 2 * i], si, s2),
+                                  fin_coef<R>(g, i, v[2 + 2 * i], si, s2));
                           }
+                          // i = J+1: both factors carry s_J, so c = sum / (s_J^2 |q_{J+1}|^2)
+                          // = sum / (the |s_J q_{J+1}|^2 sum)
+                          const bool ok = v[0] > 0.0;
+                          if (sizeof(R) == 4)
+                            put_c(g, J + 1, J + 1,
+                                  ok ? (double)((float)v[1 + 2 * (J + 1)] / (float)v[0]) : 0.0,
+                                  ok ? (double)((float)v[2 + 2 * (J + 1)] / (float)v[0]) : 0.0);
+                          else
+                            put_c(g, J + 1, J + 1, ok ? v[1 + 2 * (J + 1)] / v[0] : 0.0,
+                                  ok ? v[2 + 2 * (J + 1)] / v[0] : 0.0);
                         });
 }
 
@@ -294,8 +374,8 @@ k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
 // at most), by complex Givens rotations; z_j = y_j / |q_j|.
 __device__ void gm_lsq(double *g, int m, double tiny) {
   if (!(g[0] > 0.0)) {   // zero (or invalid) residual: no correction
-    for (int j = 0; j < 6; ++j) g[16 + j] = 0.0;
-    g[25] = 0.0;
+    for (int j = 0; j < 3; ++j) put_z(g, j, 0.0, 0.0);
+    put_k(g, 0);
     return;
   }
   double nrm[4];
@@ -344,10 +424,82 @@ __device__ void gm_lsq(double *g, int m, double tiny) {
   }
   for (int j = 0; j < 3; ++j) {
     const double2 z = j < k && nrm[j] > 0.0 ? cscale(y[j], 1.0 / nrm[j]) : make_double2(0.0, 0.0);
-    g[16 + 2 * j] = z.x;
-    g[16 + 2 * j + 1] = z.y;
+    put_z(g, j, z.x, z.y);
   }
-  g[25] = (double)k;   // vectors beyond k may hold overflow: the update skips them
+  put_k(g, k);   // vectors beyond k may hold overflow: the update skips them
+}
+
+// The same least-squares problem for complex64 cycles, in FP32 (the cycle's
+// own precision): normalised by |q_0|, H has h_ij = c_ij |q_i| / |q_j| =
+// c_ij s_j / s_i and h_{j+1,j} = s_j / s_{j+1} (s = 1/|q|, the FP32 scales),
+// the right-hand side is e_1, and z_j = y_j |q_0| / |q_j| = y_j s_j / s_0.
+// The Krylov dimension stops at the first q_{j+1} with |q_{j+1}| <= 1e-6 |q_0|
+// (|q_{j+1}|^2 <= 1e-12 |q_0|^2, the FP64 version's test).
+__device__ void gm_lsq32(double *g, int m) {
+  const float *sc = scale_slots(g);
+  if (!(g[0] > 0.0) || !(sc[0] > 0.f)) {
+    for (int j = 0; j < 3; ++j) put_z(g, j, 0.0, 0.0);
+    put_k(g, 0);
+    return;
+  }
+  int k = m;
+  for (int j = 0; j < m; ++j)
+    if (!(sc[j + 1] > 0.f) || !(sc[0] > 1e-6f * sc[j + 1])) { k = j + 1; break; }
+  float2 H[4][3], rhs[4];
+  for (int i = 0; i < 4; ++i) {
+    rhs[i] = make_float2(0.f, 0.f);
+    for (int j = 0; j < 3; ++j) H[i][j] = make_float2(0.f, 0.f);
+  }
+  rhs[0] = make_float2(1.f, 0.f);
+  for (int j = 0; j < k; ++j) {
+    for (int i = 0; i <= j; ++i) {
+      const float f = sc[j] * (1.0f / sc[i]);
+      const float2 c = get_c<float>(g, i, j);
+      H[i][j] = make_float2(c.x * f, c.y * f);
+    }
+    H[j + 1][j] = make_float2(sc[j] * (1.0f / sc[j + 1]), 0.f);
+  }
+  float2 cs[3], sn[3];
+  for (int j = 0; j < k; ++j) {
+    for (int i = 0; i < j; ++i) {   // earlier rotations on column j
+      const float2 a = H[i][j], bb = H[i + 1][j];
+      H[i][j] = cadd(cmul(cmk(cs[i].x, -cs[i].y), a), cmul(cmk(sn[i].x, -sn[i].y), bb));
+      H[i + 1][j] = csub(cmul(cs[i], bb), cmul(sn[i], a));
+    }
+    const float2 a = H[j][j], bb = H[j + 1][j];
+    const float r = sqrtf(cabs2(a) + cabs2(bb));
+    if (r > 0.f) {
+      const float ir = 1.0f / r;
+      cs[j] = cscale(a, ir);
+      sn[j] = cscale(bb, ir);
+    } else {
+      cs[j] = make_float2(1.f, 0.f);
+      sn[j] = make_float2(0.f, 0.f);
+    }
+    H[j][j] = make_float2(r, 0.f);
+    H[j + 1][j] = make_float2(0.f, 0.f);
+    const float2 g0 = rhs[j], g1 = rhs[j + 1];
+    rhs[j] = cadd(cmul(cmk(cs[j].x, -cs[j].y), g0), cmul(cmk(sn[j].x, -sn[j].y), g1));
+    rhs[j + 1] = csub(cmul(cs[j], g1), cmul(sn[j], g0));
+  }
+  float2 y[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  for (int j = k - 1; j >= 0; --j) {
+    float2 t = rhs[j];
+    for (int l = j + 1; l < k; ++l) t = csub(t, cmul(H[j][l], y[l]));
+    y[j] = H[j][j].x > 0.f ? cscale(t, 1.0f / H[j][j].x) : make_float2(0.f, 0.f);
+  }
+  const float i0 = 1.0f / sc[0];
+  for (int j = 0; j < 3; ++j) {
+    const float f = sc[j] * i0;
+    const bool ok = j < k && sc[j] > 0.f;
+    put_z(g, j, ok ? (double)(y[j].x * f) : 0.0, ok ? (double)(y[j].y * f) : 0.0);
+  }
+  put_k(g, k);
+}
+
+template <typename R> __device__ __forceinline__ void gm_lsq_r(double *g, int m, double tiny) {
+  if (sizeof(R) == 4) gm_lsq32(g, m);
+  else gm_lsq(g, m, tiny);
 }
 
 // q_{J+1} = w - sum_{i<=J} c_iJ q_i; |q_{J+1}|^2; after the last column the
@@ -368,7 +520,7 @@ k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
     C c[J + 1];
     const double *g = gsc + b * kGmresScalars;
 #pragma unroll
-    for (int i = 0; i <= J; ++i) c[i] = cmk((R)g[ci(i, J)], (R)g[ci(i, J) + 1]);
+    for (int i = 0; i <= J; ++i) c[i] = get_c<R>(g, i, J);
     const int N = L.N, P = L.P;
     const size_t off = (size_t)b * L.S;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < npts<DIM>(N);
@@ -389,9 +541,8 @@ k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
   last_block_reduce<1>(counter, parts, gridDim.x, gridDim.y, st,
                        [&](int bb, const double *v) {
                          double *g = gsc + bb * kGmresScalars;
-                         const double s = (double)kscale_of<R>(g, J);
-                         set_norm<R>(g, J + 1, s > 0.0 ? v[0] / (s * s) : v[0]);
-                         if (J + 1 == m) gm_lsq(g, m, tiny);
+                         fin_norm<R>(g, J + 1, v[0], kscale_of<R>(g, J));
+                         if (J + 1 == m) gm_lsq_r<R>(g, m, tiny);
                        });
 }
 
@@ -407,11 +558,11 @@ k_gm_update(LevelK<R> L, const typename Cx<R>::T *u_in,
   const int b = blockIdx.y;
   if (!__syncthreads_and(!(st && !st[b].active))) return;
   const double *g = gsc + b * kGmresScalars;
-  const bool zero = g[24] != 0.0;
-  const int k = min(m, (int)g[25]);
+  const bool zero = get_zero(g);
+  const int k = min(m, get_k(g));
   C z[3];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) z[j] = cmk((R)g[16 + 2 * j], (R)g[17 + 2 * j]);
+  for (int j = 0; j < 3; ++j) z[j] = get_z<R>(g, j);
   const int N = L.N, P = L.P;
   const size_t off = (size_t)b * L.S;
   for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < npts<DIM>(N);
@@ -526,7 +677,7 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
       acc[0] += r.x * r.x + r.y * r.y;
     }
     tail_reduce<1>(acc, ws, red);
-    if (threadIdx.x == 0) set_norm<R>(g, 0, red[0]);
+    if (threadIdx.x == 0) fin_norm<R>(g, 0, red[0], 1.f);
     __syncthreads();   // every thread reads the scale of q_0 next
   }
 #pragma unroll
@@ -557,13 +708,9 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
       }
       tail_reduce<6>(acc, ws, red, 2 * (J + 1));
       if (threadIdx.x == 0) {
-        const double sj = (double)sc[J];
         for (int i = 0; i <= J; ++i) {
-          const double sq = g[i];
-          const double si = (double)sc[i];
-          const bool ok = sq > 0.0 && si * sj > 0.0;
-          g[ci(i, J)] = ok ? red[2 * i] / (si * sj) / sq : 0.0;
-          g[ci(i, J) + 1] = ok ? red[2 * i + 1] / (si * sj) / sq : 0.0;
+          put_c(g, i, J, fin_coef<R>(g, i, red[2 * i], sc[i], sc[J]),
+                fin_coef<R>(g, i, red[2 * i + 1], sc[i], sc[J]));
         }
       }
       __syncthreads();
@@ -573,7 +720,7 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
       C c[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
-        c[i] = i <= J ? cmk((R)g[ci(i, J)], (R)g[ci(i, J) + 1]) : czero<C>();
+        c[i] = i <= J ? get_c<R>(g, i, J) : czero<C>();
       R acc[1] = {R(0)};
       C *qn = J + 1 < m ? Q(J + 1) : nullptr;
       for (int p = threadIdx.x; p < npt; p += TB) {
@@ -589,19 +736,18 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
       }
       tail_reduce<1>(acc, ws, red);
       if (threadIdx.x == 0) {
-        const double sj = (double)sc[J];
-        set_norm<R>(g, J + 1, sj > 0.0 ? red[0] / (sj * sj) : red[0]);
-        if (J + 1 == m) gm_lsq(g, m, tiny);
+        fin_norm<R>(g, J + 1, red[0], sc[J]);
+        if (J + 1 == m) gm_lsq_r<R>(g, m, tiny);
       }
       __syncthreads();
     }
   }
   // U = U + sum_j z_j q_j
   {
-    const int k = min(m, (int)g[25]);
+    const int k = min(m, get_k(g));
     C z[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) z[j] = cmk((R)g[16 + 2 * j], (R)g[17 + 2 * j]);
+    for (int j = 0; j < 3; ++j) z[j] = get_z<R>(g, j);
     for (int p = threadIdx.x; p < npt; p += TB) {
       C v = zero ? czero<C>() : U[p];
 #pragma unroll

@@ -5,7 +5,7 @@
 namespace hh {
 
 constexpr int kGmresMaxBatch = 64;   // right-hand sides per handle with GMRES smoothing
-constexpr int kGmresScalars = 32;    // FP64 scalars per right-hand side
+constexpr int kGmresScalars = 40;    // FP64 scalars per right-hand side (and FP32 mirrors)
 constexpr int kGmresParts = 7;       // partial sums per block and right-hand side (at most)
 
 // Workspace of one level: Krylov vectors q_0..q_3 (at stride qs = S * batch
