@@ -140,6 +140,7 @@ struct hh_handle {
   int parts_cap = 0;                // capacity of `partials` per RHS
   int gm_cap = 0;                   // most blocks of a GMRES smoothing kernel
   int gm_fuse = 1;                  // fused orthogonalisation + Arnoldi kernels
+  int pw3d = 0;                     // 3-D: point-wise kernels instead of the tile-staged ones
   cudaStream_t side = nullptr;      // branch of the stop test in the fused cycle
   cudaStream_t grp = nullptr;       // this handle's stream in a group solve (lazy)
   cudaEvent_t ev_grp = nullptr;     // its join event
@@ -321,13 +322,7 @@ inline bool stop_test(int check) { return check == CHECK_CYCLE || check == CHECK
 // and written to W.u_post[0]; W.f[0] holds the right-hand side.
 // 3-D cycles use the tile-staged kernels (hh_tiled3d.cu); HH_POINTWISE3D=1 in
 // the environment selects the point-wise kernels instead (for comparisons).
-bool pointwise3d() {
-  static const bool v = [] {
-    const char *e = std::getenv("HH_POINTWISE3D");
-    return e && std::strcmp(e, "1") == 0;
-  }();
-  return v;
-}
+bool pointwise3d(const hh_handle *h) { return h->pw3d != 0; }
 
 template <typename R> GmresWork<R> gmres_work(hh_handle *h, int l) {
   Work<R> &W = work<R>(h);
@@ -381,7 +376,7 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
       in = W.u_pre[l];
       zm = ZERO_NONE;
     }
-    if (DIM == 3 && !pointwise3d())
+    if (DIM == 3 && !pointwise3d(h))
       launch_resid_restrict3d<R>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
                                  cscal<R>(h, l, dir), batch, st, s);
     else
@@ -428,7 +423,7 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
       typename Cx<R>::T *out = ((h->opt.nu1 - 1 - j) % 2 == 0) ? W.u_pre[l] : W.tmp[l];
       const int zm = j == 0 ? (l == 0 ? zero0 : ZERO_ALL) : ZERO_NONE;
       const bool norm = l == 0 && j == 0 && stop_test(check);
-      if (DIM == 3 && !pointwise3d())
+      if (DIM == 3 && !pointwise3d(h))
         launch_smooth3d<R>(K, in, zm, W.f[l], out, om, batch, st, norm ? h->partials : nullptr, s);
       else
         launch_smooth<R, DIM>(K, in, zm, W.f[l], out, om, batch, st,
@@ -441,7 +436,7 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
       }
       in = out;
     }
-    if (DIM == 3 && !pointwise3d())
+    if (DIM == 3 && !pointwise3d(h))
       launch_resid_restrict3d<R>(K, W.u_pre[l], W.f[l], W.f[l + 1], lay_of(h, l + 1),
                                  cscal<R>(h, l, dir), batch, st, s);
     else
@@ -455,13 +450,13 @@ void enqueue_cycle(hh_handle *h, int dir, int batch, int zero0, int check,
     const typename Cx<R>::T *in = nullptr;
     for (int j = 0; j < h->opt.nu2; ++j) {
       typename Cx<R>::T *out = ((h->opt.nu2 - 1 - j) % 2 == 0) ? W.u_post[l] : W.tmp[l];
-      if (j == 0 && DIM == 3 && !pointwise3d())
+      if (j == 0 && DIM == 3 && !pointwise3d(h))
         launch_correct_smooth3d<R>(K, W.u_pre[l], W.u_post[l + 1], lay_of(h, l + 1), W.f[l],
                                    out, om, batch, st, s);
       else if (j == 0)
         launch_correct_smooth<R, DIM>(K, W.u_pre[l], W.u_post[l + 1], lay_of(h, l + 1), W.f[l],
                                       out, om, batch, st, s);
-      else if (DIM == 3 && !pointwise3d())
+      else if (DIM == 3 && !pointwise3d(h))
         launch_smooth3d<R>(K, in, ZERO_NONE, W.f[l], out, om, batch, st, nullptr, s);
       else
         launch_smooth<R, DIM>(K, in, ZERO_NONE, W.f[l], out, om, batch, st,
@@ -1034,7 +1029,7 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
                      batch, nullptr, h->err, s);
     return;
   }
-  const bool tiled = !two && !pointwise3d();   // the kernels the 3-D cycle runs
+  const bool tiled = !two && !pointwise3d(h);   // the kernels the 3-D cycle runs
   if (kernel == 0) {
     double *parts = level == 0 ? h->partials : nullptr;
     if (two) launch_smooth<R, 2>(K, W.u_post[level], ZERO_NONE, W.f[level], W.u_pre[level], om, batch, nullptr, parts, h->nparts, s);
@@ -1704,6 +1699,7 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   const hh_grid &g = h->grid;
   const int dim = g.dim, n = g.n;
   h->dim = dim;
+  if (const char *e = std::getenv("HH_POINTWISE3D")) h->pw3d = std::strcmp(e, "1") == 0;
   h->n = n;
   int L = 0;
   for (int nl = n; nl >= h->opt.coarsest; nl /= 2) ++L;
@@ -1978,7 +1974,7 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
   }
   h->nparts = h->fused ? tile_parts(h->variant[0], h->lv[0].N) : partial_blocks(h->lv[0].pts);
   // the 3-D weighted-Jacobi cycle's level-0 sweep writes one partial sum per box
-  if (dim == 3 && h->opt.smoother == HH_SMOOTH_JACOBI && !pointwise3d())
+  if (dim == 3 && h->opt.smoother == HH_SMOOTH_JACOBI && !pointwise3d(h))
     h->nparts = tiles3d(h->lv[0].N);
   // the GMRES cycle's level-0 start kernel writes one partial sum per block
   if (h->opt.smoother == HH_SMOOTH_GMRES) h->nparts = gmres_blocks(h, 0);
@@ -2954,6 +2950,9 @@ hh_status hh_smooth(hh_handle *h, int level, const void *u_in_dev,
   if (h->dim == 2)
     launch_smooth<double, 2>(K, (const double2 *)u_in_dev, ZERO_NONE, (const double2 *)f_dev,
                              (double2 *)u_out_dev, om, batch, nullptr, nullptr, 0, (cudaStream_t)stream);
+  else if (!pointwise3d(h))   // the tile-staged kernel the 3-D cycle runs
+    launch_smooth3d<double>(K, (const double2 *)u_in_dev, ZERO_NONE, (const double2 *)f_dev,
+                            (double2 *)u_out_dev, om, batch, nullptr, nullptr, (cudaStream_t)stream);
   else
     launch_smooth<double, 3>(K, (const double2 *)u_in_dev, ZERO_NONE, (const double2 *)f_dev,
                              (double2 *)u_out_dev, om, batch, nullptr, nullptr, 0, (cudaStream_t)stream);
@@ -2976,6 +2975,9 @@ hh_status hh_residual_restrict(hh_handle *h, int level, const void *u_dev,
   if (h->dim == 2)
     launch_resid_restrict<double, 2>(K, (const double2 *)u_dev, (const double2 *)f_dev,
                                      (double2 *)fc_dev, lc, c, batch, nullptr, (cudaStream_t)stream);
+  else if (!pointwise3d(h))
+    launch_resid_restrict3d<double>(K, (const double2 *)u_dev, (const double2 *)f_dev,
+                                    (double2 *)fc_dev, lc, c, batch, nullptr, (cudaStream_t)stream);
   else
     launch_resid_restrict<double, 3>(K, (const double2 *)u_dev, (const double2 *)f_dev,
                                      (double2 *)fc_dev, lc, c, batch, nullptr, (cudaStream_t)stream);
@@ -3000,6 +3002,10 @@ hh_status hh_correct_smooth(hh_handle *h, int level, const void *u_in_dev,
     launch_correct_smooth<double, 2>(K, (const double2 *)u_in_dev, (const double2 *)e_dev, lc,
                                      (const double2 *)f_dev, (double2 *)u_out_dev, om, batch,
                                      nullptr, (cudaStream_t)stream);
+  else if (!pointwise3d(h))
+    launch_correct_smooth3d<double>(K, (const double2 *)u_in_dev, (const double2 *)e_dev, lc,
+                                    (const double2 *)f_dev, (double2 *)u_out_dev, om, batch,
+                                    nullptr, (cudaStream_t)stream);
   else
     launch_correct_smooth<double, 3>(K, (const double2 *)u_in_dev, (const double2 *)e_dev, lc,
                                      (const double2 *)f_dev, (double2 *)u_out_dev, om, batch,

@@ -234,3 +234,43 @@ def test_radiating_condition_3d_cycles_match_oracle():
         got = host(mg.cycles(dev(f), dev(np.zeros_like(f)), 2))
         assert relerr(got[0], u) < 1e-10, sm
         mg.close()
+
+
+@pytest.mark.parametrize("fuse", ["0", "1"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[3]],
+                         ids=lambda c: f"{c['dim']}d-n{c['n']}-m{c['m']}")
+def test_gmres_fused_and_separate_kernels_match_oracle(case, fuse, monkeypatch):
+    """The orthogonalisation of step j fused with the Arnoldi product of step
+    j+1 (neighbours' q_{j+1} recomputed; HH_GMFUSE=1, the complex64 default)
+    and the separate kernels (HH_GMFUSE=0, the complex128 default) both
+    follow the oracle: FP64 to 1e-9, complex64 to 1e-4, after two cycles."""
+    monkeypatch.setenv("HH_GMFUSE", fuse)
+    f = W.random_field((2,) + (case["n"] - 1,) * case["dim"], 37)
+    for precision, tol in (("fp64", 1e-9), ("mixed", 1e-4)):
+        H, mg = _pair(case, precision=precision)
+        assert mg.cycle_kernels > 0
+        got = host(mg.cycles(dev(f), dev(np.zeros_like(f)), 2))
+        for b in range(2):
+            u = np.zeros_like(f[b])
+            for _ in range(2):
+                u = O.vcycle(H, 0, u, f[b])
+            assert relerr(got[b], u) < tol, (precision, b)
+        mg.close()
+
+
+def test_gmres_time_hooks():
+    """hh_time_kernel kernel 6 (one level-0 GMRES step) and kernel 4 (the
+    one-block tail) run on a GMRES handle; kernel 6 is refused on a Jacobi
+    handle."""
+    import ctypes as ct
+    from paper_1211_4752_gb300 import HelmholtzMG, _binding as B
+    s = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    mg = HelmholtzMG(256, k2=(0.625 * 256) ** 2, layers=8, precision="mixed", smoother="gmres")
+    ms = ct.c_double()
+    for kernel in (6, 4):
+        assert B.lib().hh_time_kernel(mg._h, kernel, 0, 1, 3, ct.byref(ms), s) == 0
+        assert ms.value > 0.0
+    mg.close()
+    mj = HelmholtzMG(64, k2=1600.0, layers=4, precision="mixed")
+    assert B.lib().hh_time_kernel(mj._h, 6, 0, 1, 1, ct.byref(ms), s) != 0
+    mj.close()

@@ -86,6 +86,17 @@ def test_apply_forward_and_adjoint(case):
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c['dim']}d-n{c['n']}-{c['form']}")
 def test_step_kernels(case):
+    check_step_kernels(case)
+
+
+def test_step_kernels_3d_63():
+    """The 3-D tile-staged kernels (8 x 8 x 8 boxes) on 63^3 with a k^2 field
+    and uneven ECS layers: several boxes per axis and a ragged last box on
+    every level (63, 31, 15, 7 = 8 q - 1)."""
+    check_step_kernels(dict(n=64, dim=3, k2=("field", 20.0, 40.0), layers=(4, 6), form="csl"))
+
+
+def check_step_kernels(case):
     H, mg = make_pair(case, batch=2)
     for l in range(len(H.levels) - 1):
         lv, lc = H.levels[l], H.levels[l + 1]
@@ -590,3 +601,22 @@ def test_torch_caching_allocator_serves_the_workspace(tmp_path):
     gc.enable()
     assert after == before
     ref.close()
+
+
+def test_tiled_3d_cycle_matches_pointwise(monkeypatch):
+    """The 3-D cycle's tile-staged kernels and the point-wise ones
+    (HH_POINTWISE3D=1) evaluate the same per-point arithmetic: FP64 cycles on
+    63^3 with a k^2 field agree to rounding, complex64 to its rounding."""
+    from paper_1211_4752_gb300 import HelmholtzMG
+    n = 64
+    k2 = W.smooth_k2(n, 3, 2, 20.0, 40.0)
+    f = rnd((1,) + (n - 1,) * 3, 5)
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("HH_POINTWISE3D", mode)
+        for precision in ("fp64", "mixed"):
+            mg = HelmholtzMG(n, dim=3, k2=dev(k2), layers=(4, 6), precision=precision, max_batch=1)
+            out[mode, precision] = host(mg.cycles(dev(f), dev(np.zeros_like(f)), 2))
+            mg.close()
+    assert maxrel(out["0", "fp64"], out["1", "fp64"]) < 1e-13
+    assert maxrel(out["0", "mixed"], out["1", "mixed"]) < 1e-5
