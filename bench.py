@@ -414,7 +414,9 @@ def run_ours(args):
                        "l2": "flushed between steps (256 MB write)",
                        "setup_s": setup_s,
                        "tuner": {"key": mg.tuner_key, "coarse_schedule": mg.coarse_schedule,
-                                 "tile_level0": mg.tile_shape(0)}},
+                                 "tile_level0": mg.tile_shape(0),
+                                 "tile_levels": [mg.tile_shape(l) for l in range(mg.levels)
+                                                 if mg.tile_shape(l) is not None]}},
             "solve": {("iterations" if fgm else "cycles"): last["cycles"],
                       ("restarts" if fgm else "refinements"): last["refinements"],
                       "rel_residual": last["rel_residual"], "all_ok": ok},
