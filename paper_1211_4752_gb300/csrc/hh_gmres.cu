@@ -151,8 +151,21 @@ __device__ __forceinline__ void last_block_reduce(unsigned int *counter, const d
     const int b = it / NQ;
     double v = 0.0;
     if (!(st && !st[b].active)) {
+      // four independent load streams per lane (one L2 round trip per four
+      // partials instead of per partial), combined in a fixed order
       const double *p = parts + (size_t)it * nblk;
-      for (int i = lane; i < nblk; i += 32) v += __ldcg(p + i);
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int i = lane;
+      for (; i + 96 < nblk; i += 128) {
+        const double x0 = __ldcg(p + i), x1 = __ldcg(p + i + 32), x2 = __ldcg(p + i + 64),
+                     x3 = __ldcg(p + i + 96);
+        a0 += x0;
+        a1 += x1;
+        a2 += x2;
+        a3 += x3;
+      }
+      for (; i < nblk; i += 32) a0 += __ldcg(p + i);
+      v = (a0 + a1) + (a2 + a3);
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     }
     if (lane == 0) s_sum[it] = v;
@@ -608,14 +621,16 @@ k_gm_correct(LevelK<R> L, const typename Cx<R>::T *u_in, const typename Cx<R>::T
 // ---------------------------------------------------------------------------
 constexpr int TB = 512;
 
-// Sum the first nq of NQ values per thread over the block (TB / 32 warps;
-// ws holds NQ x 32 slots, of which the first TB / 32 of each row are
-// written): each warp adds its lanes' values in their own precision, the warp
-// sums are added in FP64; valid in red[0..nq) after it.
-template <int NQ, typename A>
-__device__ __forceinline__ void tail_reduce(A (&acc)[NQ], double *ws, double *red,
-                                            int nq = NQ) {
-  static_assert(TB % 32 == 0 && TB / 32 <= 32, "one reduction slot per warp");
+// Sum the first nq of NQ values per thread over the block, then thread 0 uses
+// the sums (fin) before the block barrier that publishes its results: each
+// warp adds its lanes' values in their own precision into ws (NQ x 32 slots,
+// the first TB / 32 of each row written); warp 0 adds the warp sums (lanes 4q..4q+3 take quantity q, four warp
+// sums each, then two butterfly steps; a fixed order) and its lane 0 runs fin
+// before the block barrier that publishes fin's results.
+template <int NQ, typename A, typename Fin>
+__device__ __forceinline__ void tail_reduce_fin(A (&acc)[NQ], double *ws, double *red, int nq,
+                                                Fin fin) {
+  static_assert(TB / 32 == 16 && NQ <= 8, "16 warps, at most 8 quantities");
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
@@ -625,10 +640,17 @@ __device__ __forceinline__ void tail_reduce(A (&acc)[NQ], double *ws, double *re
     if (lane == 0) ws[q * 32 + w] = (double)v;
   }
   __syncthreads();
-  if (w < nq) {
-    double v = lane < TB / 32 ? ws[w * 32 + lane] : 0.0;   // one slot per warp of the block
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[w] = v;
+  if (w == 0) {
+    const int q = lane >> 2, part = lane & 3;
+    double v = 0.0;
+    if (q < nq)
+      v = (ws[q * 32 + 4 * part] + ws[q * 32 + 4 * part + 1]) +
+          (ws[q * 32 + 4 * part + 2] + ws[q * 32 + 4 * part + 3]);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    if (part == 0 && q < nq) red[q] = v;
+    __syncwarp();
+    if (lane == 0) fin();
   }
   __syncthreads();
 }
@@ -676,9 +698,8 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
       Q0[p] = r;
       acc[0] += r.x * r.x + r.y * r.y;
     }
-    tail_reduce<1>(acc, ws, red);
-    if (threadIdx.x == 0) fin_norm<R>(g, 0, red[0], 1.f);
-    __syncthreads();   // every thread reads the scale of q_0 next
+    // (every thread reads the scale of q_0 next)
+    tail_reduce_fin<1>(acc, ws, red, 1, [&] { fin_norm<R>(g, 0, red[0], 1.f); });
   }
 #pragma unroll
   for (int J = 0; J < 3; ++J) {
@@ -706,14 +727,11 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
           acc[2 * i + 1] += qi.x * a.y - qi.y * a.x;
         }
       }
-      tail_reduce<6>(acc, ws, red, 2 * (J + 1));
-      if (threadIdx.x == 0) {
-        for (int i = 0; i <= J; ++i) {
+      tail_reduce_fin<6>(acc, ws, red, 2 * (J + 1), [&] {
+        for (int i = 0; i <= J; ++i)
           put_c(g, i, J, fin_coef<R>(g, i, red[2 * i], sc[i], sc[J]),
                 fin_coef<R>(g, i, red[2 * i + 1], sc[i], sc[J]));
-        }
-      }
-      __syncthreads();
+      });
     }
     // q_{J+1} = A q_J - sum_i c_iJ q_i (stored below m), |q_{J+1}|^2
     {
@@ -734,12 +752,10 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
         const C vs = cscale(v, sc[J]);
         acc[0] += vs.x * vs.x + vs.y * vs.y;
       }
-      tail_reduce<1>(acc, ws, red);
-      if (threadIdx.x == 0) {
+      tail_reduce_fin<1>(acc, ws, red, 1, [&] {
         fin_norm<R>(g, J + 1, red[0], sc[J]);
         if (J + 1 == m) gm_lsq_r<R>(g, m, tiny);
-      }
-      __syncthreads();
+      });
     }
   }
   // U = U + sum_j z_j q_j
