@@ -158,7 +158,9 @@ def profile_one(args):
     k2_t = torch.from_numpy(k2).cuda() if isinstance(k2, np.ndarray) else float(k2)
     mg = HelmholtzMG(w["n"], dim=w["dim"], k2=k2_t, layers=w["layers"],
                      precision=args.precision, max_batch=1)
-    kid = {v: k for k, v in KERNELS.items()}[args.kernel]
+    names = {v: k for k, v in KERNELS.items()}
+    names.update({v: k for k, v in KERNELS3.items()})   # the 3-D level kernels (dim 3)
+    kid = names[args.kernel]
     ms = ct.c_double()
     stream = torch.cuda.current_stream()
     B.check(B.lib().hh_time_kernel(mg._h, kid, 0, 1, 1, ct.byref(ms),
@@ -882,7 +884,8 @@ def main():
     ap.add_argument("--tuner-cache", default=None,
                     help="tuner cache file of --kernel cycles (a second run with the same file "
                          "launches no tuning kernels)")
-    ap.add_argument("--kernel", choices=sorted(KERNELS.values()) + ["fgmres", "cycles"],
+    ap.add_argument("--kernel", choices=sorted(KERNELS.values()) + sorted(KERNELS3.values()) +
+                    ["fgmres", "cycles"],
                     help="launch one level-0 kernel of the workload (or one capped FGMRES "
                          "solve) and exit (for ncu)")
     ap.add_argument("--kernel-n", type=int, default=0,
