@@ -26,7 +26,12 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int BX = kTile3X, BY = kTile3Y, BZ = kTile3Z;         // fine box of the sweeps
-constexpr int CX = kCoarse3X, CY = kCoarse3Y, CZ = kCoarse3Z;   // coarse box of the restriction
+// coarse box of the restriction: complex64 8 x 4 x 4 (the residual region
+// 17 x 9 x 9 per 1024 owned fine points), complex128 4 x 4 x 4 (its shared
+// arrays within the 48 KB of static shared memory)
+template <typename R> struct CBox {
+  static constexpr int X = sizeof(R) == 4 ? 2 * kCoarse3X : kCoarse3X, Y = kCoarse3Y, Z = kCoarse3Z;
+};
 
 // dst[(z H + y) W + x] = src at (ox + x, oy + y, oz + z) over a W x H x D
 // region (zero outside the domain); a thread's loads are all issued first.
@@ -157,6 +162,7 @@ k_resid_restrict3d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u,
                    Lay lc, typename Cx<R>::T cs, const SolveState *__restrict__ st, int nbx,
                    int nby) {
   using C = typename Cx<R>::T;
+  constexpr int CX = CBox<R>::X, CY = CBox<R>::Y, CZ = CBox<R>::Z;
   constexpr int RW = 2 * CX + 1, RH = 2 * CY + 1, RD = 2 * CZ + 1;   // residual region
   constexpr int W = RW + 2, H = RH + 2, D = RD + 2;                  // u region
   __shared__ C su[W * H * D];
@@ -229,37 +235,36 @@ k_correct_smooth3d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u_in,
   stage<W, H, D>(u_in + (size_t)b * L.S, N, P, x0 - 1, y0 - 1, z0 - 1, sw);
   __syncthreads();
   {
-    // w = u + P e: per axis, fine g odd copies coarse (g-1)/2, g even averages
-    // coarse g/2-1 and g/2 (the weights of prolong_at, summed in its order)
-    for (int i = threadIdx.x; i < W * H * D; i += NT) {
-      const int x = i % W, y = (i / W) % H, z = i / (W * H);
-      const int gx = x0 - 1 + x, gy = y0 - 1 + y, gz = z0 - 1 + z;
-      if (gx >= 0 && gx < N && gy >= 0 && gy < N && gz >= 0 && gz < N) {
-        int ix[2], iy[2], iz[2];
-        R wx[2], wy[2], wz[2];
-        int nx, ny, nz;
-        auto axis = [&](int g, int o, int Nc, int *id, R *w, int &n) {
-          if (g & 1) {
-            id[0] = ((g - 1) >> 1) - o;
-            w[0] = R(1);
-            n = 1;
-          } else {
-            n = 0;
-            const int a = (g >> 1) - 1, c = g >> 1;
-            if (a >= 0) { id[n] = a - o; w[n] = R(0.5); ++n; }
-            if (c < Nc) { id[n] = c - o; w[n] = R(0.5); ++n; }
-          }
-        };
-        axis(gx, ex0, lc.N, ix, wx, nx);
-        axis(gy, ey0, lc.N, iy, wy, ny);
-        axis(gz, ez0, lc.N, iz, wz, nz);
-        C p = czero<C>();
-        for (int c = 0; c < nz; ++c)
-          for (int bb = 0; bb < ny; ++bb)
-            for (int a = 0; a < nx; ++a)
-              p = cadd(p, cscale(se[(iz[c] * EH + iy[bb]) * EW + ix[a]], wx[a] * wy[bb] * wz[c]));
-        sw[i] = cadd(sw[i], p);
-      }
+    // w = u + P e by coarse cell: the w region [x0-1, x0+BX] holds the fine
+    // pairs (2c+1, 2c+2) of the coarse c = x0/2-1 .. x0/2+BX/2-1 (local
+    // 0 .. BX/2), likewise in y and z, so a thread forms the 2 x 2 x 2 fine
+    // points of one coarse cell from its 8 coarse values, without branches.  A
+    // fine 2c+1 copies coarse c, a fine 2c+2 averages c and c+1 (the weights of
+    // prolong_at, the terms summed in its order: z outer, x inner; the weights
+    // are powers of two, so the scaled sums equal its sums of scaled terms).
+    // Coarse values outside the coarse domain are staged as zero, and fine
+    // points outside the domain get P e = 0 on a zero u: no tests needed.
+    constexpr int QX = BX / 2 + 1, QY = BY / 2 + 1, QZ = BZ / 2 + 1;
+    constexpr int PE = EW * EH;   // coarse plane
+    constexpr int PW = W * H;     // fine plane
+    const R h = R(0.5), q = R(0.25), o8 = R(0.125);
+    for (int i = threadIdx.x; i < QX * QY * QZ; i += NT) {
+      const int ox = i % QX, oy = (i / QX) % QY, oz = i / (QX * QY);
+      const C *e = se + (oz * EH + oy) * EW + ox;
+      const C e000 = e[0], e100 = e[1], e010 = e[EW], e110 = e[EW + 1];
+      const C e001 = e[PE], e101 = e[PE + 1], e011 = e[PE + EW], e111 = e[PE + EW + 1];
+      C *w = sw + ((2 * oz) * H + 2 * oy) * W + 2 * ox;
+      const C x00 = cadd(e000, e100);              // plane z, row y, along x
+      const C xy0 = cadd(cadd(x00, e010), e110);   // the four of plane z
+      w[0] = cadd(w[0], e000);
+      w[1] = cadd(w[1], cscale(x00, h));
+      w[W] = cadd(w[W], cscale(cadd(e000, e010), h));
+      w[W + 1] = cadd(w[W + 1], cscale(xy0, q));
+      w[PW] = cadd(w[PW], cscale(cadd(e000, e001), h));
+      w[PW + 1] = cadd(w[PW + 1], cscale(cadd(cadd(x00, e001), e101), q));
+      w[PW + W] = cadd(w[PW + W], cscale(cadd(cadd(cadd(e000, e010), e001), e011), q));
+      w[PW + W + 1] =
+          cadd(w[PW + W + 1], cscale(cadd(cadd(cadd(cadd(xy0, e001), e101), e011), e111), o8));
     }
   }
   __syncthreads();
@@ -299,6 +304,7 @@ void launch_resid_restrict3d(const LevelK<R> &L, const typename Cx<R>::T *u,
                              const typename Cx<R>::T *f, typename Cx<R>::T *fc, const Lay &lc,
                              typename Cx<R>::T cs, int batch, const SolveState *st,
                              cudaStream_t s) {
+  constexpr int CX = CBox<R>::X, CY = CBox<R>::Y, CZ = CBox<R>::Z;
   const int nbx = boxes(lc.N, CX), nby = boxes(lc.N, CY), nbz = boxes(lc.N, CZ);
   k_resid_restrict3d<R><<<dim3(nbx * nby * nbz, batch), NT, 0, s>>>(L, u, f, fc, lc, cs, st, nbx,
                                                                     nby);

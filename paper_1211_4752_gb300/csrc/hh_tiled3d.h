@@ -6,6 +6,7 @@ namespace hh {
 
 constexpr int kTile3X = 8, kTile3Y = 8, kTile3Z = 8;    // fine box of the sweeps
 constexpr int kCoarse3X = 4, kCoarse3Y = 4, kCoarse3Z = 4; // coarse box of the restriction
+                                                            // (x doubled for complex64)
 
 // Boxes of a level with N points per axis (one block each per right-hand
 // side; also the number of stop-test partial sums of k_smooth3d on level 0).
