@@ -23,7 +23,8 @@ void down_one(const DownMaps &maps, const LevelK<R> &L, int zero_mode, typename 
               int kconst, const Lay &lc, int batch, const SolveState *st, double *partials,
               int *err, cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
-  launch_pdl(k_down2d<R, BX, BY>, grid, dim3(256), Down2D<R, BX, BY>::smem, s, maps, L,
+  launch_pdl(k_down2d<R, BX, BY>, grid, dim3(256),
+             kconst ? Down2D<R, BX, BY>::smem_kc : Down2D<R, BX, BY>::smem, s, maps, L,
              zero_mode, v_out, fc, cs, omega, kconst, lc, st, partials, err);
 }
 
@@ -32,7 +33,8 @@ void up_one(const UpMaps &maps, const LevelK<R> &L, typename Cx<R>::T *u_out,
             typename Cx<R>::T omega, int kconst, int batch, const SolveState *st, int *err,
             cudaStream_t s) {
   const dim3 grid((L.N + BX - 1) / BX, (L.N + BY - 1) / BY, batch);
-  launch_pdl(k_up2d<R, BX, BY>, grid, dim3(256), Up2D<R, BX, BY>::smem, s, maps, L, u_out, omega,
+  launch_pdl(k_up2d<R, BX, BY>, grid, dim3(256),
+             kconst ? Up2D<R, BX, BY>::smem_kc : Up2D<R, BX, BY>::smem, s, maps, L, u_out, omega,
              kconst, st, err);
 }
 

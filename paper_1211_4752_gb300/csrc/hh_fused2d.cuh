@@ -47,13 +47,16 @@ template <typename R, int BX, int BY> struct Down2D {
   // column x0 (stride SRW), so that the column pairs (even, odd) of the paired
   // path are 16-byte aligned; their first / last column is not used
   static constexpr int SVW = BX + 4, SRW = BX + 2;
+  // the k^2 tile last: launches with constant k leave it out (smem_kc), so
+  // that one more block fits on an SM
   static constexpr size_t oU = 0;
   static constexpr size_t oF = al128(oU + sizeof(C) * UW * UH);
-  static constexpr size_t oK = al128(oF + sizeof(C) * FW * FH);
-  static constexpr size_t oV = al128(oK + sizeof(R) * KW * KH);
+  static constexpr size_t oV = al128(oF + sizeof(C) * FW * FH);
   static constexpr size_t oT = al128(oV + sizeof(C) * SVW * VH);
   static constexpr size_t oB = al128(oT + sizeof(C) * 3 * (VW + VH));
-  static constexpr size_t smem = oB + 16 + 128;   // + base alignment slack
+  static constexpr size_t oK = al128(oB + 16);
+  static constexpr size_t smem_kc = oB + 16 + 128;                   // + base alignment slack
+  static constexpr size_t smem = oK + sizeof(R) * KW * KH + 128;
   static constexpr unsigned bU = sizeof(C) * UW * UH, bF = sizeof(C) * FW * FH,
                             bK = sizeof(R) * KW * KH;
 };
@@ -67,11 +70,12 @@ template <typename R, int BX, int BY> struct Up2D {
   static constexpr size_t oV = 0;
   static constexpr size_t oE = al128(oV + sizeof(C) * VW * VH);
   static constexpr size_t oF = al128(oE + sizeof(C) * EW * EH);
-  static constexpr size_t oK = al128(oF + sizeof(C) * BX * BY);
-  static constexpr size_t oW = al128(oK + sizeof(R) * BX * BY);
+  static constexpr size_t oW = al128(oF + sizeof(C) * BX * BY);
   static constexpr size_t oT = al128(oW + sizeof(C) * SWW * WH);
   static constexpr size_t oB = al128(oT + sizeof(C) * 3 * (WW + WH));
-  static constexpr size_t smem = oB + 16 + 128;
+  static constexpr size_t oK = al128(oB + 16);   // k^2 tile last (left out with constant k)
+  static constexpr size_t smem_kc = oB + 16 + 128;
+  static constexpr size_t smem = oK + sizeof(R) * BX * BY + 128;
   static constexpr unsigned bV = sizeof(C) * VW * VH, bE = sizeof(C) * EW * EH,
                             bF = sizeof(C) * BX * BY, bK = sizeof(R) * BX * BY;
 };
@@ -534,7 +538,7 @@ __device__ __forceinline__ void down_pass_tile(
 }
 
 template <typename R, int BX, int BY>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1)
 k_down2d(const __grid_constant__ DownMaps maps, LevelK<R> L, int zero_mode,
          typename Cx<R>::T *__restrict__ v_out, typename Cx<R>::T *__restrict__ fc,
          typename Cx<R>::T cs, typename Cx<R>::T omega, int kconst, Lay lc,
@@ -776,7 +780,7 @@ __device__ __forceinline__ void up_pass_tile(const UpMaps &maps, const LevelK<R>
 }
 
 template <typename R, int BX, int BY>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1)
 k_up2d(const __grid_constant__ UpMaps maps, LevelK<R> L, typename Cx<R>::T *__restrict__ u_out,
        typename Cx<R>::T omega, int kconst, const SolveState *__restrict__ st, int *err) {
   up_pass_tile<R, BX, BY>(maps, L, u_out, omega, kconst, st, err, blockIdx.x, blockIdx.y,

@@ -42,7 +42,9 @@ namespace {
 constexpr int BX = kPersistBX, BY = kPersistBY;
 using SD = Down2D<float, BX, BY>;
 using SU = Up2D<float, BX, BY>;
-constexpr size_t kOB = SD::oB > SU::oB ? SD::oB : SU::oB;   // mbarrier after both layouts
+// the mbarrier after both layouts, their k^2 tiles (which come last) included
+constexpr size_t kEndD = SD::smem - 128, kEndU = SU::smem - 128;
+constexpr size_t kOB = al128(kEndD > kEndU ? kEndD : kEndU);
 constexpr size_t kSmem = kOB + 16 + 128;
 constexpr long long kSpinLimit = 1LL << 31;   // clock cycles, about one second
 
