@@ -231,6 +231,40 @@ def test_bump_gradient_full_size_against_central_differences():
         assert abs(fd - pred) <= 1e-4 * abs(fd)
 
 
+def test_bump_gradient_complex128_twenty_points():
+    """Config 5's check as stated: the 511^2 bump medium, 16 sources, the
+    adjoint gradient d loss / d k^2 in complex128 (GMRES(3)-smoothed cycles,
+    solves to 1e-11) against central differences of the loss at 20 seeded
+    points of the physical region, to 1e-4 relative."""
+    from paper_1211_4752_gb300 import helmholtz_solve
+    w = W.bump()
+    n, layers = w["n"], w["layers"]
+    k2 = torch.from_numpy(w["k2"]).cuda().requires_grad_(True)
+    f = torch.from_numpy(w["rhs"]).cuda()
+    rows = torch.from_numpy(w["receiver_rows"]).cuda()
+    cols = torch.from_numpy(w["receiver_cols"]).cuda()
+    d = torch.from_numpy(w["data"]).cuda()
+    kw = dict(n=n, layers=layers, smoother="gmres", precision="fp64")
+
+    def loss_of(k2v):
+        u = helmholtz_solve(k2v, f, tol=1e-11, **kw)
+        return 0.5 * (u[:, rows, cols] - d).abs().pow(2).sum()
+
+    L0 = loss_of(k2)
+    L0.backward()
+    gk = k2.grad.detach().cpu().numpy()
+    k2n = k2.detach().cpu().numpy()
+    rng = np.random.default_rng(20)
+    pts = [tuple(rng.integers(layers + 8, n - 1 - layers - 8, size=2)) for _ in range(20)]
+    with torch.no_grad():
+        for (i, j) in pts:
+            dk = 1e-3 * k2n[i, j]
+            kp = k2.detach().clone(); kp[i, j] += dk
+            km = k2.detach().clone(); km[i, j] -= dk
+            fd = (loss_of(kp) - loss_of(km)).item() / (2 * dk)
+            assert abs(fd - gk[i, j]) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(gk).max()), (i, j, fd, gk[i, j])
+
+
 def test_ecs_1023_fgmres_matches_oracle_fixture():
     """FGMRES(32) with one cycle per iteration as the preconditioner (Table 3's
     LVL-MG-FGMRES) on the 1023^2 constant-k problem, FP64 and complex64
