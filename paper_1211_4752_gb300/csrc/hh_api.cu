@@ -140,6 +140,8 @@ struct hh_handle {
   int parts_cap = 0;                // capacity of `partials` per RHS
   int gm_cap = 0;                   // most blocks of a GMRES smoothing kernel
   int gm_fuse = 1;                  // fused orthogonalisation + Arnoldi kernels
+  int gm_col = 1;                   // ... marching down columns on large 2-D levels
+  int gm_col_min = 768;             // (from this many points per axis)
   int pw3d = 0;                     // 3-D: point-wise kernels instead of the tile-staged ones
   cudaStream_t side = nullptr;      // branch of the stop test in the fused cycle
   cudaStream_t grp = nullptr;       // this handle's stream in a group solve (lazy)
@@ -346,6 +348,13 @@ int partial_blocks_of(const hh_handle *h, int l) {
   return l == 0 ? h->nparts : gmres_blocks(h, l);
 }
 
+// Kernel options of a GMRES smoothing step on a level of N points per axis
+// (launch_gmres_rest's fuse bits): fused orthogonalisation + Arnoldi, and on
+// 2-D levels with N >= gm_col_min the column-marching kernels.
+int gm_flags(const hh_handle *h, int N) {
+  return h->gm_fuse | ((h->gm_col && h->dim == 2 && N >= h->gm_col_min) ? 2 : 0);
+}
+
 // The V-cycle with GMRES(m) smoothing (Sec. 3.2): on each level nu1 GMRES
 // steps, residual + restriction, recursion, correction, nu2 GMRES steps.
 // On level 0 the first step's residual is the stop test's.
@@ -372,7 +381,7 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
         else
           launch_check_inner(h->st, h->partials, h->params, h->flag, cond, h->copies, h->err, s);
       }
-      launch_gmres_rest<R, DIM>(K, in, zm, W.u_pre[l], g, m, batch, st, nb, s, h->gm_fuse);
+      launch_gmres_rest<R, DIM>(K, in, zm, W.u_pre[l], g, m, batch, st, nb, s, gm_flags(h, K.N));
       in = W.u_pre[l];
       zm = ZERO_NONE;
     }
@@ -400,7 +409,7 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
                                  batch, st, s);
     for (int j = 0; j < h->opt.nu2; ++j) {
       launch_gmres_start<R, DIM>(K, W.u_post[l], ZERO_NONE, W.f[l], g, batch, st, g.parts, nb, s);
-      launch_gmres_rest<R, DIM>(K, W.u_post[l], ZERO_NONE, W.u_post[l], g, m, batch, st, nb, s, h->gm_fuse);
+      launch_gmres_rest<R, DIM>(K, W.u_post[l], ZERO_NONE, W.u_post[l], g, m, batch, st, nb, s, gm_flags(h, K.N));
     }
   }
 }
@@ -993,10 +1002,10 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
     typename Cx<R>::T *u = W.u_post[level];
     if (two) {
       launch_gmres_start<R, 2>(K, u, ZERO_NONE, W.f[level], g, batch, nullptr, g.parts, nb, s);
-      launch_gmres_rest<R, 2>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s, h->gm_fuse);
+      launch_gmres_rest<R, 2>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s, gm_flags(h, K.N));
     } else {
       launch_gmres_start<R, 3>(K, u, ZERO_NONE, W.f[level], g, batch, nullptr, g.parts, nb, s);
-      launch_gmres_rest<R, 3>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s, h->gm_fuse);
+      launch_gmres_rest<R, 3>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s, gm_flags(h, K.N));
     }
     return;
   }
@@ -1932,6 +1941,8 @@ hh_status setup_impl(hh_handle *h, const double *k2_dev, double k2_const,
     // bound of those kernels); HH_GMFUSE=0/1 in the environment overrides
     h->gm_fuse = h->opt.precision != HH_FP64;
     if (const char *e = std::getenv("HH_GMFUSE")) h->gm_fuse = std::atoi(e) != 0;
+    if (const char *e = std::getenv("HH_GMCOL")) h->gm_col = std::atoi(e) != 0;
+    if (const char *e = std::getenv("HH_GMCOL_MIN_N")) h->gm_col_min = std::max(1, std::atoi(e));
     HH_TRY(dev_alloc_n(h, &h->gm_counter, 1));
     HH_CK(cudaMemsetAsync(h->gm_counter, 0, sizeof(unsigned int), s));
     HH_TRY(dev_alloc_n(h, &h->gm_gsc, (size_t)kGmresScalars * B));

@@ -383,6 +383,173 @@ k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
                         });
 }
 
+// ---------------------------------------------------------------------------
+// Column-marching versions of Arnoldi step 0 and of the fused
+// orthogonalisation + Arnoldi steps, for large 2-D levels.  A thread owns one
+// column x of a 256-column chunk and marches down a run of rows: the vector
+// the operator is applied to (q_0, or q_{J+1} = w - sum c_iJ q_i) is formed
+// once per point, one row ahead, and kept in registers for the rows above and
+// below; the west and east neighbours come from the adjacent lanes by warp
+// shuffles (a warp's first and last lane form theirs from memory).  Each
+// input vector is read once per point instead of at five stencil points, and
+// q_{J+1} is formed once per point instead of five times.  The per-point
+// arithmetic is the point-wise kernels' (stencil_vals2 adds the neighbour
+// terms in the order of stencil<R, 2>), so iterates agree to rounding of the
+// sums' order.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T stencil_vals2(const LevelK<R> &L, int x, int y,
+                                                           typename Cx<R>::T uc,
+                                                           typename Cx<R>::T uw,
+                                                           typename Cx<R>::T ue,
+                                                           typename Cx<R>::T us,
+                                                           typename Cx<R>::T un) {
+  using C = typename Cx<R>::T;
+  const int N = L.N;
+  const C *c = L.coef;
+  C nb = czero<C>();
+  if (x > 0) nb = cfma(c[x], uw, nb);
+  if (x < N - 1) nb = cfma(c[2 * N + x], ue, nb);
+  c += 3 * N;
+  if (y > 0) nb = cfma(c[y], us, nb);
+  if (y < N - 1) nb = cfma(c[2 * N + y], un, nb);
+  const C D = diag_at<R, 2>(L, x, y, 0);
+  return csub(cmul(D, uc), nb);
+}
+
+template <typename C> __device__ __forceinline__ C shfl_c(C v, int delta, bool up) {
+  C r;
+  if (up) {
+    r.x = __shfl_up_sync(0xffffffffu, v.x, delta);
+    r.y = __shfl_up_sync(0xffffffffu, v.y, delta);
+  } else {
+    r.x = __shfl_down_sync(0xffffffffu, v.x, delta);
+    r.y = __shfl_down_sync(0xffffffffu, v.y, delta);
+  }
+  return r;
+}
+
+// OA = false: Arnoldi step 0 (w = A q_0, <q_0, w>), J unused.
+// OA = true: orthogonalise column J and apply the next Arnoldi product (the
+// arithmetic of k_gm_orth_arnoldi<R, 2, J>).  Grid: nchunk x ceil(N / rows)
+// blocks per right-hand side (blockIdx.x = run * nchunk + chunk).
+template <typename R, bool OA, int J>
+__global__ void __launch_bounds__(256)
+k_gm_col2d(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
+           const typename Cx<R>::T *__restrict__ w_in, typename Cx<R>::T *__restrict__ w_out,
+           const SolveState *st, double *parts, unsigned int *counter, double *gsc, int nchunk,
+           int rows) {
+  using C = typename Cx<R>::T;
+  constexpr int JJ = OA ? J : -1;        // the last stored column the step reads
+  constexpr int NV = JJ + 1;             // q_0..q_JJ carried for the inner products
+  constexpr int NQ = OA ? 1 + 2 * (J + 2) : 2;
+  const int b = blockIdx.y;
+  const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
+  R acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = R(0);
+  R sc[NV > 0 ? NV : 1];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) sc[i] = kscale_of<R>(gsc + b * kGmresScalars, i);
+  const R s_op = kscale_of<R>(gsc + b * kGmresScalars, OA ? J : 0);   // scale of the sums
+  if (act) {
+    const int N = L.N, P = L.P, lane = threadIdx.x & 31;
+    const size_t off = (size_t)b * L.S;
+    const C *qb = Q + off;
+    const C *wb = OA ? w_in + off : nullptr;
+    C c[NV > 0 ? NV : 1];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) c[i] = get_c<R>(gsc + b * kGmresScalars, i, JJ);
+    const int chunk = blockIdx.x % nchunk, run = blockIdx.x / nchunk;
+    const int x = chunk * blockDim.x + threadIdx.x;
+    const int y0 = run * rows, y1 = min(N, y0 + rows);
+    // the operand at (xx, yy), zero outside the domain; qi receives q_0..q_JJ there
+    auto operand = [&](int xx, int yy, C *qi) {
+      if (xx < 0 || xx >= N || yy < 0 || yy >= N) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) qi[i] = czero<C>();
+        return czero<C>();
+      }
+      const size_t o = (size_t)yy * P + xx;
+      if (!OA) return qb[o];
+      C v = wb[o];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        qi[i] = qb[(size_t)i * qs + o];
+        v = csub(v, cmul(c[i], qi[i]));
+      }
+      return v;
+    };
+    C qdummy[NV > 0 ? NV : 1];
+    C qcur[NV > 0 ? NV : 1], qnext[NV > 0 ? NV : 1];
+    C prev = operand(x, y0 - 1, qdummy);
+    C cur = operand(x, y0, qcur);
+    for (int y = y0; y < y1; ++y) {
+      const C next = operand(x, y + 1, qnext);
+      C wv = shfl_c(cur, 1, true), ev = shfl_c(cur, 1, false);
+      if (lane == 0) wv = operand(x - 1, y, qdummy);
+      if (lane == 31) ev = operand(x + 1, y, qdummy);
+      if (x < N) {
+        const C Aq = stencil_vals2<R>(L, x, y, cur, wv, ev, prev, next);
+        const size_t o = off + (size_t)y * P + x;
+        if (OA) Q[(size_t)(J + 1) * qs + o] = cur;
+        w_out[o] = Aq;
+        const C a = cscale(Aq, s_op);
+        if (OA) {
+          const C vs = cscale(cur, s_op);
+          acc[0] += vs.x * vs.x + vs.y * vs.y;
+#pragma unroll
+          for (int i = 0; i < NV; ++i) {
+            const C qi = cscale(qcur[i], sc[i]);
+            acc[1 + 2 * i] += qi.x * a.x + qi.y * a.y;
+            acc[2 + 2 * i] += qi.x * a.y - qi.y * a.x;
+          }
+          acc[NQ - 2] += vs.x * a.x + vs.y * a.y;
+          acc[NQ - 1] += vs.x * a.y - vs.y * a.x;
+        } else {
+          const C q0s = cscale(cur, s_op);
+          acc[0] += q0s.x * a.x + q0s.y * a.y;
+          acc[1] += q0s.x * a.y - q0s.y * a.x;
+        }
+      }
+      prev = cur;
+      cur = next;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) qcur[i] = qnext[i];
+    }
+  }
+  write_partials<NQ>(acc, act, parts, b);
+  if constexpr (!OA) {
+    last_block_reduce<NQ>(counter, parts, gridDim.x, gridDim.y, st,
+                          [&](int bb, const double *v) {
+                            double *g = gsc + bb * kGmresScalars;
+                            const float s0 = kscale_of<R>(g, 0);
+                            put_c(g, 0, 0, fin_coef<R>(g, 0, v[0], s0, s0),
+                                  fin_coef<R>(g, 0, v[1], s0, s0));
+                          });
+  } else {
+    last_block_reduce<NQ>(counter, parts, gridDim.x, gridDim.y, st,
+                          [&](int bb, const double *v) {
+                            double *g = gsc + bb * kGmresScalars;
+                            const float s2 = kscale_of<R>(g, J);
+                            fin_norm<R>(g, J + 1, v[0], s2);
+                            for (int i = 0; i <= J; ++i) {
+                              const float si = kscale_of<R>(g, i);
+                              put_c(g, i, J + 1, fin_coef<R>(g, i, v[1 + 2 * i], si, s2),
+                                    fin_coef<R>(g, i, v[2 + 2 * i], si, s2));
+                            }
+                            const bool ok = v[0] > 0.0;
+                            if (sizeof(R) == 4)
+                              put_c(g, J + 1, J + 1,
+                                    ok ? (double)((float)v[1 + 2 * (J + 1)] / (float)v[0]) : 0.0,
+                                    ok ? (double)((float)v[2 + 2 * (J + 1)] / (float)v[0]) : 0.0);
+                            else
+                              put_c(g, J + 1, J + 1, ok ? v[1 + 2 * (J + 1)] / v[0] : 0.0,
+                                    ok ? v[2 + 2 * (J + 1)] / v[0] : 0.0);
+                          });
+  }
+}
+
 // Least squares min ||beta e1 - H y|| for the Krylov dimension k (m columns
 // at most), by complex Givens rotations; z_j = y_j / |q_j|.
 __device__ void gm_lsq(double *g, int m, double tiny) {
@@ -951,7 +1118,32 @@ void launch_gmres_rest(const LevelK<R> &L, const typename Cx<R>::T *u_in, int ze
                        const SolveState *st, int nblk, cudaStream_t s, int fuse) {
   const dim3 grid(nblk, batch);
   const dim3 blk(256);
-  if (fuse && m >= 2) {
+  using C = typename Cx<R>::T;
+  if constexpr (DIM == 2) {
+    // large levels: the column-marching Arnoldi 0 and fused steps (fuse bit 1)
+    if ((fuse & 1) && (fuse & 2) && m >= 2) {
+      const int nchunk = (L.N + 255) / 256;
+      const int per = std::max(1, nblk / nchunk);   // row runs per chunk (blocks <= nblk)
+      const int rows = (L.N + per - 1) / per;
+      const dim3 gcol(nchunk * ((L.N + rows - 1) / rows), batch);
+      launch_plain(k_gm_col2d<R, false, 0>, gcol, blk, 0, s, L, g.Q, g.qs, (const C *)nullptr,
+                   g.w, st, g.parts, g.counter, g.gsc, nchunk, rows);
+      launch_plain(k_gm_col2d<R, true, 0>, gcol, blk, 0, s, L, g.Q, g.qs, (const C *)g.w, g.w2,
+                   st, g.parts, g.counter, g.gsc, nchunk, rows);
+      if (m == 2) {
+        launch_plain(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, (const C *)g.w2, st,
+                     g.parts, g.counter, g.gsc, m);
+      } else {
+        launch_plain(k_gm_col2d<R, true, 1>, gcol, blk, 0, s, L, g.Q, g.qs, (const C *)g.w2,
+                     g.w, st, g.parts, g.counter, g.gsc, nchunk, rows);
+        launch_plain(k_gm_orth<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs, (const C *)g.w, st,
+                     g.parts, g.counter, g.gsc, m);
+      }
+      launch_plain(k_gm_update<R, DIM>, grid, blk, 0, s, L, u_in, g.Q, g.qs, u_out, st, g.gsc, m);
+      return;
+    }
+  }
+  if ((fuse & 1) && m >= 2) {
     // A q_0 -> w; (q_1, A q_1) -> w2; (q_2, A q_2) -> w; orthogonalisation of
     // the last column (and the least-squares solve) from the latest buffer
     launch_plain(k_gm_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,

@@ -31,9 +31,11 @@ void launch_gmres_start(const LevelK<R> &L, const typename Cx<R>::T *u, int zero
                         const SolveState *st, double *parts, int nblk, cudaStream_t s);
 
 // The m Arnoldi steps, the least-squares solve and u_out = u_in + V y (u_in
-// read as zero where the start kernel took it as zero).  fuse: the
+// read as zero where the start kernel took it as zero).  fuse bit 0: the
 // orthogonalisation of step J and the Arnoldi product of step J+1 in one
-// kernel (m + 2 kernels instead of 2 m + 1).
+// kernel (m + 2 kernels instead of 2 m + 1); bit 1 (2-D): those kernels and
+// Arnoldi step 0 march down columns (hh_gmres.cu, k_gm_col2d; the caller sets
+// it on large levels).
 template <typename R, int DIM>
 void launch_gmres_rest(const LevelK<R> &L, const typename Cx<R>::T *u_in, int zero_mode,
                        typename Cx<R>::T *u_out, const GmresWork<R> &g, int m, int batch,

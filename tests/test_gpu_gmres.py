@@ -274,3 +274,26 @@ def test_gmres_time_hooks():
     mj = HelmholtzMG(64, k2=1600.0, layers=4, precision="mixed")
     assert B.lib().hh_time_kernel(mj._h, 6, 0, 1, 1, ct.byref(ms), s) != 0
     mj.close()
+
+
+@pytest.mark.parametrize("n", [128, 512])
+def test_gmres_column_kernels_match_oracle(n, monkeypatch):
+    """The column-marching Arnoldi and fused kernels (normally from 768^2 on;
+    HH_GMCOL_MIN_N=64 turns them on here, 128: one chunk with idle lanes, 512:
+    two 256-column chunks and a warp-edge neighbour exchange across them)
+    against the oracle's GMRES cycle: FP64 (with HH_GMFUSE=1) to 1e-9 and
+    complex64 to 1e-4, after two cycles, on a k^2 field with ECS layers."""
+    monkeypatch.setenv("HH_GMCOL_MIN_N", "64")
+    monkeypatch.setenv("HH_GMFUSE", "1")
+    case = dict(n=n, dim=2, k2=("field", 0.3 * n * n / 4, 0.35 * n * n / 4), layers=n // 16,
+                form="csl", m=3)
+    f = W.random_field((2,) + (n - 1,) * 2, 41)
+    for precision, tol in (("fp64", 1e-9), ("mixed", 1e-4)):
+        H, mg = _pair(case, precision=precision)
+        got = host(mg.cycles(dev(f), dev(np.zeros_like(f)), 2))
+        for b in range(2):
+            u = np.zeros_like(f[b])
+            for _ in range(2):
+                u = O.vcycle(H, 0, u, f[b])
+            assert relerr(got[b], u) < tol, (precision, b)
+        mg.close()
