@@ -141,7 +141,7 @@ struct hh_handle {
   int gm_cap = 0;                   // most blocks of a GMRES smoothing kernel
   int gm_fuse = 1;                  // fused orthogonalisation + Arnoldi kernels
   int gm_col = 1;                   // ... marching down columns on large 2-D levels
-  int gm_col_min = 768;             // (from this many points per axis)
+  int gm_col_min = 256;             // (from this many points per axis)
   int pw3d = 0;                     // 3-D: point-wise kernels instead of the tile-staged ones
   cudaStream_t side = nullptr;      // branch of the stop test in the fused cycle
   cudaStream_t grp = nullptr;       // this handle's stream in a group solve (lazy)

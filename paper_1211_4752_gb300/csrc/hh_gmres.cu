@@ -463,32 +463,48 @@ k_gm_col2d(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
     const int chunk = blockIdx.x % nchunk, run = blockIdx.x / nchunk;
     const int x = chunk * blockDim.x + threadIdx.x;
     const int y0 = run * rows, y1 = min(N, y0 + rows);
-    // the operand at (xx, yy), zero outside the domain; qi receives q_0..q_JJ there
-    auto operand = [&](int xx, int yy, C *qi) {
-      if (xx < 0 || xx >= N || yy < 0 || yy >= N) {
+    // the inputs of the operand at (xx, yy) (zero outside the domain), and the
+    // operand from them: loading a row two ahead and combining it an iteration
+    // later keeps its loads in flight during the current row's arithmetic
+    struct Raw {
+      C w;
+      C q[NV > 0 ? NV : 1];
+    };
+    auto load = [&](int xx, int yy) {
+      Raw r;
+      r.w = czero<C>();
 #pragma unroll
-        for (int i = 0; i < NV; ++i) qi[i] = czero<C>();
-        return czero<C>();
-      }
+      for (int i = 0; i < (NV > 0 ? NV : 1); ++i) r.q[i] = czero<C>();
+      if (xx < 0 || xx >= N || yy < 0 || yy >= N) return r;
       const size_t o = (size_t)yy * P + xx;
-      if (!OA) return qb[o];
-      C v = wb[o];
-#pragma unroll
-      for (int i = 0; i < NV; ++i) {
-        qi[i] = qb[(size_t)i * qs + o];
-        v = csub(v, cmul(c[i], qi[i]));
+      if (!OA) {
+        r.w = qb[o];
+        return r;
       }
+      r.w = wb[o];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) r.q[i] = qb[(size_t)i * qs + o];
+      return r;
+    };
+    auto combine = [&](const Raw &r) {
+      C v = r.w;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v = csub(v, cmul(c[i], r.q[i]));
       return v;
     };
-    C qdummy[NV > 0 ? NV : 1];
+    const Raw rprev = load(x, y0 - 1), rcur = load(x, y0), rnext = load(x, y0 + 1);
+    C prev = combine(rprev), cur = combine(rcur), next = combine(rnext);
     C qcur[NV > 0 ? NV : 1], qnext[NV > 0 ? NV : 1];
-    C prev = operand(x, y0 - 1, qdummy);
-    C cur = operand(x, y0, qcur);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      qcur[i] = rcur.q[i];
+      qnext[i] = rnext.q[i];
+    }
     for (int y = y0; y < y1; ++y) {
-      const C next = operand(x, y + 1, qnext);
+      const Raw r2 = load(x, y + 2);
       C wv = shfl_c(cur, 1, true), ev = shfl_c(cur, 1, false);
-      if (lane == 0) wv = operand(x - 1, y, qdummy);
-      if (lane == 31) ev = operand(x + 1, y, qdummy);
+      if (lane == 0) wv = combine(load(x - 1, y));
+      if (lane == 31) ev = combine(load(x + 1, y));
       if (x < N) {
         const C Aq = stencil_vals2<R>(L, x, y, cur, wv, ev, prev, next);
         const size_t o = off + (size_t)y * P + x;
@@ -514,8 +530,12 @@ k_gm_col2d(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
       }
       prev = cur;
       cur = next;
+      next = combine(r2);
 #pragma unroll
-      for (int i = 0; i < NV; ++i) qcur[i] = qnext[i];
+      for (int i = 0; i < NV; ++i) {
+        qcur[i] = qnext[i];
+        qnext[i] = r2.q[i];
+      }
     }
   }
   write_partials<NQ>(acc, act, parts, b);

@@ -278,7 +278,7 @@ def test_gmres_time_hooks():
 
 @pytest.mark.parametrize("n", [128, 512])
 def test_gmres_column_kernels_match_oracle(n, monkeypatch):
-    """The column-marching Arnoldi and fused kernels (normally from 768^2 on;
+    """The column-marching Arnoldi and fused kernels (normally from 256^2 on;
     HH_GMCOL_MIN_N=64 turns them on here, 128: one chunk with idle lanes, 512:
     two 256-column chunks and a warp-edge neighbour exchange across them)
     against the oracle's GMRES cycle: FP64 (with HH_GMFUSE=1) to 1e-9 and
