@@ -374,7 +374,8 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
     int zm = l == 0 ? zero0 : ZERO_ALL;
     for (int j = 0; j < h->opt.nu1; ++j) {
       const bool norm = l == 0 && j == 0 && stop_test(check);
-      launch_gmres_start<R, DIM>(K, in, zm, W.f[l], g, batch, st, norm ? h->partials : g.parts, nb, s);
+      launch_gmres_start<R, DIM>(K, in, zm, W.f[l], g, batch, st, norm ? h->partials : g.parts, nb, s,
+                                 gm_flags(h, K.N) & 2);
       if (norm) {
         if (check == CHECK_CYCLE)
           launch_check_cycle(h->st, h->partials, h->params, h->flag, cond, h->copies, h->err, s);
@@ -408,7 +409,8 @@ void enqueue_cycle_gmres(hh_handle *h, int dir, int batch, int zero0, int check,
     launch_gmres_correct<R, DIM>(K, W.u_pre[l], W.u_post[l + 1], lay_of(h, l + 1), W.u_post[l],
                                  batch, st, s);
     for (int j = 0; j < h->opt.nu2; ++j) {
-      launch_gmres_start<R, DIM>(K, W.u_post[l], ZERO_NONE, W.f[l], g, batch, st, g.parts, nb, s);
+      launch_gmres_start<R, DIM>(K, W.u_post[l], ZERO_NONE, W.f[l], g, batch, st, g.parts, nb, s,
+                                 gm_flags(h, K.N) & 2);
       launch_gmres_rest<R, DIM>(K, W.u_post[l], ZERO_NONE, W.u_post[l], g, m, batch, st, nb, s, gm_flags(h, K.N));
     }
   }
@@ -1001,7 +1003,8 @@ void time_one(hh_handle *h, int kernel, int level, int batch, cudaStream_t s) {
     const int nb = partial_blocks_of(h, level), m = h->opt.gmres_m;
     typename Cx<R>::T *u = W.u_post[level];
     if (two) {
-      launch_gmres_start<R, 2>(K, u, ZERO_NONE, W.f[level], g, batch, nullptr, g.parts, nb, s);
+      launch_gmres_start<R, 2>(K, u, ZERO_NONE, W.f[level], g, batch, nullptr, g.parts, nb, s,
+                               gm_flags(h, K.N) & 2);
       launch_gmres_rest<R, 2>(K, u, ZERO_NONE, u, g, m, batch, nullptr, nb, s, gm_flags(h, K.N));
     } else {
       launch_gmres_start<R, 3>(K, u, ZERO_NONE, W.f[level], g, batch, nullptr, g.parts, nb, s);

@@ -570,6 +570,58 @@ k_gm_col2d(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
   }
 }
 
+// The start kernel's column-marching version (2-D): q_0 = f - A u, |q_0|^2,
+// the march over u as in k_gm_col2d.  The grid has nblk blocks per
+// right-hand side like the point-wise kernel (level 0's per-block sums are
+// the stop test's); blocks past the last run of rows add nothing.
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_gm_start_col2d(LevelK<R> L, const typename Cx<R>::T *__restrict__ u, int zero_mode,
+                 const typename Cx<R>::T *__restrict__ f, typename Cx<R>::T *__restrict__ q0,
+                 const SolveState *st, double *parts, unsigned int *counter, double *gsc,
+                 int nchunk, int rows) {
+  using C = typename Cx<R>::T;
+  const int b = blockIdx.y;
+  const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
+  const bool zero =
+      __syncthreads_or(zero_mode == ZERO_ALL || (zero_mode == ZERO_FLAG && st && st[b].zero)) != 0;
+  if (act && blockIdx.x == 0 && threadIdx.x == 0)
+    put_zero(gsc + b * kGmresScalars, zero);   // for the update kernel
+  R acc[1] = {R(0)};
+  const int N = L.N, P = L.P, lane = threadIdx.x & 31;
+  const int runs = (N + rows - 1) / rows;
+  if (act && (int)blockIdx.x < nchunk * runs) {
+    const size_t off = (size_t)b * L.S;
+    const C *ub = u + off;
+    const int chunk = blockIdx.x % nchunk, run = blockIdx.x / nchunk;
+    const int x = chunk * blockDim.x + threadIdx.x;
+    const int y0 = run * rows, y1 = min(N, y0 + rows);
+    auto load = [&](int xx, int yy) {
+      return (zero || xx < 0 || xx >= N || yy < 0 || yy >= N) ? czero<C>() : ub[(size_t)yy * P + xx];
+    };
+    C prev = load(x, y0 - 1), cur = load(x, y0), next = load(x, y0 + 1);
+    for (int y = y0; y < y1; ++y) {
+      const C n2 = load(x, y + 2);
+      C wv = shfl_c(cur, 1, true), ev = shfl_c(cur, 1, false);
+      if (lane == 0) wv = load(x - 1, y);
+      if (lane == 31) ev = load(x + 1, y);
+      if (x < N) {
+        const size_t o = off + (size_t)y * P + x;
+        C r = f[o];
+        if (!zero) r = csub(r, stencil_vals2<R>(L, x, y, cur, wv, ev, prev, next));
+        q0[o] = r;
+        acc[0] += r.x * r.x + r.y * r.y;
+      }
+      prev = cur;
+      cur = next;
+      next = n2;
+    }
+  }
+  write_partials<1>(acc, act, parts, b);
+  last_block_reduce<1>(counter, parts, gridDim.x, gridDim.y, st,
+                       [&](int bb, const double *v) { fin_norm<R>(gsc + bb * kGmresScalars, 0, v[0], 1.f); });
+}
+
 // Least squares min ||beta e1 - H y|| for the Krylov dimension k (m columns
 // at most), by complex Givens rotations; z_j = y_j / |q_j|.
 __device__ void gm_lsq(double *g, int m, double tiny) {
@@ -1127,7 +1179,17 @@ void launch_gmres_tail(const GmTailArgs<R> &a, int batch, const SolveState *st, 
 template <typename R, int DIM>
 void launch_gmres_start(const LevelK<R> &L, const typename Cx<R>::T *u, int zero_mode,
                         const typename Cx<R>::T *f, const GmresWork<R> &g, int batch,
-                        const SolveState *st, double *parts, int nblk, cudaStream_t s) {
+                        const SolveState *st, double *parts, int nblk, cudaStream_t s, int col) {
+  if constexpr (DIM == 2) {
+    if (col) {
+      const int nchunk = (L.N + 255) / 256;
+      const int per = std::max(1, nblk / nchunk);
+      const int rows = (L.N + per - 1) / per;
+      launch_plain(k_gm_start_col2d<R>, dim3(nblk, batch), dim3(256), 0, s, L, u, zero_mode, f,
+                   g.Q, st, parts, g.counter, g.gsc, nchunk, rows);
+      return;
+    }
+  }
   launch_plain(k_gm_start<R, DIM>, dim3(nblk, batch), dim3(256), 0, s, L, u, zero_mode, f, g.Q, st,
              parts, g.counter, g.gsc);
 }
@@ -1213,7 +1275,8 @@ void launch_gmres_correct(const LevelK<R> &L, const typename Cx<R>::T *u_in,
 #define HH_GMRES_INST(R, DIM)                                                                  \
   template void launch_gmres_start<R, DIM>(const LevelK<R> &, const Cx<R>::T *, int,           \
                                            const Cx<R>::T *, const GmresWork<R> &, int,        \
-                                           const SolveState *, double *, int, cudaStream_t);   \
+                                           const SolveState *, double *, int, cudaStream_t,    \
+                                           int);                                               \
   template void launch_gmres_rest<R, DIM>(const LevelK<R> &, const Cx<R>::T *, int,            \
                                           Cx<R>::T *, const GmresWork<R> &, int, int,          \
                                           const SolveState *, int, cudaStream_t, int);         \

@@ -24,11 +24,12 @@ template <typename R> struct GmresWork {
 };
 
 // q_0 = f - A u and |q_0|^2; parts (layout [b][block], nblk blocks) may be the
-// stop test's partial sums on level 0.
+// stop test's partial sums on level 0.  col (2-D): the column-marching kernel.
 template <typename R, int DIM>
 void launch_gmres_start(const LevelK<R> &L, const typename Cx<R>::T *u, int zero_mode,
                         const typename Cx<R>::T *f, const GmresWork<R> &g, int batch,
-                        const SolveState *st, double *parts, int nblk, cudaStream_t s);
+                        const SolveState *st, double *parts, int nblk, cudaStream_t s,
+                        int col = 0);
 
 // The m Arnoldi steps, the least-squares solve and u_out = u_in + V y (u_in
 // read as zero where the start kernel took it as zero).  fuse bit 0: the
