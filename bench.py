@@ -156,10 +156,13 @@ def profile_one(args):
     w = getattr(W, args.workload)(**({"n": args.kernel_n} if args.kernel_n else {}))
     k2 = w["k2"]
     k2_t = torch.from_numpy(k2).cuda() if isinstance(k2, np.ndarray) else float(k2)
+    gm = args.kernel == "gmres_step"
     mg = HelmholtzMG(w["n"], dim=w["dim"], k2=k2_t, layers=w["layers"],
-                     precision=args.precision, max_batch=1)
+                     precision=args.precision, max_batch=1,
+                     **({"smoother": "gmres"} if gm else {}))
     names = {v: k for k, v in KERNELS.items()}
     names.update({v: k for k, v in KERNELS3.items()})   # the 3-D level kernels (dim 3)
+    names["gmres_step"] = 6                             # one level-0 GMRES(3) step
     kid = names[args.kernel]
     ms = ct.c_double()
     stream = torch.cuda.current_stream()
@@ -296,8 +299,9 @@ def run_ours(args):
         achieved = bpp * pts / (ms.value * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": "gmres_step_level0", "achieved": achieved,
                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None, "bytes_per_point": bpp,
-                    "launch_ms": {"gmres_step_level0": ms.value}}
+                    "frac": achieved / peak,
+                    "traffic": stored_traffic(w["name"], args.precision, "gmres_step_level0"),
+                    "bytes_per_point": bpp, "launch_ms": {"gmres_step_level0": ms.value}}
     if fused:
         dom = max((0, 2), key=lambda k: kt[k])
         name = KERNELS[dom]
@@ -441,12 +445,23 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def stored_traffic(workload, precision, kernel):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from one
+    ncu capture of the current kernels (profiles/traffic.json), or None."""
+    tf = ROOT / "profiles" / "traffic.json"
+    if not tf.exists():
+        return None
+    return json.loads(tf.read_text()).get(f"{workload}:{precision}:{kernel}")
+
+
 # Algorithmic bytes per point of one GMRES(3) smoothing step on a level
 # (complex64 vectors, constant k; each kernel reads and writes its vectors
-# once): start: u, f -> q_0 (24 B); Arnoldi step J: q_0..q_J -> w (8 (J + 2));
-# orthogonalisation J: w, q_0..q_J -> q_{J+1} (8 (J + 3)); update:
-# u, q_0..q_2 -> u (40 B).  Sum over J = 0..2: 232 B.
-GMRES_STEP_BYTES = 232.0
+# once): start: u, f -> q_0 (24 B); Arnoldi steps J = 0, 1: q_0..q_J -> w
+# (8 (J + 2)); orthogonalisations J = 0, 1: w, q_0..q_J -> q_{J+1}
+# (8 (J + 3)); the last Arnoldi step reads q_0..q_2 and forms only sums
+# (24 B; |q_3| follows from them); update: u, q_0..q_2 -> u (40 B).
+# Sum: 184 B.
+GMRES_STEP_BYTES = 184.0
 
 
 def gmres_record(w, args, k2_t, f, stream, flush):
@@ -487,8 +502,9 @@ def gmres_record(w, args, k2_t, f, stream, flush):
                      "max_cycles": args.gmres_max_cycles},
            "roofline": {"bound": "hbm", "kernel": "gmres_step_level0", "achieved": achieved,
                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": None, "bytes_per_point": bpp,
-                        "launch_ms": {"gmres_step_level0": step_ms}}}
+                        "frac": achieved / peak,
+                        "traffic": stored_traffic(w["name"], args.precision, "gmres_step_level0"),
+                        "bytes_per_point": bpp, "launch_ms": {"gmres_step_level0": step_ms}}}
     mg.close()
     return rec
 
@@ -885,7 +901,7 @@ def main():
                     help="tuner cache file of --kernel cycles (a second run with the same file "
                          "launches no tuning kernels)")
     ap.add_argument("--kernel", choices=sorted(KERNELS.values()) + sorted(KERNELS3.values()) +
-                    ["fgmres", "cycles"],
+                    ["gmres_step", "fgmres", "cycles"],
                     help="launch one level-0 kernel of the workload (or one capped FGMRES "
                          "solve) and exit (for ncu)")
     ap.add_argument("--kernel-n", type=int, default=0,

@@ -2611,13 +2611,14 @@ int hh_cycle_kernels(const hh_handle *h) {
     if (h->mid && h->opt.precision == HH_MIXED) return 2 * h->mid0 + 2;
     return 2 * (1 + h->ngroups) + 2;
   }
-  if (h->opt.smoother == HH_SMOOTH_GMRES) {  // per level: steps of 2m + 2 kernels
-    // (m + 3 with the fused orthogonalisation + Arnoldi kernels, m >= 2),
-    // residual + restriction, correction; then the tail (or the coarsest LU)
-    // and the stop test
+  if (h->opt.smoother == HH_SMOOTH_GMRES) {  // per level: steps of 2m + 1 kernels
+    // (start, m Arnoldi products, m - 1 orthogonalisations, update; m + 2 with
+    // the fused orthogonalisation + Arnoldi kernels, m >= 2), residual +
+    // restriction, correction; then the tail (or the coarsest LU) and the
+    // stop test
     const int T = h->gtail0 > 0 ? h->gtail0 : h->L - 1;
     const int m = h->opt.gmres_m;
-    const int step = h->gm_fuse && m >= 2 ? m + 3 : 2 * m + 2;
+    const int step = h->gm_fuse && m >= 2 ? m + 2 : 2 * m + 1;
     return T * ((h->opt.nu1 + h->opt.nu2) * step + 2) + 2;
   }
   // per level nu1 sweeps, residual + restriction, nu2 sweeps; stop test; LU

@@ -14,9 +14,14 @@
 // small per-right-hand-side FP64 array that the next kernel reads.
 //
 // Kernels of one step: start (q_0, |q_0|^2), then for j < m: arnoldi
-// (w = A q_j, <q_i, w>) and orth (q_{j+1}, |q_{j+1}|^2), then update
-// (u + sum z_j q_j).  Right-hand sides whose loop has stopped skip the work
-// but still arrive at the last-block count.
+// (w = A q_j, <q_i, w>) and, for j < m - 1, orth (q_{j+1}, |q_{j+1}|^2),
+// then update (u + sum z_j q_j).  The last column q_m enters the
+// least-squares problem only through its norm, which the last Arnoldi kernel
+// forms without the vector: the q_i are orthogonal, so
+//     |q_m|^2 = |A q_{m-1}|^2 - sum_{i<m} |c_{i,m-1}|^2 |q_i|^2,
+// and that kernel also solves the least-squares problem.  Right-hand sides
+// whose loop has stopped skip the work but still arrive at the last-block
+// count.
 #include "hh_kernels.cuh"
 #include "hh_launch.cuh"
 #include "hh_gmres.h"
@@ -129,6 +134,26 @@ template <typename R> __device__ __forceinline__ typename Cx<R>::T get_z(const d
 }
 __device__ __forceinline__ int get_k(const double *g) { return (int)fmirror(g)[19]; }
 __device__ __forceinline__ bool get_zero(const double *g) { return fmirror(g)[18] != 0.f; }
+
+// |q_{J+1}|^2 and its scale without forming q_{J+1} = A q_J - sum c_iJ q_i:
+// the q_i (i <= J) are orthogonal, so |q_{J+1}|^2 = |A q_J|^2 - sum_i
+// |c_iJ|^2 |q_i|^2.  aa = the sum of |s_ref A q_J|^2 (s_ref: the scale the
+// kernel applied; 1 for complex128); called after c_0J..c_JJ are stored.  A
+// difference below zero (rounding, where q_{J+1} vanishes) is taken as zero.
+template <typename R> __device__ __forceinline__ void fin_norm_next(double *g, int J, double aa,
+                                                                    float s_ref) {
+  const double s2 = sizeof(R) == 4 ? (double)s_ref * (double)s_ref : 1.0;
+  double sum = aa;
+  for (int i = 0; i <= J; ++i) {
+    const double cr = g[ci(i, J)], cm = g[ci(i, J) + 1];
+    sum -= (cr * cr + cm * cm) * (g[i] * s2);
+  }
+  fin_norm<R>(g, J + 1, sum > 0.0 ? sum : 0.0, s_ref);
+}
+
+// least-squares solve of the step (defined below)
+template <typename R> __device__ __forceinline__ void gm_lsq_r(double *g, int m, double tiny);
+template <typename R> constexpr double lsq_tiny() { return sizeof(R) == 4 ? 1e-12 : 1e-26; }
 
 // Called by every block after it wrote its NQ partial sums (layout
 // [b][q][block]): the last block to arrive adds each right-hand side's sums in
@@ -243,14 +268,17 @@ k_gm_start(LevelK<R> L, const typename Cx<R>::T *__restrict__ u, int zero_mode,
                        [&](int bb, const double *v) { fin_norm<R>(gsc + bb * kGmresScalars, 0, v[0], 1.f); });
 }
 
-// w = A q_J; <q_i, w> for i <= J; c_iJ = <q_i, w> / |q_i|^2.
-template <typename R, int DIM, int J>
+// w = A q_J; <q_i, w> for i <= J; c_iJ = <q_i, w> / |q_i|^2.  LAST (J = m - 1):
+// also |w|^2, from which |q_m|^2 (fin_norm_next) and the least-squares solve;
+// w is then not stored (nothing reads it).
+template <typename R, int DIM, int J, bool LAST>
 __global__ void __launch_bounds__(256)
 k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
              typename Cx<R>::T *__restrict__ w, const SolveState *st, double *parts,
              unsigned int *counter, double *gsc) {
   using C = typename Cx<R>::T;
-  constexpr int NQ = 2 * (J + 1);
+  constexpr int NI = 2 * (J + 1);
+  constexpr int NQ = NI + (LAST ? 1 : 0);
   const int b = blockIdx.y;
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
   R acc[NQ];
@@ -271,7 +299,7 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
       const size_t o = at<DIM>(x, y, z, N, P);
       C Aq, D, qc;
       stencil<R, DIM>(L, x, y, z, get, Aq, D, qc);
-      w[off + o] = Aq;
+      if (!LAST) w[off + o] = Aq;
       const C a = cscale(Aq, sc[J]);
 #pragma unroll
       for (int i = 0; i <= J; ++i) {
@@ -279,6 +307,7 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
         acc[2 * i] += qi.x * a.x + qi.y * a.y;       // Re conj(q_i) Aq (scaled)
         acc[2 * i + 1] += qi.x * a.y - qi.y * a.x;   // Im
       }
+      if (LAST) acc[NQ - 1] += a.x * a.x + a.y * a.y;
     }
   }
   write_partials<NQ>(acc, act, parts, b);
@@ -290,6 +319,10 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
                             const float si = kscale_of<R>(g, i);
                             put_c(g, i, J, fin_coef<R>(g, i, v[2 * i], si, sj),
                                   fin_coef<R>(g, i, v[2 * i + 1], si, sj));
+                          }
+                          if (LAST) {
+                            fin_norm_next<R>(g, J, v[NQ - 1], sj);
+                            gm_lsq_r<R>(g, J + 1, lsq_tiny<R>());
                           }
                         });
 }
@@ -304,14 +337,17 @@ k_gm_arnoldi(LevelK<R> L, const typename Cx<R>::T *__restrict__ Q, size_t qs,
 // still read w_in around this block's points.  The complex64 per-thread sums
 // scale q_{J+1} and A q_{J+1} by s_J, the scale of q_J (q_{J+1}'s own is
 // not known before this pass ends): |s_J q_{J+1}| ~ ||A|| and
-// |s_J A q_{J+1}| ~ ||A||^2 stay far inside the FP32 range.
-template <typename R, int DIM, int J>
+// |s_J A q_{J+1}| ~ ||A||^2 stay far inside the FP32 range.  LAST (J + 2 = m):
+// also |A q_{J+1}|^2, from which |q_m|^2 and the least-squares solve, and
+// A q_{J+1} is not stored.
+template <typename R, int DIM, int J, bool LAST>
 __global__ void __launch_bounds__(256)
 k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
                   const typename Cx<R>::T *__restrict__ w_in, typename Cx<R>::T *__restrict__ w_out,
                   const SolveState *st, double *parts, unsigned int *counter, double *gsc) {
   using C = typename Cx<R>::T;
-  constexpr int NQ = 1 + 2 * (J + 2);   // |q_{J+1}|^2; <q_i, A q_{J+1}>, i <= J+1
+  constexpr int NI = 1 + 2 * (J + 2);   // |q_{J+1}|^2; <q_i, A q_{J+1}>, i <= J+1
+  constexpr int NQ = NI + (LAST ? 1 : 0);
   static_assert(NQ <= kGmresParts, "partial-sum slots");
   const int b = blockIdx.y;
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
@@ -346,7 +382,7 @@ k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
       C Aq, D, qc;
       stencil<R, DIM>(L, x, y, z, qnext, Aq, D, qc);   // qc = q_{J+1} here
       Q[(size_t)(J + 1) * qs + off + o] = qc;
-      w_out[off + o] = Aq;
+      if (!LAST) w_out[off + o] = Aq;
       const C vs = cscale(qc, sj), a = cscale(Aq, sj);
       acc[0] += vs.x * vs.x + vs.y * vs.y;
 #pragma unroll
@@ -357,6 +393,7 @@ k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
       }
       acc[1 + 2 * (J + 1)] += vs.x * a.x + vs.y * a.y;
       acc[2 + 2 * (J + 1)] += vs.x * a.y - vs.y * a.x;
+      if (LAST) acc[NQ - 1] += a.x * a.x + a.y * a.y;
     }
   }
   write_partials<NQ>(acc, act, parts, b);
@@ -380,6 +417,10 @@ k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
                           else
                             put_c(g, J + 1, J + 1, ok ? v[1 + 2 * (J + 1)] / v[0] : 0.0,
                                   ok ? v[2 + 2 * (J + 1)] / v[0] : 0.0);
+                          if (LAST) {
+                            fin_norm_next<R>(g, J + 1, v[NQ - 1], s2);
+                            gm_lsq_r<R>(g, J + 2, lsq_tiny<R>());
+                          }
                         });
 }
 
@@ -431,18 +472,22 @@ template <typename C> __device__ __forceinline__ C shfl_c(C v, int delta, bool u
 
 // OA = false: Arnoldi step 0 (w = A q_0, <q_0, w>), J unused.
 // OA = true: orthogonalise column J and apply the next Arnoldi product (the
-// arithmetic of k_gm_orth_arnoldi<R, 2, J>).  Grid: nchunk x ceil(N / rows)
-// blocks per right-hand side (blockIdx.x = run * nchunk + chunk).
-template <typename R, bool OA, int J>
+// arithmetic of k_gm_orth_arnoldi<R, 2, J, LAST>; LAST: J + 2 = m).  Grid:
+// nchunk x ceil(N / rows) blocks per right-hand side (blockIdx.x = run *
+// nchunk + chunk).
+template <typename R, bool OA, int J, bool LAST>
 __global__ void __launch_bounds__(256)
 k_gm_col2d(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
            const typename Cx<R>::T *__restrict__ w_in, typename Cx<R>::T *__restrict__ w_out,
            const SolveState *st, double *parts, unsigned int *counter, double *gsc, int nchunk,
            int rows) {
   using C = typename Cx<R>::T;
+  static_assert(OA || !LAST, "Arnoldi step 0 of the column kernels is never the last (m >= 2)");
   constexpr int JJ = OA ? J : -1;        // the last stored column the step reads
   constexpr int NV = JJ + 1;             // q_0..q_JJ carried for the inner products
-  constexpr int NQ = OA ? 1 + 2 * (J + 2) : 2;
+  constexpr int NI = OA ? 1 + 2 * (J + 2) : 2;
+  constexpr int NQ = NI + (LAST ? 1 : 0);
+  static_assert(NQ <= kGmresParts, "partial-sum slots");
   const int b = blockIdx.y;
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
   R acc[NQ];
@@ -509,7 +554,7 @@ k_gm_col2d(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
         const C Aq = stencil_vals2<R>(L, x, y, cur, wv, ev, prev, next);
         const size_t o = off + (size_t)y * P + x;
         if (OA) Q[(size_t)(J + 1) * qs + o] = cur;
-        w_out[o] = Aq;
+        if (!LAST) w_out[o] = Aq;
         const C a = cscale(Aq, s_op);
         if (OA) {
           const C vs = cscale(cur, s_op);
@@ -520,8 +565,9 @@ k_gm_col2d(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
             acc[1 + 2 * i] += qi.x * a.x + qi.y * a.y;
             acc[2 + 2 * i] += qi.x * a.y - qi.y * a.x;
           }
-          acc[NQ - 2] += vs.x * a.x + vs.y * a.y;
-          acc[NQ - 1] += vs.x * a.y - vs.y * a.x;
+          acc[NI - 2] += vs.x * a.x + vs.y * a.y;
+          acc[NI - 1] += vs.x * a.y - vs.y * a.x;
+          if (LAST) acc[NQ - 1] += a.x * a.x + a.y * a.y;
         } else {
           const C q0s = cscale(cur, s_op);
           acc[0] += q0s.x * a.x + q0s.y * a.y;
@@ -566,6 +612,10 @@ k_gm_col2d(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
                             else
                               put_c(g, J + 1, J + 1, ok ? v[1 + 2 * (J + 1)] / v[0] : 0.0,
                                     ok ? v[2 + 2 * (J + 1)] / v[0] : 0.0);
+                            if (LAST) {
+                              fin_norm_next<R>(g, J + 1, v[NQ - 1], s2);
+                              gm_lsq_r<R>(g, J + 2, lsq_tiny<R>());
+                            }
                           });
   }
 }
@@ -709,7 +759,8 @@ __device__ void gm_lsq32(double *g, int m) {
       const float2 c = get_c<float>(g, i, j);
       H[i][j] = make_float2(c.x * f, c.y * f);
     }
-    H[j + 1][j] = make_float2(sc[j] * (1.0f / sc[j + 1]), 0.f);
+    // (a vanished q_{j+1}, scale 0, ends the Krylov space: h_{j+1,j} = 0)
+    H[j + 1][j] = make_float2(sc[j + 1] > 0.f ? sc[j] * (1.0f / sc[j + 1]) : 0.f, 0.f);
   }
   float2 cs[3], sn[3];
   for (int j = 0; j < k; ++j) {
@@ -754,15 +805,13 @@ template <typename R> __device__ __forceinline__ void gm_lsq_r(double *g, int m,
   else gm_lsq(g, m, tiny);
 }
 
-// q_{J+1} = w - sum_{i<=J} c_iJ q_i; |q_{J+1}|^2; after the last column the
-// least-squares solve.
-// (at most 64 registers, 4 blocks per SM: the least-squares solve of the
-// last block, which would need more, may spill)
+// q_{J+1} = w - sum_{i<=J} c_iJ q_i and |q_{J+1}|^2, for J + 1 < m (the last
+// column's norm comes from the last Arnoldi kernel, fin_norm_next).
 template <typename R, int DIM, int J>
 __global__ void __launch_bounds__(256, 4)
 k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
           const typename Cx<R>::T *__restrict__ w, const SolveState *st, double *parts,
-          unsigned int *counter, double *gsc, int m) {
+          unsigned int *counter, double *gsc) {
   using C = typename Cx<R>::T;
   const int b = blockIdx.y;
   const bool act = __syncthreads_and(!(st && !st[b].active)) != 0;
@@ -789,12 +838,10 @@ k_gm_orth(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
     }
   }
   write_partials<1>(acc, act, parts, b);
-  const double tiny = sizeof(R) == 4 ? 1e-12 : 1e-26;
   last_block_reduce<1>(counter, parts, gridDim.x, gridDim.y, st,
                        [&](int bb, const double *v) {
                          double *g = gsc + bb * kGmresScalars;
                          fin_norm<R>(g, J + 1, v[0], kscale_of<R>(g, J));
-                         if (J + 1 == m) gm_lsq_r<R>(g, m, tiny);
                        });
 }
 
@@ -948,11 +995,13 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
     R sc[3];   // scales of q_0..q_J (written before the last barrier)
 #pragma unroll
     for (int i = 0; i < 3; ++i) sc[i] = i <= J ? kscale_of<R>(g, i) : R(0);
-    // <q_i, A q_J> for i <= J
+    // <q_i, A q_J> for i <= J; in the last column also |A q_J|^2, from which
+    // |q_m|^2 and the least-squares solve (q_m itself is not formed)
+    const bool last = J + 1 == m;
     {
-      R acc[6];
+      R acc[7];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) acc[i] = R(0);
+      for (int i = 0; i < 7; ++i) acc[i] = R(0);
       for (int p = threadIdx.x; p < npt; p += TB) {
         int x, y, z;
         coords<DIM>(p, N, x, y, z);
@@ -965,21 +1014,27 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
           acc[2 * i] += qi.x * a.x + qi.y * a.y;
           acc[2 * i + 1] += qi.x * a.y - qi.y * a.x;
         }
+        acc[2 * (J + 1)] += a.x * a.x + a.y * a.y;   // used in the last column only
       }
-      tail_reduce_fin<6>(acc, ws, red, 2 * (J + 1), [&] {
+      tail_reduce_fin<7>(acc, ws, red, 2 * (J + 1) + (last ? 1 : 0), [&] {
         for (int i = 0; i <= J; ++i)
           put_c(g, i, J, fin_coef<R>(g, i, red[2 * i], sc[i], sc[J]),
                 fin_coef<R>(g, i, red[2 * i + 1], sc[i], sc[J]));
+        if (last) {
+          fin_norm_next<R>(g, J, red[2 * (J + 1)], sc[J]);
+          gm_lsq_r<R>(g, m, tiny);
+        }
       });
     }
-    // q_{J+1} = A q_J - sum_i c_iJ q_i (stored below m), |q_{J+1}|^2
+    if (last) break;
+    // q_{J+1} = A q_J - sum_i c_iJ q_i (J + 1 < m), |q_{J+1}|^2
     {
       C c[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
         c[i] = i <= J ? get_c<R>(g, i, J) : czero<C>();
       R acc[1] = {R(0)};
-      C *qn = J + 1 < m ? Q(J + 1) : nullptr;
+      C *qn = Q(J + 1);
       for (int p = threadIdx.x; p < npt; p += TB) {
         int x, y, z;
         coords<DIM>(p, N, x, y, z);
@@ -987,14 +1042,11 @@ __device__ void tail_gm_step(const LevelK<R> &K, typename Cx<R>::T *U,
         stencil<R, DIM>(K, x, y, z, get, v, D, qc);
 #pragma unroll
         for (int i = 0; i <= J; ++i) v = csub(v, cmul(c[i], Q(i)[p]));
-        if (qn) qn[p] = v;
+        qn[p] = v;
         const C vs = cscale(v, sc[J]);
         acc[0] += vs.x * vs.x + vs.y * vs.y;
       }
-      tail_reduce_fin<1>(acc, ws, red, 1, [&] {
-        fin_norm<R>(g, J + 1, red[0], sc[J]);
-        if (J + 1 == m) gm_lsq_r<R>(g, m, tiny);
-      });
+      tail_reduce_fin<1>(acc, ws, red, 1, [&] { fin_norm<R>(g, J + 1, red[0], sc[J]); });
     }
   }
   // U = U + sum_j z_j q_j
@@ -1027,8 +1079,8 @@ __global__ void __launch_bounds__(TB) k_gm_tail(const __grid_constant__ GmTailAr
   const int mm = A.mm;
   int *spiv = reinterpret_cast<int *>(slu + mm * mm);
   __shared__ double g[kGmresScalars];
-  __shared__ double ws[6 * 32];
-  __shared__ double red[6];
+  __shared__ double ws[7 * 32];
+  __shared__ double red[7];
   C *const Q0 = cm + A.offQ[0], *const Q1 = cm + A.offQ[1], *const Q2 = cm + A.offQ[2];
   // stage the top right-hand side, every level's tables and k^2, the LU
   {
@@ -1208,56 +1260,55 @@ void launch_gmres_rest(const LevelK<R> &L, const typename Cx<R>::T *u_in, int ze
       const int per = std::max(1, nblk / nchunk);   // row runs per chunk (blocks <= nblk)
       const int rows = (L.N + per - 1) / per;
       const dim3 gcol(nchunk * ((L.N + rows - 1) / rows), batch);
-      launch_plain(k_gm_col2d<R, false, 0>, gcol, blk, 0, s, L, g.Q, g.qs, (const C *)nullptr,
-                   g.w, st, g.parts, g.counter, g.gsc, nchunk, rows);
-      launch_plain(k_gm_col2d<R, true, 0>, gcol, blk, 0, s, L, g.Q, g.qs, (const C *)g.w, g.w2,
-                   st, g.parts, g.counter, g.gsc, nchunk, rows);
+      launch_plain(k_gm_col2d<R, false, 0, false>, gcol, blk, 0, s, L, g.Q, g.qs,
+                   (const C *)nullptr, g.w, st, g.parts, g.counter, g.gsc, nchunk, rows);
       if (m == 2) {
-        launch_plain(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, (const C *)g.w2, st,
-                     g.parts, g.counter, g.gsc, m);
+        launch_plain(k_gm_col2d<R, true, 0, true>, gcol, blk, 0, s, L, g.Q, g.qs, (const C *)g.w,
+                     g.w2, st, g.parts, g.counter, g.gsc, nchunk, rows);
       } else {
-        launch_plain(k_gm_col2d<R, true, 1>, gcol, blk, 0, s, L, g.Q, g.qs, (const C *)g.w2,
-                     g.w, st, g.parts, g.counter, g.gsc, nchunk, rows);
-        launch_plain(k_gm_orth<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs, (const C *)g.w, st,
-                     g.parts, g.counter, g.gsc, m);
+        launch_plain(k_gm_col2d<R, true, 0, false>, gcol, blk, 0, s, L, g.Q, g.qs,
+                     (const C *)g.w, g.w2, st, g.parts, g.counter, g.gsc, nchunk, rows);
+        launch_plain(k_gm_col2d<R, true, 1, true>, gcol, blk, 0, s, L, g.Q, g.qs,
+                     (const C *)g.w2, g.w, st, g.parts, g.counter, g.gsc, nchunk, rows);
       }
       launch_plain(k_gm_update<R, DIM>, grid, blk, 0, s, L, u_in, g.Q, g.qs, u_out, st, g.gsc, m);
       return;
     }
   }
   if ((fuse & 1) && m >= 2) {
-    // A q_0 -> w; (q_1, A q_1) -> w2; (q_2, A q_2) -> w; orthogonalisation of
-    // the last column (and the least-squares solve) from the latest buffer
-    launch_plain(k_gm_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-               g.counter, g.gsc);
-    launch_plain(k_gm_orth_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs,
-               (const typename Cx<R>::T *)g.w, g.w2, st, g.parts, g.counter, g.gsc);
+    // A q_0 -> w; (q_1, A q_1) -> w2; for m = 3 (q_2, A q_2), whose product
+    // only enters |q_3|^2 and the least-squares solve
+    launch_plain(k_gm_arnoldi<R, DIM, 0, false>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
+                 g.counter, g.gsc);
     if (m == 2) {
-      launch_plain(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs,
-                 (const typename Cx<R>::T *)g.w2, st, g.parts, g.counter, g.gsc, m);
+      launch_plain(k_gm_orth_arnoldi<R, DIM, 0, true>, grid, blk, 0, s, L, g.Q, g.qs,
+                   (const C *)g.w, g.w2, st, g.parts, g.counter, g.gsc);
     } else {
-      launch_plain(k_gm_orth_arnoldi<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs,
-                 (const typename Cx<R>::T *)g.w2, g.w, st, g.parts, g.counter, g.gsc);
-      launch_plain(k_gm_orth<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs,
-                 (const typename Cx<R>::T *)g.w, st, g.parts, g.counter, g.gsc, m);
+      launch_plain(k_gm_orth_arnoldi<R, DIM, 0, false>, grid, blk, 0, s, L, g.Q, g.qs,
+                   (const C *)g.w, g.w2, st, g.parts, g.counter, g.gsc);
+      launch_plain(k_gm_orth_arnoldi<R, DIM, 1, true>, grid, blk, 0, s, L, g.Q, g.qs,
+                   (const C *)g.w2, g.w, st, g.parts, g.counter, g.gsc);
     }
   } else {
-    for (int j = 0; j < m; ++j) {
-      if (j == 0) {
-        launch_plain(k_gm_arnoldi<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                   g.counter, g.gsc);
-        launch_plain(k_gm_orth<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                   g.counter, g.gsc, m);
-      } else if (j == 1) {
-        launch_plain(k_gm_arnoldi<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                   g.counter, g.gsc);
-        launch_plain(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                   g.counter, g.gsc, m);
+    // Arnoldi step j, then (j < m - 1) its orthogonalisation
+    if (m == 1) {
+      launch_plain(k_gm_arnoldi<R, DIM, 0, true>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st,
+                   g.parts, g.counter, g.gsc);
+    } else {
+      launch_plain(k_gm_arnoldi<R, DIM, 0, false>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st,
+                   g.parts, g.counter, g.gsc);
+      launch_plain(k_gm_orth<R, DIM, 0>, grid, blk, 0, s, L, g.Q, g.qs, (const C *)g.w, st,
+                   g.parts, g.counter, g.gsc);
+      if (m == 2) {
+        launch_plain(k_gm_arnoldi<R, DIM, 1, true>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st,
+                     g.parts, g.counter, g.gsc);
       } else {
-        launch_plain(k_gm_arnoldi<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                   g.counter, g.gsc);
-        launch_plain(k_gm_orth<R, DIM, 2>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st, g.parts,
-                   g.counter, g.gsc, m);
+        launch_plain(k_gm_arnoldi<R, DIM, 1, false>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st,
+                     g.parts, g.counter, g.gsc);
+        launch_plain(k_gm_orth<R, DIM, 1>, grid, blk, 0, s, L, g.Q, g.qs, (const C *)g.w, st,
+                     g.parts, g.counter, g.gsc);
+        launch_plain(k_gm_arnoldi<R, DIM, 2, true>, grid, blk, 0, s, L, g.Q, g.qs, g.w, st,
+                     g.parts, g.counter, g.gsc);
       }
     }
   }

@@ -6,11 +6,11 @@ namespace hh {
 
 constexpr int kGmresMaxBatch = 64;   // right-hand sides per handle with GMRES smoothing
 constexpr int kGmresScalars = 40;    // FP64 scalars per right-hand side (and FP32 mirrors)
-constexpr int kGmresParts = 7;       // partial sums per block and right-hand side (at most)
+constexpr int kGmresParts = 8;       // partial sums per block and right-hand side (at most)
 
 // Workspace of one level: Krylov vectors q_0..q_3 (at stride qs = S * batch
-// capacity), w = A q_j (two buffers), per-block partial sums (up to 7 per
-// right-hand side),
+// capacity; q_0..q_{m-1} are written), w = A q_j (two buffers), per-block
+// partial sums (up to 8 per right-hand side),
 // the last-block arrival counter (starts at 0; the last block resets it) and
 // the per-right-hand-side FP64 scalars.
 template <typename R> struct GmresWork {
@@ -32,9 +32,11 @@ void launch_gmres_start(const LevelK<R> &L, const typename Cx<R>::T *u, int zero
                         int col = 0);
 
 // The m Arnoldi steps, the least-squares solve and u_out = u_in + V y (u_in
-// read as zero where the start kernel took it as zero).  fuse bit 0: the
-// orthogonalisation of step J and the Arnoldi product of step J+1 in one
-// kernel (m + 2 kernels instead of 2 m + 1); bit 1 (2-D): those kernels and
+// read as zero where the start kernel took it as zero): 2 m kernels (Arnoldi
+// products, the orthogonalisations of columns 0..m-2, the update; the last
+// Arnoldi kernel forms |q_m| and solves the least-squares problem).  fuse
+// bit 0 (m >= 2): the orthogonalisation of step J and the Arnoldi product of
+// step J+1 in one kernel (m + 1 kernels); bit 1 (2-D): those kernels and
 // Arnoldi step 0 march down columns (hh_gmres.cu, k_gm_col2d; the caller sets
 // it on large levels).
 template <typename R, int DIM>
