@@ -60,27 +60,38 @@ template <typename R> __device__ __forceinline__ void set_norm(double *g, int i,
 // scale the kernel applied; 1 for q_0).  complex64: without an FP64 square
 // root or division (FP32 reciprocals of scales, which lie far inside the FP32
 // range, and FP64 products): s_i = s_ref / sqrt(sum).
+__device__ __forceinline__ float fin_norm32(double *g, int i, double sum, float s_ref,
+                                            double &gi) {
+  const double inv = s_ref > 0.f ? (double)(1.0f / s_ref) : 1.0;
+  gi = sum * inv * inv;
+  g[i] = gi;
+  const float fs = (float)sum;
+  const float sc = (sum > 0.0 && fs > 1e-36f && fs < 1e36f) ? s_ref * rsqrtf(fs)
+                                                            : (float)kscale<float>(gi);
+  scale_slots(g)[i] = sc;
+  return sc;   // (gi and the scale also returned, for finishers that go on from them)
+}
 template <typename R> __device__ __forceinline__ void fin_norm(double *g, int i, double sum,
                                                                float s_ref) {
   if (sizeof(R) == 8) {
     set_norm<R>(g, i, sum);
     return;
   }
-  const double inv = s_ref > 0.f ? (double)(1.0f / s_ref) : 1.0;
-  g[i] = sum * inv * inv;
-  const float fs = (float)sum;
-  scale_slots(g)[i] = (sum > 0.0 && fs > 1e-36f && fs < 1e36f) ? s_ref * rsqrtf(fs)
-                                                                 : (float)kscale<R>(g[i]);
+  double gi;
+  fin_norm32(g, i, sum, s_ref, gi);
 }
 
 // c_ij = <q_i, A q_j> / |q_i|^2 from a sum of s_i q_i . s_ref A q_j (complex64:
 // |q_i|^-2 = s_i^2, so c_ij = sum s_i / s_ref; complex128: the scales are 1).
+__device__ __forceinline__ double fin_coef32(double gi, double sum, float si, float s_ref) {
+  if (!(gi > 0.0) || !(si > 0.f) || !(s_ref > 0.f)) return 0.0;
+  return sum * (double)(si * (1.0f / s_ref));
+}
 template <typename R> __device__ __forceinline__ double fin_coef(const double *g, int i,
                                                                  double sum, float si,
                                                                  float s_ref) {
   if (sizeof(R) == 8) return g[i] > 0.0 ? sum / g[i] : 0.0;
-  if (!(g[i] > 0.0) || !(si > 0.f) || !(s_ref > 0.f)) return 0.0;
-  return sum * (double)(si * (1.0f / s_ref));
+  return fin_coef32(g[i], sum, si, s_ref);
 }
 
 // per right-hand side scalars (FP64): |q_i|^2 at 0..3; c_ij (complex) at
@@ -154,6 +165,75 @@ template <typename R> __device__ __forceinline__ void fin_norm_next(double *g, i
 // least-squares solve of the step (defined below)
 template <typename R> __device__ __forceinline__ void gm_lsq_r(double *g, int m, double tiny);
 template <typename R> constexpr double lsq_tiny() { return sizeof(R) == 4 ? 1e-12 : 1e-26; }
+__device__ void gm_lsq32_core(double *g, int m, bool q0pos, const float *sc, const float2 *cc);
+
+// Finisher of a fused orthogonalisation J + Arnoldi J+1 kernel from its sums v
+// (layout of k_gm_orth_arnoldi): |q_{J+1}|^2 and its scale, c_{i,J+1} for
+// i <= J+1, and for LAST (J + 2 = m) |q_m|^2 and the least-squares solve.
+// The sums carry the scale s_J of q_J.  Complex64: the values of earlier
+// kernels are loaded together first and every derived scalar stays in
+// registers, so that no load waits behind this thread's own stores (one L2
+// round trip each in the one thread that finishes); the arithmetic and its
+// order are those of fin_norm, fin_coef, fin_norm_next and gm_lsq32.
+template <typename R, int J, bool LAST>
+__device__ __forceinline__ void fin_fused(double *g, const double *v) {
+  constexpr int NI = 1 + 2 * (J + 2);
+  if constexpr (sizeof(R) == 4) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    double n[4] = {0.0, 0.0, 0.0, 0.0};
+    float2 cc[6];
+    double cre[J + 2], cim[J + 2];   // c_{i,J+1}
+#pragma unroll
+    for (int i = 0; i <= J; ++i) {
+      s[i] = scale_slots(g)[i];
+      n[i] = g[i];
+    }
+    if (LAST) {
+#pragma unroll
+      for (int j = 0; j <= J; ++j)
+#pragma unroll
+        for (int i = 0; i <= j; ++i) cc[j * (j + 1) / 2 + i] = get_c<float>(g, i, j);
+    }
+    const float sj = s[J];
+    s[J + 1] = fin_norm32(g, J + 1, v[0], sj, n[J + 1]);
+#pragma unroll
+    for (int i = 0; i <= J; ++i) {
+      cre[i] = fin_coef32(n[i], v[1 + 2 * i], s[i], sj);
+      cim[i] = fin_coef32(n[i], v[2 + 2 * i], s[i], sj);
+    }
+    const bool ok = v[0] > 0.0;
+    cre[J + 1] = ok ? (double)((float)v[1 + 2 * (J + 1)] / (float)v[0]) : 0.0;
+    cim[J + 1] = ok ? (double)((float)v[2 + 2 * (J + 1)] / (float)v[0]) : 0.0;
+#pragma unroll
+    for (int i = 0; i <= J + 1; ++i) {
+      put_c(g, i, J + 1, cre[i], cim[i]);
+      cc[(J + 1) * (J + 2) / 2 + i] = make_float2((float)cre[i], (float)cim[i]);
+    }
+    if (LAST) {
+      const double s2 = (double)sj * (double)sj;
+      double sum = v[NI];
+#pragma unroll
+      for (int i = 0; i <= J + 1; ++i) sum -= (cre[i] * cre[i] + cim[i] * cim[i]) * (n[i] * s2);
+      s[J + 2] = fin_norm32(g, J + 2, sum > 0.0 ? sum : 0.0, sj, n[J + 2]);
+      gm_lsq32_core(g, J + 2, n[0] > 0.0, s, cc);
+    }
+  } else {
+    const float s2 = kscale_of<R>(g, J);
+    fin_norm<R>(g, J + 1, v[0], s2);
+    for (int i = 0; i <= J; ++i) {
+      const float si = kscale_of<R>(g, i);
+      put_c(g, i, J + 1, fin_coef<R>(g, i, v[1 + 2 * i], si, s2),
+            fin_coef<R>(g, i, v[2 + 2 * i], si, s2));
+    }
+    const bool ok = v[0] > 0.0;
+    put_c(g, J + 1, J + 1, ok ? v[1 + 2 * (J + 1)] / v[0] : 0.0,
+          ok ? v[2 + 2 * (J + 1)] / v[0] : 0.0);
+    if (LAST) {
+      fin_norm_next<R>(g, J + 1, v[NI], s2);
+      gm_lsq_r<R>(g, J + 2, lsq_tiny<R>());
+    }
+  }
+}
 
 // Called by every block after it wrote its NQ partial sums (layout
 // [b][q][block]): the last block to arrive adds each right-hand side's sums in
@@ -399,28 +479,7 @@ k_gm_orth_arnoldi(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
   write_partials<NQ>(acc, act, parts, b);
   last_block_reduce<NQ>(counter, parts, gridDim.x, gridDim.y, st,
                         [&](int bb, const double *v) {
-                          double *g = gsc + bb * kGmresScalars;
-                          const float s2 = kscale_of<R>(g, J);
-                          fin_norm<R>(g, J + 1, v[0], s2);
-                          for (int i = 0; i <= J; ++i) {
-                            const float si = kscale_of<R>(g, i);
-                            put_c(g, i, J + 1, fin_coef<R>(g, i, v[1 + 2 * i], si, s2),
-                                  fin_coef<R>(g, i, v[2 + 2 * i], si, s2));
-                          }
-                          // i = J+1: both factors carry s_J, so c = sum / (s_J^2 |q_{J+1}|^2)
-                          // = sum / (the |s_J q_{J+1}|^2 sum)
-                          const bool ok = v[0] > 0.0;
-                          if (sizeof(R) == 4)
-                            put_c(g, J + 1, J + 1,
-                                  ok ? (double)((float)v[1 + 2 * (J + 1)] / (float)v[0]) : 0.0,
-                                  ok ? (double)((float)v[2 + 2 * (J + 1)] / (float)v[0]) : 0.0);
-                          else
-                            put_c(g, J + 1, J + 1, ok ? v[1 + 2 * (J + 1)] / v[0] : 0.0,
-                                  ok ? v[2 + 2 * (J + 1)] / v[0] : 0.0);
-                          if (LAST) {
-                            fin_norm_next<R>(g, J + 1, v[NQ - 1], s2);
-                            gm_lsq_r<R>(g, J + 2, lsq_tiny<R>());
-                          }
+                          fin_fused<R, J, LAST>(gsc + bb * kGmresScalars, v);
                         });
 }
 
@@ -596,26 +655,7 @@ k_gm_col2d(LevelK<R> L, typename Cx<R>::T *__restrict__ Q, size_t qs,
   } else {
     last_block_reduce<NQ>(counter, parts, gridDim.x, gridDim.y, st,
                           [&](int bb, const double *v) {
-                            double *g = gsc + bb * kGmresScalars;
-                            const float s2 = kscale_of<R>(g, J);
-                            fin_norm<R>(g, J + 1, v[0], s2);
-                            for (int i = 0; i <= J; ++i) {
-                              const float si = kscale_of<R>(g, i);
-                              put_c(g, i, J + 1, fin_coef<R>(g, i, v[1 + 2 * i], si, s2),
-                                    fin_coef<R>(g, i, v[2 + 2 * i], si, s2));
-                            }
-                            const bool ok = v[0] > 0.0;
-                            if (sizeof(R) == 4)
-                              put_c(g, J + 1, J + 1,
-                                    ok ? (double)((float)v[1 + 2 * (J + 1)] / (float)v[0]) : 0.0,
-                                    ok ? (double)((float)v[2 + 2 * (J + 1)] / (float)v[0]) : 0.0);
-                            else
-                              put_c(g, J + 1, J + 1, ok ? v[1 + 2 * (J + 1)] / v[0] : 0.0,
-                                    ok ? v[2 + 2 * (J + 1)] / v[0] : 0.0);
-                            if (LAST) {
-                              fin_norm_next<R>(g, J + 1, v[NQ - 1], s2);
-                              gm_lsq_r<R>(g, J + 2, lsq_tiny<R>());
-                            }
+                            fin_fused<R, J, LAST>(gsc + bb * kGmresScalars, v);
                           });
   }
 }
@@ -737,9 +777,10 @@ __device__ void gm_lsq(double *g, int m, double tiny) {
 // the right-hand side is e_1, and z_j = y_j |q_0| / |q_j| = y_j s_j / s_0.
 // The Krylov dimension stops at the first q_{j+1} with |q_{j+1}| <= 1e-6 |q_0|
 // (|q_{j+1}|^2 <= 1e-12 |q_0|^2, the FP64 version's test).
-__device__ void gm_lsq32(double *g, int m) {
-  const float *sc = scale_slots(g);
-  if (!(g[0] > 0.0) || !(sc[0] > 0.f)) {
+// sc: the scales s_0..s_m; cc[j (j + 1) / 2 + i]: c_ij (FP32) for i <= j < m;
+// q0pos: |q_0|^2 > 0.  Stores z and the Krylov dimension.
+__device__ void gm_lsq32_core(double *g, int m, bool q0pos, const float *sc, const float2 *cc) {
+  if (!q0pos || !(sc[0] > 0.f)) {
     for (int j = 0; j < 3; ++j) put_z(g, j, 0.0, 0.0);
     put_k(g, 0);
     return;
@@ -756,7 +797,7 @@ __device__ void gm_lsq32(double *g, int m) {
   for (int j = 0; j < k; ++j) {
     for (int i = 0; i <= j; ++i) {
       const float f = sc[j] * (1.0f / sc[i]);
-      const float2 c = get_c<float>(g, i, j);
+      const float2 c = cc[j * (j + 1) / 2 + i];
       H[i][j] = make_float2(c.x * f, c.y * f);
     }
     // (a vanished q_{j+1}, scale 0, ends the Krylov space: h_{j+1,j} = 0)
@@ -798,6 +839,15 @@ __device__ void gm_lsq32(double *g, int m) {
     put_z(g, j, ok ? (double)(y[j].x * f) : 0.0, ok ? (double)(y[j].y * f) : 0.0);
   }
   put_k(g, k);
+}
+// the same from the stored scalars
+__device__ void gm_lsq32(double *g, int m) {
+  float sc[4];
+  float2 cc[6];
+  for (int i = 0; i < 4; ++i) sc[i] = scale_slots(g)[i];
+  for (int j = 0; j < 3; ++j)
+    for (int i = 0; i <= j; ++i) cc[j * (j + 1) / 2 + i] = get_c<float>(g, i, j);
+  gm_lsq32_core(g, m, g[0] > 0.0, sc, cc);
 }
 
 template <typename R> __device__ __forceinline__ void gm_lsq_r(double *g, int m, double tiny) {
