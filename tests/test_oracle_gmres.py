@@ -161,3 +161,34 @@ def test_ionization_model_matches_table8():
     H = O.build_hierarchy(w["n"], 2, w["k2"], layers=w["layers"])
     with pytest.raises(O.DivergedError):
         O.solve(H, w["rhs"][0], tol=1e-7, max_cycles=600)
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
+def test_last_krylov_norm_follows_from_the_arnoldi_sums(level):
+    """A GMRES(3) step needs its last Krylov vector q_3 only through |q_3|
+    (the entry h_{3,2} of the least-squares problem).  With the classical
+    Gram-Schmidt basis q_{j+1} = A q_j - sum_i c_ij q_i, c_ij = <q_i, A q_j> /
+    |q_i|^2, the q_i are orthogonal, so |q_3|^2 = |A q_2|^2 - sum_i |c_i2|^2
+    |q_i|^2: the sums of the last Arnoldi product determine it without
+    forming q_3 (the CUDA path's reading).  Checked on every level of a
+    shifted ECS hierarchy with a k^2 field (63^2 .. 3^2), where |q_3|^2 /
+    |A q_2|^2 ranges from about 0.5 down to 1e-2, for a random residual and
+    for a point source."""
+    n = 64
+    k2 = W.smooth_k2(n, 2, 4, 30.0, 50.0)
+    lv = O.build_hierarchy(n, 2, k2, layers=8, smoother="gmres").levels[level]
+    rng = np.random.default_rng(level)
+    shape = lv.shape
+    point = np.zeros(shape, complex)
+    point[shape[0] // 2, shape[1] // 3] = 1.0
+    for r0 in (rng.standard_normal(shape) + 1j * rng.standard_normal(shape), point):
+        q = [r0.ravel()]
+        for j in range(3):
+            w = O.apply_operator(lv, q[j].reshape(shape)).ravel()
+            c = [np.vdot(q[i], w) / np.vdot(q[i], q[i]).real for i in range(j + 1)]
+            q.append(w - sum(c[i] * q[i] for i in range(j + 1)))
+        explicit = np.vdot(q[3], q[3]).real
+        by_sums = np.vdot(w, w).real - sum(abs(c[i]) ** 2 * np.vdot(q[i], q[i]).real
+                                           for i in range(3))
+        assert explicit > 0.0
+        assert abs(by_sums - explicit) <= 1e-9 * explicit, (level, explicit, by_sums)
