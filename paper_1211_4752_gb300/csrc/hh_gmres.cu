@@ -60,6 +60,8 @@ template <typename R> __device__ __forceinline__ void set_norm(double *g, int i,
 // scale the kernel applied; 1 for q_0).  complex64: without an FP64 square
 // root or division (FP32 reciprocals of scales, which lie far inside the FP32
 // range, and FP64 products): s_i = s_ref / sqrt(sum).
+// complex64 part of fin_norm: stores |q_i|^2 and its scale, returns the scale
+// and passes |q_i|^2 back in gi (for finishers that go on from them)
 __device__ __forceinline__ float fin_norm32(double *g, int i, double sum, float s_ref,
                                             double &gi) {
   const double inv = s_ref > 0.f ? (double)(1.0f / s_ref) : 1.0;
@@ -69,7 +71,7 @@ __device__ __forceinline__ float fin_norm32(double *g, int i, double sum, float 
   const float sc = (sum > 0.0 && fs > 1e-36f && fs < 1e36f) ? s_ref * rsqrtf(fs)
                                                             : (float)kscale<float>(gi);
   scale_slots(g)[i] = sc;
-  return sc;   // (gi and the scale also returned, for finishers that go on from them)
+  return sc;
 }
 template <typename R> __device__ __forceinline__ void fin_norm(double *g, int i, double sum,
                                                                float s_ref) {
